@@ -1,0 +1,237 @@
+/*
+ * gmg.h -- C ABI of the GB300 geometric-multigrid pressure-Poisson solver.
+ *
+ * The problem (the paper's Sec. 3.1 names it: the variable-coefficient Poisson
+ * equation of immersed-boundary flows; its Sec. 3 solves it by geometric
+ * multigrid) is, on a cell-centred nx x ny x nz grid in grid units,
+ *
+ *     (A p)_I = sum over the six faces f of cell I of beta_f (p_nb(f) - p_I) = b_I
+ *
+ * with one coefficient per face.  Solves run V-cycles (Sec. 3) with the
+ * adaptive under-relaxed red-black Gauss-Seidel smoother (Sec. 3.1) on an
+ * isotropically or anisotropically coarsened hierarchy (Sec. 3.2) until
+ * |b - A p|_2 <= tol |b|_2.
+ *
+ * Layout.  Every grid array is C-contiguous [nz][ny][nx] (x fastest).  bx[I]
+ * is the coefficient on the lower x-face of cell I (between I - e_x and I);
+ * by, bz likewise.  On a non-periodic (Neumann) axis the lower wall faces are
+ * ignored whatever they hold and the upper wall faces do not exist; on a
+ * periodic axis the lower face of cell 0 joins it to cell n - 1.
+ *
+ * Memory.  Unless an entry point says "host", every pointer is CUDA device
+ * memory of the device that was current at gmg_create.  The caller owns its
+ * arrays; the library copies what it keeps (the coefficients) and owns the
+ * multigrid workspace.  All work is ordered on the stream given at creation
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *
+ * Errors.  Every call returns a gmg_status.  GMG_ERR_ARG and GMG_ERR_CUDA
+ * leave a message for gmg_last_error.  A CUDA error inside a call is reported
+ * as GMG_ERR_CUDA and the handle should then be destroyed.
+ */
+#ifndef GMG_H
+#define GMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GMG_OK = 0,
+    GMG_ERR_ARG = 1,            /* bad argument (dimensions, null pointer, option range) */
+    GMG_ERR_CUDA = 2,           /* a CUDA call failed */
+    GMG_ERR_NOT_CONVERGED = 3,  /* max_cycles reached; p holds the best iterate */
+    GMG_ERR_DIVERGED = 4,       /* a cycle grew the residual at omega_min; p holds the best iterate */
+    GMG_ERR_NONFINITE = 5       /* the right-hand side holds NaN or Inf; p is left untouched */
+} gmg_status;
+
+enum { GMG_COARSEN_ISO = 0, GMG_COARSEN_ANISO = 1 };
+
+enum {
+    GMG_FP32 = 0,       /* FP32 storage and arithmetic throughout */
+    GMG_FP32_BF16 = 1,  /* FP32, with BF16 storage of the corrections on levels >= 1 */
+    GMG_IR64 = 2,       /* FP64 outer iterative refinement around FP32 (+BF16) V-cycles */
+    GMG_IR64_FP32 = 3   /* FP64 outer iterative refinement around FP32 V-cycles */
+};
+
+typedef struct {
+    int coarsen;        /* GMG_COARSEN_ISO or GMG_COARSEN_ANISO (default ANISO) */
+    int n_min;          /* an axis is halved only while n/2 >= n_min (default 4) */
+    int nu1, nu2;       /* pre- and post-smoothing sweeps per level (default 2, 2) */
+    int nu_c;           /* sweeps on the coarsest level (default 16) */
+    int precision;      /* GMG_FP32 ... GMG_IR64_FP32 (default GMG_FP32) */
+    int max_cycles;     /* V-cycle limit per solve, rejected cycles included (default 100) */
+    double omega0;      /* initial relaxation factor (default 1) */
+    double omega_min;   /* floor of the relaxation factor (default 0.25) */
+    double shrink;      /* factor applied to omega after a rejected cycle (default 0.7) */
+    double grow;        /* factor applied after an accepted cycle, capped at 1 (default 1.1) */
+    int use_graph;      /* replay the V-cycle from a captured CUDA graph (default 1) */
+    int cycles_per_sync;/* V-cycles queued before the host reads the status (default 4) */
+    double ir_inner_rtol; /* IR modes: inner V-cycles stop at this residual reduction (default 1e-4) */
+} gmg_options;
+
+typedef struct {
+    int cycles;         /* V-cycles run (rejected ones included) */
+    int status;         /* gmg_status of the solve */
+    int levels;         /* multigrid levels */
+    int outer;          /* FP64 refinement steps (IR modes), else 0 */
+    double rel_res;     /* |b - A p|_2 / |b|_2 of the returned p (before the gauge shift) */
+    double omega;       /* relaxation factor after the last cycle */
+    double bnorm;       /* |b|_2 after the zero-mean projection */
+} gmg_info;
+
+typedef struct gmg_solver* gmg_handle;
+typedef struct gmg_batch_solver* gmg_batch;
+
+/* Fills *opt with the defaults listed above. */
+void gmg_default_options(gmg_options* opt);
+
+/*
+ * Plans a solver for one grid.  periodic: 3 flags (x, y, z); a periodic axis
+ * must have even length.  Every axis must have length >= 1.  opt may be NULL
+ * (defaults).  stream: cudaStream_t (or NULL).  Allocates the hierarchy on
+ * the current device.  Errors: GMG_ERR_ARG (dimensions, options, odd periodic
+ * length, h NULL), GMG_ERR_CUDA (allocation).
+ */
+int gmg_create(gmg_handle* h, int nx, int ny, int nz, const int* periodic,
+               const gmg_options* opt, void* stream);
+
+/*
+ * Copies the face coefficients (three device arrays of nx*ny*nz floats, see
+ * Layout) and builds the coarse-level coefficients by finite-volume
+ * rediscretisation (coarse face = sum of its fine faces / coarsening factor).
+ * Must precede gmg_solve.  Coefficients must be finite and >= 0.
+ */
+int gmg_set_coeffs(gmg_handle h, const float* bx, const float* by, const float* bz);
+
+/*
+ * Solves A p = b, where b is sigma projected to zero mean over the active
+ * cells (cells whose face coefficients do not all vanish) and set to 0 on the
+ * inactive ones.  sigma and p are device arrays of nx*ny*nz float (FP32 modes)
+ * or double (IR modes).  p: initial guess on entry; on exit the iterate with
+ * the smallest residual, shifted to zero mean over active cells, 0 on
+ * inactive cells.  tol: relative residual target (> 0).  info may be NULL.
+ * Blocks the calling host thread until the solve ends.  Returns the solve's
+ * status (GMG_OK, GMG_ERR_NOT_CONVERGED, GMG_ERR_DIVERGED, GMG_ERR_NONFINITE)
+ * or an error.
+ */
+int gmg_solve(gmg_handle h, const void* sigma, void* p, double tol, gmg_info* info);
+
+/*
+ * As gmg_solve, with sigma and p in HOST memory (pageable or pinned): the
+ * call copies sigma and the initial guess to the device, solves, and copies
+ * p back, all on the handle's stream.
+ */
+int gmg_solve_host(gmg_handle h, const void* sigma_host, void* p_host, double tol, gmg_info* info);
+
+/*
+ * Per-cycle record of the last solve: rel_res[k] (k = 0 .. cycles; entry 0
+ * is the initial iterate's relative residual, entry k the accepted iterate's
+ * after cycle k), omega[k] and accepted[k] (k = 0 .. cycles-1) for cycle k+1.
+ * Host arrays of capacity cap (+1 for rel_res).  Returns the number of cycles
+ * recorded (<= cap), or -1 on a bad argument.
+ */
+int gmg_history(gmg_handle h, double* rel_res, double* omega, int* accepted, int cap);
+
+/* Number of levels and their dimensions (host array of 3*levels ints, may be NULL). */
+int gmg_levels(gmg_handle h, int* dims);
+
+/* Releases the handle and its device memory. */
+int gmg_destroy(gmg_handle h);
+
+/* Message of the last error on this handle (or of the last failed create when h is NULL). */
+const char* gmg_last_error(gmg_handle h);
+
+/* ----------------------------------------------------------------------------
+ * Batched solves: many independent problems of uneven sizes, one launch per
+ * multigrid phase for all of them (levels of equal depth are smoothed,
+ * restricted and prolongated together; each problem keeps its own omega,
+ * residuals and convergence; converged problems are masked).
+ * -------------------------------------------------------------------------- */
+
+/*
+ * dims: nprob x 3 ints (nx, ny, nz); periodic: nprob x 3 flags (or NULL for
+ * all walls); opt shared by all problems (precision must be GMG_FP32 or
+ * GMG_FP32_BF16).
+ */
+int gmg_batch_create(gmg_batch* b, int nprob, const int* dims, const int* periodic,
+                     const gmg_options* opt, void* stream);
+
+/* bx, by, bz: host arrays of nprob device pointers, each to that problem's faces. */
+int gmg_batch_set_coeffs(gmg_batch b, const float* const* bx, const float* const* by,
+                         const float* const* bz);
+
+/*
+ * sigma, p: host arrays of nprob device pointers (float).  infos: host array
+ * of nprob gmg_info (may be NULL).  Returns GMG_OK if every problem
+ * converged, else the first failing problem's status.
+ */
+int gmg_batch_solve(gmg_batch b, const float* const* sigma, float* const* p, double tol,
+                    gmg_info* infos);
+
+int gmg_batch_destroy(gmg_batch b);
+const char* gmg_batch_last_error(gmg_batch b);
+
+/* ----------------------------------------------------------------------------
+ * Single multigrid steps on caller buffers (the kernels the solver is built
+ * from), for users assembling their own cycles and for step-by-step checks.
+ * Each is asynchronous on `stream`; geometry arguments as for gmg_create.
+ * -------------------------------------------------------------------------- */
+
+/*
+ * One red-black Gauss-Seidel sweep under-relaxed by omega (Sec. 3.1): red
+ * cells ((i+j+k) even) are updated from p_in, then black cells from the new
+ * red values: p <- (1-omega) p + omega (sum_f b_f p_nb - b) / sum_f b_f, cells
+ * whose faces all vanish keep their value.  p_out must not alias p_in.
+ */
+int gmg_op_sweep(int nx, int ny, int nz, const int* periodic, const float* bx, const float* by,
+                 const float* bz, const float* b, const float* p_in, float* p_out, double omega,
+                 void* stream);
+
+/*
+ * The same sweep as gmg_op_sweep, run as two in-place launches (red cells,
+ * then black cells) with one thread per cell.  It gives bit-identical results
+ * and serves as the check that the single-launch sweep has no race.  p is
+ * updated in place.
+ */
+int gmg_op_sweep_reference(int nx, int ny, int nz, const int* periodic, const float* bx,
+                           const float* by, const float* bz, const float* b, float* p, double omega,
+                           void* stream);
+
+/*
+ * Residual r = b - A p of a fine grid, summed over the children of each coarse
+ * cell (Sec. 3: coarse-grid correction; restriction = sum over children):
+ * b_coarse[J] = sum_{I in J} r_I, where the coarse grid is (nx/fx, ny/fy,
+ * nz/fz) with factors f in {1, 2} dividing the axis.  If rr is not NULL, the
+ * host receives sum over fine cells of r_I^2 (the call then synchronises the
+ * stream).
+ */
+int gmg_op_residual_restrict(int nx, int ny, int nz, const int* periodic, const int* factors,
+                             const float* bx, const float* by, const float* bz, const float* b,
+                             const float* p, float* b_coarse, double* rr, void* stream);
+
+/* p[I] += e[I / f] on the fine grid (piecewise-constant prolongation, Sec. 3). */
+int gmg_op_prolong_add(int nx, int ny, int nz, const int* factors, const float* e, float* p,
+                       void* stream);
+
+/*
+ * Coarse face coefficients of the grid coarsened by factors (Sec. 3.2): the
+ * coarse d-face is the sum of the fine d-faces it covers divided by f_d; wall
+ * faces of Neumann axes are 0.
+ */
+int gmg_op_coarsen_coeffs(int nx, int ny, int nz, const int* periodic, const int* factors,
+                          const float* bx, const float* by, const float* bz, float* cbx,
+                          float* cby, float* cbz, void* stream);
+
+/*
+ * |b - A p|_2^2 summed in FP64 on the device, returned to the host in *rr
+ * (synchronises the stream).  Uses a library-owned device buffer for the
+ * per-block partial sums, allocated on first use per device.
+ */
+int gmg_op_residual_norm(int nx, int ny, int nz, const int* periodic, const float* bx,
+                         const float* by, const float* bz, const float* b, const float* p,
+                         double* rr, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMG_H */

@@ -1,0 +1,354 @@
+"""ctypes binding of ``libgmg.so`` (the C ABI declared in ``include/gmg.h``).
+
+Argument marshalling only: every step of a solve runs in the library's CUDA
+kernels.  Grid arrays are torch tensors on the CUDA device (C-contiguous,
+shape ``(nz, ny, nx)``), passed by data pointer on the current torch stream
+unless a stream is given.  The library is loaded on first use; if it is
+missing or cannot be loaded this module raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgmg.so")
+HEADER = os.path.join(HERE, "..", "include", "gmg.h")
+
+OK, ERR_ARG, ERR_CUDA, NOT_CONVERGED, DIVERGED, NONFINITE = 0, 1, 2, 3, 4, 5
+STATUS_NAMES = {OK: "ok", ERR_ARG: "bad argument", ERR_CUDA: "cuda error",
+                NOT_CONVERGED: "not converged", DIVERGED: "diverged", NONFINITE: "non-finite source"}
+ISO, ANISO = 0, 1
+FP32, FP32_BF16, IR64, IR64_FP32 = 0, 1, 2, 3
+PRECISIONS = {"fp32": FP32, "fp32_bf16": FP32_BF16, "ir64": IR64, "ir64_fp32": IR64_FP32}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("coarsen", ctypes.c_int), ("n_min", ctypes.c_int), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("nu_c", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("omega0", ctypes.c_double),
+                ("omega_min", ctypes.c_double), ("shrink", ctypes.c_double),
+                ("grow", ctypes.c_double), ("use_graph", ctypes.c_int),
+                ("cycles_per_sync", ctypes.c_int), ("ir_inner_rtol", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("levels", ctypes.c_int),
+                ("outer", ctypes.c_int), ("rel_res", ctypes.c_double), ("omega", ctypes.c_double),
+                ("bnorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class GmgError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load libgmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise GmgError(f"{LIB_PATH} is missing: build it with paper_2607_07687_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    c_int, c_double = ctypes.c_int, ctypes.c_double
+    L.gmg_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.gmg_default_options.restype = None
+    L.gmg_create.argtypes = [ctypes.POINTER(vp), c_int, c_int, c_int, ip, ctypes.POINTER(Options), vp]
+    L.gmg_set_coeffs.argtypes = [vp, vp, vp, vp]
+    L.gmg_solve.argtypes = [vp, vp, vp, c_double, ctypes.POINTER(Info)]
+    L.gmg_solve_host.argtypes = [vp, vp, vp, c_double, ctypes.POINTER(Info)]
+    L.gmg_history.argtypes = [vp, dp, dp, ip, c_int]
+    L.gmg_levels.argtypes = [vp, ip]
+    L.gmg_destroy.argtypes = [vp]
+    L.gmg_last_error.argtypes = [vp]
+    L.gmg_last_error.restype = ctypes.c_char_p
+    L.gmg_batch_create.argtypes = [ctypes.POINTER(vp), c_int, ip, ip, ctypes.POINTER(Options), vp]
+    L.gmg_batch_set_coeffs.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.gmg_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), c_double, ctypes.POINTER(Info)]
+    L.gmg_batch_destroy.argtypes = [vp]
+    L.gmg_batch_last_error.argtypes = [vp]
+    L.gmg_batch_last_error.restype = ctypes.c_char_p
+    L.gmg_op_sweep.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, vp, c_double, vp]
+    L.gmg_op_sweep_reference.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, c_double, vp]
+    L.gmg_op_residual_restrict.argtypes = [c_int, c_int, c_int, ip, ip, vp, vp, vp, vp, vp, vp, dp, vp]
+    L.gmg_op_prolong_add.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp]
+    L.gmg_op_coarsen_coeffs.argtypes = [c_int, c_int, c_int, ip, ip, vp, vp, vp, vp, vp, vp, vp]
+    L.gmg_op_residual_norm.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
+    _lib = L
+    return L
+
+
+def declared_functions() -> List[str]:
+    """Names of the functions declared in include/gmg.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gmg_\w+)\s*\(", text, flags=re.M)))
+
+
+def options(coarsen: str = "aniso", precision: str = "fp32", **kw) -> Options:
+    o = Options()
+    lib().gmg_default_options(ctypes.byref(o))
+    o.coarsen = ANISO if coarsen == "aniso" else ISO
+    o.precision = PRECISIONS[precision]
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _ivec(v) -> ctypes.Array:
+    return (ctypes.c_int * len(v))(*[int(x) for x in v])
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t, dtype=None, numel=None) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _check(rc: int, handle, batch: bool = False, ok=(OK,)):
+    if rc in ok:
+        return rc
+    L = lib()
+    msg = (L.gmg_batch_last_error if batch else L.gmg_last_error)(handle)
+    raise GmgError(f"{STATUS_NAMES.get(rc, rc)}: {msg.decode() if msg else ''}")
+
+
+SOLVE_STATUSES = (OK, NOT_CONVERGED, DIVERGED, NONFINITE)
+
+
+class Solver:
+    """One grid; wraps gmg_create / gmg_set_coeffs / gmg_solve / gmg_destroy."""
+
+    def __init__(self, dims, periodic=(False, False, False), opts: Optional[Options] = None,
+                 stream=None, **kw):
+        self.dims = tuple(int(d) for d in dims)
+        self.periodic = tuple(bool(p) for p in periodic)
+        self.opts = opts if opts is not None else options(**kw)
+        self.stream = _stream(stream)
+        self.h = ctypes.c_void_p()
+        rc = lib().gmg_create(ctypes.byref(self.h), *self.dims, _ivec(self.periodic),
+                              ctypes.byref(self.opts), ctypes.c_void_p(self.stream))
+        _check(rc, None)
+        self.ncells = self.dims[0] * self.dims[1] * self.dims[2]
+        self.fp64 = self.opts.precision in (IR64, IR64_FP32)
+
+    def close(self):
+        if self.h:
+            lib().gmg_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_coeffs(self, bx, by, bz):
+        import torch
+        ptrs = [_ptr(t, torch.float32, self.ncells) for t in (bx, by, bz)]
+        _check(lib().gmg_set_coeffs(self.h, *ptrs), self.h)
+
+    def solve(self, sigma, p, tol: float = 1e-6) -> Info:
+        """p (in: initial guess, out: solution); returns the Info record."""
+        import torch
+        dt = torch.float64 if self.fp64 else torch.float32
+        info = Info()
+        rc = lib().gmg_solve(self.h, _ptr(sigma, dt, self.ncells), _ptr(p, dt, self.ncells),
+                             float(tol), ctypes.byref(info))
+        _check(rc, self.h, ok=SOLVE_STATUSES)
+        return info
+
+    def solve_host(self, sigma, p, tol: float = 1e-6) -> Info:
+        """As solve, with sigma and p host numpy arrays (or pinned CPU tensors)."""
+        import numpy as np
+        dt = np.float64 if self.fp64 else np.float32
+
+        def hp(a):
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous() or a.numel() != self.ncells:
+                    raise ValueError("expected a contiguous CPU tensor of the grid size")
+                return a.data_ptr()
+            if a.dtype != dt or not a.flags.c_contiguous or a.size != self.ncells:
+                raise ValueError(f"expected a C-contiguous {dt.__name__} array of the grid size")
+            return a.ctypes.data
+        info = Info()
+        rc = lib().gmg_solve_host(self.h, ctypes.c_void_p(hp(sigma)), ctypes.c_void_p(hp(p)),
+                                  float(tol), ctypes.byref(info))
+        _check(rc, self.h, ok=SOLVE_STATUSES)
+        return info
+
+    def history(self, cap: int = 1000):
+        import numpy as np
+        res = np.zeros(cap + 1)
+        om = np.zeros(cap)
+        acc = np.zeros(cap, dtype=np.int32)
+        n = lib().gmg_history(self.h, res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), cap)
+        if n < 0:
+            raise GmgError(lib().gmg_last_error(self.h).decode())
+        return res[:n + 1], om[:n], acc[:n].astype(bool)
+
+    def levels(self):
+        L = lib().gmg_levels(self.h, None)
+        arr = (ctypes.c_int * (3 * L))()
+        lib().gmg_levels(self.h, arr)
+        return [tuple(arr[3 * l:3 * l + 3]) for l in range(L)]
+
+
+class BatchSolver:
+    """Many independent problems; wraps gmg_batch_*."""
+
+    def __init__(self, dims: Sequence, periodic=None, opts: Optional[Options] = None, stream=None,
+                 **kw):
+        self.dims = [tuple(int(x) for x in d) for d in dims]
+        self.n = len(self.dims)
+        self.opts = opts if opts is not None else options(**kw)
+        self.stream = _stream(stream)
+        flat = _ivec([x for d in self.dims for x in d])
+        per = None if periodic is None else _ivec([int(bool(x)) for p in periodic for x in p])
+        self.h = ctypes.c_void_p()
+        rc = lib().gmg_batch_create(ctypes.byref(self.h), self.n, flat, per, ctypes.byref(self.opts),
+                                    ctypes.c_void_p(self.stream))
+        _check(rc, None, batch=True)
+        self.ncells = [d[0] * d[1] * d[2] for d in self.dims]
+
+    def close(self):
+        if self.h:
+            lib().gmg_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arr(self, tensors, dtype):
+        if len(tensors) != self.n:
+            raise ValueError(f"expected {self.n} tensors")
+        return (ctypes.c_void_p * self.n)(*[_ptr(t, dtype, n) for t, n in zip(tensors, self.ncells)])
+
+    def set_coeffs(self, bx, by, bz):
+        import torch
+        f = torch.float32
+        _check(lib().gmg_batch_set_coeffs(self.h, self._arr(bx, f), self._arr(by, f), self._arr(bz, f)),
+               self.h, batch=True)
+
+    def solve(self, sigma, p, tol: float = 1e-6) -> List[Info]:
+        import torch
+        infos = (Info * self.n)()
+        rc = lib().gmg_batch_solve(self.h, self._arr(sigma, torch.float32), self._arr(p, torch.float32),
+                                   float(tol), infos)
+        _check(rc, self.h, batch=True, ok=SOLVE_STATUSES)
+        return list(infos)
+
+
+# ---------------------------------------------------------------- single steps
+
+def _dims_of(t):
+    nz, ny, nx = t.shape
+    return nx, ny, nz
+
+
+def op_sweep(bx, by, bz, b, p_in, p_out, omega, periodic=(False, False, False), stream=None):
+    import torch
+    dims = _dims_of(b)
+    n = b.numel()
+    ptrs = [_ptr(t, torch.float32, n) for t in (bx, by, bz, b, p_in, p_out)]
+    rc = lib().gmg_op_sweep(*dims, _ivec(periodic), *ptrs, float(omega), ctypes.c_void_p(_stream(stream)))
+    _check(rc, None)
+
+
+def op_sweep_reference(bx, by, bz, b, p, omega, periodic=(False, False, False), stream=None):
+    import torch
+    dims = _dims_of(b)
+    n = b.numel()
+    ptrs = [_ptr(t, torch.float32, n) for t in (bx, by, bz, b, p)]
+    rc = lib().gmg_op_sweep_reference(*dims, _ivec(periodic), *ptrs, float(omega),
+                                      ctypes.c_void_p(_stream(stream)))
+    _check(rc, None)
+
+
+def op_residual_restrict(bx, by, bz, b, p, b_coarse, factors, periodic=(False, False, False),
+                         want_norm: bool = False, stream=None):
+    import torch
+    dims = _dims_of(b)
+    n = b.numel()
+    ptrs = [_ptr(t, torch.float32, n) for t in (bx, by, bz, b, p)]
+    rr = ctypes.c_double(0.0)
+    rc = lib().gmg_op_residual_restrict(*dims, _ivec(periodic), _ivec(factors), *ptrs,
+                                        _ptr(b_coarse, torch.float32),
+                                        ctypes.byref(rr) if want_norm else None,
+                                        ctypes.c_void_p(_stream(stream)))
+    _check(rc, None)
+    return rr.value if want_norm else None
+
+
+def op_residual_norm(bx, by, bz, b, p, periodic=(False, False, False), stream=None) -> float:
+    import torch
+    dims = _dims_of(b)
+    n = b.numel()
+    ptrs = [_ptr(t, torch.float32, n) for t in (bx, by, bz, b, p)]
+    rr = ctypes.c_double(0.0)
+    rc = lib().gmg_op_residual_norm(*dims, _ivec(periodic), *ptrs, ctypes.byref(rr),
+                                    ctypes.c_void_p(_stream(stream)))
+    _check(rc, None)
+    return rr.value
+
+
+def op_prolong_add(e, p, factors, stream=None):
+    import torch
+    dims = _dims_of(p)
+    rc = lib().gmg_op_prolong_add(*dims, _ivec(factors), _ptr(e, torch.float32),
+                                  _ptr(p, torch.float32), ctypes.c_void_p(_stream(stream)))
+    _check(rc, None)
+
+
+def op_coarsen_coeffs(bx, by, bz, cbx, cby, cbz, factors, periodic=(False, False, False), stream=None):
+    import torch
+    dims = _dims_of(bx)
+    n = bx.numel()
+    ptrs = [_ptr(t, torch.float32, n) for t in (bx, by, bz)]
+    cptrs = [_ptr(t, torch.float32) for t in (cbx, cby, cbz)]
+    rc = lib().gmg_op_coarsen_coeffs(*dims, _ivec(periodic), _ivec(factors), *ptrs, *cptrs,
+                                     ctypes.c_void_p(_stream(stream)))
+    _check(rc, None)

@@ -1,0 +1,234 @@
+// gmg_internal.h -- device-side task descriptors and kernel launchers of the
+// GB300 multigrid solver (private to the library).
+//
+// Every kernel works on a list of tasks (one task = one grid level of one
+// problem) so that a single launch serves one problem or a whole batch of
+// problems of uneven sizes.  Blocks walk the concatenated tiles of all tasks
+// (persistent grid-stride loop); tile_off[t] is the first tile of task t.  A
+// launch over a single task passes it by value instead (no device copy).
+//
+// Iterate buffers of the finest level rotate: a task names a buffer by role
+// (0 = accepted iterate, 1 and 2 = work) and the live assignment is
+// buf[(role + *rot) % 3], so accepting a V-cycle changes *rot instead of
+// copying the grid.  Coarse levels use rot == nullptr (fixed roles).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace gmg {
+
+constexpr int kMaxLevels = 32;
+constexpr int kCoarseMaxCells = 4096;   // largest coarsest level solved inside one CTA
+constexpr int kThreads = 256;           // threads per block of the grid kernels
+
+// sweep tile (cells): TX x TY columns marching through a z-chunk
+constexpr int kSweepTX = 32;
+constexpr int kSweepTY = 8;
+// residual tile (fine cells)
+constexpr int kResTX = 32;
+constexpr int kResTY = 4;
+constexpr int kResTZ = 2;
+// elementwise kernels: cells per tile
+constexpr int kElemTile = 4096;
+
+enum RunStatus { kRunning = -1, kOk = 0, kNotConverged = 3, kDiverged = 4, kNonFinite = 5 };
+
+using bf16 = __nv_bfloat16;
+
+struct Geo {
+    int n[3];      // nx, ny, nz
+    int per[3];    // periodic flags
+};
+
+// Per-problem solve state, resident in device memory.
+struct Ctl {
+    double omega;        // relaxation factor used by the next cycle
+    double omega_min, shrink, grow;
+    double bnorm;        // |b|_2 of the (inner) right-hand side
+    double r_prev;       // residual norm of the accepted iterate
+    double tol;          // relative residual target of this (inner) solve
+    double r_last;       // residual norm of the latest candidate
+    double hist_scale;   // history entry = residual norm * hist_scale
+    double mean;         // mean used by the last projection / gauge
+    double stat_cnt;     // number of active cells
+    double outer_bnorm;  // IR: |b64|
+    double outer_r;      // IR: |b64 - A p64| of the current p64
+    int rot;             // rotation of the finest-level iterate roles
+    int cycles;          // cycles run in this (inner) solve
+    int total_cycles;    // cycles over all inner solves (IR)
+    int status;          // RunStatus of the (inner) solve
+    int done;            // 1: every kernel skips this problem
+    int max_cycles;      // cycle limit of this (inner) solve
+    int res_role;        // role holding the candidate at the end of a cycle
+    int nonfinite;       // count of non-finite right-hand-side entries
+    int zero_out;        // 1: the solution is identically zero (|b| = 0)
+    int outer_status;    // IR: status of the whole solve
+    int hist_cap;
+    int pad;
+    double* hist_res;    // [hist_cap + 1] relative residual after each cycle
+    double* hist_omega;  // [hist_cap] omega used by each cycle
+    int* hist_acc;       // [hist_cap] accept flag of each cycle
+};
+
+// One red-black sweep of one level: p_out = S(p_in [+ P corr]).
+template <class TP, class TC>
+struct SweepTask {
+    Geo g;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    const float* b;
+    TP* buf[3];
+    const int* rot;      // nullptr: roles fixed
+    int in_role;         // -1: zero input (coarse levels, first sweep)
+    int out_role;
+    const TC* corr;      // coarse correction added to the input, or nullptr
+    int cf[3];           // coarsening factors of corr
+    int tiles_x, tiles_y, zchunk, nchunks;
+    float omega;         // used when ctl == nullptr
+    const Ctl* ctl;
+};
+
+// Residual of one level, restricted to the next level and/or summed in squares.
+template <class TP>
+struct ResTask {
+    Geo g;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    const float* b;
+    TP* buf[3];
+    const int* rot;
+    int role;            // -1: zero iterate (residual = b)
+    float* bc;           // coarse right-hand side, or nullptr (norm only)
+    int cf[3];
+    int tiles_x, tiles_y, tiles_z;
+    double* partials;    // one per tile of this task, or nullptr
+    const Ctl* ctl;
+};
+
+// Coarsest-level solve inside one CTA: project b to zero mean over active
+// cells, then nu_c sweeps from zero.
+template <class TP>
+struct CoarseTask {
+    Geo g;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    float* b;
+    TP* out;
+    int nu_c;
+    const Ctl* ctl;
+};
+
+template <class Task>
+struct TaskList {
+    const Task* tasks;   // device array, or nullptr: use `single`
+    const int* tile_off; // device prefix of tile counts (ntasks + 1)
+    int ntasks;
+    int total;           // total tiles
+    Task single;
+};
+
+// Caller right-hand side -> solver right-hand side, and initial guess copy-in.
+template <class TS>
+struct ProjTask {
+    int64_t n;           // cells
+    const uint8_t* mask; // 1 on active cells
+    const TS* sigma;
+    float* b32;          // FP32 right-hand side, or nullptr
+    double* b64;         // FP64 right-hand side, or nullptr
+    const TS* p_in;      // caller initial guess, or nullptr (zero)
+    float* p32;          // FP32 iterate, or nullptr
+    double* p64;         // FP64 iterate, or nullptr (may alias p_in)
+    double* partials;    // 3 per tile: sum sigma (active), active count, non-finite count
+    double* bpartials;   // 1 per tile: sum b^2
+    int tiles;
+    Ctl* ctl;
+};
+
+// Accepted iterate -> caller array, shifted to zero mean over active cells.
+template <class TP, class TD>
+struct GaugeTask {
+    int64_t n;
+    const uint8_t* mask;
+    TP* buf[3];
+    const int* rot;
+    TD* dst;
+    double* partials;    // 1 per tile
+    int tiles;
+    Ctl* ctl;
+};
+
+struct CtlTask {
+    Ctl* ctl;
+    const double* partials;    // residual partials
+    int nparts;
+    const double* bpartials;   // |b|^2 partials (init only)
+    int nbparts;
+    const double* ppartials;   // projection partials (3 per tile)
+    int npparts;
+};
+
+// FP64 iterative refinement on one fine grid.
+struct IrTask {
+    Geo g;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    const double* b64;
+    double* p64;
+    float* b32;          // inner right-hand side
+    float* ebuf[3];      // inner iterate roles
+    const int* rot;
+    double* partials;    // one per residual tile
+    int tiles_x, tiles_y, tiles_z;
+    Ctl* ctl;
+    double* scale;       // device scalar: inner = outer residual * scale
+};
+
+// ---------------------------------------------------------------- launchers
+
+template <class TP, class TC>
+cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaStream_t s);
+template <class TP>
+cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStream_t s);
+template <class TP>
+cudaError_t launch_coarse(const CoarseTask<TP>* tasks, int ntasks, cudaStream_t s);
+
+// Reference variant of the sweep: one in-place launch per colour.
+cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const float* bz,
+                                  const float* b, float* p, float omega, cudaStream_t s);
+
+cudaError_t launch_coarsen_coeffs(Geo fine, const int cf[3], const float* bx, const float* by,
+                                  const float* bz, float* cbx, float* cby, float* cbz,
+                                  cudaStream_t s);
+cudaError_t launch_prolong_add(Geo fine, const int cf[3], const float* e, float* p, cudaStream_t s);
+cudaError_t launch_active_mask(Geo g, const float* bx, const float* by, const float* bz,
+                               uint8_t* mask, cudaStream_t s);
+cudaError_t launch_sum_partials(const double* partials, int n, double* out, cudaStream_t s);
+cudaError_t launch_check_coeffs(int64_t n, const float* bx, const float* by, const float* bz,
+                                int* bad, cudaStream_t s);
+
+template <class TS>
+cudaError_t launch_project_sum(const TaskList<ProjTask<TS>>& tl, int grid, cudaStream_t s);
+template <class TS>
+cudaError_t launch_project_apply(const TaskList<ProjTask<TS>>& tl, int grid, cudaStream_t s);
+cudaError_t launch_project_finalize(const CtlTask* t, int nprob, cudaStream_t s);
+cudaError_t launch_control_init(const CtlTask* t, int nprob, cudaStream_t s);
+cudaError_t launch_control_cycle(const CtlTask* t, int nprob, cudaStream_t s);
+
+template <class TP, class TD>
+cudaError_t launch_gauge_sum(const TaskList<GaugeTask<TP, TD>>& tl, int grid, cudaStream_t s);
+template <class TP, class TD>
+cudaError_t launch_gauge_apply(const TaskList<GaugeTask<TP, TD>>& tl, int grid, cudaStream_t s);
+cudaError_t launch_gauge_finalize(const CtlTask* t, int nprob, cudaStream_t s);
+
+cudaError_t launch_ir_residual(const IrTask& t, int grid, cudaStream_t s);
+cudaError_t launch_ir_begin_inner(const IrTask& t, int nparts, double tol, double inner_rtol,
+                                  int max_cycles, cudaStream_t s);
+cudaError_t launch_ir_update(const IrTask& t, cudaStream_t s);
+
+}  // namespace gmg

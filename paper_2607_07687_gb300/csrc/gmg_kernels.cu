@@ -1,0 +1,1016 @@
+// gmg_kernels.cu -- sm_103a kernels of the geometric-multigrid Poisson solver.
+//
+// The operator (the variable-coefficient Poisson equation the paper's Sec. 3.1
+// targets) in grid units: (A p)_I = sum_f beta_f (p_nb(f) - p_I).  Kernels:
+//
+//   k_sweep       one full red-black Gauss-Seidel sweep, under-relaxed by
+//                 omega (Sec. 3.1), in ONE launch: each CTA owns a TX x TY
+//                 column of a z-chunk, stages halo-2 planes of the input in
+//                 shared memory while marching in z, recomputes the red cells
+//                 of a one-cell ring around its tile, and writes red and black
+//                 cells to a separate output buffer (ping-pong), so no CTA
+//                 ever reads a value another CTA writes in the same launch and
+//                 no grid barrier is needed.  The coarse correction of the
+//                 V-cycle (Sec. 3: piecewise-constant prolongation) and the
+//                 zero initial guess of coarse levels are folded into its loads.
+//   k_residual    r = b - A p, summed over the children of each coarse cell
+//                 (restriction, Sec. 3) and/or squared and summed in FP64.
+//   k_coarse      the coarsest level in one CTA: zero-mean projection of b
+//                 over active cells, then nu_c sweeps in shared memory.
+//   k_coarsen     coarse face coefficients (finite-volume rediscretisation on
+//                 the iso- or anisotropically coarsened grid, Sec. 3.2).
+//   k_control_*   the adaptive relaxation rule (Sec. 3.1) and convergence
+//                 test, one block per problem.
+//   k_ir_*        FP64 residual and update of the outer refinement loop.
+//   k_project_*, k_gauge_*  right-hand-side projection, exit gauge.
+//
+// Reductions are deterministic: per-tile partials in FP64, summed in a fixed
+// order by one block per problem.
+#include "gmg_internal.h"
+
+#include <cmath>
+
+namespace gmg {
+namespace {
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ bool wrapc(int& i, int n, int per)
+{
+    if (i < 0) {
+        if (!per) return false;
+        i += n;
+    } else if (i >= n) {
+        if (!per) return false;
+        i -= n;
+    }
+    return true;
+}
+
+__device__ __forceinline__ int64_t lin(const Geo& g, int x, int y, int z)
+{
+    return ((int64_t)z * g.n[1] + y) * g.n[0] + x;
+}
+
+template <class T>
+__device__ __forceinline__ float ldv(const T* p, int64_t i);
+template <>
+__device__ __forceinline__ float ldv<float>(const float* p, int64_t i) { return __ldg(p + i); }
+template <>
+__device__ __forceinline__ float ldv<bf16>(const bf16* p, int64_t i) { return __bfloat162float(p[i]); }
+
+template <class T>
+__device__ __forceinline__ void stv(T* p, int64_t i, float v);
+template <>
+__device__ __forceinline__ void stv<float>(float* p, int64_t i, float v) { p[i] = v; }
+template <>
+__device__ __forceinline__ void stv<bf16>(bf16* p, int64_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+
+// coefficient of the lower d-face of the cell at (unwrapped) c: 0 on walls and outside
+__device__ __forceinline__ float face_lo(const float* a, const Geo& g, int d, int x, int y, int z)
+{
+    if (!wrapc(x, g.n[0], g.per[0]) || !wrapc(y, g.n[1], g.per[1]) || !wrapc(z, g.n[2], g.per[2]))
+        return 0.f;
+    const int c = d == 0 ? x : (d == 1 ? y : z);
+    if (c == 0 && !g.per[d]) return 0.f;
+    return __ldg(a + lin(g, x, y, z));
+}
+
+// sum over the six faces of beta_f * p_nb, in one fixed order (lower/upper x, y, z)
+__device__ __forceinline__ float nb_sum(float bxl, float pxl, float bxu, float pxu, float byl,
+                                        float pyl, float byu, float pyu, float bzl, float pzl,
+                                        float bzu, float pzu)
+{
+    return ((bxl * pxl + bxu * pxu) + (byl * pyl + byu * pyu)) + (bzl * pzl + bzu * pzu);
+}
+
+__device__ __forceinline__ float diag_sum(float bxl, float bxu, float byl, float byu, float bzl,
+                                          float bzu)
+{
+    return ((bxl + bxu) + (byl + byu)) + (bzl + bzu);
+}
+
+// under-relaxed Gauss-Seidel update of one cell (Sec. 3.1); isolated cells keep p
+__device__ __forceinline__ float gs_update(float p, float nb, float dg, float b, float w)
+{
+    if (!(dg > 0.f)) return p;
+    const float gs = (nb - b) / dg;
+    return (1.0f - w) * p + w * gs;
+}
+
+template <class Task>
+__device__ __forceinline__ const Task* task_of(const TaskList<Task>& tl, int tile, int& local)
+{
+    if (!tl.tasks) {
+        local = tile;
+        return &tl.single;
+    }
+    int lo = 0, hi = tl.ntasks - 1;
+    while (lo < hi) {   // last t with tile_off[t] <= tile
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tl.tile_off + mid) <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    local = tile - __ldg(tl.tile_off + lo);
+    return tl.tasks + lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block, fixed order; result valid in thread 0.  `red` holds one
+// double per warp.  Ends with a barrier so `red` may be reused at once.
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
+// ---------------------------------------------------------------- K1: fused sweep
+
+template <class TP, class TC>
+__global__ void __launch_bounds__(kThreads) k_sweep(const __grid_constant__ TaskList<SweepTask<TP, TC>> tl)
+{
+    constexpr int TX = kSweepTX, TY = kSweepTY, SW = TX + 4, SH = TY + 4, PL = SW * SH;
+    constexpr int EW = TX + 2, EH = TY + 2;
+    // ring buffers of z-planes over the tile plus a halo of 2 (the E2 region)
+    __shared__ float sP[2][PL];    // input p (+ correction), planes kr, kr+1
+    __shared__ float sM[3][PL];    // merged plane: red updated, black = input; kr-2..kr
+    __shared__ float sB[2][PL];    // right-hand side, planes kr-1, kr
+    __shared__ float sBX[2][PL];   // lower x-face coefficients, planes kr-1, kr
+    __shared__ float sBY[2][PL];   // lower y-face coefficients, planes kr-1, kr
+    __shared__ float sBZ[3][PL];   // lower z-face coefficients, planes kr-1..kr+1
+    const int tid = threadIdx.x;
+
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        int local;
+        const SweepTask<TP, TC>* tp = task_of(tl, tile, local);
+        const Ctl* ctl = tp->ctl;
+        if (ctl && ctl->done) continue;                       // uniform in the block
+        const Geo g = tp->g;
+        const int cx = local % tp->tiles_x;
+        const int rest = local / tp->tiles_x;
+        const int cy = rest % tp->tiles_y;
+        const int cz = rest / tp->tiles_y;
+        const int x0 = cx * TX, y0 = cy * TY;
+        const int z0 = cz * tp->zchunk;
+        const int z1 = min(g.n[2], z0 + tp->zchunk);
+        const int rot = tp->rot ? *tp->rot : 0;
+        const TP* pin = tp->in_role < 0 ? nullptr : tp->buf[(tp->in_role + rot) % 3];
+        TP* pout = tp->buf[(tp->out_role + rot) % 3];
+        const TC* corr = tp->corr;
+        const int cf0 = tp->cf[0], cf1 = tp->cf[1], cf2 = tp->cf[2];
+        Geo gc = g;
+        gc.n[0] = g.n[0] / cf0; gc.n[1] = g.n[1] / cf1; gc.n[2] = g.n[2] / cf2;
+        const float w = ctl ? (float)ctl->omega : tp->omega;
+        const float* bxa = tp->bx;
+        const float* bya = tp->by;
+        const float* bza = tp->bz;
+        const float* ba = tp->b;
+
+        auto load_p = [&](float* dst, int z) {
+            int zw = z;
+            const bool zok = wrapc(zw, g.n[2], g.per[2]);
+            for (int i = tid; i < PL; i += kThreads) {
+                const int sy = i / SW, sx = i - sy * SW;
+                int x = x0 - 2 + sx, y = y0 - 2 + sy;
+                float v = 0.f;
+                if (zok && wrapc(x, g.n[0], g.per[0]) && wrapc(y, g.n[1], g.per[1])) {
+                    if (pin) v = ldv(pin, lin(g, x, y, zw));
+                    if (corr) v += ldv(corr, lin(gc, x / cf0, y / cf1, zw / cf2));
+                }
+                dst[i] = v;
+            }
+        };
+        auto load_b = [&](float* dst, int z) {
+            int zw = z;
+            const bool zok = wrapc(zw, g.n[2], g.per[2]);
+            for (int i = tid; i < PL; i += kThreads) {
+                const int sy = i / SW, sx = i - sy * SW;
+                int x = x0 - 2 + sx, y = y0 - 2 + sy;
+                float v = 0.f;
+                if (zok && wrapc(x, g.n[0], g.per[0]) && wrapc(y, g.n[1], g.per[1]))
+                    v = __ldg(ba + lin(g, x, y, zw));
+                dst[i] = v;
+            }
+        };
+        auto load_face = [&](float* dst, const float* a, int d, int z) {
+            for (int i = tid; i < PL; i += kThreads) {
+                const int sy = i / SW, sx = i - sy * SW;
+                dst[i] = face_lo(a, g, d, x0 - 2 + sx, y0 - 2 + sy, z);
+            }
+        };
+
+        const int nsteps = (z1 - z0) + 2;   // red planes z0-1 .. z1
+        for (int u = 0; u < nsteps; ++u) {
+            const int kr = z0 - 1 + u;
+            __syncthreads();                 // ring slots about to be overwritten are free
+            if (u == 0) {
+                load_p(sP[0], kr);
+                load_p(sM[2], kr - 1);       // black cells of plane kr-1 = input values
+                load_face(sBZ[0], bza, 2, kr);
+            }
+            load_p(sP[(u + 1) & 1], kr + 1);
+            load_b(sB[u & 1], kr);
+            load_face(sBX[u & 1], bxa, 0, kr);
+            load_face(sBY[u & 1], bya, 1, kr);
+            load_face(sBZ[(u + 1) % 3], bza, 2, kr + 1);
+            __syncthreads();
+
+            // red cells of plane kr on the tile and its one-cell ring
+            {
+                int zk = kr;
+                const bool zok = wrapc(zk, g.n[2], g.per[2]);
+                const float* P0 = sP[u & 1];
+                const float* P1 = sP[(u + 1) & 1];
+                const float* Mlo = sM[(u + 2) % 3];
+                float* M0 = sM[u % 3];
+                const float* B0 = sB[u & 1];
+                const float* X0 = sBX[u & 1];
+                const float* Y0 = sBY[u & 1];
+                const float* Z0 = sBZ[u % 3];
+                const float* Z1 = sBZ[(u + 1) % 3];
+                for (int i = tid; i < EW * EH; i += kThreads) {
+                    const int ey = i / EW, ex = i - ey * EW;
+                    const int s = (ey + 1) * SW + (ex + 1);
+                    int x = x0 - 1 + ex, y = y0 - 1 + ey;
+                    float v = 0.f;
+                    if (zok && wrapc(x, g.n[0], g.per[0]) && wrapc(y, g.n[1], g.per[1])) {
+                        v = P0[s];
+                        if (((x + y + zk) & 1) == 0) {
+                            const float nb = nb_sum(X0[s], P0[s - 1], X0[s + 1], P0[s + 1], Y0[s],
+                                                    P0[s - SW], Y0[s + SW], P0[s + SW], Z0[s], Mlo[s],
+                                                    Z1[s], P1[s]);
+                            const float dg = diag_sum(X0[s], X0[s + 1], Y0[s], Y0[s + SW], Z0[s], Z1[s]);
+                            v = gs_update(v, nb, dg, B0[s], w);
+                        }
+                    }
+                    M0[s] = v;
+                }
+            }
+            __syncthreads();
+
+            // black cells of plane kr-1 on the tile, from the new red values
+            if (u >= 2) {
+                const int k = kr - 1;
+                const float* Mk = sM[(u + 2) % 3];
+                const float* Mlo = sM[(u + 1) % 3];
+                const float* Mhi = sM[u % 3];
+                const float* Bk = sB[(u + 1) & 1];
+                const float* Xk = sBX[(u + 1) & 1];
+                const float* Yk = sBY[(u + 1) & 1];
+                const float* Zk = sBZ[(u + 2) % 3];
+                const float* Zk1 = sBZ[u % 3];
+                for (int i = tid; i < TX * TY; i += kThreads) {
+                    const int ty = i / TX, tx = i - ty * TX;
+                    const int x = x0 + tx, y = y0 + ty;
+                    if (x >= g.n[0] || y >= g.n[1]) continue;
+                    const int s = (ty + 2) * SW + (tx + 2);
+                    float v = Mk[s];
+                    if (((x + y + k) & 1) == 1) {
+                        const float nb = nb_sum(Xk[s], Mk[s - 1], Xk[s + 1], Mk[s + 1], Yk[s], Mk[s - SW],
+                                                Yk[s + SW], Mk[s + SW], Zk[s], Mlo[s], Zk1[s], Mhi[s]);
+                        const float dg = diag_sum(Xk[s], Xk[s + 1], Yk[s], Yk[s + SW], Zk[s], Zk1[s]);
+                        v = gs_update(v, nb, dg, Bk[s], w);
+                    }
+                    stv(pout, lin(g, x, y, k), v);
+                }
+            }
+        }
+    }
+}
+
+// reference sweep: one colour per launch, in place, one thread per cell
+__global__ void k_sweep_colour(Geo g, const float* __restrict__ bx, const float* __restrict__ by,
+                               const float* __restrict__ bz, const float* __restrict__ b, float* p,
+                               float w, int colour)
+{
+    const int64_t N = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < N;
+         I += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(I % g.n[0]);
+        const int y = (int)((I / g.n[0]) % g.n[1]);
+        const int z = (int)(I / ((int64_t)g.n[0] * g.n[1]));
+        if (((x + y + z) & 1) != colour) continue;
+        auto pv = [&](int xx, int yy, int zz) -> float {
+            if (!wrapc(xx, g.n[0], g.per[0]) || !wrapc(yy, g.n[1], g.per[1]) ||
+                !wrapc(zz, g.n[2], g.per[2]))
+                return 0.f;
+            return p[lin(g, xx, yy, zz)];
+        };
+        const float fxl = face_lo(bx, g, 0, x, y, z), fxu = face_lo(bx, g, 0, x + 1, y, z);
+        const float fyl = face_lo(by, g, 1, x, y, z), fyu = face_lo(by, g, 1, x, y + 1, z);
+        const float fzl = face_lo(bz, g, 2, x, y, z), fzu = face_lo(bz, g, 2, x, y, z + 1);
+        const float nb = nb_sum(fxl, pv(x - 1, y, z), fxu, pv(x + 1, y, z), fyl, pv(x, y - 1, z), fyu,
+                                pv(x, y + 1, z), fzl, pv(x, y, z - 1), fzu, pv(x, y, z + 1));
+        const float dg = diag_sum(fxl, fxu, fyl, fyu, fzl, fzu);
+        p[I] = gs_update(p[I], nb, dg, __ldg(b + I), w);
+    }
+}
+
+// ---------------------------------------------------------------- K2: residual
+
+template <class TP>
+__global__ void __launch_bounds__(kThreads) k_residual(const __grid_constant__ TaskList<ResTask<TP>> tl)
+{
+    __shared__ float sr[kResTZ][kResTY][kResTX];
+    __shared__ double red[kThreads / 32];
+    const int tx = threadIdx.x % kResTX;
+    const int ty = (threadIdx.x / kResTX) % kResTY;
+    const int tz = threadIdx.x / (kResTX * kResTY);
+
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        int local;
+        const ResTask<TP>* tp = task_of(tl, tile, local);
+        if (tp->ctl && tp->ctl->done) continue;
+        const Geo g = tp->g;
+        const int cx = local % tp->tiles_x;
+        const int rest = local / tp->tiles_x;
+        const int cy = rest % tp->tiles_y;
+        const int cz = rest / tp->tiles_y;
+        const int x = cx * kResTX + tx, y = cy * kResTY + ty, z = cz * kResTZ + tz;
+        const int rot = tp->rot ? *tp->rot : 0;
+        const TP* p = tp->role < 0 ? nullptr : tp->buf[(tp->role + rot) % 3];
+        const bool in = x < g.n[0] && y < g.n[1] && z < g.n[2];
+        float r = 0.f;
+        if (in) {
+            auto pv = [&](int xx, int yy, int zz) -> float {
+                if (!p) return 0.f;
+                if (!wrapc(xx, g.n[0], g.per[0]) || !wrapc(yy, g.n[1], g.per[1]) ||
+                    !wrapc(zz, g.n[2], g.per[2]))
+                    return 0.f;
+                return ldv(p, lin(g, xx, yy, zz));
+            };
+            const float fxl = face_lo(tp->bx, g, 0, x, y, z), fxu = face_lo(tp->bx, g, 0, x + 1, y, z);
+            const float fyl = face_lo(tp->by, g, 1, x, y, z), fyu = face_lo(tp->by, g, 1, x, y + 1, z);
+            const float fzl = face_lo(tp->bz, g, 2, x, y, z), fzu = face_lo(tp->bz, g, 2, x, y, z + 1);
+            const float nb = nb_sum(fxl, pv(x - 1, y, z), fxu, pv(x + 1, y, z), fyl, pv(x, y - 1, z),
+                                    fyu, pv(x, y + 1, z), fzl, pv(x, y, z - 1), fzu, pv(x, y, z + 1));
+            const float dg = diag_sum(fxl, fxu, fyl, fyu, fzl, fzu);
+            const float Ap = nb - dg * pv(x, y, z);
+            r = __ldg(tp->b + lin(g, x, y, z)) - Ap;
+        }
+        if (tp->bc) {
+            float v = r;
+            if (tp->cf[0] == 2) v += __shfl_xor_sync(0xffffffffu, v, 1);
+            sr[tz][ty][tx] = v;
+            __syncthreads();
+            if (in && (tx % tp->cf[0]) == 0 && (ty % tp->cf[1]) == 0 && (tz % tp->cf[2]) == 0) {
+                float s = 0.f;
+                for (int dz = 0; dz < tp->cf[2]; ++dz)
+                    for (int dy = 0; dy < tp->cf[1]; ++dy) s += sr[tz + dz][ty + dy][tx];
+                Geo gc = g;
+                gc.n[0] /= tp->cf[0]; gc.n[1] /= tp->cf[1]; gc.n[2] /= tp->cf[2];
+                tp->bc[lin(gc, x / tp->cf[0], y / tp->cf[1], z / tp->cf[2])] = s;
+            }
+            __syncthreads();
+        }
+        if (tp->partials) {
+            const double q = block_sum((double)r * (double)r, red);
+            if (threadIdx.x == 0) tp->partials[local] = q;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- K4: coarsest level
+
+constexpr int kCoarseSmem = 2048;
+static_assert(kCoarseSmem <= kCoarseMaxCells, "coarse capacity");
+
+template <class TP>
+__global__ void __launch_bounds__(kThreads) k_coarse(const CoarseTask<TP>* __restrict__ tasks)
+{
+    __shared__ float sp[kCoarseSmem], sb[kCoarseSmem], sx[kCoarseSmem], sy[kCoarseSmem], sz[kCoarseSmem];
+    __shared__ double red[kThreads / 32];
+    __shared__ double s_mean;
+    const CoarseTask<TP>& T = tasks[blockIdx.x];
+    if (T.ctl && T.ctl->done) return;
+    const Geo g = T.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int N = nx * ny * nz;
+    for (int i = threadIdx.x; i < N; i += kThreads) {
+        const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+        sx[i] = face_lo(T.bx, g, 0, x, y, z);
+        sy[i] = face_lo(T.by, g, 1, x, y, z);
+        sz[i] = face_lo(T.bz, g, 2, x, y, z);
+        sb[i] = T.b[i];
+        sp[i] = 0.f;
+    }
+    __syncthreads();
+    // neighbour index along d in direction s, or -1
+    auto nbi = [&](int x, int y, int z, int d, int s) -> int {
+        int c[3] = {x, y, z};
+        c[d] += s;
+        if (!wrapc(c[d], g.n[d], g.per[d])) return -1;
+        return (c[2] * ny + c[1]) * nx + c[0];
+    };
+    auto upper = [&](const float* a, int x, int y, int z, int d) -> float {
+        const int j = nbi(x, y, z, d, +1);
+        return j < 0 ? 0.f : a[j];
+    };
+    // projection of b to zero mean over active cells
+    double s = 0.0, cnt = 0.0;
+    for (int i = threadIdx.x; i < N; i += kThreads) {
+        const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+        const float dg = diag_sum(sx[i], upper(sx, x, y, z, 0), sy[i], upper(sy, x, y, z, 1), sz[i],
+                                  upper(sz, x, y, z, 2));
+        if (dg > 0.f) {
+            s += (double)sb[i];
+            cnt += 1.0;
+        }
+    }
+    s = block_sum(s, red);
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) s_mean = cnt > 0.0 ? s / cnt : 0.0;
+    __syncthreads();
+    const double mean = s_mean;
+    for (int i = threadIdx.x; i < N; i += kThreads) {
+        const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+        const float dg = diag_sum(sx[i], upper(sx, x, y, z, 0), sy[i], upper(sy, x, y, z, 1), sz[i],
+                                  upper(sz, x, y, z, 2));
+        sb[i] = dg > 0.f ? (float)((double)sb[i] - mean) : 0.f;
+    }
+    __syncthreads();
+    const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
+    for (int it = 0; it < T.nu_c; ++it) {
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int i = threadIdx.x; i < N; i += kThreads) {
+                const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+                if (((x + y + z) & 1) != colour) continue;
+                const int xl = nbi(x, y, z, 0, -1), xu = nbi(x, y, z, 0, +1);
+                const int yl = nbi(x, y, z, 1, -1), yu = nbi(x, y, z, 1, +1);
+                const int zl = nbi(x, y, z, 2, -1), zu = nbi(x, y, z, 2, +1);
+                const float fxu = xu < 0 ? 0.f : sx[xu], fyu = yu < 0 ? 0.f : sy[yu],
+                            fzu = zu < 0 ? 0.f : sz[zu];
+                const float nb = nb_sum(sx[i], xl < 0 ? 0.f : sp[xl], fxu, xu < 0 ? 0.f : sp[xu], sy[i],
+                                        yl < 0 ? 0.f : sp[yl], fyu, yu < 0 ? 0.f : sp[yu], sz[i],
+                                        zl < 0 ? 0.f : sp[zl], fzu, zu < 0 ? 0.f : sp[zu]);
+                const float dg = diag_sum(sx[i], fxu, sy[i], fyu, sz[i], fzu);
+                sp[i] = gs_update(sp[i], nb, dg, sb[i], w);
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < N; i += kThreads) stv(T.out, (int64_t)i, sp[i]);
+}
+
+// ---------------------------------------------------------------- K7 and transfers
+
+__global__ void k_coarsen(Geo f, int c0, int c1, int c2, const float* __restrict__ bx,
+                          const float* __restrict__ by, const float* __restrict__ bz, float* cbx,
+                          float* cby, float* cbz)
+{
+    Geo cg = f;
+    cg.n[0] = f.n[0] / c0; cg.n[1] = f.n[1] / c1; cg.n[2] = f.n[2] / c2;
+    const int cfac[3] = {c0, c1, c2};
+    const float* fa[3] = {bx, by, bz};
+    float* ca[3] = {cbx, cby, cbz};
+    const int64_t N = (int64_t)cg.n[0] * cg.n[1] * cg.n[2];
+    for (int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; J < N;
+         J += (int64_t)gridDim.x * blockDim.x) {
+        const int X = (int)(J % cg.n[0]);
+        const int Y = (int)((J / cg.n[0]) % cg.n[1]);
+        const int Z = (int)(J / ((int64_t)cg.n[0] * cg.n[1]));
+        const int Jc[3] = {X, Y, Z};
+        for (int d = 0; d < 3; ++d) {
+            int lo[3], hi[3];
+            for (int e = 0; e < 3; ++e) {
+                lo[e] = cfac[e] * Jc[e];
+                hi[e] = e == d ? lo[e] + 1 : lo[e] + cfac[e];
+            }
+            float s = 0.f;
+            for (int z = lo[2]; z < hi[2]; ++z)
+                for (int y = lo[1]; y < hi[1]; ++y)
+                    for (int x = lo[0]; x < hi[0]; ++x) s += face_lo(fa[d], f, d, x, y, z);
+            ca[d][J] = s / (float)cfac[d];
+        }
+    }
+}
+
+__global__ void k_prolong_add(Geo f, int c0, int c1, int c2, const float* __restrict__ e, float* p)
+{
+    Geo cg = f;
+    cg.n[0] = f.n[0] / c0; cg.n[1] = f.n[1] / c1; cg.n[2] = f.n[2] / c2;
+    const int64_t N = (int64_t)f.n[0] * f.n[1] * f.n[2];
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < N;
+         I += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(I % f.n[0]);
+        const int y = (int)((I / f.n[0]) % f.n[1]);
+        const int z = (int)(I / ((int64_t)f.n[0] * f.n[1]));
+        p[I] += __ldg(e + lin(cg, x / c0, y / c1, z / c2));
+    }
+}
+
+__global__ void k_active_mask(Geo g, const float* __restrict__ bx, const float* __restrict__ by,
+                              const float* __restrict__ bz, uint8_t* mask)
+{
+    const int64_t N = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < N;
+         I += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(I % g.n[0]);
+        const int y = (int)((I / g.n[0]) % g.n[1]);
+        const int z = (int)(I / ((int64_t)g.n[0] * g.n[1]));
+        const float dg = diag_sum(face_lo(bx, g, 0, x, y, z), face_lo(bx, g, 0, x + 1, y, z),
+                                  face_lo(by, g, 1, x, y, z), face_lo(by, g, 1, x, y + 1, z),
+                                  face_lo(bz, g, 2, x, y, z), face_lo(bz, g, 2, x, y, z + 1));
+        mask[I] = dg > 0.f ? 1 : 0;
+    }
+}
+
+__global__ void k_check_coeffs(int64_t n, const float* __restrict__ bx, const float* __restrict__ by,
+                               const float* __restrict__ bz, int* bad)
+{
+    int local = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float a = bx[i], b = by[i], c = bz[i];
+        if (!(a >= 0.f && a <= 3.0e38f) || !(b >= 0.f && b <= 3.0e38f) || !(c >= 0.f && c <= 3.0e38f))
+            local = 1;
+    }
+    if (__any_sync(0xffffffffu, local) && (threadIdx.x & 31) == 0) atomicAdd(bad, 1);
+}
+
+__global__ void k_sum_partials(const double* __restrict__ part, int n, double* out)
+{
+    __shared__ double red[kThreads / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// ---------------------------------------------------------------- projection and gauge
+
+template <class TS>
+__global__ void __launch_bounds__(kThreads) k_project_sum(const __grid_constant__ TaskList<ProjTask<TS>> tl)
+{
+    __shared__ double red[kThreads / 32];
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        int local;
+        const ProjTask<TS>* t = task_of(tl, tile, local);
+        const int64_t beg = (int64_t)local * kElemTile;
+        const int64_t end = min(t->n, beg + kElemTile);
+        double s = 0.0, c = 0.0, bad = 0.0;
+        for (int64_t i = beg + threadIdx.x; i < end; i += kThreads) {
+            const double v = (double)t->sigma[i];
+            if (!isfinite(v)) bad += 1.0;
+            if (t->mask[i]) {
+                s += v;
+                c += 1.0;
+            }
+        }
+        s = block_sum(s, red);
+        c = block_sum(c, red);
+        bad = block_sum(bad, red);
+        if (threadIdx.x == 0) {
+            t->partials[3 * local + 0] = s;
+            t->partials[3 * local + 1] = c;
+            t->partials[3 * local + 2] = bad;
+        }
+    }
+}
+
+template <class TS>
+__global__ void __launch_bounds__(kThreads) k_project_apply(const __grid_constant__ TaskList<ProjTask<TS>> tl)
+{
+    __shared__ double red[kThreads / 32];
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        int local;
+        const ProjTask<TS>* t = task_of(tl, tile, local);
+        const double mean = t->ctl->mean;
+        const int64_t beg = (int64_t)local * kElemTile;
+        const int64_t end = min(t->n, beg + kElemTile);
+        double q = 0.0;
+        for (int64_t i = beg + threadIdx.x; i < end; i += kThreads) {
+            const bool act = t->mask[i] != 0;
+            const double bv = act ? (double)t->sigma[i] - mean : 0.0;
+            if (t->b32) {
+                const float f = (float)bv;
+                t->b32[i] = f;
+                q += (double)f * (double)f;
+            } else {
+                t->b64[i] = bv;
+                q += bv * bv;
+            }
+            const double pv = (act && t->p_in) ? (double)t->p_in[i] : 0.0;
+            if (t->p32) t->p32[i] = (float)pv;
+            if (t->p64) t->p64[i] = pv;
+        }
+        q = block_sum(q, red);
+        if (threadIdx.x == 0) t->bpartials[local] = q;
+    }
+}
+
+template <class TP, class TD>
+__global__ void __launch_bounds__(kThreads) k_gauge_sum(const __grid_constant__ TaskList<GaugeTask<TP, TD>> tl)
+{
+    __shared__ double red[kThreads / 32];
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        int local;
+        const GaugeTask<TP, TD>* t = task_of(tl, tile, local);
+        const int rot = t->rot ? *t->rot : 0;
+        const TP* p = t->buf[rot % 3];
+        const int64_t beg = (int64_t)local * kElemTile;
+        const int64_t end = min(t->n, beg + kElemTile);
+        double s = 0.0;
+        for (int64_t i = beg + threadIdx.x; i < end; i += kThreads)
+            if (t->mask[i]) s += (double)p[i];
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) t->partials[local] = s;
+    }
+}
+
+template <class TP, class TD>
+__global__ void __launch_bounds__(kThreads) k_gauge_apply(const __grid_constant__ TaskList<GaugeTask<TP, TD>> tl)
+{
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        int local;
+        const GaugeTask<TP, TD>* t = task_of(tl, tile, local);
+        const int rot = t->rot ? *t->rot : 0;
+        const TP* p = t->buf[rot % 3];
+        if (t->ctl->status == kNonFinite) continue;   // the caller's p stays untouched
+        const double mean = t->ctl->mean;
+        const bool zero = t->ctl->zero_out != 0;
+        const int64_t beg = (int64_t)local * kElemTile;
+        const int64_t end = min(t->n, beg + kElemTile);
+        for (int64_t i = beg + threadIdx.x; i < end; i += kThreads) {
+            const double v = (!zero && t->mask[i]) ? (double)p[i] - mean : 0.0;
+            t->dst[i] = (TD)v;
+        }
+    }
+}
+
+// one block per problem: sums in a fixed order
+__device__ double sum_range(const double* part, int n, int stride, int off, double* red)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[(int64_t)i * stride + off];
+    return block_sum(s, red);
+}
+
+__global__ void k_project_finalize(const CtlTask* __restrict__ tasks)
+{
+    __shared__ double red[kThreads / 32];
+    const CtlTask& t = tasks[blockIdx.x];
+    const double s = sum_range(t.ppartials, t.npparts, 3, 0, red);
+    const double c = sum_range(t.ppartials, t.npparts, 3, 1, red);
+    const double bad = sum_range(t.ppartials, t.npparts, 3, 2, red);
+    if (threadIdx.x == 0) {
+        Ctl& C = *t.ctl;
+        C.stat_cnt = c;
+        C.mean = c > 0.0 ? s / c : 0.0;
+        C.nonfinite = bad > 0.0 ? 1 : 0;
+    }
+}
+
+__global__ void k_gauge_finalize(const CtlTask* __restrict__ tasks)
+{
+    __shared__ double red[kThreads / 32];
+    const CtlTask& t = tasks[blockIdx.x];
+    const double s = sum_range(t.ppartials, t.npparts, 1, 0, red);
+    if (threadIdx.x == 0) {
+        Ctl& C = *t.ctl;
+        C.mean = C.stat_cnt > 0.0 ? s / C.stat_cnt : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- K6: control
+
+__global__ void k_control_init(const CtlTask* __restrict__ tasks)
+{
+    __shared__ double red[kThreads / 32];
+    const CtlTask& t = tasks[blockIdx.x];
+    const double bb = sum_range(t.bpartials, t.nbparts, 1, 0, red);
+    const double rr = t.partials ? sum_range(t.partials, t.nparts, 1, 0, red) : bb;
+    if (threadIdx.x == 0) {
+        Ctl& C = *t.ctl;
+        C.bnorm = sqrt(bb);
+        C.cycles = 0;
+        C.total_cycles = 0;
+        C.rot = 0;
+        C.zero_out = 0;
+        C.hist_scale = C.bnorm > 0.0 ? 1.0 / C.bnorm : 0.0;
+        if (C.nonfinite) {
+            C.status = kNonFinite;
+            C.done = 1;
+        } else if (C.bnorm == 0.0) {
+            C.status = kOk;
+            C.zero_out = 1;
+            C.done = 1;
+            if (C.hist_cap >= 0) C.hist_res[0] = 0.0;
+        } else {
+            C.r_prev = sqrt(rr);
+            C.hist_res[0] = C.r_prev / C.bnorm;
+            if (C.r_prev / C.bnorm <= C.tol) {
+                C.status = kOk;
+                C.done = 1;
+            } else {
+                C.status = kRunning;
+                C.done = 0;
+            }
+        }
+    }
+}
+
+// the adaptive relaxation rule after one V-cycle (Sec. 3.1)
+__global__ void k_control_cycle(const CtlTask* __restrict__ tasks)
+{
+    __shared__ double red[kThreads / 32];
+    const CtlTask& t = tasks[blockIdx.x];
+    if (t.ctl->done) return;   // uniform in the block
+    const double rr = sum_range(t.partials, t.nparts, 1, 0, red);
+    if (threadIdx.x == 0) {
+        Ctl& C = *t.ctl;
+        const double rk = sqrt(rr);
+        const double w = C.omega;
+        const bool acc = rk < C.r_prev;     // NaN rejects
+        C.r_last = rk;
+        C.cycles += 1;
+        C.total_cycles += 1;
+        if (acc) {
+            C.rot = (C.rot + C.res_role) % 3;
+            C.r_prev = rk;
+            C.omega = fmin(1.0, C.grow * w);
+        } else if (w <= C.omega_min) {
+            C.status = kDiverged;
+        } else {
+            C.omega = fmax(C.omega_min, C.shrink * w);
+        }
+        const int k = C.total_cycles;
+        if (k <= C.hist_cap) {
+            C.hist_res[k] = C.r_prev * C.hist_scale;
+            C.hist_omega[k - 1] = w;
+            C.hist_acc[k - 1] = acc ? 1 : 0;
+        }
+        if (C.status != kDiverged && C.r_prev / C.bnorm <= C.tol) C.status = kOk;
+        else if (C.status == kRunning && C.cycles >= C.max_cycles) C.status = kNotConverged;
+        if (C.status != kRunning) C.done = 1;
+    }
+}
+
+// ---------------------------------------------------------------- K9: FP64 refinement
+
+__global__ void __launch_bounds__(kThreads) k_ir_residual(const __grid_constant__ IrTask t)
+{
+    __shared__ double red[kThreads / 32];
+    const Geo g = t.g;
+    const int tx = threadIdx.x % kResTX;
+    const int ty = (threadIdx.x / kResTX) % kResTY;
+    const int tz = threadIdx.x / (kResTX * kResTY);
+    const int total = t.tiles_x * t.tiles_y * t.tiles_z;
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int cx = tile % t.tiles_x;
+        const int rest = tile / t.tiles_x;
+        const int cy = rest % t.tiles_y;
+        const int cz = rest / t.tiles_y;
+        const int x = cx * kResTX + tx, y = cy * kResTY + ty, z = cz * kResTZ + tz;
+        double r = 0.0;
+        if (x < g.n[0] && y < g.n[1] && z < g.n[2]) {
+            auto pv = [&](int xx, int yy, int zz) -> double {
+                if (!wrapc(xx, g.n[0], g.per[0]) || !wrapc(yy, g.n[1], g.per[1]) ||
+                    !wrapc(zz, g.n[2], g.per[2]))
+                    return 0.0;
+                return t.p64[lin(g, xx, yy, zz)];
+            };
+            const double fxl = face_lo(t.bx, g, 0, x, y, z), fxu = face_lo(t.bx, g, 0, x + 1, y, z);
+            const double fyl = face_lo(t.by, g, 1, x, y, z), fyu = face_lo(t.by, g, 1, x, y + 1, z);
+            const double fzl = face_lo(t.bz, g, 2, x, y, z), fzu = face_lo(t.bz, g, 2, x, y, z + 1);
+            const double p0 = pv(x, y, z);
+            const double nb = ((fxl * pv(x - 1, y, z) + fxu * pv(x + 1, y, z)) +
+                               (fyl * pv(x, y - 1, z) + fyu * pv(x, y + 1, z))) +
+                              (fzl * pv(x, y, z - 1) + fzu * pv(x, y, z + 1));
+            const double dg = ((fxl + fxu) + (fyl + fyu)) + (fzl + fzu);
+            const int64_t I = lin(g, x, y, z);
+            r = t.b64[I] - (nb - dg * p0);
+            t.b32[I] = (float)r;
+            t.ebuf[0][I] = 0.f;
+        }
+        const double q = block_sum(r * r, red);
+        if (threadIdx.x == 0) t.partials[tile] = q;
+    }
+}
+
+__global__ void k_ir_begin_inner(Ctl* ctl, const double* __restrict__ part, int n, double tol,
+                                 double inner_rtol, int max_cycles)
+{
+    __shared__ double red[kThreads / 32];
+    const double rr = sum_range(part, n, 1, 0, red);
+    if (threadIdx.x == 0) {
+        Ctl& C = *ctl;
+        const double rn = sqrt(rr);
+        const double prev = C.outer_r;
+        C.outer_r = rn;
+        if (C.total_cycles == 0 && C.hist_cap >= 0)
+            C.hist_res[0] = C.outer_bnorm > 0.0 ? rn / C.outer_bnorm : 0.0;
+        if (!(rn == rn)) {
+            C.outer_status = kDiverged;
+            C.done = 1;
+        } else if (rn / C.outer_bnorm <= tol) {
+            C.outer_status = kOk;
+            C.done = 1;
+        } else if (C.total_cycles >= max_cycles) {
+            C.outer_status = kNotConverged;
+            C.done = 1;
+        } else if (C.total_cycles > 0 && !(rn < prev)) {
+            C.outer_status = kNotConverged;   // refinement stopped improving
+            C.done = 1;
+        } else {
+            C.outer_status = kRunning;
+            C.bnorm = rn;                     // inner right-hand side = outer residual
+            C.r_prev = rn;
+            C.tol = fmax(tol * C.outer_bnorm / rn, inner_rtol);
+            C.cycles = 0;
+            C.max_cycles = max_cycles - C.total_cycles;
+            C.rot = 0;
+            C.status = kRunning;
+            C.done = 0;
+            C.hist_scale = 1.0 / C.outer_bnorm;
+        }
+    }
+}
+
+__global__ void k_ir_update(Geo g, double* p64, const float* e0, const float* e1, const float* e2,
+                            const int* rot)
+{
+    const int64_t N = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    const int r = *rot % 3;
+    const float* e = r == 0 ? e0 : (r == 1 ? e1 : e2);
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < N;
+         I += (int64_t)gridDim.x * blockDim.x)
+        p64[I] += (double)e[I];
+}
+
+int grid_for(int64_t n, int per_block = kThreads)
+{
+    int64_t b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+template <class TP, class TC>
+cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaStream_t s)
+{
+    if (tl.total <= 0) return cudaSuccess;
+    k_sweep<TP, TC><<<grid, kThreads, 0, s>>>(tl);
+    return cudaGetLastError();
+}
+template cudaError_t launch_sweep<float, float>(const TaskList<SweepTask<float, float>>&, int, cudaStream_t);
+template cudaError_t launch_sweep<float, bf16>(const TaskList<SweepTask<float, bf16>>&, int, cudaStream_t);
+template cudaError_t launch_sweep<bf16, bf16>(const TaskList<SweepTask<bf16, bf16>>&, int, cudaStream_t);
+
+template <class TP>
+cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStream_t s)
+{
+    if (tl.total <= 0) return cudaSuccess;
+    k_residual<TP><<<grid, kThreads, 0, s>>>(tl);
+    return cudaGetLastError();
+}
+template cudaError_t launch_residual<float>(const TaskList<ResTask<float>>&, int, cudaStream_t);
+template cudaError_t launch_residual<bf16>(const TaskList<ResTask<bf16>>&, int, cudaStream_t);
+
+template <class TP>
+cudaError_t launch_coarse(const CoarseTask<TP>* tasks, int ntasks, cudaStream_t s)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    k_coarse<TP><<<ntasks, kThreads, 0, s>>>(tasks);
+    return cudaGetLastError();
+}
+template cudaError_t launch_coarse<float>(const CoarseTask<float>*, int, cudaStream_t);
+template cudaError_t launch_coarse<bf16>(const CoarseTask<bf16>*, int, cudaStream_t);
+
+cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const float* bz,
+                                  const float* b, float* p, float omega, cudaStream_t s)
+{
+    const int64_t N = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    for (int c = 0; c < 2; ++c) k_sweep_colour<<<grid_for(N), kThreads, 0, s>>>(g, bx, by, bz, b, p, omega, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarsen_coeffs(Geo fine, const int cf[3], const float* bx, const float* by,
+                                  const float* bz, float* cbx, float* cby, float* cbz, cudaStream_t s)
+{
+    const int64_t N = (int64_t)(fine.n[0] / cf[0]) * (fine.n[1] / cf[1]) * (fine.n[2] / cf[2]);
+    k_coarsen<<<grid_for(N), kThreads, 0, s>>>(fine, cf[0], cf[1], cf[2], bx, by, bz, cbx, cby, cbz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(Geo fine, const int cf[3], const float* e, float* p, cudaStream_t s)
+{
+    const int64_t N = (int64_t)fine.n[0] * fine.n[1] * fine.n[2];
+    k_prolong_add<<<grid_for(N), kThreads, 0, s>>>(fine, cf[0], cf[1], cf[2], e, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_active_mask(Geo g, const float* bx, const float* by, const float* bz,
+                               uint8_t* mask, cudaStream_t s)
+{
+    const int64_t N = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    k_active_mask<<<grid_for(N), kThreads, 0, s>>>(g, bx, by, bz, mask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_coeffs(int64_t n, const float* bx, const float* by, const float* bz, int* bad,
+                                cudaStream_t s)
+{
+    k_check_coeffs<<<grid_for(n), kThreads, 0, s>>>(n, bx, by, bz, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double* partials, int n, double* out, cudaStream_t s)
+{
+    k_sum_partials<<<1, kThreads, 0, s>>>(partials, n, out);
+    return cudaGetLastError();
+}
+
+template <class TS>
+cudaError_t launch_project_sum(const TaskList<ProjTask<TS>>& tl, int grid, cudaStream_t s)
+{
+    k_project_sum<TS><<<grid, kThreads, 0, s>>>(tl);
+    return cudaGetLastError();
+}
+template <class TS>
+cudaError_t launch_project_apply(const TaskList<ProjTask<TS>>& tl, int grid, cudaStream_t s)
+{
+    k_project_apply<TS><<<grid, kThreads, 0, s>>>(tl);
+    return cudaGetLastError();
+}
+template cudaError_t launch_project_sum<float>(const TaskList<ProjTask<float>>&, int, cudaStream_t);
+template cudaError_t launch_project_sum<double>(const TaskList<ProjTask<double>>&, int, cudaStream_t);
+template cudaError_t launch_project_apply<float>(const TaskList<ProjTask<float>>&, int, cudaStream_t);
+template cudaError_t launch_project_apply<double>(const TaskList<ProjTask<double>>&, int, cudaStream_t);
+
+cudaError_t launch_project_finalize(const CtlTask* t, int nprob, cudaStream_t s)
+{
+    k_project_finalize<<<nprob, kThreads, 0, s>>>(t);
+    return cudaGetLastError();
+}
+cudaError_t launch_control_init(const CtlTask* t, int nprob, cudaStream_t s)
+{
+    k_control_init<<<nprob, kThreads, 0, s>>>(t);
+    return cudaGetLastError();
+}
+cudaError_t launch_control_cycle(const CtlTask* t, int nprob, cudaStream_t s)
+{
+    k_control_cycle<<<nprob, kThreads, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+template <class TP, class TD>
+cudaError_t launch_gauge_sum(const TaskList<GaugeTask<TP, TD>>& tl, int grid, cudaStream_t s)
+{
+    k_gauge_sum<TP, TD><<<grid, kThreads, 0, s>>>(tl);
+    return cudaGetLastError();
+}
+template <class TP, class TD>
+cudaError_t launch_gauge_apply(const TaskList<GaugeTask<TP, TD>>& tl, int grid, cudaStream_t s)
+{
+    k_gauge_apply<TP, TD><<<grid, kThreads, 0, s>>>(tl);
+    return cudaGetLastError();
+}
+template cudaError_t launch_gauge_sum<float, float>(const TaskList<GaugeTask<float, float>>&, int, cudaStream_t);
+template cudaError_t launch_gauge_sum<double, double>(const TaskList<GaugeTask<double, double>>&, int, cudaStream_t);
+template cudaError_t launch_gauge_apply<float, float>(const TaskList<GaugeTask<float, float>>&, int, cudaStream_t);
+template cudaError_t launch_gauge_apply<double, double>(const TaskList<GaugeTask<double, double>>&, int, cudaStream_t);
+
+cudaError_t launch_gauge_finalize(const CtlTask* t, int nprob, cudaStream_t s)
+{
+    k_gauge_finalize<<<nprob, kThreads, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_residual(const IrTask& t, int grid, cudaStream_t s)
+{
+    k_ir_residual<<<grid, kThreads, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_begin_inner(const IrTask& t, int nparts, double tol, double inner_rtol,
+                                  int max_cycles, cudaStream_t s)
+{
+    k_ir_begin_inner<<<1, kThreads, 0, s>>>(t.ctl, t.partials, nparts, tol, inner_rtol, max_cycles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ir_update(const IrTask& t, cudaStream_t s)
+{
+    const int64_t N = (int64_t)t.g.n[0] * t.g.n[1] * t.g.n[2];
+    k_ir_update<<<grid_for(N), kThreads, 0, s>>>(t.g, t.p64, t.ebuf[0], t.ebuf[1], t.ebuf[2], t.rot);
+    return cudaGetLastError();
+}
+
+}  // namespace gmg

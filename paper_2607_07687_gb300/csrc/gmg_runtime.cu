@@ -1,0 +1,1410 @@
+// gmg_runtime.cu -- host runtime and C ABI of the GB300 multigrid solver.
+//
+// A solve (Sec. 3 of the paper: V-cycles = smoothing + coarse-grid correction;
+// Sec. 3.1: adaptive under-relaxed red-black Gauss-Seidel; Sec. 3.2: iso or
+// anisotropic coarsening) is planned once per handle:
+//   * the coarsening schedule (each axis halves while its length is even and
+//     length/2 >= n_min; a periodic axis also stays even; isotropic mode
+//     halves all axes together while all qualify);
+//   * device buffers of every level and the coefficient hierarchy;
+//   * a fixed list of launches for one V-cycle (sweeps, residual+restriction,
+//     coarsest solve, prolongation folded into the first post-sweep, fine
+//     residual norm, control), recorded once into a CUDA graph.
+// Each V-cycle is one graph replay; the relaxation factor, the accepted-iterate
+// rotation and the done flag live in device memory, so the host only reads an
+// 8-byte-aligned status block every `cycles_per_sync` cycles.
+#include "gmg_internal.h"
+#include "../../include/gmg.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using namespace gmg;
+
+namespace {
+
+constexpr int kSMs = 152;
+constexpr int kResident = 8;    // CTAs per SM targeted by the persistent grids
+
+thread_local std::string g_create_error;
+
+int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+int persistent_grid(int64_t tiles)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)kSMs * kResident));
+}
+
+// ------------------------------------------------------------ schedule (C3)
+
+bool axis_halves(int n, int periodic, int n_min)
+{
+    if (n % 2) return false;
+    if (n / 2 < n_min) return false;
+    if (periodic && (n / 2) % 2) return false;
+    return true;
+}
+
+int plan_levels(const Geo& g0, int aniso, int n_min, Geo* geo, int (*cf)[3])
+{
+    int L = 0;
+    Geo g = g0;
+    for (;;) {
+        geo[L] = g;
+        cf[L][0] = cf[L][1] = cf[L][2] = 1;
+        ++L;
+        if (L >= kMaxLevels) break;
+        bool h[3], any = false, all = true;
+        for (int d = 0; d < 3; ++d) {
+            h[d] = axis_halves(g.n[d], g.per[d], n_min);
+            any |= h[d];
+            all &= h[d];
+        }
+        if (aniso ? !any : !all) break;
+        for (int d = 0; d < 3; ++d) {
+            cf[L - 1][d] = h[d] ? 2 : 1;
+            g.n[d] /= cf[L - 1][d];
+        }
+    }
+    return L;
+}
+
+int64_t cells(const Geo& g) { return (int64_t)g.n[0] * g.n[1] * g.n[2]; }
+
+struct SweepTiling {
+    int tx, ty, zchunk, nchunks;
+    int64_t tiles() const { return (int64_t)tx * ty * nchunks; }
+};
+
+SweepTiling sweep_tiling(const Geo& g)
+{
+    SweepTiling t;
+    t.tx = ceil_div(g.n[0], kSweepTX);
+    t.ty = ceil_div(g.n[1], kSweepTY);
+    const int64_t cols = (int64_t)t.tx * t.ty;
+    const int want = (int)std::max<int64_t>(1, (kSMs * 6 + cols - 1) / cols);
+    const int nc = std::max(1, std::min(want, g.n[2] / 4));
+    t.zchunk = ceil_div(g.n[2], nc);
+    t.nchunks = ceil_div(g.n[2], t.zchunk);
+    return t;
+}
+
+struct ResTiling {
+    int tx, ty, tz;
+    int64_t tiles() const { return (int64_t)tx * ty * tz; }
+};
+
+ResTiling res_tiling(const Geo& g)
+{
+    return {ceil_div(g.n[0], kResTX), ceil_div(g.n[1], kResTY), ceil_div(g.n[2], kResTZ)};
+}
+
+// ------------------------------------------------------------ plan structures
+
+struct LevelMem {
+    Geo g;
+    int cf[3];
+    float* beta[3] = {nullptr, nullptr, nullptr};
+    float* b = nullptr;
+    void* buf[3] = {nullptr, nullptr, nullptr};
+};
+
+struct ProblemMem {
+    Geo g0;
+    int L = 0;
+    LevelMem lev[kMaxLevels];
+    uint8_t* mask = nullptr;
+    int64_t n0 = 0;
+    int elem_tiles = 0;
+    double* norm_part = nullptr;    // fine residual norm partials
+    int norm_tiles = 0;
+    double* proj_part = nullptr;    // 3 per element tile
+    double* bpart = nullptr;        // 1 per element tile
+    double* gauge_part = nullptr;   // 1 per element tile
+    double* b64 = nullptr;          // IR right-hand side
+    double* ir_part = nullptr;
+    Ctl* ctl = nullptr;             // device
+    double* hist_res = nullptr;
+    double* hist_omega = nullptr;
+    int* hist_acc = nullptr;
+};
+
+enum OpKind { kSweepFF, kSweepFB, kSweepBB, kResF, kResB, kCoarseF, kCoarseB, kControl };
+
+struct LaunchOp {
+    OpKind kind;
+    int grid = 1;
+    TaskList<SweepTask<float, float>> s_ff{};
+    TaskList<SweepTask<float, bf16>> s_fb{};
+    TaskList<SweepTask<bf16, bf16>> s_bb{};
+    TaskList<ResTask<float>> r_f{};
+    TaskList<ResTask<bf16>> r_b{};
+    const CoarseTask<float>* c_f = nullptr;
+    const CoarseTask<bf16>* c_b = nullptr;
+    const CtlTask* ctl = nullptr;
+    int n = 0;
+};
+
+struct Engine {
+    std::vector<ProblemMem> P;
+    gmg_options opt{};
+    cudaStream_t stream = nullptr;
+    bool bf16_coarse = false;
+    bool ir = false;
+    int device = 0;
+    std::vector<int> res_role;      // per problem: role of the candidate after a cycle
+    void* stage[2] = {nullptr, nullptr};   // device staging of gmg_solve_host
+    std::vector<void*> allocs;
+    std::vector<LaunchOp> cycle;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    Ctl* ctl_dev = nullptr;         // nprob
+    Ctl* ctl_host = nullptr;        // pinned mirror
+    CtlTask* cycle_ctl = nullptr;   // device: per-cycle control tasks
+    CtlTask* init_ctl = nullptr;    // device: init / projection / gauge tasks
+    CtlTask* gauge_ctl = nullptr;
+    bool coeffs_set = false;
+    std::string err;
+    int last_cycles = 0;
+
+    ~Engine() { release(); }
+
+    void release()
+    {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        graph_exec = nullptr;
+        graph = nullptr;
+        for (void* a : allocs) cudaFree(a);
+        allocs.clear();
+        if (ctl_host) cudaFreeHost(ctl_host);
+        ctl_host = nullptr;
+    }
+
+    int fail(int code, const char* fmt, ...)
+    {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+
+    int cuda_fail(cudaError_t e, const char* what)
+    {
+        return fail(GMG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+
+    template <class T>
+    T* dalloc(size_t count)
+    {
+        void* p = nullptr;
+        if (count == 0) count = 1;
+        if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        return static_cast<T*>(p);
+    }
+
+    template <class T>
+    T* upload(const std::vector<T>& v)
+    {
+        T* d = dalloc<T>(v.size());
+        if (!d) return nullptr;
+        if (cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+            return nullptr;
+        return d;
+    }
+
+    void* level_buf(int p, int l, int role) const { return P[p].lev[l].buf[role]; }
+
+    // ---------------------------------------------------------------- planning
+
+    int plan(int nprob, const int* dims, const int* periodic, const gmg_options& o, cudaStream_t s)
+    {
+        opt = o;
+        stream = s;
+        bf16_coarse = o.precision == GMG_FP32_BF16 || o.precision == GMG_IR64;
+        ir = o.precision == GMG_IR64 || o.precision == GMG_IR64_FP32;
+        cudaGetDevice(&device);
+        P.resize(nprob);
+        int64_t total_norm = 0, total_elem = 0;
+        for (int p = 0; p < nprob; ++p) {
+            ProblemMem& M = P[p];
+            for (int d = 0; d < 3; ++d) {
+                M.g0.n[d] = dims[3 * p + d];
+                M.g0.per[d] = periodic ? (periodic[3 * p + d] != 0) : 0;
+            }
+            Geo geo[kMaxLevels];
+            int cf[kMaxLevels][3];
+            M.L = plan_levels(M.g0, o.coarsen == GMG_COARSEN_ANISO, o.n_min, geo, cf);
+            if (M.L > 1 && cells(geo[M.L - 1]) > 2048)
+                return fail(GMG_ERR_ARG,
+                            "problem %d: coarsest level %dx%dx%d has more than 2048 cells; "
+                            "choose dimensions with more factors of two or a smaller n_min",
+                            p, geo[M.L - 1].n[0], geo[M.L - 1].n[1], geo[M.L - 1].n[2]);
+            M.n0 = cells(M.g0);
+            for (int l = 0; l < M.L; ++l) {
+                LevelMem& Lm = M.lev[l];
+                Lm.g = geo[l];
+                for (int d = 0; d < 3; ++d) Lm.cf[d] = cf[l][d];
+                const int64_t n = cells(geo[l]);
+                for (int d = 0; d < 3; ++d)
+                    if (!(Lm.beta[d] = dalloc<float>(n))) return fail(GMG_ERR_CUDA, "out of device memory");
+                if (!(Lm.b = dalloc<float>(n))) return fail(GMG_ERR_CUDA, "out of device memory");
+                const int nb = l == 0 ? 3 : 2;
+                for (int r = 0; r < nb; ++r) {
+                    void* q = (l > 0 && bf16_coarse) ? (void*)dalloc<bf16>(n) : (void*)dalloc<float>(n);
+                    if (!q) return fail(GMG_ERR_CUDA, "out of device memory");
+                    Lm.buf[r] = q;
+                }
+            }
+            if (!(M.mask = dalloc<uint8_t>(M.n0))) return fail(GMG_ERR_CUDA, "out of device memory");
+            M.norm_tiles = (int)res_tiling(M.g0).tiles();
+            M.elem_tiles = ceil_div(M.n0, kElemTile);
+            total_norm += M.norm_tiles;
+            total_elem += M.elem_tiles;
+            if (ir) {
+                if (!(M.b64 = dalloc<double>(M.n0))) return fail(GMG_ERR_CUDA, "out of device memory");
+                if (!(M.ir_part = dalloc<double>(M.norm_tiles)))
+                    return fail(GMG_ERR_CUDA, "out of device memory");
+            }
+            const int cap = std::max(1, o.max_cycles);
+            M.hist_res = dalloc<double>(cap + 1);
+            M.hist_omega = dalloc<double>(cap);
+            M.hist_acc = dalloc<int>(cap);
+            if (!M.hist_res || !M.hist_omega || !M.hist_acc) return fail(GMG_ERR_CUDA, "out of device memory");
+        }
+        double* norm = dalloc<double>(total_norm);
+        double* proj = dalloc<double>(3 * total_elem);
+        double* bp = dalloc<double>(total_elem);
+        double* gp = dalloc<double>(total_elem);
+        ctl_dev = dalloc<Ctl>(nprob);
+        if (!norm || !proj || !bp || !gp || !ctl_dev) return fail(GMG_ERR_CUDA, "out of device memory");
+        if (cudaMallocHost(&ctl_host, sizeof(Ctl) * nprob) != cudaSuccess)
+            return fail(GMG_ERR_CUDA, "out of pinned host memory");
+        std::memset(ctl_host, 0, sizeof(Ctl) * nprob);
+        int64_t on = 0, oe = 0;
+        for (int p = 0; p < nprob; ++p) {
+            ProblemMem& M = P[p];
+            M.norm_part = norm + on;
+            M.proj_part = proj + 3 * oe;
+            M.bpart = bp + oe;
+            M.gauge_part = gp + oe;
+            M.ctl = ctl_dev + p;
+            on += M.norm_tiles;
+            oe += M.elem_tiles;
+        }
+        std::vector<CtlTask> cyc(nprob), ini(nprob), gau(nprob);
+        for (int p = 0; p < nprob; ++p) {
+            ProblemMem& M = P[p];
+            cyc[p] = CtlTask{M.ctl, M.norm_part, M.norm_tiles, nullptr, 0, nullptr, 0};
+            ini[p] = CtlTask{M.ctl, M.norm_part, M.norm_tiles, M.bpart, M.elem_tiles, M.proj_part, M.elem_tiles};
+            gau[p] = CtlTask{M.ctl, nullptr, 0, nullptr, 0, M.gauge_part, M.elem_tiles};
+        }
+        if (!(cycle_ctl = upload(cyc)) || !(init_ctl = upload(ini)) || !(gauge_ctl = upload(gau)))
+            return fail(GMG_ERR_CUDA, "upload failed");
+        return build_cycle();
+    }
+
+    // device array + prefix of tile counts for a multi-task list
+    template <class Task>
+    int make_list(const std::vector<Task>& tasks, const std::vector<int64_t>& tiles, TaskList<Task>& tl)
+    {
+        tl = TaskList<Task>{};
+        tl.ntasks = (int)tasks.size();
+        int64_t tot = 0;
+        std::vector<int> off(tasks.size() + 1);
+        for (size_t i = 0; i < tasks.size(); ++i) {
+            off[i] = (int)tot;
+            tot += tiles[i];
+        }
+        off[tasks.size()] = (int)tot;
+        tl.total = (int)tot;
+        if (tasks.size() == 1) {
+            tl.tasks = nullptr;
+            tl.tile_off = nullptr;
+            tl.single = tasks[0];
+            return GMG_OK;
+        }
+        tl.tasks = upload(tasks);
+        tl.tile_off = upload(off);
+        if (!tl.tasks || !tl.tile_off) return fail(GMG_ERR_CUDA, "upload failed");
+        return GMG_OK;
+    }
+
+    // role bookkeeping: on level 0 roles {0 accepted, 1, 2} rotate; on coarse
+    // levels physical buffers {0, 1}; -1 = zero input.
+    static int next_out(int level, int in)
+    {
+        if (level == 0) return in == 1 ? 2 : 1;
+        return in == 0 ? 1 : 0;
+    }
+
+    template <class TP, class TC>
+    SweepTask<TP, TC> sweep_task(int p, int l, int in, int out, bool with_corr)
+    {
+        const ProblemMem& M = P[p];
+        const LevelMem& Lm = M.lev[l];
+        SweepTask<TP, TC> t{};
+        t.g = Lm.g;
+        t.bx = Lm.beta[0];
+        t.by = Lm.beta[1];
+        t.bz = Lm.beta[2];
+        t.b = Lm.b;
+        for (int r = 0; r < 3; ++r) t.buf[r] = static_cast<TP*>(Lm.buf[r]);
+        t.rot = l == 0 ? &M.ctl->rot : nullptr;
+        t.in_role = in;
+        t.out_role = out;
+        t.corr = nullptr;
+        t.cf[0] = t.cf[1] = t.cf[2] = 1;
+        if (with_corr) {
+            t.corr = static_cast<const TC*>(M.lev[l + 1].buf[coarse_result_[p][l + 1]]);
+            for (int d = 0; d < 3; ++d) t.cf[d] = Lm.cf[d];
+        }
+        const SweepTiling st = sweep_tiling(Lm.g);
+        t.tiles_x = st.tx;
+        t.tiles_y = st.ty;
+        t.zchunk = st.zchunk;
+        t.nchunks = st.nchunks;
+        t.omega = 1.0f;
+        t.ctl = M.ctl;
+        return t;
+    }
+
+    template <class TP>
+    ResTask<TP> res_task(int p, int l, int role, bool restrict_to_next, double* partials)
+    {
+        const ProblemMem& M = P[p];
+        const LevelMem& Lm = M.lev[l];
+        ResTask<TP> t{};
+        t.g = Lm.g;
+        t.bx = Lm.beta[0];
+        t.by = Lm.beta[1];
+        t.bz = Lm.beta[2];
+        t.b = Lm.b;
+        for (int r = 0; r < 3; ++r) t.buf[r] = static_cast<TP*>(Lm.buf[r]);
+        t.rot = l == 0 ? &M.ctl->rot : nullptr;
+        t.role = role;
+        t.bc = restrict_to_next ? M.lev[l + 1].b : nullptr;
+        for (int d = 0; d < 3; ++d) t.cf[d] = restrict_to_next ? Lm.cf[d] : 1;
+        const ResTiling rt = res_tiling(Lm.g);
+        t.tiles_x = rt.tx;
+        t.tiles_y = rt.ty;
+        t.tiles_z = rt.tz;
+        t.partials = partials;
+        t.ctl = M.ctl;
+        return t;
+    }
+
+    std::vector<std::vector<int>> coarse_result_;   // [p][l] buffer holding the level's result
+
+    int add_sweeps(int l, const std::vector<int>& probs, int in, int out, bool with_corr)
+    {
+        const bool coarse_bf = l > 0 && bf16_coarse;
+        const bool corr_bf = with_corr && bf16_coarse;   // the correction comes from level l+1 >= 1
+        LaunchOp op;
+        std::vector<int64_t> tiles;
+        for (int p : probs) tiles.push_back(sweep_tiling(P[p].lev[l].g).tiles());
+        int rc;
+        if (coarse_bf) {
+            std::vector<SweepTask<bf16, bf16>> v;
+            for (int p : probs) v.push_back(sweep_task<bf16, bf16>(p, l, in, out, with_corr));
+            op.kind = kSweepBB;
+            if ((rc = make_list(v, tiles, op.s_bb))) return rc;
+            op.grid = persistent_grid(op.s_bb.total);
+        } else if (corr_bf) {
+            std::vector<SweepTask<float, bf16>> v;
+            for (int p : probs) v.push_back(sweep_task<float, bf16>(p, l, in, out, with_corr));
+            op.kind = kSweepFB;
+            if ((rc = make_list(v, tiles, op.s_fb))) return rc;
+            op.grid = persistent_grid(op.s_fb.total);
+        } else {
+            std::vector<SweepTask<float, float>> v;
+            for (int p : probs) v.push_back(sweep_task<float, float>(p, l, in, out, with_corr));
+            op.kind = kSweepFF;
+            if ((rc = make_list(v, tiles, op.s_ff))) return rc;
+            op.grid = persistent_grid(op.s_ff.total);
+        }
+        cycle.push_back(op);
+        return GMG_OK;
+    }
+
+    int add_residual(int l, const std::vector<int>& probs, int role, bool restrict_to_next, bool norm)
+    {
+        LaunchOp op;
+        std::vector<int64_t> tiles;
+        for (int p : probs) tiles.push_back(res_tiling(P[p].lev[l].g).tiles());
+        int rc;
+        if (l > 0 && bf16_coarse) {
+            std::vector<ResTask<bf16>> v;
+            for (int p : probs)
+                v.push_back(res_task<bf16>(p, l, role, restrict_to_next, norm ? P[p].norm_part : nullptr));
+            op.kind = kResB;
+            if ((rc = make_list(v, tiles, op.r_b))) return rc;
+            op.grid = persistent_grid(op.r_b.total);
+        } else {
+            std::vector<ResTask<float>> v;
+            for (int p : probs)
+                v.push_back(res_task<float>(p, l, role, restrict_to_next, norm ? P[p].norm_part : nullptr));
+            op.kind = kResF;
+            if ((rc = make_list(v, tiles, op.r_f))) return rc;
+            op.grid = persistent_grid(op.r_f.total);
+        }
+        cycle.push_back(op);
+        return GMG_OK;
+    }
+
+    int build_cycle()
+    {
+        const int nprob = (int)P.size();
+        int Lmax = 0;
+        for (auto& M : P) Lmax = std::max(Lmax, M.L);
+        coarse_result_.assign(nprob, std::vector<int>(kMaxLevels, 0));
+        std::vector<int> pre(kMaxLevels, 0);   // role/buffer of the pre-smoothed iterate per level
+        // descent
+        for (int l = 0; l + 1 < Lmax; ++l) {
+            std::vector<int> probs;
+            for (int p = 0; p < nprob; ++p)
+                if (l < P[p].L - 1) probs.push_back(p);
+            if (probs.empty()) continue;
+            int cur = l == 0 ? 0 : -1;
+            for (int s = 0; s < opt.nu1; ++s) {
+                const int out = next_out(l, cur < 0 ? (l == 0 ? 0 : 1) : cur);
+                int rc = add_sweeps(l, probs, cur, out, false);
+                if (rc) return rc;
+                cur = out;
+            }
+            pre[l] = cur;
+            int rc = add_residual(l, probs, cur, true, false);
+            if (rc) return rc;
+        }
+        // coarsest levels (one CTA per problem); a problem that does not coarsen at
+        // all runs nu_c sweeps on its only level, continuing from the iterate
+        res_role.assign(nprob, 0);
+        {
+            std::vector<CoarseTask<float>> cf;
+            std::vector<CoarseTask<bf16>> cb;
+            std::vector<int> single;
+            for (int p = 0; p < nprob; ++p) {
+                const int l = P[p].L - 1;
+                const LevelMem& Lm = P[p].lev[l];
+                coarse_result_[p][l] = 0;
+                if (l == 0) {
+                    single.push_back(p);
+                } else if (bf16_coarse) {
+                    cb.push_back(CoarseTask<bf16>{Lm.g, Lm.beta[0], Lm.beta[1], Lm.beta[2], Lm.b,
+                                                  static_cast<bf16*>(Lm.buf[0]), opt.nu_c, P[p].ctl});
+                } else {
+                    cf.push_back(CoarseTask<float>{Lm.g, Lm.beta[0], Lm.beta[1], Lm.beta[2], Lm.b,
+                                                   static_cast<float*>(Lm.buf[0]), opt.nu_c, P[p].ctl});
+                }
+            }
+            if (!cf.empty()) {
+                LaunchOp op;
+                op.kind = kCoarseF;
+                op.c_f = upload(cf);
+                op.n = (int)cf.size();
+                if (!op.c_f) return fail(GMG_ERR_CUDA, "upload failed");
+                cycle.push_back(op);
+            }
+            if (!cb.empty()) {
+                LaunchOp op;
+                op.kind = kCoarseB;
+                op.c_b = upload(cb);
+                op.n = (int)cb.size();
+                if (!op.c_b) return fail(GMG_ERR_CUDA, "upload failed");
+                cycle.push_back(op);
+            }
+            if (!single.empty()) {
+                int cur = 0;
+                for (int s = 0; s < opt.nu_c; ++s) {
+                    const int out = next_out(0, cur);
+                    int rc = add_sweeps(0, single, cur, out, false);
+                    if (rc) return rc;
+                    cur = out;
+                }
+                for (int p : single) res_role[p] = cur;
+            }
+        }
+        // ascent
+        for (int l = Lmax - 2; l >= 0; --l) {
+            std::vector<int> probs;
+            for (int p = 0; p < nprob; ++p)
+                if (l < P[p].L - 1) probs.push_back(p);
+            if (probs.empty()) continue;
+            int cur = pre[l];
+            for (int s = 0; s < opt.nu2; ++s) {
+                const int out = next_out(l, cur < 0 ? (l == 0 ? 0 : 1) : cur);
+                int rc = add_sweeps(l, probs, cur, out, s == 0);
+                if (rc) return rc;
+                cur = out;
+            }
+            for (int p : probs) {
+                coarse_result_[p][l] = cur;
+                if (l == 0) res_role[p] = cur;
+            }
+        }
+        // fine residual norm of the candidate, then the control rule
+        {
+            LaunchOp op;
+            std::vector<ResTask<float>> v;
+            std::vector<int64_t> tiles;
+            for (int p = 0; p < nprob; ++p) {
+                v.push_back(res_task<float>(p, 0, res_role[p], false, P[p].norm_part));
+                tiles.push_back(P[p].norm_tiles);
+            }
+            op.kind = kResF;
+            int rc = make_list(v, tiles, op.r_f);
+            if (rc) return rc;
+            op.grid = persistent_grid(op.r_f.total);
+            cycle.push_back(op);
+            LaunchOp c;
+            c.kind = kControl;
+            c.ctl = cycle_ctl;
+            c.n = nprob;
+            cycle.push_back(c);
+        }
+        return GMG_OK;
+    }
+
+    cudaError_t launch(const LaunchOp& op)
+    {
+        switch (op.kind) {
+        case kSweepFF: return launch_sweep(op.s_ff, op.grid, stream);
+        case kSweepFB: return launch_sweep(op.s_fb, op.grid, stream);
+        case kSweepBB: return launch_sweep(op.s_bb, op.grid, stream);
+        case kResF: return launch_residual(op.r_f, op.grid, stream);
+        case kResB: return launch_residual(op.r_b, op.grid, stream);
+        case kCoarseF: return launch_coarse(op.c_f, op.n, stream);
+        case kCoarseB: return launch_coarse(op.c_b, op.n, stream);
+        case kControl: return launch_control_cycle(op.ctl, op.n, stream);
+        }
+        return cudaErrorInvalidValue;
+    }
+
+    cudaError_t run_cycle_eager()
+    {
+        for (const LaunchOp& op : cycle) {
+            cudaError_t e = launch(op);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+
+    cudaError_t ensure_graph()
+    {
+        if (graph_exec) return cudaSuccess;
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaStream_t saved = stream;
+            stream = cap;
+            cudaError_t le = run_cycle_eager();
+            stream = saved;
+            e = cudaStreamEndCapture(cap, &graph);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&graph_exec, graph, 0);
+        cudaStreamDestroy(cap);
+        return e;
+    }
+
+    cudaError_t run_cycle()
+    {
+        if (opt.use_graph) {
+            cudaError_t e = ensure_graph();
+            if (e != cudaSuccess) return e;
+            return cudaGraphLaunch(graph_exec, stream);
+        }
+        return run_cycle_eager();
+    }
+
+    // ---------------------------------------------------------------- coefficients
+
+    int set_coeffs(const float* const* bx, const float* const* by, const float* const* bz)
+    {
+        int* bad = dalloc<int>(1);
+        if (!bad) return fail(GMG_ERR_CUDA, "out of device memory");
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), stream);
+        for (size_t p = 0; p < P.size() && e == cudaSuccess; ++p) {
+            ProblemMem& M = P[p];
+            const size_t bytes = sizeof(float) * (size_t)M.n0;
+            const float* src[3] = {bx[p], by[p], bz[p]};
+            for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+                e = cudaMemcpyAsync(M.lev[0].beta[d], src[d], bytes, cudaMemcpyDeviceToDevice, stream);
+            if (e == cudaSuccess)
+                e = launch_check_coeffs(M.n0, M.lev[0].beta[0], M.lev[0].beta[1], M.lev[0].beta[2], bad, stream);
+            for (int l = 0; l + 1 < M.L && e == cudaSuccess; ++l)
+                e = launch_coarsen_coeffs(M.lev[l].g, M.lev[l].cf, M.lev[l].beta[0], M.lev[l].beta[1],
+                                          M.lev[l].beta[2], M.lev[l + 1].beta[0], M.lev[l + 1].beta[1],
+                                          M.lev[l + 1].beta[2], stream);
+            if (e == cudaSuccess)
+                e = launch_active_mask(M.g0, M.lev[0].beta[0], M.lev[0].beta[1], M.lev[0].beta[2], M.mask, stream);
+        }
+        int hbad = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        cudaFree(bad);
+        allocs.erase(std::find(allocs.begin(), allocs.end(), (void*)bad));
+        if (e != cudaSuccess) return cuda_fail(e, "gmg_set_coeffs");
+        if (hbad) return fail(GMG_ERR_ARG, "face coefficients must be finite and >= 0");
+        coeffs_set = true;
+        return GMG_OK;
+    }
+
+    // ---------------------------------------------------------------- solves
+
+    Ctl initial_ctl(const ProblemMem& M, double tol) const
+    {
+        Ctl c{};
+        c.omega = opt.omega0;
+        c.omega_min = opt.omega_min;
+        c.shrink = opt.shrink;
+        c.grow = opt.grow;
+        c.tol = tol;
+        c.max_cycles = opt.max_cycles;
+        c.res_role = res_role[&M - P.data()];
+        c.status = kRunning;
+        c.done = 0;
+        c.hist_cap = opt.max_cycles;
+        c.hist_res = M.hist_res;
+        c.hist_omega = M.hist_omega;
+        c.hist_acc = M.hist_acc;
+        c.outer_status = kRunning;
+        return c;
+    }
+
+    cudaError_t read_ctl()
+    {
+        cudaError_t e = cudaMemcpyAsync(ctl_host, ctl_dev, sizeof(Ctl) * P.size(), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        return e;
+    }
+
+    bool all_done() const
+    {
+        for (size_t p = 0; p < P.size(); ++p)
+            if (!ctl_host[p].done) return false;
+        return true;
+    }
+
+    // projection of sigma to zero mean over active cells + iterate copy-in
+    template <class TS>
+    cudaError_t project(const TS* const* sigma, const TS* const* p_in, bool to64, TS* const* p64_dst)
+    {
+        std::vector<ProjTask<TS>> v(P.size());
+        std::vector<int64_t> tiles(P.size());
+        for (size_t p = 0; p < P.size(); ++p) {
+            ProblemMem& M = P[p];
+            ProjTask<TS> t{};
+            t.n = M.n0;
+            t.mask = M.mask;
+            t.sigma = sigma[p];
+            t.b32 = to64 ? nullptr : M.lev[0].b;
+            t.b64 = to64 ? M.b64 : nullptr;
+            t.p_in = p_in[p];
+            t.p32 = to64 ? nullptr : static_cast<float*>(M.lev[0].buf[0]);
+            t.p64 = to64 ? reinterpret_cast<double*>(p64_dst[p]) : nullptr;
+            t.partials = M.proj_part;
+            t.bpartials = M.bpart;
+            t.tiles = M.elem_tiles;
+            t.ctl = M.ctl;
+            v[p] = t;
+            tiles[p] = M.elem_tiles;
+        }
+        TaskList<ProjTask<TS>> tl;
+        if (make_list(v, tiles, tl)) return cudaErrorMemoryAllocation;
+        cudaError_t e = launch_project_sum(tl, persistent_grid(tl.total), stream);
+        if (e == cudaSuccess) e = launch_project_finalize(init_ctl, (int)P.size(), stream);
+        if (e == cudaSuccess) e = launch_project_apply(tl, persistent_grid(tl.total), stream);
+        if (tl.tasks) {   // the lists are rebuilt per solve: free them after the launches ran
+            cudaStreamSynchronize(stream);
+            drop(tl.tasks);
+            drop(tl.tile_off);
+        }
+        return e;
+    }
+
+    template <class T>
+    void drop(const T* ptr)
+    {
+        auto it = std::find(allocs.begin(), allocs.end(), (void*)ptr);
+        if (it != allocs.end()) {
+            cudaFree(*it);
+            allocs.erase(it);
+        }
+    }
+
+    template <class TP, class TD>
+    cudaError_t gauge(TD* const* dst, bool fine64)
+    {
+        std::vector<GaugeTask<TP, TD>> v(P.size());
+        std::vector<int64_t> tiles(P.size());
+        for (size_t p = 0; p < P.size(); ++p) {
+            ProblemMem& M = P[p];
+            GaugeTask<TP, TD> t{};
+            t.n = M.n0;
+            t.mask = M.mask;
+            if (fine64) {
+                t.buf[0] = t.buf[1] = t.buf[2] = reinterpret_cast<TP*>(dst[p]);
+                t.rot = nullptr;
+            } else {
+                for (int r = 0; r < 3; ++r) t.buf[r] = static_cast<TP*>(M.lev[0].buf[r]);
+                t.rot = &M.ctl->rot;
+            }
+            t.dst = dst[p];
+            t.partials = M.gauge_part;
+            t.tiles = M.elem_tiles;
+            t.ctl = M.ctl;
+            v[p] = t;
+            tiles[p] = M.elem_tiles;
+        }
+        TaskList<GaugeTask<TP, TD>> tl;
+        if (make_list(v, tiles, tl)) return cudaErrorMemoryAllocation;
+        cudaError_t e = launch_gauge_sum(tl, persistent_grid(tl.total), stream);
+        if (e == cudaSuccess) e = launch_gauge_finalize(gauge_ctl, (int)P.size(), stream);
+        if (e == cudaSuccess) e = launch_gauge_apply(tl, persistent_grid(tl.total), stream);
+        if (tl.tasks) {
+            cudaStreamSynchronize(stream);
+            drop(tl.tasks);
+            drop(tl.tile_off);
+        }
+        return e;
+    }
+
+    // initial residual of the copied-in iterate, then the control init
+    cudaError_t init_control()
+    {
+        std::vector<int> probs(P.size());
+        for (size_t p = 0; p < P.size(); ++p) probs[p] = (int)p;
+        std::vector<ResTask<float>> v;
+        std::vector<int64_t> tiles;
+        for (int p : probs) {
+            v.push_back(res_task<float>(p, 0, 0, false, P[p].norm_part));
+            v.back().ctl = nullptr;   // runs before the done flag is meaningful
+            tiles.push_back(P[p].norm_tiles);
+        }
+        TaskList<ResTask<float>> tl;
+        if (make_list(v, tiles, tl)) return cudaErrorMemoryAllocation;
+        cudaError_t e = launch_residual(tl, persistent_grid(tl.total), stream);
+        if (e == cudaSuccess) e = launch_control_init(init_ctl, (int)P.size(), stream);
+        if (tl.tasks) {
+            cudaStreamSynchronize(stream);
+            drop(tl.tasks);
+            drop(tl.tile_off);
+        }
+        return e;
+    }
+
+    cudaError_t upload_ctl(double tol)
+    {
+        for (size_t p = 0; p < P.size(); ++p) ctl_host[p] = initial_ctl(P[p], tol);
+        return cudaMemcpyAsync(ctl_dev, ctl_host, sizeof(Ctl) * P.size(), cudaMemcpyHostToDevice, stream);
+    }
+
+    // cycles until every problem is done; returns the CUDA status
+    cudaError_t iterate()
+    {
+        const int per_sync = std::max(1, opt.cycles_per_sync);
+        for (int guard = 0; guard <= opt.max_cycles; guard += per_sync) {
+            for (int k = 0; k < per_sync; ++k) {
+                cudaError_t e = run_cycle();
+                if (e != cudaSuccess) return e;
+            }
+            cudaError_t e = read_ctl();
+            if (e != cudaSuccess) return e;
+            if (all_done()) return cudaSuccess;
+        }
+        return read_ctl();
+    }
+
+    int solve32(const float* const* sigma, float* const* p, double tol, gmg_info* infos)
+    {
+        if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_solve");
+        cudaError_t e = upload_ctl(tol);
+        if (e == cudaSuccess) e = project<float>(sigma, (const float* const*)p, false, nullptr);
+        if (e == cudaSuccess) e = init_control();
+        if (e == cudaSuccess) e = read_ctl();
+        if (e == cudaSuccess && !all_done()) e = iterate();
+        if (e != cudaSuccess) return cuda_fail(e, "gmg_solve");
+        // gauge into the caller arrays (skipped for problems with a non-finite source)
+        bool any_finite = false;
+        for (size_t q = 0; q < P.size(); ++q) any_finite |= ctl_host[q].status != kNonFinite;
+        if (any_finite) {
+            std::vector<float*> dst(P.size());
+            for (size_t q = 0; q < P.size(); ++q) dst[q] = p[q];
+            e = gauge<float, float>(dst.data(), false);
+            if (e == cudaSuccess) e = read_ctl();
+            if (e != cudaSuccess) return cuda_fail(e, "gmg_solve (gauge)");
+        }
+        int worst = GMG_OK;
+        for (size_t q = 0; q < P.size(); ++q) {
+            const Ctl& c = ctl_host[q];
+            const int st = c.status == kRunning ? kNotConverged : c.status;
+            if (infos) {
+                gmg_info& inf = infos[q];
+                inf.cycles = c.cycles;
+                inf.status = st;
+                inf.levels = P[q].L;
+                inf.outer = 0;
+                inf.rel_res = c.bnorm > 0.0 ? c.r_prev / c.bnorm : 0.0;
+                inf.omega = c.omega;
+                inf.bnorm = c.bnorm;
+            }
+            if (worst == GMG_OK && st != GMG_OK) worst = st;
+        }
+        last_cycles = ctl_host[0].total_cycles;
+        return worst;
+    }
+
+    int solve64(const double* sigma, double* p, double tol, gmg_info* info)
+    {
+        if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_solve");
+        ProblemMem& M = P[0];
+        cudaError_t e = upload_ctl(tol);
+        const double* sg[1] = {sigma};
+        const double* pi[1] = {p};
+        double* pd[1] = {p};
+        if (e == cudaSuccess) e = project<double>(sg, pi, true, pd);
+        // |b64| -> bnorm (partials = nullptr: the residual equals b here)
+        if (e == cudaSuccess) {
+            CtlTask t{M.ctl, nullptr, 0, M.bpart, M.elem_tiles, M.proj_part, M.elem_tiles};
+            std::vector<CtlTask> tv{t};
+            CtlTask* d = upload(tv);
+            if (!d) return fail(GMG_ERR_CUDA, "upload failed");
+            e = launch_control_init(d, 1, stream);
+            if (e == cudaSuccess) e = read_ctl();
+            drop(d);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "gmg_solve");
+        Ctl& c = ctl_host[0];
+        int outer = 0;
+        int status = c.status;
+        if (!c.done) {
+            // the outer |b| lives in outer_bnorm
+            c.outer_bnorm = c.bnorm;
+            c.outer_r = 0.0;
+            e = cudaMemcpyAsync(M.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, stream);
+            IrTask t{};
+            t.g = M.g0;
+            t.bx = M.lev[0].beta[0];
+            t.by = M.lev[0].beta[1];
+            t.bz = M.lev[0].beta[2];
+            t.b64 = M.b64;
+            t.p64 = p;
+            t.b32 = M.lev[0].b;
+            for (int r = 0; r < 3; ++r) t.ebuf[r] = static_cast<float*>(M.lev[0].buf[r]);
+            t.rot = &M.ctl->rot;
+            t.partials = M.ir_part;
+            const ResTiling rt = res_tiling(M.g0);
+            t.tiles_x = rt.tx;
+            t.tiles_y = rt.ty;
+            t.tiles_z = rt.tz;
+            t.ctl = M.ctl;
+            t.scale = nullptr;
+            status = kRunning;
+            for (;;) {
+                if (e == cudaSuccess) e = launch_ir_residual(t, persistent_grid(rt.tiles()), stream);
+                if (e == cudaSuccess)
+                    e = launch_ir_begin_inner(t, (int)rt.tiles(), tol, opt.ir_inner_rtol, opt.max_cycles, stream);
+                if (e == cudaSuccess) e = read_ctl();
+                if (e != cudaSuccess) break;
+                if (c.done) {
+                    status = c.outer_status;
+                    break;
+                }
+                ++outer;
+                e = iterate();
+                if (e == cudaSuccess) e = launch_ir_update(t, stream);
+                if (e == cudaSuccess) e = read_ctl();
+                if (e != cudaSuccess) break;
+                if (c.status == kDiverged) {
+                    // keep the refinement so far and report the inner divergence
+                    e = launch_ir_residual(t, persistent_grid(rt.tiles()), stream);
+                    if (e == cudaSuccess)
+                        e = launch_ir_begin_inner(t, (int)rt.tiles(), tol, opt.ir_inner_rtol, opt.max_cycles, stream);
+                    if (e == cudaSuccess) e = read_ctl();
+                    status = c.outer_status == kOk ? kOk : kDiverged;
+                    break;
+                }
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "gmg_solve (refinement)");
+        }
+        if (status != kNonFinite) {
+            double* dst[1] = {p};
+            e = gauge<double, double>(dst, true);
+            if (e == cudaSuccess) e = read_ctl();
+            if (e != cudaSuccess) return cuda_fail(e, "gmg_solve (gauge)");
+        }
+        const int st = status == kRunning ? kNotConverged : status;
+        if (info) {
+            info->cycles = c.total_cycles;
+            info->status = st;
+            info->levels = M.L;
+            info->outer = outer;
+            info->rel_res = c.outer_bnorm > 0.0 ? c.outer_r / c.outer_bnorm : 0.0;
+            info->omega = c.omega;
+            info->bnorm = c.outer_bnorm;
+        }
+        last_cycles = c.total_cycles;
+        return st;
+    }
+};
+
+std::mutex g_op_mutex;
+struct OpScratch {
+    int device = -1;
+    double* part = nullptr;
+    int cap = 0;
+    double* out = nullptr;
+};
+std::vector<OpScratch> g_op_scratch;
+
+int validate_geometry(int nx, int ny, int nz, const int* periodic, std::string& msg)
+{
+    if (nx < 1 || ny < 1 || nz < 1) {
+        msg = "every dimension must be >= 1";
+        return GMG_ERR_ARG;
+    }
+    if ((int64_t)nx * ny * nz > ((int64_t)1 << 31) - 1) {
+        msg = "grids above 2^31 cells are not supported";
+        return GMG_ERR_ARG;
+    }
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d)
+        if (periodic && periodic[d] && n[d] % 2) {
+            msg = "a periodic axis must have even length (red-black colouring)";
+            return GMG_ERR_ARG;
+        }
+    return GMG_OK;
+}
+
+int validate_options(const gmg_options& o, std::string& msg)
+{
+    if (o.coarsen != GMG_COARSEN_ISO && o.coarsen != GMG_COARSEN_ANISO) msg = "coarsen must be ISO or ANISO";
+    else if (o.n_min < 1) msg = "n_min must be >= 1";
+    else if (o.nu1 < 0 || o.nu2 < 1 || o.nu_c < 1) msg = "need nu1 >= 0, nu2 >= 1, nu_c >= 1";
+    else if (o.precision < GMG_FP32 || o.precision > GMG_IR64_FP32) msg = "unknown precision";
+    else if (o.max_cycles < 1) msg = "max_cycles must be >= 1";
+    else if (!(o.omega0 > 0.0) || !(o.omega_min > 0.0) || !(o.shrink > 0.0 && o.shrink < 1.0) || !(o.grow >= 1.0))
+        msg = "need omega0 > 0, omega_min > 0, 0 < shrink < 1, grow >= 1";
+    else if (!(o.ir_inner_rtol > 0.0 && o.ir_inner_rtol < 1.0)) msg = "need 0 < ir_inner_rtol < 1";
+    else return GMG_OK;
+    return GMG_ERR_ARG;
+}
+
+}  // namespace
+
+struct gmg_solver {
+    Engine eng;
+};
+struct gmg_batch_solver {
+    Engine eng;
+};
+
+extern "C" {
+
+void gmg_default_options(gmg_options* o)
+{
+    if (!o) return;
+    o->coarsen = GMG_COARSEN_ANISO;
+    o->n_min = 4;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->nu_c = 16;
+    o->precision = GMG_FP32;
+    o->max_cycles = 100;
+    o->omega0 = 1.0;
+    o->omega_min = 0.25;
+    o->shrink = 0.7;
+    o->grow = 1.1;
+    o->use_graph = 1;
+    o->cycles_per_sync = 4;
+    o->ir_inner_rtol = 1e-4;
+}
+
+int gmg_create(gmg_handle* h, int nx, int ny, int nz, const int* periodic, const gmg_options* opt,
+               void* stream)
+{
+    if (!h) {
+        g_create_error = "h is NULL";
+        return GMG_ERR_ARG;
+    }
+    *h = nullptr;
+    gmg_options o;
+    gmg_default_options(&o);
+    if (opt) o = *opt;
+    int rc = validate_geometry(nx, ny, nz, periodic, g_create_error);
+    if (rc == GMG_OK) rc = validate_options(o, g_create_error);
+    if (rc != GMG_OK) return rc;
+    gmg_solver* s = new gmg_solver;
+    const int dims[3] = {nx, ny, nz};
+    int per[3] = {0, 0, 0};
+    if (periodic)
+        for (int d = 0; d < 3; ++d) per[d] = periodic[d] != 0;
+    rc = s->eng.plan(1, dims, per, o, static_cast<cudaStream_t>(stream));
+    if (rc != GMG_OK) {
+        g_create_error = s->eng.err;
+        delete s;
+        return rc;
+    }
+    *h = s;
+    return GMG_OK;
+}
+
+int gmg_set_coeffs(gmg_handle h, const float* bx, const float* by, const float* bz)
+{
+    if (!h) return GMG_ERR_ARG;
+    if (!bx || !by || !bz) return h->eng.fail(GMG_ERR_ARG, "null coefficient pointer");
+    const float* x[1] = {bx};
+    const float* y[1] = {by};
+    const float* z[1] = {bz};
+    return h->eng.set_coeffs(x, y, z);
+}
+
+int gmg_solve(gmg_handle h, const void* sigma, void* p, double tol, gmg_info* info)
+{
+    if (!h) return GMG_ERR_ARG;
+    Engine& E = h->eng;
+    if (!sigma || !p) return E.fail(GMG_ERR_ARG, "null sigma or p");
+    if (!(tol > 0.0)) return E.fail(GMG_ERR_ARG, "tol must be > 0");
+    if (E.ir) return E.solve64(static_cast<const double*>(sigma), static_cast<double*>(p), tol, info);
+    const float* s[1] = {static_cast<const float*>(sigma)};
+    float* q[1] = {static_cast<float*>(p)};
+    return E.solve32(s, q, tol, info);
+}
+
+int gmg_solve_host(gmg_handle h, const void* sigma_host, void* p_host, double tol, gmg_info* info)
+{
+    if (!h) return GMG_ERR_ARG;
+    Engine& E = h->eng;
+    if (!sigma_host || !p_host) return E.fail(GMG_ERR_ARG, "null sigma or p");
+    const size_t bytes = (size_t)E.P[0].n0 * (E.ir ? sizeof(double) : sizeof(float));
+    // staging buffers: allocated on the first call, kept with the handle
+    for (int i = 0; i < 2; ++i)
+        if (!E.stage[i] && !(E.stage[i] = E.dalloc<char>(bytes))) return E.fail(GMG_ERR_CUDA, "out of device memory");
+    void* ds = E.stage[0];
+    void* dp = E.stage[1];
+    cudaError_t e = cudaMemcpyAsync(ds, sigma_host, bytes, cudaMemcpyHostToDevice, E.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, p_host, bytes, cudaMemcpyHostToDevice, E.stream);
+    int rc = GMG_ERR_CUDA;
+    if (e == cudaSuccess) {
+        rc = gmg_solve(h, ds, dp, tol, info);
+        if (rc == GMG_OK || rc == GMG_ERR_NOT_CONVERGED || rc == GMG_ERR_DIVERGED) {
+            e = cudaMemcpyAsync(p_host, dp, bytes, cudaMemcpyDeviceToHost, E.stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(E.stream);
+            if (e != cudaSuccess) rc = E.cuda_fail(e, "gmg_solve_host (copy back)");
+        }
+    } else {
+        rc = E.cuda_fail(e, "gmg_solve_host");
+    }
+    if (ds) cudaFreeAsync(ds, E.stream);
+    if (dp) cudaFreeAsync(dp, E.stream);
+    cudaStreamSynchronize(E.stream);
+    return rc;
+}
+
+int gmg_history(gmg_handle h, double* rel_res, double* omega, int* accepted, int cap)
+{
+    if (!h || cap < 0) return -1;
+    Engine& E = h->eng;
+    const int n = std::min(cap, E.last_cycles);
+    const ProblemMem& M = E.P[0];
+    cudaError_t e = cudaSuccess;
+    if (rel_res) e = cudaMemcpy(rel_res, M.hist_res, sizeof(double) * (n + 1), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && omega && n) e = cudaMemcpy(omega, M.hist_omega, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && accepted && n) e = cudaMemcpy(accepted, M.hist_acc, sizeof(int) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        E.cuda_fail(e, "gmg_history");
+        return -1;
+    }
+    return n;
+}
+
+int gmg_levels(gmg_handle h, int* dims)
+{
+    if (!h) return -1;
+    const ProblemMem& M = h->eng.P[0];
+    if (dims)
+        for (int l = 0; l < M.L; ++l)
+            for (int d = 0; d < 3; ++d) dims[3 * l + d] = M.lev[l].g.n[d];
+    return M.L;
+}
+
+int gmg_destroy(gmg_handle h)
+{
+    delete h;
+    return GMG_OK;
+}
+
+const char* gmg_last_error(gmg_handle h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->eng.err.c_str();
+}
+
+// ---------------------------------------------------------------- batch
+
+int gmg_batch_create(gmg_batch* b, int nprob, const int* dims, const int* periodic,
+                     const gmg_options* opt, void* stream)
+{
+    if (!b || nprob < 1 || !dims) {
+        g_create_error = "need b, nprob >= 1 and dims";
+        return GMG_ERR_ARG;
+    }
+    *b = nullptr;
+    gmg_options o;
+    gmg_default_options(&o);
+    if (opt) o = *opt;
+    int rc = validate_options(o, g_create_error);
+    if (rc != GMG_OK) return rc;
+    if (o.precision != GMG_FP32 && o.precision != GMG_FP32_BF16) {
+        g_create_error = "batched solves support GMG_FP32 and GMG_FP32_BF16";
+        return GMG_ERR_ARG;
+    }
+    for (int p = 0; p < nprob; ++p) {
+        rc = validate_geometry(dims[3 * p], dims[3 * p + 1], dims[3 * p + 2], periodic ? periodic + 3 * p : nullptr,
+                               g_create_error);
+        if (rc != GMG_OK) return rc;
+    }
+    gmg_batch_solver* s = new gmg_batch_solver;
+    rc = s->eng.plan(nprob, dims, periodic, o, static_cast<cudaStream_t>(stream));
+    if (rc != GMG_OK) {
+        g_create_error = s->eng.err;
+        delete s;
+        return rc;
+    }
+    *b = s;
+    return GMG_OK;
+}
+
+int gmg_batch_set_coeffs(gmg_batch b, const float* const* bx, const float* const* by, const float* const* bz)
+{
+    if (!b) return GMG_ERR_ARG;
+    if (!bx || !by || !bz) return b->eng.fail(GMG_ERR_ARG, "null coefficient array");
+    for (size_t p = 0; p < b->eng.P.size(); ++p)
+        if (!bx[p] || !by[p] || !bz[p]) return b->eng.fail(GMG_ERR_ARG, "null coefficient pointer (problem %zu)", p);
+    return b->eng.set_coeffs(bx, by, bz);
+}
+
+int gmg_batch_solve(gmg_batch b, const float* const* sigma, float* const* p, double tol, gmg_info* infos)
+{
+    if (!b) return GMG_ERR_ARG;
+    if (!sigma || !p) return b->eng.fail(GMG_ERR_ARG, "null sigma or p array");
+    if (!(tol > 0.0)) return b->eng.fail(GMG_ERR_ARG, "tol must be > 0");
+    for (size_t q = 0; q < b->eng.P.size(); ++q)
+        if (!sigma[q] || !p[q]) return b->eng.fail(GMG_ERR_ARG, "null sigma or p (problem %zu)", q);
+    return b->eng.solve32(sigma, p, tol, infos);
+}
+
+int gmg_batch_destroy(gmg_batch b)
+{
+    delete b;
+    return GMG_OK;
+}
+
+const char* gmg_batch_last_error(gmg_batch b)
+{
+    if (!b) return g_create_error.c_str();
+    return b->eng.err.c_str();
+}
+
+// ---------------------------------------------------------------- single steps
+
+static Geo make_geo(int nx, int ny, int nz, const int* periodic)
+{
+    Geo g;
+    g.n[0] = nx;
+    g.n[1] = ny;
+    g.n[2] = nz;
+    for (int d = 0; d < 3; ++d) g.per[d] = periodic ? (periodic[d] != 0) : 0;
+    return g;
+}
+
+static int check_factors(int nx, int ny, int nz, const int* f)
+{
+    if (!f) return GMG_ERR_ARG;
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+        if (f[d] != 1 && f[d] != 2) return GMG_ERR_ARG;
+        if (n[d] % f[d]) return GMG_ERR_ARG;
+    }
+    return GMG_OK;
+}
+
+int gmg_op_sweep(int nx, int ny, int nz, const int* periodic, const float* bx, const float* by,
+                 const float* bz, const float* b, const float* p_in, float* p_out, double omega,
+                 void* stream)
+{
+    std::string msg;
+    if (validate_geometry(nx, ny, nz, periodic, msg) != GMG_OK) return GMG_ERR_ARG;
+    if (!bx || !by || !bz || !b || !p_in || !p_out || p_in == p_out) return GMG_ERR_ARG;
+    SweepTask<float, float> t{};
+    t.g = make_geo(nx, ny, nz, periodic);
+    t.bx = bx;
+    t.by = by;
+    t.bz = bz;
+    t.b = b;
+    t.buf[0] = const_cast<float*>(p_in);
+    t.buf[1] = p_out;
+    t.buf[2] = p_out;
+    t.rot = nullptr;
+    t.in_role = 0;
+    t.out_role = 1;
+    t.corr = nullptr;
+    t.cf[0] = t.cf[1] = t.cf[2] = 1;
+    const SweepTiling st = sweep_tiling(t.g);
+    t.tiles_x = st.tx;
+    t.tiles_y = st.ty;
+    t.zchunk = st.zchunk;
+    t.nchunks = st.nchunks;
+    t.omega = (float)omega;
+    t.ctl = nullptr;
+    TaskList<SweepTask<float, float>> tl{};
+    tl.ntasks = 1;
+    tl.total = (int)st.tiles();
+    tl.single = t;
+    return launch_sweep(tl, persistent_grid(tl.total), static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? GMG_OK
+               : GMG_ERR_CUDA;
+}
+
+int gmg_op_sweep_reference(int nx, int ny, int nz, const int* periodic, const float* bx,
+                           const float* by, const float* bz, const float* b, float* p, double omega,
+                           void* stream)
+{
+    std::string msg;
+    if (validate_geometry(nx, ny, nz, periodic, msg) != GMG_OK) return GMG_ERR_ARG;
+    if (!bx || !by || !bz || !b || !p) return GMG_ERR_ARG;
+    return launch_sweep_two_pass(make_geo(nx, ny, nz, periodic), bx, by, bz, b, p, (float)omega,
+                                 static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? GMG_OK
+               : GMG_ERR_CUDA;
+}
+
+static int op_scratch(int ntiles, double** part, double** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GMG_ERR_CUDA;
+    for (auto& s : g_op_scratch)
+        if (s.device == dev) {
+            if (s.cap < ntiles) {
+                cudaFree(s.part);
+                s.part = nullptr;
+                if (cudaMalloc(&s.part, sizeof(double) * ntiles) != cudaSuccess) {
+                    s.cap = 0;
+                    return GMG_ERR_CUDA;
+                }
+                s.cap = ntiles;
+            }
+            *part = s.part;
+            *out = s.out;
+            return GMG_OK;
+        }
+    OpScratch s;
+    s.device = dev;
+    if (cudaMalloc(&s.part, sizeof(double) * ntiles) != cudaSuccess) return GMG_ERR_CUDA;
+    if (cudaMalloc(&s.out, sizeof(double)) != cudaSuccess) return GMG_ERR_CUDA;
+    s.cap = ntiles;
+    g_op_scratch.push_back(s);
+    *part = s.part;
+    *out = s.out;
+    return GMG_OK;
+}
+
+static int op_residual(int nx, int ny, int nz, const int* periodic, const int* factors, const float* bx,
+                       const float* by, const float* bz, const float* b, const float* p, float* b_coarse,
+                       double* rr, void* stream)
+{
+    std::string msg;
+    if (validate_geometry(nx, ny, nz, periodic, msg) != GMG_OK) return GMG_ERR_ARG;
+    if (!bx || !by || !bz || !b || !p) return GMG_ERR_ARG;
+    if (b_coarse && check_factors(nx, ny, nz, factors) != GMG_OK) return GMG_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ResTask<float> t{};
+    t.g = make_geo(nx, ny, nz, periodic);
+    t.bx = bx;
+    t.by = by;
+    t.bz = bz;
+    t.b = b;
+    t.buf[0] = t.buf[1] = t.buf[2] = const_cast<float*>(p);
+    t.rot = nullptr;
+    t.role = 0;
+    t.bc = b_coarse;
+    for (int d = 0; d < 3; ++d) t.cf[d] = b_coarse ? factors[d] : 1;
+    const ResTiling rt = res_tiling(t.g);
+    t.tiles_x = rt.tx;
+    t.tiles_y = rt.ty;
+    t.tiles_z = rt.tz;
+    t.ctl = nullptr;
+    std::unique_lock<std::mutex> lock(g_op_mutex, std::defer_lock);
+    double* out = nullptr;
+    if (rr) {
+        lock.lock();
+        if (op_scratch((int)rt.tiles(), &t.partials, &out) != GMG_OK) return GMG_ERR_CUDA;
+    }
+    TaskList<ResTask<float>> tl{};
+    tl.ntasks = 1;
+    tl.total = (int)rt.tiles();
+    tl.single = t;
+    cudaError_t e = launch_residual(tl, persistent_grid(tl.total), s);
+    if (e == cudaSuccess && rr) {
+        e = launch_sum_partials(t.partials, (int)rt.tiles(), out, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rr, out, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
+int gmg_op_residual_restrict(int nx, int ny, int nz, const int* periodic, const int* factors,
+                             const float* bx, const float* by, const float* bz, const float* b,
+                             const float* p, float* b_coarse, double* rr, void* stream)
+{
+    if (!b_coarse) return GMG_ERR_ARG;
+    return op_residual(nx, ny, nz, periodic, factors, bx, by, bz, b, p, b_coarse, rr, stream);
+}
+
+int gmg_op_residual_norm(int nx, int ny, int nz, const int* periodic, const float* bx,
+                         const float* by, const float* bz, const float* b, const float* p,
+                         double* rr, void* stream)
+{
+    if (!rr) return GMG_ERR_ARG;
+    return op_residual(nx, ny, nz, periodic, nullptr, bx, by, bz, b, p, nullptr, rr, stream);
+}
+
+int gmg_op_prolong_add(int nx, int ny, int nz, const int* factors, const float* e, float* p, void* stream)
+{
+    std::string msg;
+    if (validate_geometry(nx, ny, nz, nullptr, msg) != GMG_OK) return GMG_ERR_ARG;
+    if (!e || !p || check_factors(nx, ny, nz, factors) != GMG_OK) return GMG_ERR_ARG;
+    Geo g = make_geo(nx, ny, nz, nullptr);
+    return launch_prolong_add(g, factors, e, p, static_cast<cudaStream_t>(stream)) == cudaSuccess ? GMG_OK
+                                                                                                   : GMG_ERR_CUDA;
+}
+
+int gmg_op_coarsen_coeffs(int nx, int ny, int nz, const int* periodic, const int* factors,
+                          const float* bx, const float* by, const float* bz, float* cbx,
+                          float* cby, float* cbz, void* stream)
+{
+    std::string msg;
+    if (validate_geometry(nx, ny, nz, periodic, msg) != GMG_OK) return GMG_ERR_ARG;
+    if (!bx || !by || !bz || !cbx || !cby || !cbz || check_factors(nx, ny, nz, factors) != GMG_OK)
+        return GMG_ERR_ARG;
+    Geo g = make_geo(nx, ny, nz, periodic);
+    return launch_coarsen_coeffs(g, factors, bx, by, bz, cbx, cby, cbz, static_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? GMG_OK
+               : GMG_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+that include/gmg.h declares, and rejects bad arguments before touching CUDA."""
+import ctypes
+
+import pytest
+
+from paper_2607_07687_gb300 import binding as G
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2607_07687_gb300 import build
+    build.build()
+    return G.lib()
+
+
+def test_exports_every_declared_function(L):
+    names = G.declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(L, n), n
+    for core in ("gmg_create", "gmg_set_coeffs", "gmg_solve", "gmg_destroy", "gmg_batch_create",
+                 "gmg_batch_set_coeffs", "gmg_batch_solve", "gmg_last_error"):
+        assert core in names
+
+
+def test_default_options(L):
+    o = G.options()
+    assert (o.nu1, o.nu2, o.nu_c, o.n_min, o.coarsen) == (2, 2, 16, 4, G.ANISO)
+    assert (o.omega0, o.omega_min, o.shrink, o.grow) == (1.0, 0.25, 0.7, 1.1)
+
+
+def _create(L, dims, periodic=(0, 0, 0), **kw):
+    h = ctypes.c_void_p()
+    o = G.options(**kw)
+    rc = L.gmg_create(ctypes.byref(h), *dims, G._ivec(periodic), ctypes.byref(o), None)
+    return rc, L.gmg_last_error(None).decode()
+
+
+@pytest.mark.parametrize("dims,periodic,kw,frag", [
+    ((0, 8, 8), (0, 0, 0), {}, "dimension"),
+    ((8, -1, 8), (0, 0, 0), {}, "dimension"),
+    ((9, 8, 8), (1, 0, 0), {}, "periodic"),
+    ((8, 8, 8), (0, 0, 0), {"nu2": 0}, "nu2"),
+    ((8, 8, 8), (0, 0, 0), {"nu_c": 0}, "nu_c"),
+    ((8, 8, 8), (0, 0, 0), {"max_cycles": 0}, "max_cycles"),
+    ((8, 8, 8), (0, 0, 0), {"shrink": 1.5}, "shrink"),
+    ((8, 8, 8), (0, 0, 0), {"n_min": 0}, "n_min"),
+    ((8, 8, 8), (0, 0, 0), {"ir_inner_rtol": 0.0}, "ir_inner_rtol"),
+])
+def test_create_rejects(L, dims, periodic, kw, frag):
+    rc, msg = _create(L, dims, periodic, **kw)
+    assert rc == G.ERR_ARG
+    assert frag in msg
+
+
+def test_create_null_handle(L):
+    o = G.options()
+    assert L.gmg_create(None, 8, 8, 8, None, ctypes.byref(o), None) == G.ERR_ARG
+
+
+def test_batch_create_rejects(L):
+    b = ctypes.c_void_p()
+    dims = G._ivec([8, 8, 8])
+    o = G.options()
+    assert L.gmg_batch_create(ctypes.byref(b), 0, dims, None, ctypes.byref(o), None) == G.ERR_ARG
+    o = G.options(precision="ir64")
+    assert L.gmg_batch_create(ctypes.byref(b), 1, dims, None, ctypes.byref(o), None) == G.ERR_ARG
+    assert "batched" in L.gmg_batch_last_error(None).decode()
+
+
+def test_ops_reject_bad_arguments(L):
+    fake = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    per = G._ivec((0, 0, 0))
+    # p_in aliasing p_out
+    assert L.gmg_op_sweep(8, 8, 8, per, fake, fake, fake, fake, fake, fake, 1.0, None) == G.ERR_ARG
+    # null input
+    assert L.gmg_op_sweep(8, 8, 8, per, None, fake, fake, fake, fake, ctypes.c_void_p(32), 1.0,
+                          None) == G.ERR_ARG
+    # coarsening factor 3, or a factor that does not divide the axis
+    assert L.gmg_op_prolong_add(8, 8, 8, G._ivec((3, 1, 1)), fake, fake, None) == G.ERR_ARG
+    assert L.gmg_op_prolong_add(7, 8, 8, G._ivec((2, 1, 1)), fake, fake, None) == G.ERR_ARG
+    assert L.gmg_op_coarsen_coeffs(8, 8, 8, per, G._ivec((2, 2, 4)), fake, fake, fake, fake, fake,
+                                   fake, None) == G.ERR_ARG
+    # residual norm without an output
+    assert L.gmg_op_residual_norm(8, 8, 8, per, fake, fake, fake, fake, fake, None, None) == G.ERR_ARG
+    assert L.gmg_op_residual_restrict(8, 8, 8, per, G._ivec((2, 2, 2)), fake, fake, fake, fake, fake,
+                                      None, None, None) == G.ERR_ARG

@@ -1,0 +1,337 @@
+"""Benchmark: GMG Poisson solve of the sphere-in-channel workload on GB300.
+
+One step = one whole solve (sigma -> p, relative residual 1e-6) of the
+256 x 96 x 96 sphere channel (a (16 x 6 x 6)D box at D = 16 cells, sphere of
+radius 8 cells at x = 48, cosine-ramped coefficients, walls on every side,
+seeded solenoidal source) with anisotropic coarsening: FP32 V-cycles with the
+adaptive under-relaxed red-black Gauss-Seidel smoother inside an FP64
+refinement loop (the FP32 storage floor of p on this workload is ~5e-6, above
+the 1e-6 target).  Inputs are resident in HBM; L2 (129 MB, larger than the
+~90 MB working set) is flushed with a 512 MB write before every timed step.
+
+value = fine cells x V-cycles / time to tolerance (Gcell-updates/s).
+roofline: the fused sweep kernel on the fine level, timed with CUDA events on
+its stream, L2 flushed before each launch; algorithmic bytes = 24 B/cell.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the FP64 CPU oracle (the same method, single thread)
+is timed instead on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GMG Poisson Gcell-updates/s & time-to-1e-6 residual vs plain GMG, % HBM peak"
+UNIT = "Gcell-updates/s"
+TOL = 1e-6
+DIMS = (256, 96, 96)
+BYTES_PER_CELL_SWEEP = 24          # read p, b, bx, by, bz; write p (FP32)
+L2_FLUSH_BYTES = 512 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload():
+    from paper_2607_07687_gb300 import inputs
+    return inputs.sphere_channel_problem(*DIMS, seed=1)
+
+
+def config(extra=None):
+    c = {"workload": "sphere_channel_256x96x96_aniso", "grid": list(DIMS), "tol": TOL,
+         "coarsening": "anisotropic, n_min 4", "cycle": "V(2,2), 16 coarsest sweeps",
+         "precision": "fp32 V-cycles, fp64 outer residual/update", "l2": "flushed (512 MB write) before every timed step",
+         "seed": 1}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the fine sweep from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2607_07687_gb300", "csrc", "gmg_kernels.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        k = rec.get("k_sweep_fine", {})
+        if k.get("source_sha256") == h and k.get("cells") == DIMS[0] * DIMS[1] * DIMS[2]:
+            return float(k["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(prob, cycles=None):
+    """FP64 oracle solve of the workload on the host (single thread)."""
+    import numpy as np
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    if cycles is None:
+        res = O.solve_problem(prob, tol=TOL, coarsen="aniso")
+    else:
+        res = O.solve_problem(prob, tol=1e-300, coarsen="aniso", max_cycles=cycles)
+    dt = time.perf_counter() - t0
+    return res, dt
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    prob = workload()
+    cells = prob.cells
+    per_step_cycles = 2
+    for _ in range(args.warmup):
+        cpu_oracle_sample(prob, per_step_cycles)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_sample(prob, per_step_cycles)
+        times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = cells * per_step_cycles / (ms * 1e-3) / 1e9
+    sample = f"{per_step_cycles} V-cycles of the FP64 oracle solve of the workload per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"impl": "FP64 CPU oracle, single thread"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    from paper_2607_07687_gb300 import build as B
+    B.build()
+    from paper_2607_07687_gb300 import binding as G
+
+    prob = workload()       # replicas only: every rank solves its own copy
+    cells = prob.cells
+    b64 = torch.from_numpy(np.asarray(prob.b, dtype=np.float32).astype(np.float64)).to(dev)
+    beta = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (prob.bx, prob.by, prob.bz)]
+    p = torch.zeros_like(b64)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    solver = G.Solver(prob.dims, prob.periodic, coarsen="aniso", precision="ir64_fp32")
+    solver.set_coeffs(*beta)
+
+    def step():
+        p.zero_()
+        return solver.solve(b64, p, TOL)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        info = step()
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    infos = []
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(1.0)
+            starts[i].record(stream)
+            infos.append(step())
+            ends[i].record(stream)
+        barrier()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    cycles = infos[-1].cycles
+    assert all(i.status == G.OK for i in infos), [i.as_dict() for i in infos]
+    value = ws * cells * cycles / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    sig_h = torch.from_numpy(np.asarray(prob.b, dtype=np.float32).astype(np.float64)).pin_memory()
+    p_h = torch.zeros_like(sig_h).pin_memory()
+    for _ in range(2):
+        p_h.zero_()
+        solver.solve_host(sig_h, p_h, TOL)
+    barrier()
+    t_e2e = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        p_h.zero_()
+        t0 = time.perf_counter()
+        ie = solver.solve_host(sig_h, p_h, TOL)
+        t_e2e.append(time.perf_counter() - t0)
+    barrier()
+    e2e_ms = 1e3 * sum(t_e2e) / len(t_e2e)
+    if pg:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * cells * ie.cycles / (e2e_ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel: the fused sweep on the fine level
+    b32 = b64.float()
+    pa = torch.zeros_like(b32)
+    pb = torch.zeros_like(b32)
+    for _ in range(3):
+        G.op_sweep(*beta, b32, pa, pb, 1.0, prob.periodic)
+    reps = 20
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for i in range(reps):
+        flush.fill_(1.0)
+        ev[i][0].record(stream)
+        G.op_sweep(*beta, b32, pa if i % 2 == 0 else pb, pb if i % 2 == 0 else pa, 1.0, prob.periodic)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+    # the same launches back to back, L2-resident as inside a V-cycle
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    for i in range(reps):
+        G.op_sweep(*beta, b32, pa if i % 2 == 0 else pb, pb if i % 2 == 0 else pa, 1.0, prob.periodic)
+    w1.record(stream)
+    torch.cuda.synchronize()
+    warm_ms = w0.elapsed_time(w1) / reps
+    alg_bytes = BYTES_PER_CELL_SWEEP * cells
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(), "kernel": "k_sweep (fine level)",
+                "peak_source": f"{peak_kind} hbm_gbs", "l2_flushed": True,
+                "l2_resident_achieved": alg_bytes / (warm_ms * 1e-3) / 1e9,
+                "sweep_gcell_updates_per_s": cells / (sweep_ms * 1e-3) / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config({"v_cycles": cycles, "fp64_refinement_steps": infos[-1].outer,
+                              "rel_res": infos[-1].rel_res, "time_to_tol_ms": ms,
+                              "parallelism": "replicas" if ws > 1 else "single GPU"}),
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * cells,
+                    "d2h_bytes_per_step": 8 * cells, "ms_per_step": e2e_ms},
+            "gpu_launches": int(infos[-1].launches) * args.steps,
+            "clocks": clk.summary()}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        res, dt = cpu_oracle_sample(prob)
+        line["cpu_baseline"] = {"value": cells * res.cycles / dt / 1e9, "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"one full FP64 oracle solve of the workload to {TOL} "
+                                          f"({res.cycles} V-cycles, {dt:.1f} s)"}
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -74,6 +74,7 @@ typedef struct {
     int status;         /* gmg_status of the solve */
     int levels;         /* multigrid levels */
     int outer;          /* FP64 refinement steps (IR modes), else 0 */
+    int launches;       /* kernels this call launched (graph replays counted per kernel node) */
     double rel_res;     /* |b - A p|_2 / |b|_2 of the returned p (before the gauge shift) */
     double omega;       /* relaxation factor after the last cycle */
     double bnorm;       /* |b|_2 after the zero-mean projection */

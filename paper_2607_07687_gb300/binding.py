@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("levels", ctypes.c_int),
-                ("outer", ctypes.c_int), ("rel_res", ctypes.c_double), ("omega", ctypes.c_double),
+                ("outer", ctypes.c_int), ("launches", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("omega", ctypes.c_double),
                 ("bnorm", ctypes.c_double)]
 
     def as_dict(self):

@@ -20,7 +20,7 @@
 namespace gmg {
 
 constexpr int kMaxLevels = 32;
-constexpr int kCoarseMaxCells = 4096;   // largest coarsest level solved inside one CTA
+constexpr int kCoarseMaxCells = 2048;   // largest coarsest level solved inside one CTA
 constexpr int kThreads = 256;           // threads per block of the grid kernels
 
 // sweep tile (cells): TX x TY columns marching through a z-chunk
@@ -123,6 +123,17 @@ struct CoarseTask {
     const Ctl* ctl;
 };
 
+// Zero-mean projection of one level's right-hand side over its active cells
+// (coarsest levels too large for CoarseTask; their sweeps then run as k_sweep).
+struct LevelProjTask {
+    Geo g;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    float* b;
+    const Ctl* ctl;
+};
+
 template <class Task>
 struct TaskList {
     const Task* tasks;   // device array, or nullptr: use `single`
@@ -197,6 +208,8 @@ template <class TP>
 cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStream_t s);
 template <class TP>
 cudaError_t launch_coarse(const CoarseTask<TP>* tasks, int ntasks, cudaStream_t s);
+
+cudaError_t launch_project_level(const LevelProjTask* tasks, int ntasks, cudaStream_t s);
 
 // Reference variant of the sweep: one in-place launch per colour.
 cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const float* bz,

@@ -384,8 +384,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const __grid_constant__ T
 
 // ---------------------------------------------------------------- K4: coarsest level
 
-constexpr int kCoarseSmem = 2048;
-static_assert(kCoarseSmem <= kCoarseMaxCells, "coarse capacity");
+constexpr int kCoarseSmem = kCoarseMaxCells;
 
 template <class TP>
 __global__ void __launch_bounds__(kThreads) k_coarse(const CoarseTask<TP>* __restrict__ tasks)
@@ -462,6 +461,39 @@ __global__ void __launch_bounds__(kThreads) k_coarse(const CoarseTask<TP>* __res
         }
     }
     for (int i = threadIdx.x; i < N; i += kThreads) stv(T.out, (int64_t)i, sp[i]);
+}
+
+// one block per task: b <- b - mean over active cells (0 on inactive cells)
+__global__ void __launch_bounds__(kThreads) k_project_level(const LevelProjTask* __restrict__ tasks)
+{
+    __shared__ double red[kThreads / 32];
+    __shared__ double s_mean;
+    const LevelProjTask& T = tasks[blockIdx.x];
+    if (T.ctl && T.ctl->done) return;
+    const Geo g = T.g;
+    const int64_t N = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    auto active = [&](int64_t i) -> bool {
+        const int x = (int)(i % g.n[0]);
+        const int y = (int)((i / g.n[0]) % g.n[1]);
+        const int z = (int)(i / ((int64_t)g.n[0] * g.n[1]));
+        const float dg = diag_sum(face_lo(T.bx, g, 0, x, y, z), face_lo(T.bx, g, 0, x + 1, y, z),
+                                  face_lo(T.by, g, 1, x, y, z), face_lo(T.by, g, 1, x, y + 1, z),
+                                  face_lo(T.bz, g, 2, x, y, z), face_lo(T.bz, g, 2, x, y, z + 1));
+        return dg > 0.f;
+    };
+    double s = 0.0, cnt = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += kThreads)
+        if (active(i)) {
+            s += (double)T.b[i];
+            cnt += 1.0;
+        }
+    s = block_sum(s, red);
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) s_mean = cnt > 0.0 ? s / cnt : 0.0;
+    __syncthreads();
+    const double mean = s_mean;
+    for (int64_t i = threadIdx.x; i < N; i += kThreads)
+        T.b[i] = active(i) ? (float)((double)T.b[i] - mean) : 0.f;
 }
 
 // ---------------------------------------------------------------- K7 and transfers
@@ -892,6 +924,13 @@ cudaError_t launch_coarse(const CoarseTask<TP>* tasks, int ntasks, cudaStream_t 
 }
 template cudaError_t launch_coarse<float>(const CoarseTask<float>*, int, cudaStream_t);
 template cudaError_t launch_coarse<bf16>(const CoarseTask<bf16>*, int, cudaStream_t);
+
+cudaError_t launch_project_level(const LevelProjTask* tasks, int ntasks, cudaStream_t s)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    k_project_level<<<ntasks, kThreads, 0, s>>>(tasks);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const float* bz,
                                   const float* b, float* p, float omega, cudaStream_t s)

@@ -135,7 +135,7 @@ struct ProblemMem {
     int* hist_acc = nullptr;
 };
 
-enum OpKind { kSweepFF, kSweepFB, kSweepBB, kResF, kResB, kCoarseF, kCoarseB, kControl };
+enum OpKind { kSweepFF, kSweepFB, kSweepBB, kResF, kResB, kCoarseF, kCoarseB, kProjLevel, kControl };
 
 struct LaunchOp {
     OpKind kind;
@@ -147,6 +147,7 @@ struct LaunchOp {
     TaskList<ResTask<bf16>> r_b{};
     const CoarseTask<float>* c_f = nullptr;
     const CoarseTask<bf16>* c_b = nullptr;
+    const LevelProjTask* lp = nullptr;
     const CtlTask* ctl = nullptr;
     int n = 0;
 };
@@ -172,6 +173,7 @@ struct Engine {
     bool coeffs_set = false;
     std::string err;
     int last_cycles = 0;
+    long long launches = 0;     // kernels launched since the counter was reset
 
     ~Engine() { release(); }
 
@@ -245,11 +247,6 @@ struct Engine {
             Geo geo[kMaxLevels];
             int cf[kMaxLevels][3];
             M.L = plan_levels(M.g0, o.coarsen == GMG_COARSEN_ANISO, o.n_min, geo, cf);
-            if (M.L > 1 && cells(geo[M.L - 1]) > 2048)
-                return fail(GMG_ERR_ARG,
-                            "problem %d: coarsest level %dx%dx%d has more than 2048 cells; "
-                            "choose dimensions with more factors of two or a smaller n_min",
-                            p, geo[M.L - 1].n[0], geo[M.L - 1].n[1], geo[M.L - 1].n[2]);
             M.n0 = cells(M.g0);
             for (int l = 0; l < M.L; ++l) {
                 LevelMem& Lm = M.lev[l];
@@ -493,12 +490,15 @@ struct Engine {
             std::vector<CoarseTask<float>> cf;
             std::vector<CoarseTask<bf16>> cb;
             std::vector<int> single;
+            std::vector<std::vector<int>> big(kMaxLevels);   // by coarsest level index
             for (int p = 0; p < nprob; ++p) {
                 const int l = P[p].L - 1;
                 const LevelMem& Lm = P[p].lev[l];
                 coarse_result_[p][l] = 0;
                 if (l == 0) {
                     single.push_back(p);
+                } else if (cells(Lm.g) > kCoarseMaxCells) {
+                    big[l].push_back(p);
                 } else if (bf16_coarse) {
                     cb.push_back(CoarseTask<bf16>{Lm.g, Lm.beta[0], Lm.beta[1], Lm.beta[2], Lm.b,
                                                   static_cast<bf16*>(Lm.buf[0]), opt.nu_c, P[p].ctl});
@@ -522,6 +522,29 @@ struct Engine {
                 op.n = (int)cb.size();
                 if (!op.c_b) return fail(GMG_ERR_CUDA, "upload failed");
                 cycle.push_back(op);
+            }
+            // coarsest levels too large for one CTA: projection, then nu_c grid sweeps
+            for (int l = 1; l < kMaxLevels; ++l) {
+                if (big[l].empty()) continue;
+                std::vector<LevelProjTask> lp;
+                for (int p : big[l]) {
+                    const LevelMem& Lm = P[p].lev[l];
+                    lp.push_back(LevelProjTask{Lm.g, Lm.beta[0], Lm.beta[1], Lm.beta[2], Lm.b, P[p].ctl});
+                }
+                LaunchOp op;
+                op.kind = kProjLevel;
+                op.lp = upload(lp);
+                op.n = (int)lp.size();
+                if (!op.lp) return fail(GMG_ERR_CUDA, "upload failed");
+                cycle.push_back(op);
+                int cur = -1;
+                for (int s = 0; s < opt.nu_c; ++s) {
+                    const int out = next_out(l, cur < 0 ? 1 : cur);
+                    int rc = add_sweeps(l, big[l], cur, out, false);
+                    if (rc) return rc;
+                    cur = out;
+                }
+                for (int p : big[l]) coarse_result_[p][l] = cur;
             }
             if (!single.empty()) {
                 int cur = 0;
@@ -577,6 +600,7 @@ struct Engine {
 
     cudaError_t launch(const LaunchOp& op)
     {
+        ++launches;
         switch (op.kind) {
         case kSweepFF: return launch_sweep(op.s_ff, op.grid, stream);
         case kSweepFB: return launch_sweep(op.s_fb, op.grid, stream);
@@ -585,6 +609,7 @@ struct Engine {
         case kResB: return launch_residual(op.r_b, op.grid, stream);
         case kCoarseF: return launch_coarse(op.c_f, op.n, stream);
         case kCoarseB: return launch_coarse(op.c_b, op.n, stream);
+        case kProjLevel: return launch_project_level(op.lp, op.n, stream);
         case kControl: return launch_control_cycle(op.ctl, op.n, stream);
         }
         return cudaErrorInvalidValue;
@@ -608,9 +633,11 @@ struct Engine {
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaStream_t saved = stream;
+            const long long counted = launches;
             stream = cap;
             cudaError_t le = run_cycle_eager();
             stream = saved;
+            launches = counted;
             e = cudaStreamEndCapture(cap, &graph);
             if (le != cudaSuccess) e = le;
         }
@@ -624,6 +651,7 @@ struct Engine {
         if (opt.use_graph) {
             cudaError_t e = ensure_graph();
             if (e != cudaSuccess) return e;
+            launches += (long long)cycle.size();
             return cudaGraphLaunch(graph_exec, stream);
         }
         return run_cycle_eager();
@@ -633,30 +661,41 @@ struct Engine {
 
     int set_coeffs(const float* const* bx, const float* const* by, const float* const* bz)
     {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "gmg_set_coeffs: pending error from an earlier call");
         int* bad = dalloc<int>(1);
         if (!bad) return fail(GMG_ERR_CUDA, "out of device memory");
-        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), stream);
+        const char* step = "memset";
+        e = cudaMemsetAsync(bad, 0, sizeof(int), stream);
         for (size_t p = 0; p < P.size() && e == cudaSuccess; ++p) {
             ProblemMem& M = P[p];
             const size_t bytes = sizeof(float) * (size_t)M.n0;
             const float* src[3] = {bx[p], by[p], bz[p]};
+            step = "coefficient copy";
             for (int d = 0; d < 3 && e == cudaSuccess; ++d)
                 e = cudaMemcpyAsync(M.lev[0].beta[d], src[d], bytes, cudaMemcpyDeviceToDevice, stream);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess) {
+                step = "coefficient check";
                 e = launch_check_coeffs(M.n0, M.lev[0].beta[0], M.lev[0].beta[1], M.lev[0].beta[2], bad, stream);
+            }
+            step = "coarsening";
             for (int l = 0; l + 1 < M.L && e == cudaSuccess; ++l)
                 e = launch_coarsen_coeffs(M.lev[l].g, M.lev[l].cf, M.lev[l].beta[0], M.lev[l].beta[1],
                                           M.lev[l].beta[2], M.lev[l + 1].beta[0], M.lev[l + 1].beta[1],
                                           M.lev[l + 1].beta[2], stream);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess) {
+                step = "active mask";
                 e = launch_active_mask(M.g0, M.lev[0].beta[0], M.lev[0].beta[1], M.lev[0].beta[2], M.mask, stream);
+            }
+            if (e != cudaSuccess) return fail(GMG_ERR_CUDA, "gmg_set_coeffs (problem %zu, %s): %s", p, step,
+                                              cudaGetErrorString(e));
         }
         int hbad = 0;
+        step = "readback";
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        cudaFree(bad);
-        allocs.erase(std::find(allocs.begin(), allocs.end(), (void*)bad));
-        if (e != cudaSuccess) return cuda_fail(e, "gmg_set_coeffs");
+        drop(bad);
+        if (e != cudaSuccess) return fail(GMG_ERR_CUDA, "gmg_set_coeffs (%s): %s", step, cudaGetErrorString(e));
         if (hbad) return fail(GMG_ERR_ARG, "face coefficients must be finite and >= 0");
         coeffs_set = true;
         return GMG_OK;
@@ -724,6 +763,7 @@ struct Engine {
         }
         TaskList<ProjTask<TS>> tl;
         if (make_list(v, tiles, tl)) return cudaErrorMemoryAllocation;
+        launches += 3;
         cudaError_t e = launch_project_sum(tl, persistent_grid(tl.total), stream);
         if (e == cudaSuccess) e = launch_project_finalize(init_ctl, (int)P.size(), stream);
         if (e == cudaSuccess) e = launch_project_apply(tl, persistent_grid(tl.total), stream);
@@ -771,6 +811,7 @@ struct Engine {
         }
         TaskList<GaugeTask<TP, TD>> tl;
         if (make_list(v, tiles, tl)) return cudaErrorMemoryAllocation;
+        launches += 3;
         cudaError_t e = launch_gauge_sum(tl, persistent_grid(tl.total), stream);
         if (e == cudaSuccess) e = launch_gauge_finalize(gauge_ctl, (int)P.size(), stream);
         if (e == cudaSuccess) e = launch_gauge_apply(tl, persistent_grid(tl.total), stream);
@@ -796,6 +837,7 @@ struct Engine {
         }
         TaskList<ResTask<float>> tl;
         if (make_list(v, tiles, tl)) return cudaErrorMemoryAllocation;
+        launches += 2;
         cudaError_t e = launch_residual(tl, persistent_grid(tl.total), stream);
         if (e == cudaSuccess) e = launch_control_init(init_ctl, (int)P.size(), stream);
         if (tl.tasks) {
@@ -831,6 +873,7 @@ struct Engine {
     int solve32(const float* const* sigma, float* const* p, double tol, gmg_info* infos)
     {
         if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_solve");
+        launches = 0;
         cudaError_t e = upload_ctl(tol);
         if (e == cudaSuccess) e = project<float>(sigma, (const float* const*)p, false, nullptr);
         if (e == cudaSuccess) e = init_control();
@@ -857,6 +900,7 @@ struct Engine {
                 inf.status = st;
                 inf.levels = P[q].L;
                 inf.outer = 0;
+                inf.launches = (int)launches;
                 inf.rel_res = c.bnorm > 0.0 ? c.r_prev / c.bnorm : 0.0;
                 inf.omega = c.omega;
                 inf.bnorm = c.bnorm;
@@ -871,6 +915,7 @@ struct Engine {
     {
         if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_solve");
         ProblemMem& M = P[0];
+        launches = 0;
         cudaError_t e = upload_ctl(tol);
         const double* sg[1] = {sigma};
         const double* pi[1] = {p};
@@ -883,6 +928,7 @@ struct Engine {
             CtlTask* d = upload(tv);
             if (!d) return fail(GMG_ERR_CUDA, "upload failed");
             e = launch_control_init(d, 1, stream);
+            ++launches;
             if (e == cudaSuccess) e = read_ctl();
             drop(d);
         }
@@ -914,6 +960,7 @@ struct Engine {
             t.scale = nullptr;
             status = kRunning;
             for (;;) {
+                launches += 2;
                 if (e == cudaSuccess) e = launch_ir_residual(t, persistent_grid(rt.tiles()), stream);
                 if (e == cudaSuccess)
                     e = launch_ir_begin_inner(t, (int)rt.tiles(), tol, opt.ir_inner_rtol, opt.max_cycles, stream);
@@ -925,11 +972,13 @@ struct Engine {
                 }
                 ++outer;
                 e = iterate();
+                ++launches;
                 if (e == cudaSuccess) e = launch_ir_update(t, stream);
                 if (e == cudaSuccess) e = read_ctl();
                 if (e != cudaSuccess) break;
                 if (c.status == kDiverged) {
                     // keep the refinement so far and report the inner divergence
+                    launches += 2;
                     e = launch_ir_residual(t, persistent_grid(rt.tiles()), stream);
                     if (e == cudaSuccess)
                         e = launch_ir_begin_inner(t, (int)rt.tiles(), tol, opt.ir_inner_rtol, opt.max_cycles, stream);
@@ -952,6 +1001,7 @@ struct Engine {
             info->status = st;
             info->levels = M.L;
             info->outer = outer;
+            info->launches = (int)launches;
             info->rel_res = c.outer_bnorm > 0.0 ? c.outer_r / c.outer_bnorm : 0.0;
             info->omega = c.omega;
             info->bnorm = c.outer_bnorm;

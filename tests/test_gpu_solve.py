@@ -24,12 +24,23 @@ def O():
     return oracle
 
 
-def _parity(got, info, ref, cycles_tol=1, l2=1e-5):
+def _parity(got, info, ref, cycles_tol=1, l2=1e-5, same=None):
+    """Cycle counts within +-1; the solution against the oracle's iterate after
+    the SAME number of V-cycles (`same` runs the oracle for a given count):
+    two valid iterates one cycle apart differ by a whole cycle's correction,
+    which at a contraction of ~0.6 per cycle is far above FP32 rounding."""
     assert info.status == 0, info.as_dict()
     assert abs(info.cycles - ref.cycles) <= cycles_tol, (info.cycles, ref.cycles)
-    err = rel_l2(got, ref.p)
-    assert err <= l2, err
+    target = ref if (info.cycles == ref.cycles or same is None) else same(info.cycles)
+    err = rel_l2(got, target.p)
+    assert err <= l2, (err, info.cycles, ref.cycles)
     return err
+
+
+def _same(O, prob, **kw):
+    def run(k):
+        return O.solve_problem(prob, tol=1e-300, max_cycles=k, **kw)
+    return run
 
 
 def test_taylor_green_32_iso(O):
@@ -38,11 +49,12 @@ def test_taylor_green_32_iso(O):
     ref = oracle_cached(("tg", 32, 0), 1e-6, coarsen="iso")
     got, info, (hist, om, acc) = gpu_solve(prob, 1e-6, coarsen="iso")
     assert info.levels == 4
-    _parity(got, info, ref)
+    _parity(got, info, ref, same=_same(O, prob, coarsen="iso"))
     fft = O.fft_solve_periodic(f32(prob.b))
     assert rel_l2(got, fft) <= 3 * 32 ** 2 / math.pi ** 2 * 1e-6
     assert np.all(np.diff(hist) <= 0)
-    np.testing.assert_allclose(hist, ref.history, rtol=1e-3)
+    above = ref.history[:len(hist)] > 1e-5          # well above the FP32 floor (~1e-7 here)
+    np.testing.assert_allclose(hist[above], ref.history[:len(hist)][above], rtol=1e-4)
 
 
 def test_sphere_channel_fp32_aniso(O):
@@ -51,7 +63,7 @@ def test_sphere_channel_fp32_aniso(O):
     ref = oracle_cached(("sphere",), 1e-5, coarsen="aniso")
     got, info, (hist, _, _) = gpu_solve(prob, 1e-5, coarsen="aniso")
     assert info.levels == 7
-    _parity(got, info, ref)
+    _parity(got, info, ref, same=_same(O, prob, coarsen="aniso"))
     assert np.all(np.diff(hist) <= 0)
 
 
@@ -60,7 +72,7 @@ def test_sphere_channel_fp32_iso(O):
     ref = oracle_cached(("sphere",), 1e-5, coarsen="iso")
     got, info, _ = gpu_solve(prob, 1e-5, coarsen="iso")
     assert info.levels == 5
-    _parity(got, info, ref)
+    _parity(got, info, ref, same=_same(O, prob, coarsen="iso"))
 
 
 @pytest.mark.parametrize("precision", ["ir64_fp32", "ir64"])
@@ -73,7 +85,8 @@ def test_sphere_channel_refined_to_1e6(O, precision):
     assert info.outer >= 1
     slack = 1 if precision == "ir64_fp32" else 4
     assert abs(info.cycles - ref.cycles) <= slack, (info.cycles, ref.cycles)
-    assert rel_l2(got, ref.p) <= 1e-5
+    same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles)
+    assert rel_l2(got, same.p) <= 1e-5
 
 
 def test_bf16_corrections_converge(O):
@@ -107,7 +120,7 @@ def test_random_coefficients(O, dims, periodic, coarsen):
     prob = I.random_small_problem(dims, periodic, seed=sum(dims))
     ref = O.solve_problem(prob, tol=1e-5, coarsen=coarsen, max_cycles=300)
     got, info, _ = gpu_solve(prob, 1e-5, coarsen=coarsen, max_cycles=300)
-    _parity(got, info, ref)
+    _parity(got, info, ref, same=_same(O, prob, coarsen=coarsen))
 
 
 def test_zero_rhs():
@@ -134,9 +147,10 @@ def test_warm_start_matches_oracle(O):
     prob = I.sphere_channel_problem(96, 32, 32, seed=4, radius=6, center_x=30)
     rng = np.random.default_rng(0)
     p0 = f32(rng.standard_normal(prob.shape))
-    ref = O.solve(f32(prob.b), f32(prob.bx), f32(prob.by), f32(prob.bz), prob.periodic, tol=1e-5, p0=p0)
+    args = (f32(prob.b), f32(prob.bx), f32(prob.by), f32(prob.bz), prob.periodic)
+    ref = O.solve(*args, tol=1e-5, p0=p0)
     got, info, _ = gpu_solve(prob, 1e-5, p0=p0)
-    _parity(got, info, ref)
+    _parity(got, info, ref, same=lambda k: O.solve(*args, tol=1e-300, p0=p0, max_cycles=k))
 
 
 def test_omega_adapts_like_oracle(O):
@@ -215,4 +229,4 @@ def test_batch_equals_single_and_oracle(O):
         assert np.array_equal(host(o), single)
         ref = O.solve_problem(prob, tol=1e-5)
         if ref.bnorm > 0:
-            _parity(host(o), inf, ref)
+            _parity(host(o), inf, ref, same=_same(O, prob))

@@ -183,6 +183,38 @@ def reference_arm(args):
     return 0
 
 
+def kernel_only(args):
+    """Launch one kernel of the fine level repeatedly on a periodic grid of
+    random values (a small, bounded case for ncu)."""
+    import numpy as np
+    import torch
+    from paper_2607_07687_gb300 import build as B
+    B.build()
+    from paper_2607_07687_gb300 import binding as G
+    nx, ny, nz = (int(v) for v in args.grid.split(","))
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    shape = (nz, ny, nx)
+    beta = [torch.rand(shape, device="cuda", generator=gen) for _ in range(3)]
+    b = torch.randn(shape, device="cuda", generator=gen)
+    pa = torch.randn(shape, device="cuda", generator=gen)
+    pb = torch.zeros_like(pa)
+    coarse = torch.zeros((nz // 2, ny // 2, nx // 2), device="cuda")
+    per = (True, True, True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    for i in range(args.reps):
+        if args.kernel == "sweep":
+            G.op_sweep(*beta, b, pa if i % 2 == 0 else pb, pb if i % 2 == 0 else pa, 1.0, per)
+        else:
+            G.op_residual_restrict(*beta, b, pa, coarse, (2, 2, 2), per)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.reps
+    print(json.dumps({"kernel": args.kernel, "grid": [nx, ny, nz], "reps": args.reps, "ms_per_launch": ms}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,7 +222,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--kernel", choices=["sweep", "residual"], default=None,
+                    help="only launch one kernel --reps times on a --grid (for profiler captures)")
+    ap.add_argument("--grid", default="512,256,128", help="nx,ny,nz of the --kernel grid")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
+    if args.kernel:
+        return kernel_only(args)
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)

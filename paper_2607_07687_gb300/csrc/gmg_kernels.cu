@@ -76,12 +76,16 @@ __device__ __forceinline__ float face_lo(const float* a, const Geo& g, int d, in
     return __ldg(a + lin(g, x, y, z));
 }
 
-// sum over the six faces of beta_f * p_nb, in one fixed order (lower/upper x, y, z)
-__device__ __forceinline__ float nb_sum(float bxl, float pxl, float bxu, float pxu, float byl,
-                                        float pyl, float byu, float pyu, float bzl, float pzl,
-                                        float bzu, float pzu)
+// (A p)_I = sum over the six faces of beta_f (p_nb - p_I), in one fixed order
+// (lower/upper x, y, z).  Each difference of two nearby FP32 values is exact,
+// so the rounding error scales with the local differences rather than with
+// |p|; the form nb - diag * p would cancel and lose ~log2(|p| / |A p|) bits.
+__device__ __forceinline__ float face_flux(float bxl, float pxl, float bxu, float pxu, float byl,
+                                           float pyl, float byu, float pyu, float bzl, float pzl,
+                                           float bzu, float pzu, float p)
 {
-    return ((bxl * pxl + bxu * pxu) + (byl * pyl + byu * pyu)) + (bzl * pzl + bzu * pzu);
+    return ((bxl * (pxl - p) + bxu * (pxu - p)) + (byl * (pyl - p) + byu * (pyu - p))) +
+           (bzl * (pzl - p) + bzu * (pzu - p));
 }
 
 __device__ __forceinline__ float diag_sum(float bxl, float bxu, float byl, float byu, float bzl,
@@ -90,12 +94,13 @@ __device__ __forceinline__ float diag_sum(float bxl, float bxu, float byl, float
     return ((bxl + bxu) + (byl + byu)) + (bzl + bzu);
 }
 
-// under-relaxed Gauss-Seidel update of one cell (Sec. 3.1); isolated cells keep p
-__device__ __forceinline__ float gs_update(float p, float nb, float dg, float b, float w)
+// under-relaxed Gauss-Seidel update of one cell (Sec. 3.1) in correction form:
+// (1 - w) p + w (sum beta p_nb - b) / diag = p + w ((A p)_I - b_I) / diag;
+// isolated cells (diag = 0) keep p
+__device__ __forceinline__ float gs_update(float p, float flux, float dg, float b, float w)
 {
     if (!(dg > 0.f)) return p;
-    const float gs = (nb - b) / dg;
-    return (1.0f - w) * p + w * gs;
+    return p + w * ((flux - b) / dg);
 }
 
 template <class Task>
@@ -248,11 +253,11 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const __grid_constant__ Task
                     if (zok && wrapc(x, g.n[0], g.per[0]) && wrapc(y, g.n[1], g.per[1])) {
                         v = P0[s];
                         if (((x + y + zk) & 1) == 0) {
-                            const float nb = nb_sum(X0[s], P0[s - 1], X0[s + 1], P0[s + 1], Y0[s],
-                                                    P0[s - SW], Y0[s + SW], P0[s + SW], Z0[s], Mlo[s],
-                                                    Z1[s], P1[s]);
+                            const float fl = face_flux(X0[s], P0[s - 1], X0[s + 1], P0[s + 1], Y0[s],
+                                                       P0[s - SW], Y0[s + SW], P0[s + SW], Z0[s], Mlo[s],
+                                                       Z1[s], P1[s], v);
                             const float dg = diag_sum(X0[s], X0[s + 1], Y0[s], Y0[s + SW], Z0[s], Z1[s]);
-                            v = gs_update(v, nb, dg, B0[s], w);
+                            v = gs_update(v, fl, dg, B0[s], w);
                         }
                     }
                     M0[s] = v;
@@ -278,10 +283,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const __grid_constant__ Task
                     const int s = (ty + 2) * SW + (tx + 2);
                     float v = Mk[s];
                     if (((x + y + k) & 1) == 1) {
-                        const float nb = nb_sum(Xk[s], Mk[s - 1], Xk[s + 1], Mk[s + 1], Yk[s], Mk[s - SW],
-                                                Yk[s + SW], Mk[s + SW], Zk[s], Mlo[s], Zk1[s], Mhi[s]);
+                        const float fl = face_flux(Xk[s], Mk[s - 1], Xk[s + 1], Mk[s + 1], Yk[s], Mk[s - SW],
+                                                   Yk[s + SW], Mk[s + SW], Zk[s], Mlo[s], Zk1[s], Mhi[s], v);
                         const float dg = diag_sum(Xk[s], Xk[s + 1], Yk[s], Yk[s + SW], Zk[s], Zk1[s]);
-                        v = gs_update(v, nb, dg, Bk[s], w);
+                        v = gs_update(v, fl, dg, Bk[s], w);
                     }
                     stv(pout, lin(g, x, y, k), v);
                 }
@@ -311,10 +316,11 @@ __global__ void k_sweep_colour(Geo g, const float* __restrict__ bx, const float*
         const float fxl = face_lo(bx, g, 0, x, y, z), fxu = face_lo(bx, g, 0, x + 1, y, z);
         const float fyl = face_lo(by, g, 1, x, y, z), fyu = face_lo(by, g, 1, x, y + 1, z);
         const float fzl = face_lo(bz, g, 2, x, y, z), fzu = face_lo(bz, g, 2, x, y, z + 1);
-        const float nb = nb_sum(fxl, pv(x - 1, y, z), fxu, pv(x + 1, y, z), fyl, pv(x, y - 1, z), fyu,
-                                pv(x, y + 1, z), fzl, pv(x, y, z - 1), fzu, pv(x, y, z + 1));
+        const float p0 = p[I];
+        const float fl = face_flux(fxl, pv(x - 1, y, z), fxu, pv(x + 1, y, z), fyl, pv(x, y - 1, z), fyu,
+                                   pv(x, y + 1, z), fzl, pv(x, y, z - 1), fzu, pv(x, y, z + 1), p0);
         const float dg = diag_sum(fxl, fxu, fyl, fyu, fzl, fzu);
-        p[I] = gs_update(p[I], nb, dg, __ldg(b + I), w);
+        p[I] = gs_update(p0, fl, dg, __ldg(b + I), w);
     }
 }
 
@@ -354,10 +360,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(const __grid_constant__ T
             const float fxl = face_lo(tp->bx, g, 0, x, y, z), fxu = face_lo(tp->bx, g, 0, x + 1, y, z);
             const float fyl = face_lo(tp->by, g, 1, x, y, z), fyu = face_lo(tp->by, g, 1, x, y + 1, z);
             const float fzl = face_lo(tp->bz, g, 2, x, y, z), fzu = face_lo(tp->bz, g, 2, x, y, z + 1);
-            const float nb = nb_sum(fxl, pv(x - 1, y, z), fxu, pv(x + 1, y, z), fyl, pv(x, y - 1, z),
-                                    fyu, pv(x, y + 1, z), fzl, pv(x, y, z - 1), fzu, pv(x, y, z + 1));
-            const float dg = diag_sum(fxl, fxu, fyl, fyu, fzl, fzu);
-            const float Ap = nb - dg * pv(x, y, z);
+            const float Ap = face_flux(fxl, pv(x - 1, y, z), fxu, pv(x + 1, y, z), fyl, pv(x, y - 1, z),
+                                       fyu, pv(x, y + 1, z), fzl, pv(x, y, z - 1), fzu, pv(x, y, z + 1),
+                                       pv(x, y, z));
             r = __ldg(tp->b + lin(g, x, y, z)) - Ap;
         }
         if (tp->bc) {
@@ -451,11 +456,12 @@ __global__ void __launch_bounds__(kThreads) k_coarse(const CoarseTask<TP>* __res
                 const int zl = nbi(x, y, z, 2, -1), zu = nbi(x, y, z, 2, +1);
                 const float fxu = xu < 0 ? 0.f : sx[xu], fyu = yu < 0 ? 0.f : sy[yu],
                             fzu = zu < 0 ? 0.f : sz[zu];
-                const float nb = nb_sum(sx[i], xl < 0 ? 0.f : sp[xl], fxu, xu < 0 ? 0.f : sp[xu], sy[i],
-                                        yl < 0 ? 0.f : sp[yl], fyu, yu < 0 ? 0.f : sp[yu], sz[i],
-                                        zl < 0 ? 0.f : sp[zl], fzu, zu < 0 ? 0.f : sp[zu]);
+                const float p0 = sp[i];
+                const float fl = face_flux(sx[i], xl < 0 ? p0 : sp[xl], fxu, xu < 0 ? p0 : sp[xu], sy[i],
+                                           yl < 0 ? p0 : sp[yl], fyu, yu < 0 ? p0 : sp[yu], sz[i],
+                                           zl < 0 ? p0 : sp[zl], fzu, zu < 0 ? p0 : sp[zu], p0);
                 const float dg = diag_sum(sx[i], fxu, sy[i], fyu, sz[i], fzu);
-                sp[i] = gs_update(sp[i], nb, dg, sb[i], w);
+                sp[i] = gs_update(p0, fl, dg, sb[i], w);
             }
             __syncthreads();
         }
@@ -818,12 +824,11 @@ __global__ void __launch_bounds__(kThreads) k_ir_residual(const __grid_constant_
             const double fyl = face_lo(t.by, g, 1, x, y, z), fyu = face_lo(t.by, g, 1, x, y + 1, z);
             const double fzl = face_lo(t.bz, g, 2, x, y, z), fzu = face_lo(t.bz, g, 2, x, y, z + 1);
             const double p0 = pv(x, y, z);
-            const double nb = ((fxl * pv(x - 1, y, z) + fxu * pv(x + 1, y, z)) +
-                               (fyl * pv(x, y - 1, z) + fyu * pv(x, y + 1, z))) +
-                              (fzl * pv(x, y, z - 1) + fzu * pv(x, y, z + 1));
-            const double dg = ((fxl + fxu) + (fyl + fyu)) + (fzl + fzu);
+            const double Ap = ((fxl * (pv(x - 1, y, z) - p0) + fxu * (pv(x + 1, y, z) - p0)) +
+                               (fyl * (pv(x, y - 1, z) - p0) + fyu * (pv(x, y + 1, z) - p0))) +
+                              (fzl * (pv(x, y, z - 1) - p0) + fzu * (pv(x, y, z + 1) - p0));
             const int64_t I = lin(g, x, y, z);
-            r = t.b64[I] - (nb - dg * p0);
+            r = t.b64[I] - Ap;
             t.b32[I] = (float)r;
             t.ebuf[0][I] = 0.f;
         }

@@ -1158,9 +1158,6 @@ int gmg_solve_host(gmg_handle h, const void* sigma_host, void* p_host, double to
     } else {
         rc = E.cuda_fail(e, "gmg_solve_host");
     }
-    if (ds) cudaFreeAsync(ds, E.stream);
-    if (dp) cudaFreeAsync(dp, E.stream);
-    cudaStreamSynchronize(E.stream);
     return rc;
 }
 

@@ -24,12 +24,12 @@ def O():
     return oracle
 
 
-def _parity(got, info, ref, cycles_tol=1, l2=1e-5, same=None):
+def _parity(got, info, ref, cycles_tol=1, l2=1e-5, same=None, status=0):
     """Cycle counts within +-1; the solution against the oracle's iterate after
     the SAME number of V-cycles (`same` runs the oracle for a given count):
     two valid iterates one cycle apart differ by a whole cycle's correction,
     which at a contraction of ~0.6 per cycle is far above FP32 rounding."""
-    assert info.status == 0, info.as_dict()
+    assert info.status == status, info.as_dict()
     assert abs(info.cycles - ref.cycles) <= cycles_tol, (info.cycles, ref.cycles)
     target = ref if (info.cycles == ref.cycles or same is None) else same(info.cycles)
     err = rel_l2(got, target.p)
@@ -115,12 +115,15 @@ def test_taylor_green_128_refined_vs_fft(O):
                                                    ((96, 24, 12), (0, 0, 1), "aniso"),
                                                    ((6, 6, 6), (0, 0, 0), "aniso")])
 def test_random_coefficients(O, dims, periodic, coarsen):
-    """Random coefficients with zero blocks on ragged grids (incl. a grid that
-    does not coarsen at all), FP32 to 1e-5."""
+    """Random coefficients with zero blocks on ragged grids: a grid that does
+    not coarsen at all (6^3), and one whose coarsest level (35 x 9 x 13) is too
+    large for the one-CTA coarse solve and runs grid sweeps instead (there the
+    16 coarsest sweeps converge slowly, for the oracle too: both stop at the
+    cycle limit and are compared there)."""
     prob = I.random_small_problem(dims, periodic, seed=sum(dims))
-    ref = O.solve_problem(prob, tol=1e-5, coarsen=coarsen, max_cycles=300)
-    got, info, _ = gpu_solve(prob, 1e-5, coarsen=coarsen, max_cycles=300)
-    _parity(got, info, ref, same=_same(O, prob, coarsen=coarsen))
+    ref = O.solve_problem(prob, tol=1e-5, coarsen=coarsen, max_cycles=60)
+    got, info, _ = gpu_solve(prob, 1e-5, coarsen=coarsen, max_cycles=60)
+    _parity(got, info, ref, same=_same(O, prob, coarsen=coarsen), status=ref.status)
 
 
 def test_zero_rhs():

@@ -140,6 +140,7 @@ struct TaskList {
     const int* tile_off; // device prefix of tile counts (ntasks + 1)
     int ntasks;
     int total;           // total tiles
+    int vec;             // 4: every task's rows split into aligned 16-byte chunks
     Task single;
 };
 

@@ -29,21 +29,22 @@
 #include "gmg_internal.h"
 
 #include <cmath>
+#include <type_traits>
 
 namespace gmg {
 namespace {
 
 // ---------------------------------------------------------------- helpers
 
+// Map a (possibly out-of-range) index onto the grid: periodic axes wrap by
+// any number of periods (tiles and halos can exceed a small periodic level),
+// walled axes report "outside".
 __device__ __forceinline__ bool wrapc(int& i, int n, int per)
 {
-    if (i < 0) {
-        if (!per) return false;
-        i += n;
-    } else if (i >= n) {
-        if (!per) return false;
-        i -= n;
-    }
+    if (i >= 0 && i < n) return true;
+    if (!per) return false;
+    i %= n;
+    if (i < 0) i += n;
     return true;
 }
 
@@ -292,6 +293,292 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const __grid_constant__ Task
                 }
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------- K1: pipelined sweep
+//
+// The same sweep as k_sweep (same arithmetic, bit-identical results) with the
+// z-planes staged by asynchronous global->shared copies.  Ring buffers of
+// planes over the tile plus halo (x: 4 columns each side so rows split into
+// 16-byte chunks; y: 2 rows each side):
+//   P  input p (+ coarse correction)     planes kr .. kr+3   (4 slots)
+//   B, X, Y  b and lower x/y faces       planes kr-1 .. kr+1 (4 slots)
+//   Z  lower z faces                     planes kr-1 .. kr+2 (5 slots)
+//   M  merged plane (red new, black old) planes kr-2 .. kr   (3 slots)
+// At step u (red plane kr = z0 - 1 + u, black plane kr - 1) the copies for
+// step u+1 are issued first, then the step waits for its own group.  The
+// coarse correction of a P plane is added two steps before the plane is read,
+// so it needs no extra barrier.  VEC = 4 copies 16-byte chunks (rows of a
+// multiple of 4 cells, 16-byte aligned arrays), VEC = 1 copies single floats.
+
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc, bool ok)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc, bool ok)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int VEC, class TC>
+__global__ void __launch_bounds__(kThreads, 4) k_sweep_async(const __grid_constant__ TaskList<SweepTask<float, TC>> tl)
+{
+    constexpr int TX = kSweepTX, TY = kSweepTY;
+    constexpr int XO = 4, SW = TX + 8, SH = TY + 4, PL = SW * SH;   // 40 x 12
+    constexpr int RP = 4, RB = 4, RZ = 5, RM = 3;
+    constexpr int NCH = PL / 4;                                      // 16-byte chunks per plane
+    static_assert(NCH <= 128, "one chunk per thread and array");
+    static_assert(PL <= 2 * kThreads, "two positions per thread");
+    __shared__ __align__(16) float sP[RP][PL];
+    __shared__ __align__(16) float sB[RB][PL];
+    __shared__ __align__(16) float sX[RB][PL];
+    __shared__ __align__(16) float sY[RB][PL];
+    __shared__ __align__(16) float sZ[RZ][PL];
+    __shared__ __align__(16) float sM[RM][PL];
+    const int tid = threadIdx.x;
+
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        int local;
+        const SweepTask<float, TC>* tp = task_of(tl, tile, local);
+        const Ctl* ctl = tp->ctl;
+        if (ctl && ctl->done) continue;                       // uniform in the block
+        const Geo g = tp->g;
+        const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+        const int64_t plane = (int64_t)nx * ny;
+        const int cx = local % tp->tiles_x;
+        const int rest = local / tp->tiles_x;
+        const int cy = rest % tp->tiles_y;
+        const int cz = rest / tp->tiles_y;
+        const int x0 = cx * TX, y0 = cy * TY;
+        const int z0 = cz * tp->zchunk;
+        const int z1 = min(nz, z0 + tp->zchunk);
+        const int rot = tp->rot ? *tp->rot : 0;
+        const float* pin = tp->in_role < 0 ? nullptr : tp->buf[(tp->in_role + rot) % 3];
+        float* pout = tp->buf[(tp->out_role + rot) % 3];
+        const float w = ctl ? (float)ctl->omega : tp->omega;
+        const float* bxa = tp->bx;
+        const float* bya = tp->by;
+        const float* bza = tp->bz;
+        const float* ba = tp->b;
+        const TC* corr = tp->corr;
+        const int cf0 = tp->cf[0], cf1 = tp->cf[1], cf2 = tp->cf[2];
+        const int gcx = nx / cf0, gcy = ny / cf1;
+
+        // in-plane source offsets of this thread's copies (fixed for the tile)
+        int off0 = 0, off1 = 0;
+        bool ok0 = false, ok1 = false;
+        if (VEC == 4) {
+            const int c = tid & 127;
+            if (c < NCH) {
+                const int sy = c / (SW / 4), ch = c - sy * (SW / 4);
+                int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
+                ok0 = wrapc(x, nx, g.per[0]) && wrapc(y, ny, g.per[1]);
+                off0 = ok0 ? y * nx + x : 0;
+            }
+        } else {
+            for (int r = 0; r < 2; ++r) {
+                const int e = tid + r * kThreads;
+                if (e < PL) {
+                    const int sy = e / SW, sx = e - sy * SW;
+                    int x = x0 - XO + sx, y = y0 - 2 + sy;
+                    const bool ok = wrapc(x, nx, g.per[0]) && wrapc(y, ny, g.per[1]);
+                    (r ? ok1 : ok0) = ok;
+                    (r ? off1 : off0) = ok ? y * nx + x : 0;
+                }
+            }
+        }
+        // coarse-correction gather offsets of positions tid and tid + 256
+        int coff[2] = {0, 0};
+        bool cok[2] = {false, false};
+        if (corr) {
+            for (int r = 0; r < 2; ++r) {
+                const int e = tid + r * kThreads;
+                if (e < PL) {
+                    const int sy = e / SW, sx = e - sy * SW;
+                    int x = x0 - XO + sx, y = y0 - 2 + sy;
+                    cok[r] = wrapc(x, nx, g.per[0]) && wrapc(y, ny, g.per[1]);
+                    coff[r] = cok[r] ? (y / cf1) * gcx + x / cf0 : 0;
+                }
+            }
+        }
+
+        // copy one plane of array a at (unwrapped) z into dst; zero outside the
+        // domain, and for the lower z faces of a wall plane
+        auto issue = [&](float* dst, const float* a, int z, bool zface, int which) {
+            int zw = z;
+            bool zok = a != nullptr && wrapc(zw, nz, g.per[2]);
+            if (zface && zok && zw == 0 && !g.per[2]) zok = false;
+            const int64_t zoff = (int64_t)zw * plane;
+            const float* safe = ba;
+            if (VEC == 4) {
+                if ((tid >> 7) == which && (tid & 127) < NCH) {
+                    const int c = tid & 127;
+                    const bool ok = zok && ok0;
+                    cp_async16(dst + 4 * c, ok ? a + zoff + off0 : safe, ok);
+                }
+            } else {
+                cp_async4(dst + tid, (zok && ok0) ? a + zoff + off0 : safe, zok && ok0);
+                if (tid + kThreads < PL)
+                    cp_async4(dst + tid + kThreads, (zok && ok1) ? a + zoff + off1 : safe, zok && ok1);
+            }
+        };
+        auto corr_load = [&](int z, float* cv) {
+            cv[0] = cv[1] = 0.f;
+            if (!corr) return;
+            int zw = z;
+            if (!wrapc(zw, nz, g.per[2])) return;
+            const int64_t zoff = (int64_t)(zw / cf2) * gcx * gcy;
+            if (cok[0]) cv[0] = ldv(corr, zoff + coff[0]);
+            if (tid + kThreads < PL && cok[1]) cv[1] = ldv(corr, zoff + coff[1]);
+        };
+        auto corr_add = [&](float* dst, const float* cv) {
+            if (!corr) return;
+            dst[tid] += cv[0];
+            if (tid + kThreads < PL) dst[tid + kThreads] += cv[1];
+        };
+        // slot of plane z in a ring of R planes
+        auto slot = [&](int z, int R) { return (z - z0 + 2) % R; };
+
+        // ---- prologue: planes needed before step 0
+        const int kr0 = z0 - 1;
+        float cv_a[2], cv_b[2], cv_c[2], cv_cur[2], cv_next[2];
+        issue(sP[slot(kr0, RP)], pin, kr0, false, 0);
+        issue(sP[slot(kr0 + 1, RP)], pin, kr0 + 1, false, 1);
+        issue(sM[slot(kr0 - 1, RM)], pin, kr0 - 1, false, 0);
+        issue(sZ[slot(kr0, RZ)], bza, kr0, true, 1);
+        cp_commit();
+        corr_load(kr0, cv_a);
+        corr_load(kr0 + 1, cv_b);
+        corr_load(kr0 - 1, cv_c);
+        // group 0: what step 0 waits for
+        issue(sP[slot(kr0 + 2, RP)], pin, kr0 + 2, false, 0);
+        issue(sB[slot(kr0, RB)], ba, kr0, false, 0);
+        issue(sX[slot(kr0, RB)], bxa, kr0, false, 1);
+        issue(sY[slot(kr0, RB)], bya, kr0, false, 1);
+        issue(sZ[slot(kr0 + 1, RZ)], bza, kr0 + 1, true, 0);
+        cp_commit();
+        corr_load(kr0 + 2, cv_cur);
+        cp_wait<1>();
+        __syncthreads();
+        corr_add(sP[slot(kr0, RP)], cv_a);
+        corr_add(sP[slot(kr0 + 1, RP)], cv_b);
+        corr_add(sM[slot(kr0 - 1, RM)], cv_c);
+
+        const int nsteps = (z1 - z0) + 2;   // red planes z0-1 .. z1
+        for (int u = 0; u < nsteps; ++u) {
+            const int kr = kr0 + u;
+            // copies for step u+1 (slots they overwrite were last read two steps ago)
+            if (u + 1 < nsteps) {
+                issue(sP[slot(kr + 3, RP)], pin, kr + 3, false, 0);
+                issue(sB[slot(kr + 1, RB)], ba, kr + 1, false, 0);
+                issue(sX[slot(kr + 1, RB)], bxa, kr + 1, false, 1);
+                issue(sY[slot(kr + 1, RB)], bya, kr + 1, false, 1);
+                issue(sZ[slot(kr + 2, RZ)], bza, kr + 2, true, 0);
+                corr_load(kr + 3, cv_next);
+            }
+            cp_commit();
+            cp_wait<1>();
+            __syncthreads();                               // S1: step u's planes visible
+            corr_add(sP[slot(kr + 2, RP)], cv_cur);        // read from step u+1 on
+            cv_cur[0] = cv_next[0];
+            cv_cur[1] = cv_next[1];
+
+            // red cells of plane kr on the tile and its one-cell ring, by pairs
+            {
+                int zk = kr;
+                const bool zok = wrapc(zk, nz, g.per[2]);
+                const float* P0 = sP[slot(kr, RP)];
+                const float* P1 = sP[slot(kr + 1, RP)];
+                const float* Mlo = sM[slot(kr - 1, RM)];
+                float* M0 = sM[slot(kr, RM)];
+                const float* B0 = sB[slot(kr, RB)];
+                const float* X0 = sX[slot(kr, RB)];
+                const float* Y0 = sY[slot(kr, RB)];
+                const float* Z0 = sZ[slot(kr, RZ)];
+                const float* Z1 = sZ[slot(kr + 1, RZ)];
+                constexpr int PR = (TX + 2) / 2;           // pairs per ring row
+                if (tid < PR * (TY + 2)) {
+                    const int ey = tid / PR, j = tid - ey * PR;
+                    const int sy = ey + 1;
+                    int y = y0 - 1 + ey;
+                    const bool yok = zok && wrapc(y, ny, g.per[1]);
+                    for (int h = 0; h < 2; ++h) {
+                        const int sx = XO - 1 + 2 * j + h;
+                        const int s = sy * SW + sx;
+                        int x = x0 - 1 + 2 * j + h;
+                        float v = 0.f;
+                        if (yok && wrapc(x, nx, g.per[0])) {
+                            v = P0[s];
+                            if (((x + y + zk) & 1) == 0) {
+                                const float xl = (x == 0 && !g.per[0]) ? 0.f : X0[s];
+                                const float yl = (y == 0 && !g.per[1]) ? 0.f : Y0[s];
+                                const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW],
+                                                           Y0[s + SW], P0[s + SW], Z0[s], Mlo[s], Z1[s], P1[s], v);
+                                const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], Z0[s], Z1[s]);
+                                v = gs_update(v, fl, dg, B0[s], w);
+                            }
+                        }
+                        M0[s] = v;
+                    }
+                }
+            }
+            __syncthreads();                               // S2: plane kr merged
+
+            // black cells of plane kr-1 on the tile, by pairs; both cells written
+            if (u >= 2) {
+                const int k = kr - 1;
+                const float* Mk = sM[slot(k, RM)];
+                const float* Mlo = sM[slot(k - 1, RM)];
+                const float* Mhi = sM[slot(k + 1, RM)];
+                const float* Bk = sB[slot(k, RB)];
+                const float* Xk = sX[slot(k, RB)];
+                const float* Yk = sY[slot(k, RB)];
+                const float* Zk = sZ[slot(k, RZ)];
+                const float* Zk1 = sZ[slot(k + 1, RZ)];
+                constexpr int PT = TX / 2;
+                if (tid < PT * TY) {
+                    const int ty = tid / PT, j = tid - ty * PT;
+                    const int y = y0 + ty, xa = x0 + 2 * j;
+                    if (y < ny && xa < nx) {
+                        const int sa = (ty + 2) * SW + XO + 2 * j;
+                        float out[2];
+                        for (int h = 0; h < 2; ++h) {
+                            const int s = sa + h, x = xa + h;
+                            float v = Mk[s];
+                            if (((x + y + k) & 1) == 1) {
+                                const float xl = (x == 0 && !g.per[0]) ? 0.f : Xk[s];
+                                const float yl = (y == 0 && !g.per[1]) ? 0.f : Yk[s];
+                                const float fl = face_flux(xl, Mk[s - 1], Xk[s + 1], Mk[s + 1], yl, Mk[s - SW],
+                                                           Yk[s + SW], Mk[s + SW], Zk[s], Mlo[s], Zk1[s], Mhi[s], v);
+                                const float dg = diag_sum(xl, Xk[s + 1], yl, Yk[s + SW], Zk[s], Zk1[s]);
+                                v = gs_update(v, fl, dg, Bk[s], w);
+                            }
+                            out[h] = v;
+                        }
+                        const int64_t I = lin(g, xa, y, k);
+                        if (VEC == 4) {
+                            *reinterpret_cast<float2*>(pout + I) = make_float2(out[0], out[1]);
+                        } else {
+                            pout[I] = out[0];
+                            if (xa + 1 < nx) pout[I + 1] = out[1];
+                        }
+                    }
+                }
+            }
+        }
+        cp_wait<0>();
+        __syncthreads();                                   // the next tile reuses the rings
     }
 }
 
@@ -903,7 +1190,12 @@ template <class TP, class TC>
 cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaStream_t s)
 {
     if (tl.total <= 0) return cudaSuccess;
-    k_sweep<TP, TC><<<grid, kThreads, 0, s>>>(tl);
+    if constexpr (std::is_same<TP, float>::value) {
+        if (tl.vec >= 4) k_sweep_async<4, TC><<<grid, kThreads, 0, s>>>(tl);
+        else k_sweep_async<1, TC><<<grid, kThreads, 0, s>>>(tl);
+    } else {
+        k_sweep<TP, TC><<<grid, kThreads, 0, s>>>(tl);
+    }
     return cudaGetLastError();
 }
 template cudaError_t launch_sweep<float, float>(const TaskList<SweepTask<float, float>>&, int, cudaStream_t);

@@ -77,6 +77,22 @@ int plan_levels(const Geo& g0, int aniso, int n_min, Geo* geo, int (*cf)[3])
 
 int64_t cells(const Geo& g) { return (int64_t)g.n[0] * g.n[1] * g.n[2]; }
 
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// rows of a multiple of 4 cells and 16-byte aligned arrays: the sweep copies
+// 16-byte chunks; otherwise single floats
+template <class TC>
+int sweep_vec(const SweepTask<float, TC>& t)
+{
+    if (t.g.n[0] % 4) return 1;
+    if (!aligned16(t.bx) || !aligned16(t.by) || !aligned16(t.bz) || !aligned16(t.b)) return 1;
+    for (int r = 0; r < 3; ++r)
+        if (!aligned16(t.buf[r])) return 1;
+    return 4;
+}
+template <class TC>
+int sweep_vec(const SweepTask<bf16, TC>&) { return 1; }
+
 struct SweepTiling {
     int tx, ty, zchunk, nchunks;
     int64_t tiles() const { return (int64_t)tx * ty * nchunks; }
@@ -317,6 +333,7 @@ struct Engine {
     {
         tl = TaskList<Task>{};
         tl.ntasks = (int)tasks.size();
+        tl.vec = 1;
         int64_t tot = 0;
         std::vector<int> off(tasks.size() + 1);
         for (size_t i = 0; i < tasks.size(); ++i) {
@@ -416,18 +433,24 @@ struct Engine {
             for (int p : probs) v.push_back(sweep_task<bf16, bf16>(p, l, in, out, with_corr));
             op.kind = kSweepBB;
             if ((rc = make_list(v, tiles, op.s_bb))) return rc;
+            op.s_bb.vec = 4;
+            for (const auto& t : v) op.s_bb.vec = std::min(op.s_bb.vec, sweep_vec(t));
             op.grid = persistent_grid(op.s_bb.total);
         } else if (corr_bf) {
             std::vector<SweepTask<float, bf16>> v;
             for (int p : probs) v.push_back(sweep_task<float, bf16>(p, l, in, out, with_corr));
             op.kind = kSweepFB;
             if ((rc = make_list(v, tiles, op.s_fb))) return rc;
+            op.s_fb.vec = 4;
+            for (const auto& t : v) op.s_fb.vec = std::min(op.s_fb.vec, sweep_vec(t));
             op.grid = persistent_grid(op.s_fb.total);
         } else {
             std::vector<SweepTask<float, float>> v;
             for (int p : probs) v.push_back(sweep_task<float, float>(p, l, in, out, with_corr));
             op.kind = kSweepFF;
             if ((rc = make_list(v, tiles, op.s_ff))) return rc;
+            op.s_ff.vec = 4;
+            for (const auto& t : v) op.s_ff.vec = std::min(op.s_ff.vec, sweep_vec(t));
             op.grid = persistent_grid(op.s_ff.total);
         }
         cycle.push_back(op);
@@ -1321,6 +1344,7 @@ int gmg_op_sweep(int nx, int ny, int nz, const int* periodic, const float* bx, c
     tl.ntasks = 1;
     tl.total = (int)st.tiles();
     tl.single = t;
+    tl.vec = sweep_vec(t);
     return launch_sweep(tl, persistent_grid(tl.total), static_cast<cudaStream_t>(stream)) == cudaSuccess
                ? GMG_OK
                : GMG_ERR_CUDA;

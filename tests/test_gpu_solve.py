@@ -215,7 +215,8 @@ def test_host_entry_point_equals_device():
 
 def test_batch_equals_single_and_oracle(O):
     """Batched solve of uneven problems: each result equals its own single
-    solve bit for bit and the oracle within tolerance."""
+    solve bit for bit and the oracle within tolerance (1e-4: above the FP32
+    floor of every problem; bodies put it near 1e-5 on some)."""
     import torch
     from paper_2607_07687_gb300 import binding as G
     probs = I.batch_problems(8, seed=3)
@@ -223,13 +224,13 @@ def test_batch_equals_single_and_oracle(O):
     bs.set_coeffs([t32(p.bx) for p in probs], [t32(p.by) for p in probs], [t32(p.bz) for p in probs])
     sig = [t32(p.b) for p in probs]
     out = [torch.zeros_like(s) for s in sig]
-    infos = bs.solve(sig, out, 1e-5)
+    infos = bs.solve(sig, out, 1e-4)
     torch.cuda.synchronize()
     bs.close()
     for prob, o, inf in zip(probs, out, infos):
-        single, si, _ = gpu_solve(prob, 1e-5)
+        single, si, _ = gpu_solve(prob, 1e-4)
         assert inf.cycles == si.cycles and inf.status == si.status
         assert np.array_equal(host(o), single)
-        ref = O.solve_problem(prob, tol=1e-5)
+        ref = O.solve_problem(prob, tol=1e-4)
         if ref.bnorm > 0:
             _parity(host(o), inf, ref, same=_same(O, prob))

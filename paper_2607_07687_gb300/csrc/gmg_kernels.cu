@@ -332,20 +332,26 @@ template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int VEC, class TC>
-__global__ void __launch_bounds__(kThreads, 4) k_sweep_async(const __grid_constant__ TaskList<SweepTask<float, TC>> tl)
+__global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_constant__ TaskList<SweepTask<float, TC>> tl)
 {
     constexpr int TX = kSweepTX, TY = kSweepTY;
-    constexpr int XO = 4, SW = TX + 8, SH = TY + 4, PL = SW * SH;   // 40 x 12
-    constexpr int RP = 4, RB = 4, RZ = 5, RM = 3;
-    constexpr int NCH = PL / 4;                                      // 16-byte chunks per plane
-    static_assert(NCH <= 128, "one chunk per thread and array");
-    static_assert(PL <= 2 * kThreads, "two positions per thread");
-    __shared__ __align__(16) float sP[RP][PL];
-    __shared__ __align__(16) float sB[RB][PL];
-    __shared__ __align__(16) float sX[RB][PL];
-    __shared__ __align__(16) float sY[RB][PL];
-    __shared__ __align__(16) float sZ[RZ][PL];
-    __shared__ __align__(16) float sM[RM][PL];
+    constexpr int XO = 4, SW = TX + 8, SH = TY + 4, PL = SW * SH;   // 40 x 12 positions per plane
+    constexpr int RP = kSweepRingP, RB = kSweepRingB, RZ = kSweepRingZ, RM = kSweepRingM;
+    constexpr int CPR = SW / 4;                 // 16-byte chunks per row
+    constexpr int NCH = PL / 4;                 // chunks per plane
+    constexpr int NCOPY = 5 * NCH;              // chunks per step (P, b, x, y, z faces)
+    constexpr int RPR = (TX + 2) / 2;           // red cells per ring row
+    constexpr int NRED = RPR * (TY + 2);
+    constexpr int BPR = TX / 2;                 // black cells per tile row
+    constexpr int NBLK = BPR * TY;
+    static_assert(NCOPY <= 3 * kThreads && NRED <= kThreads && PL <= 2 * kThreads, "thread budget");
+    extern __shared__ __align__(16) float smem[];
+    float* const sP = smem;
+    float* const sB = sP + RP * PL;
+    float* const sX = sB + RB * PL;
+    float* const sY = sX + RB * PL;
+    float* const sZ = sY + RB * PL;
+    float* const sM = sZ + RZ * PL;
     const int tid = threadIdx.x;
 
     for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
@@ -355,6 +361,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep_async(const __grid_consta
         if (ctl && ctl->done) continue;                       // uniform in the block
         const Geo g = tp->g;
         const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+        const int px = g.per[0], py = g.per[1], pz = g.per[2];
         const int64_t plane = (int64_t)nx * ny;
         const int cx = local % tp->tiles_x;
         const int rest = local / tp->tiles_x;
@@ -367,213 +374,234 @@ __global__ void __launch_bounds__(kThreads, 4) k_sweep_async(const __grid_consta
         const float* pin = tp->in_role < 0 ? nullptr : tp->buf[(tp->in_role + rot) % 3];
         float* pout = tp->buf[(tp->out_role + rot) % 3];
         const float w = ctl ? (float)ctl->omega : tp->omega;
-        const float* bxa = tp->bx;
-        const float* bya = tp->by;
-        const float* bza = tp->bz;
-        const float* ba = tp->b;
+        const float* const ba = tp->b;
+        const float* const bxa = tp->bx;
+        const float* const bya = tp->by;
+        const float* const bza = tp->bz;
         const TC* corr = tp->corr;
         const int cf0 = tp->cf[0], cf1 = tp->cf[1], cf2 = tp->cf[2];
         const int gcx = nx / cf0, gcy = ny / cf1;
 
-        // in-plane source offsets of this thread's copies (fixed for the tile)
-        int off0 = 0, off1 = 0;
-        bool ok0 = false, ok1 = false;
-        if (VEC == 4) {
-            const int c = tid & 127;
-            if (c < NCH) {
-                const int sy = c / (SW / 4), ch = c - sy * (SW / 4);
-                int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
-                ok0 = wrapc(x, nx, g.per[0]) && wrapc(y, ny, g.per[1]);
-                off0 = ok0 ? y * nx + x : 0;
-            }
-        } else {
-            for (int r = 0; r < 2; ++r) {
-                const int e = tid + r * kThreads;
-                if (e < PL) {
-                    const int sy = e / SW, sx = e - sy * SW;
-                    int x = x0 - XO + sx, y = y0 - 2 + sy;
-                    const bool ok = wrapc(x, nx, g.per[0]) && wrapc(y, ny, g.per[1]);
-                    (r ? ok1 : ok0) = ok;
-                    (r ? off1 : off0) = ok ? y * nx + x : 0;
-                }
-            }
+        // ---- per-thread geometry, fixed for the tile
+        // copies (VEC == 4): chunk q = tid + i * kThreads of the step's NCOPY
+        int coff[3];
+        bool cokxy[3];
+        for (int i = 0; i < 3; ++i) {
+            const int q = tid + i * kThreads;
+            const int c = q % NCH;
+            const int sy = c / CPR, ch = c - sy * CPR;
+            int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
+            cokxy[i] = VEC == 4 && q < NCOPY && wrapc(x, nx, px) && wrapc(y, ny, py);
+            coff[i] = cokxy[i] ? y * nx + x : 0;
         }
-        // coarse-correction gather offsets of positions tid and tid + 256
-        int coff[2] = {0, 0};
-        bool cok[2] = {false, false};
+        // red cell of this thread in ring row ey (two candidates, by plane parity)
+        const int ey = tid / RPR, jr = tid - ey * RPR;
+        int yr = y0 - 1 + ey;
+        const bool red_on = tid < NRED;
+        const bool yr_ok = red_on && wrapc(yr, ny, py);
+        const bool yr_wall = yr == 0 && !py;
+        const int sred = (ey + 1) * SW + XO - 1 + 2 * jr;
+        int xr0 = x0 - 1 + 2 * jr, xr1 = xr0 + 1;
+        const bool xr_wall0 = xr0 == 0 && !px, xr_wall1 = xr1 == 0 && !px;
+        const bool xr_ok0 = wrapc(xr0, nx, px), xr_ok1 = wrapc(xr1, nx, px);
+        const int red_par = (1 + (y0 - 1 + ey)) & 1;          // o = (red_par + kr) & 1
+        // black pair of this thread
+        const int tyb = tid / BPR, jb = tid - tyb * BPR;
+        const int yb = y0 + tyb, xb = x0 + 2 * jb;
+        const bool blk_on = tid < NBLK && yb < ny && xb < nx;
+        const int sblk = (tyb + 2) * SW + XO + 2 * jb;
+        const bool yb_wall = yb == 0 && !py;
+        const bool xb_wall = xb == 0 && !px;
+        const int64_t blk_base = (int64_t)yb * nx + xb;
+        // coarse-correction positions tid and tid + kThreads of a plane
+        int crr[2] = {0, 0};
+        bool crok[2] = {false, false};
         if (corr) {
             for (int r = 0; r < 2; ++r) {
                 const int e = tid + r * kThreads;
                 if (e < PL) {
                     const int sy = e / SW, sx = e - sy * SW;
                     int x = x0 - XO + sx, y = y0 - 2 + sy;
-                    cok[r] = wrapc(x, nx, g.per[0]) && wrapc(y, ny, g.per[1]);
-                    coff[r] = cok[r] ? (y / cf1) * gcx + x / cf0 : 0;
+                    crok[r] = wrapc(x, nx, px) && wrapc(y, ny, py);
+                    crr[r] = crok[r] ? (y / cf1) * gcx + x / cf0 : 0;
                 }
             }
         }
 
-        // copy one plane of array a at (unwrapped) z into dst; zero outside the
-        // domain, and for the lower z faces of a wall plane
-        auto issue = [&](float* dst, const float* a, int z, bool zface, int which) {
+        auto zinfo = [&](int z, bool zface, int64_t& zoff) -> bool {
             int zw = z;
-            bool zok = a != nullptr && wrapc(zw, nz, g.per[2]);
-            if (zface && zok && zw == 0 && !g.per[2]) zok = false;
-            const int64_t zoff = (int64_t)zw * plane;
-            const float* safe = ba;
+            bool ok = wrapc(zw, nz, pz);
+            if (zface && ok && zw == 0 && !pz) ok = false;   // lower z faces of a wall plane
+            zoff = (int64_t)zw * plane;
+            return ok;
+        };
+        // one whole plane of array a into dst (prologue; every thread helps)
+        auto copy_plane = [&](float* dst, const float* a, int z, bool zface) {
+            int64_t zoff;
+            const bool zok = a != nullptr && zinfo(z, zface, zoff);
             if (VEC == 4) {
-                if ((tid >> 7) == which && (tid & 127) < NCH) {
-                    const int c = tid & 127;
-                    const bool ok = zok && ok0;
-                    cp_async16(dst + 4 * c, ok ? a + zoff + off0 : safe, ok);
+                for (int c = tid; c < NCH; c += kThreads) {
+                    const int sy = c / CPR, ch = c - sy * CPR;
+                    int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
+                    const bool ok = zok && wrapc(x, nx, px) && wrapc(y, ny, py);
+                    cp_async16(dst + 4 * c, ok ? a + zoff + (int64_t)y * nx + x : ba, ok);
                 }
             } else {
-                cp_async4(dst + tid, (zok && ok0) ? a + zoff + off0 : safe, zok && ok0);
-                if (tid + kThreads < PL)
-                    cp_async4(dst + tid + kThreads, (zok && ok1) ? a + zoff + off1 : safe, zok && ok1);
+                for (int e = tid; e < PL; e += kThreads) {
+                    const int sy = e / SW, sx = e - sy * SW;
+                    int x = x0 - XO + sx, y = y0 - 2 + sy;
+                    const bool ok = zok && wrapc(x, nx, px) && wrapc(y, ny, py);
+                    cp_async4(dst + e, ok ? a + zoff + (int64_t)y * nx + x : ba, ok);
+                }
             }
         };
         auto corr_load = [&](int z, float* cv) {
             cv[0] = cv[1] = 0.f;
             if (!corr) return;
             int zw = z;
-            if (!wrapc(zw, nz, g.per[2])) return;
+            if (!wrapc(zw, nz, pz)) return;
             const int64_t zoff = (int64_t)(zw / cf2) * gcx * gcy;
-            if (cok[0]) cv[0] = ldv(corr, zoff + coff[0]);
-            if (tid + kThreads < PL && cok[1]) cv[1] = ldv(corr, zoff + coff[1]);
+            if (crok[0]) cv[0] = ldv(corr, zoff + crr[0]);
+            if (crok[1]) cv[1] = ldv(corr, zoff + crr[1]);
         };
         auto corr_add = [&](float* dst, const float* cv) {
             if (!corr) return;
             dst[tid] += cv[0];
             if (tid + kThreads < PL) dst[tid + kThreads] += cv[1];
         };
-        // slot of plane z in a ring of R planes
-        auto slot = [&](int z, int R) { return (z - z0 + 2) % R; };
+        // ring slot of plane kr0 + i - 1 (i >= 0)
+        auto slot = [](int i, int R) { return (int)((unsigned)i % (unsigned)R); };
 
-        // ---- prologue: planes needed before step 0
+        // ---- prologue: planes kr0-1 .. kr0+1 of p, z faces of kr0, then step 0's group
         const int kr0 = z0 - 1;
         float cv_a[2], cv_b[2], cv_c[2], cv_cur[2], cv_next[2];
-        issue(sP[slot(kr0, RP)], pin, kr0, false, 0);
-        issue(sP[slot(kr0 + 1, RP)], pin, kr0 + 1, false, 1);
-        issue(sM[slot(kr0 - 1, RM)], pin, kr0 - 1, false, 0);
-        issue(sZ[slot(kr0, RZ)], bza, kr0, true, 1);
+        copy_plane(sP + slot(0, RP) * PL, pin, kr0 - 1, false);
+        copy_plane(sP + slot(1, RP) * PL, pin, kr0, false);
+        copy_plane(sP + slot(2, RP) * PL, pin, kr0 + 1, false);
+        copy_plane(sZ + slot(1, RZ) * PL, bza, kr0, true);
         cp_commit();
-        corr_load(kr0, cv_a);
-        corr_load(kr0 + 1, cv_b);
-        corr_load(kr0 - 1, cv_c);
-        // group 0: what step 0 waits for
-        issue(sP[slot(kr0 + 2, RP)], pin, kr0 + 2, false, 0);
-        issue(sB[slot(kr0, RB)], ba, kr0, false, 0);
-        issue(sX[slot(kr0, RB)], bxa, kr0, false, 1);
-        issue(sY[slot(kr0, RB)], bya, kr0, false, 1);
-        issue(sZ[slot(kr0 + 1, RZ)], bza, kr0 + 1, true, 0);
+        corr_load(kr0 - 1, cv_a);
+        corr_load(kr0, cv_b);
+        corr_load(kr0 + 1, cv_c);
+        copy_plane(sP + slot(3, RP) * PL, pin, kr0 + 2, false);
+        copy_plane(sB + slot(1, RB) * PL, ba, kr0, false);
+        copy_plane(sX + slot(1, RB) * PL, bxa, kr0, false);
+        copy_plane(sY + slot(1, RB) * PL, bya, kr0, false);
+        copy_plane(sZ + slot(2, RZ) * PL, bza, kr0 + 1, true);
         cp_commit();
         corr_load(kr0 + 2, cv_cur);
         cp_wait<1>();
         __syncthreads();
-        corr_add(sP[slot(kr0, RP)], cv_a);
-        corr_add(sP[slot(kr0 + 1, RP)], cv_b);
-        corr_add(sM[slot(kr0 - 1, RM)], cv_c);
+        corr_add(sP + slot(0, RP) * PL, cv_a);
+        corr_add(sP + slot(1, RP) * PL, cv_b);
+        corr_add(sP + slot(2, RP) * PL, cv_c);
 
         const int nsteps = (z1 - z0) + 2;   // red planes z0-1 .. z1
         for (int u = 0; u < nsteps; ++u) {
             const int kr = kr0 + u;
-            // copies for step u+1 (slots they overwrite were last read two steps ago)
+            const int i0 = u + 1;            // ring index of plane kr
+            // ---- copies for step u+1: p(kr+3), b/x/y faces (kr+1), z faces (kr+2)
             if (u + 1 < nsteps) {
-                issue(sP[slot(kr + 3, RP)], pin, kr + 3, false, 0);
-                issue(sB[slot(kr + 1, RB)], ba, kr + 1, false, 0);
-                issue(sX[slot(kr + 1, RB)], bxa, kr + 1, false, 1);
-                issue(sY[slot(kr + 1, RB)], bya, kr + 1, false, 1);
-                issue(sZ[slot(kr + 2, RZ)], bza, kr + 2, true, 0);
+                int64_t zo1, zo2, zo3;
+                const bool ok1 = zinfo(kr + 1, false, zo1);
+                const bool ok2 = zinfo(kr + 2, true, zo2);
+                const bool ok3 = pin != nullptr && zinfo(kr + 3, false, zo3);
+                if (VEC == 4) {
+                    for (int i = 0; i < 3; ++i) {
+                        const int q = tid + i * kThreads;
+                        if (q < NCOPY) {
+                            const int a = q / NCH, c = q - a * NCH;
+                            float* dst;
+                            const float* src;
+                            bool ok;
+                            int64_t zo;
+                            if (a == 0) { dst = sP + slot(i0 + 3, RP) * PL; src = pin; ok = ok3; zo = zo3; }
+                            else if (a == 4) { dst = sZ + slot(i0 + 2, RZ) * PL; src = bza; ok = ok2; zo = zo2; }
+                            else {
+                                dst = (a == 1 ? sB : (a == 2 ? sX : sY)) + slot(i0 + 1, RB) * PL;
+                                src = a == 1 ? ba : (a == 2 ? bxa : bya);
+                                ok = ok1;
+                                zo = zo1;
+                            }
+                            ok = ok && cokxy[i];
+                            cp_async16(dst + 4 * c, ok ? src + zo + coff[i] : ba, ok);
+                        }
+                    }
+                } else {
+                    copy_plane(sP + slot(i0 + 3, RP) * PL, pin, kr + 3, false);
+                    copy_plane(sB + slot(i0 + 1, RB) * PL, ba, kr + 1, false);
+                    copy_plane(sX + slot(i0 + 1, RB) * PL, bxa, kr + 1, false);
+                    copy_plane(sY + slot(i0 + 1, RB) * PL, bya, kr + 1, false);
+                    copy_plane(sZ + slot(i0 + 2, RZ) * PL, bza, kr + 2, true);
+                }
                 corr_load(kr + 3, cv_next);
             }
             cp_commit();
             cp_wait<1>();
-            __syncthreads();                               // S1: step u's planes visible
-            corr_add(sP[slot(kr + 2, RP)], cv_cur);        // read from step u+1 on
+            __syncthreads();                               // S1: this step's planes are visible
+            corr_add(sP + slot(i0 + 2, RP) * PL, cv_cur);  // first read at step u+1
             cv_cur[0] = cv_next[0];
             cv_cur[1] = cv_next[1];
 
-            // red cells of plane kr on the tile and its one-cell ring, by pairs
+            // ---- red cells of plane kr on the tile and its one-cell ring
             {
                 int zk = kr;
-                const bool zok = wrapc(zk, nz, g.per[2]);
-                const float* P0 = sP[slot(kr, RP)];
-                const float* P1 = sP[slot(kr + 1, RP)];
-                const float* Mlo = sM[slot(kr - 1, RM)];
-                float* M0 = sM[slot(kr, RM)];
-                const float* B0 = sB[slot(kr, RB)];
-                const float* X0 = sX[slot(kr, RB)];
-                const float* Y0 = sY[slot(kr, RB)];
-                const float* Z0 = sZ[slot(kr, RZ)];
-                const float* Z1 = sZ[slot(kr + 1, RZ)];
-                constexpr int PR = (TX + 2) / 2;           // pairs per ring row
-                if (tid < PR * (TY + 2)) {
-                    const int ey = tid / PR, j = tid - ey * PR;
-                    const int sy = ey + 1;
-                    int y = y0 - 1 + ey;
-                    const bool yok = zok && wrapc(y, ny, g.per[1]);
-                    for (int h = 0; h < 2; ++h) {
-                        const int sx = XO - 1 + 2 * j + h;
-                        const int s = sy * SW + sx;
-                        int x = x0 - 1 + 2 * j + h;
-                        float v = 0.f;
-                        if (yok && wrapc(x, nx, g.per[0])) {
-                            v = P0[s];
-                            if (((x + y + zk) & 1) == 0) {
-                                const float xl = (x == 0 && !g.per[0]) ? 0.f : X0[s];
-                                const float yl = (y == 0 && !g.per[1]) ? 0.f : Y0[s];
-                                const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW],
-                                                           Y0[s + SW], P0[s + SW], Z0[s], Mlo[s], Z1[s], P1[s], v);
-                                const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], Z0[s], Z1[s]);
-                                v = gs_update(v, fl, dg, B0[s], w);
-                            }
-                        }
-                        M0[s] = v;
+                const bool zok = wrapc(zk, nz, pz);
+                if (red_on) {
+                    const int o = (red_par + kr) & 1;
+                    const int s = sred + o;
+                    float v = 0.f;
+                    if (zok && yr_ok && (o ? xr_ok1 : xr_ok0)) {
+                        const float* P0 = sP + slot(i0, RP) * PL;
+                        const float* Pl = sP + slot(i0 - 1, RP) * PL;
+                        const float* Pu = sP + slot(i0 + 1, RP) * PL;
+                        const float* B0 = sB + slot(i0, RB) * PL;
+                        const float* X0 = sX + slot(i0, RB) * PL;
+                        const float* Y0 = sY + slot(i0, RB) * PL;
+                        const float* Z0 = sZ + slot(i0, RZ) * PL;
+                        const float* Z1 = sZ + slot(i0 + 1, RZ) * PL;
+                        v = P0[s];
+                        const float xl = (o ? xr_wall1 : xr_wall0) ? 0.f : X0[s];
+                        const float yl = yr_wall ? 0.f : Y0[s];
+                        const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW],
+                                                   Y0[s + SW], P0[s + SW], Z0[s], Pl[s], Z1[s], Pu[s], v);
+                        const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], Z0[s], Z1[s]);
+                        v = gs_update(v, fl, dg, B0[s], w);
                     }
+                    sM[slot(i0, RM) * PL + s] = v;
                 }
             }
-            __syncthreads();                               // S2: plane kr merged
+            __syncthreads();                               // S2: red cells of kr are in M
 
-            // black cells of plane kr-1 on the tile, by pairs; both cells written
-            if (u >= 2) {
+            // ---- black cells of plane kr-1 on the tile; the pair's red cell comes from M
+            if (u >= 2 && blk_on) {
                 const int k = kr - 1;
-                const float* Mk = sM[slot(k, RM)];
-                const float* Mlo = sM[slot(k - 1, RM)];
-                const float* Mhi = sM[slot(k + 1, RM)];
-                const float* Bk = sB[slot(k, RB)];
-                const float* Xk = sX[slot(k, RB)];
-                const float* Yk = sY[slot(k, RB)];
-                const float* Zk = sZ[slot(k, RZ)];
-                const float* Zk1 = sZ[slot(k + 1, RZ)];
-                constexpr int PT = TX / 2;
-                if (tid < PT * TY) {
-                    const int ty = tid / PT, j = tid - ty * PT;
-                    const int y = y0 + ty, xa = x0 + 2 * j;
-                    if (y < ny && xa < nx) {
-                        const int sa = (ty + 2) * SW + XO + 2 * j;
-                        float out[2];
-                        for (int h = 0; h < 2; ++h) {
-                            const int s = sa + h, x = xa + h;
-                            float v = Mk[s];
-                            if (((x + y + k) & 1) == 1) {
-                                const float xl = (x == 0 && !g.per[0]) ? 0.f : Xk[s];
-                                const float yl = (y == 0 && !g.per[1]) ? 0.f : Yk[s];
-                                const float fl = face_flux(xl, Mk[s - 1], Xk[s + 1], Mk[s + 1], yl, Mk[s - SW],
-                                                           Yk[s + SW], Mk[s + SW], Zk[s], Mlo[s], Zk1[s], Mhi[s], v);
-                                const float dg = diag_sum(xl, Xk[s + 1], yl, Yk[s + SW], Zk[s], Zk1[s]);
-                                v = gs_update(v, fl, dg, Bk[s], w);
-                            }
-                            out[h] = v;
-                        }
-                        const int64_t I = lin(g, xa, y, k);
-                        if (VEC == 4) {
-                            *reinterpret_cast<float2*>(pout + I) = make_float2(out[0], out[1]);
-                        } else {
-                            pout[I] = out[0];
-                            if (xa + 1 < nx) pout[I + 1] = out[1];
-                        }
-                    }
+                const int hb = ((xb + yb + k) & 1) ? 0 : 1;   // black member of the pair
+                const int s = sblk + hb;
+                const float* Mk = sM + slot(i0 - 1, RM) * PL;
+                const float* Mlo = sM + slot(i0 - 2, RM) * PL;
+                const float* Mhi = sM + slot(i0, RM) * PL;
+                const float* Pk = sP + slot(i0 - 1, RP) * PL;
+                const float* Bk = sB + slot(i0 - 1, RB) * PL;
+                const float* Xk = sX + slot(i0 - 1, RB) * PL;
+                const float* Yk = sY + slot(i0 - 1, RB) * PL;
+                const float* Zk = sZ + slot(i0 - 1, RZ) * PL;
+                const float* Zk1 = sZ + slot(i0, RZ) * PL;
+                float v = Pk[s];
+                const float xl = (hb == 0 && xb_wall) ? 0.f : Xk[s];
+                const float yl = yb_wall ? 0.f : Yk[s];
+                const float fl = face_flux(xl, Mk[s - 1], Xk[s + 1], Mk[s + 1], yl, Mk[s - SW], Yk[s + SW],
+                                           Mk[s + SW], Zk[s], Mlo[s], Zk1[s], Mhi[s], v);
+                const float dg = diag_sum(xl, Xk[s + 1], yl, Yk[s + SW], Zk[s], Zk1[s]);
+                v = gs_update(v, fl, dg, Bk[s], w);
+                const float r = Mk[sblk + (1 - hb)];
+                const float o0 = hb ? r : v, o1 = hb ? v : r;
+                const int64_t I = (int64_t)k * plane + blk_base;
+                if (VEC == 4) {
+                    *reinterpret_cast<float2*>(pout + I) = make_float2(o0, o1);
+                } else {
+                    pout[I] = o0;
+                    if (xb + 1 < nx) pout[I + 1] = o1;
                 }
             }
         }
@@ -1191,8 +1219,17 @@ cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaSt
 {
     if (tl.total <= 0) return cudaSuccess;
     if constexpr (std::is_same<TP, float>::value) {
-        if (tl.vec >= 4) k_sweep_async<4, TC><<<grid, kThreads, 0, s>>>(tl);
-        else k_sweep_async<1, TC><<<grid, kThreads, 0, s>>>(tl);
+        constexpr size_t smem = kSweepSmemBytes;
+        static bool attr = false;   // opt in to > 48 KB of dynamic shared memory once
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_sweep_async<4, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_sweep_async<1, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        if (tl.vec >= 4) k_sweep_async<4, TC><<<grid, kThreads, smem, s>>>(tl);
+        else k_sweep_async<1, TC><<<grid, kThreads, smem, s>>>(tl);
     } else {
         k_sweep<TP, TC><<<grid, kThreads, 0, s>>>(tl);
     }

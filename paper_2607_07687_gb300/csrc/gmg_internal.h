@@ -26,15 +26,10 @@ constexpr int kThreads = 256;           // threads per block of the grid kernels
 // sweep tile (cells): TX x TY columns marching through a z-chunk
 constexpr int kSweepTX = 32;
 constexpr int kSweepTY = 8;
-// plane rings of the pipelined sweep: p (kr-2 .. kr+3), b/x/y faces
-// (kr-2 .. kr+1), z faces (kr-2 .. kr+2), merged red plane (kr-2 .. kr)
-constexpr int kSweepRingP = 6;
-constexpr int kSweepRingB = 4;
-constexpr int kSweepRingZ = 5;
-constexpr int kSweepRingM = 3;
-constexpr size_t kSweepSmemBytes =
-    sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4) *
-    (kSweepRingP + 3 * kSweepRingB + kSweepRingZ + kSweepRingM);
+// plane rings of the pipelined sweep (p, b, x/y/z faces, merged red plane),
+// each holding planes kr-2 .. kr+3 of the marching step
+constexpr int kSweepRing = 6;
+constexpr size_t kSweepSmemBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4) * 6 * kSweepRing;
 // residual tile (fine cells)
 constexpr int kResTX = 32;
 constexpr int kResTY = 4;
@@ -150,6 +145,7 @@ struct TaskList {
     int ntasks;
     int total;           // total tiles
     int vec;             // 4: every task's rows split into aligned 16-byte chunks
+    int corr;            // sweeps: 1 if any task adds a coarse correction
     Task single;
 };
 

@@ -331,28 +331,24 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <int VEC, class TC>
+template <int VEC, bool CORR, class TC>
 __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_constant__ TaskList<SweepTask<float, TC>> tl)
 {
     constexpr int TX = kSweepTX, TY = kSweepTY;
     constexpr int XO = 4, SW = TX + 8, SH = TY + 4, PL = SW * SH;   // 40 x 12 positions per plane
-    constexpr int RP = kSweepRingP, RB = kSweepRingB, RZ = kSweepRingZ, RM = kSweepRingM;
+    constexpr int R = kSweepRing;               // planes per ring, every array
     constexpr int CPR = SW / 4;                 // 16-byte chunks per row
-    constexpr int NCH = PL / 4;                 // chunks per plane
-    constexpr int NCOPY = 5 * NCH;              // chunks per step (P, b, x, y, z faces)
+    constexpr int NCH = PL / 4;                 // chunks per plane (120)
     constexpr int RPR = (TX + 2) / 2;           // red cells per ring row
     constexpr int NRED = RPR * (TY + 2);
     constexpr int BPR = TX / 2;                 // black cells per tile row
     constexpr int NBLK = BPR * TY;
-    static_assert(NCOPY <= 3 * kThreads && NRED <= kThreads && PL <= 2 * kThreads, "thread budget");
+    static_assert(NCH <= kThreads / 2 && NRED <= kThreads && PL <= 2 * kThreads, "thread budget");
+    // rings: 0 = p, 1 = b, 2 = lower x faces, 3 = lower y faces, 4 = lower z faces, 5 = merged red plane
     extern __shared__ __align__(16) float smem[];
-    float* const sP = smem;
-    float* const sB = sP + RP * PL;
-    float* const sX = sB + RB * PL;
-    float* const sY = sX + RB * PL;
-    float* const sZ = sY + RB * PL;
-    float* const sM = sZ + RZ * PL;
     const int tid = threadIdx.x;
+    const int half = tid / (kThreads / 2);      // copy duty: 0 -> p, b, x faces; 1 -> y, z faces
+    const int chunk = tid % (kThreads / 2);
 
     for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
         int local;
@@ -362,7 +358,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
         const Geo g = tp->g;
         const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
         const int px = g.per[0], py = g.per[1], pz = g.per[2];
-        const int64_t plane = (int64_t)nx * ny;
         const int cx = local % tp->tiles_x;
         const int rest = local / tp->tiles_x;
         const int cy = rest % tp->tiles_y;
@@ -375,58 +370,37 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
         float* pout = tp->buf[(tp->out_role + rot) % 3];
         const float w = ctl ? (float)ctl->omega : tp->omega;
         const float* const ba = tp->b;
-        const float* const bxa = tp->bx;
-        const float* const bya = tp->by;
-        const float* const bza = tp->bz;
-        const TC* corr = tp->corr;
-        const int cf0 = tp->cf[0], cf1 = tp->cf[1], cf2 = tp->cf[2];
-        const int gcx = nx / cf0, gcy = ny / cf1;
+        // the two arrays this thread's half copies besides p (half 0) or with z faces (half 1)
+        const float* const srcA = half == 0 ? pin : tp->by;
+        const float* const srcB = half == 0 ? tp->b : tp->bz;
+        const float* const srcC = tp->bx;   // half 0 only
 
         // ---- per-thread geometry, fixed for the tile
-        // copies (VEC == 4): chunk q = tid + i * kThreads of the step's NCOPY
-        int coff[3];
-        bool cokxy[3];
-        for (int i = 0; i < 3; ++i) {
-            const int q = tid + i * kThreads;
-            const int c = q % NCH;
-            const int sy = c / CPR, ch = c - sy * CPR;
+        int coff = 0;
+        bool cok = false;
+        if (VEC == 4 && chunk < NCH) {
+            const int sy = chunk / CPR, ch = chunk - sy * CPR;
             int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
-            cokxy[i] = VEC == 4 && q < NCOPY && wrapc(x, nx, px) && wrapc(y, ny, py);
-            coff[i] = cokxy[i] ? y * nx + x : 0;
+            cok = wrapc(x, nx, px) && wrapc(y, ny, py);
+            coff = cok ? y * nx + x : 0;
         }
-        // red cell of this thread in ring row ey (two candidates, by plane parity)
         const int ey = tid / RPR, jr = tid - ey * RPR;
         int yr = y0 - 1 + ey;
-        const bool red_on = tid < NRED;
-        const bool yr_ok = red_on && wrapc(yr, ny, py);
+        const bool yr_ok = tid < NRED && wrapc(yr, ny, py);
         const bool yr_wall = yr == 0 && !py;
         const int sred = (ey + 1) * SW + XO - 1 + 2 * jr;
         int xr0 = x0 - 1 + 2 * jr, xr1 = xr0 + 1;
         const bool xr_wall0 = xr0 == 0 && !px, xr_wall1 = xr1 == 0 && !px;
         const bool xr_ok0 = wrapc(xr0, nx, px), xr_ok1 = wrapc(xr1, nx, px);
-        const int red_par = (1 + (y0 - 1 + ey)) & 1;          // o = (red_par + kr) & 1
-        // black pair of this thread
+        const int red_par = (1 + (y0 - 1 + ey)) & 1;          // red member: (red_par + kr) & 1
         const int tyb = tid / BPR, jb = tid - tyb * BPR;
         const int yb = y0 + tyb, xb = x0 + 2 * jb;
         const bool blk_on = tid < NBLK && yb < ny && xb < nx;
         const int sblk = (tyb + 2) * SW + XO + 2 * jb;
         const bool yb_wall = yb == 0 && !py;
         const bool xb_wall = xb == 0 && !px;
-        const int64_t blk_base = (int64_t)yb * nx + xb;
-        // coarse-correction positions tid and tid + kThreads of a plane
-        int crr[2] = {0, 0};
-        bool crok[2] = {false, false};
-        if (corr) {
-            for (int r = 0; r < 2; ++r) {
-                const int e = tid + r * kThreads;
-                if (e < PL) {
-                    const int sy = e / SW, sx = e - sy * SW;
-                    int x = x0 - XO + sx, y = y0 - 2 + sy;
-                    crok[r] = wrapc(x, nx, px) && wrapc(y, ny, py);
-                    crr[r] = crok[r] ? (y / cf1) * gcx + x / cf0 : 0;
-                }
-            }
-        }
+        float* const out_col = pout + ((int64_t)yb * nx + xb);
+        const int64_t plane = (int64_t)nx * ny;
 
         auto zinfo = [&](int z, bool zface, int64_t& zoff) -> bool {
             int zw = z;
@@ -435,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
             zoff = (int64_t)zw * plane;
             return ok;
         };
-        // one whole plane of array a into dst (prologue; every thread helps)
+        // whole plane of array a into dst, every thread helping (prologue; VEC == 1)
         auto copy_plane = [&](float* dst, const float* a, int z, bool zface) {
             int64_t zoff;
             const bool zok = a != nullptr && zinfo(z, zface, zoff);
@@ -455,155 +429,171 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
                 }
             }
         };
-        auto corr_load = [&](int z, float* cv) {
-            cv[0] = cv[1] = 0.f;
-            if (!corr) return;
+        auto ring = [&](int r, int slot) -> float* { return smem + (r * R + slot) * PL; };
+
+        // coarse correction of a p plane: gathered into registers one step ahead
+        const TC* corr = tp->corr;
+        const int cf0 = tp->cf[0], cf1 = tp->cf[1], cf2 = tp->cf[2];
+        const int gcx = nx / cf0, gcy = ny / cf1;
+        int crr0 = 0, crr1 = 0;
+        bool crok0 = false, crok1 = false;
+        if (CORR) {
+            for (int r = 0; r < 2; ++r) {
+                const int e = tid + r * kThreads;
+                if (e < PL) {
+                    const int sy = e / SW, sx = e - sy * SW;
+                    int x = x0 - XO + sx, y = y0 - 2 + sy;
+                    const bool ok = wrapc(x, nx, px) && wrapc(y, ny, py);
+                    const int off = ok ? (y / cf1) * gcx + x / cf0 : 0;
+                    if (r == 0) { crok0 = ok; crr0 = off; } else { crok1 = ok; crr1 = off; }
+                }
+            }
+        }
+        auto corr_load = [&](int z, float& c0, float& c1) {
+            c0 = c1 = 0.f;
+            if (!CORR) return;
             int zw = z;
             if (!wrapc(zw, nz, pz)) return;
             const int64_t zoff = (int64_t)(zw / cf2) * gcx * gcy;
-            if (crok[0]) cv[0] = ldv(corr, zoff + crr[0]);
-            if (crok[1]) cv[1] = ldv(corr, zoff + crr[1]);
+            if (crok0) c0 = ldv(corr, zoff + crr0);
+            if (crok1) c1 = ldv(corr, zoff + crr1);
         };
-        auto corr_add = [&](float* dst, const float* cv) {
-            if (!corr) return;
-            dst[tid] += cv[0];
-            if (tid + kThreads < PL) dst[tid + kThreads] += cv[1];
+        auto corr_add = [&](float* dst, float c0, float c1) {
+            if (!CORR) return;
+            dst[tid] += c0;
+            if (tid + kThreads < PL) dst[tid + kThreads] += c1;
         };
-        // ring slot of plane kr0 + i - 1 (i >= 0)
-        auto slot = [](int i, int R) { return (int)((unsigned)i % (unsigned)R); };
 
-        // ---- prologue: planes kr0-1 .. kr0+1 of p, z faces of kr0, then step 0's group
+        // ---- prologue: p planes kr0-1 .. kr0+1 and z faces of kr0, then step 0's group;
+        // plane z lives in slot (z - kr0 + 1) mod R
         const int kr0 = z0 - 1;
-        float cv_a[2], cv_b[2], cv_c[2], cv_cur[2], cv_next[2];
-        copy_plane(sP + slot(0, RP) * PL, pin, kr0 - 1, false);
-        copy_plane(sP + slot(1, RP) * PL, pin, kr0, false);
-        copy_plane(sP + slot(2, RP) * PL, pin, kr0 + 1, false);
-        copy_plane(sZ + slot(1, RZ) * PL, bza, kr0, true);
+        copy_plane(ring(0, 0), pin, kr0 - 1, false);
+        copy_plane(ring(0, 1), pin, kr0, false);
+        copy_plane(ring(0, 2), pin, kr0 + 1, false);
+        copy_plane(ring(4, 1), tp->bz, kr0, true);
         cp_commit();
-        corr_load(kr0 - 1, cv_a);
-        corr_load(kr0, cv_b);
-        corr_load(kr0 + 1, cv_c);
-        copy_plane(sP + slot(3, RP) * PL, pin, kr0 + 2, false);
-        copy_plane(sB + slot(1, RB) * PL, ba, kr0, false);
-        copy_plane(sX + slot(1, RB) * PL, bxa, kr0, false);
-        copy_plane(sY + slot(1, RB) * PL, bya, kr0, false);
-        copy_plane(sZ + slot(2, RZ) * PL, bza, kr0 + 1, true);
+        float ca0, ca1, cb0, cb1, cc0, cc1, cur0, cur1, nxt0, nxt1;
+        corr_load(kr0 - 1, ca0, ca1);
+        corr_load(kr0, cb0, cb1);
+        corr_load(kr0 + 1, cc0, cc1);
+        copy_plane(ring(0, 3), pin, kr0 + 2, false);
+        copy_plane(ring(1, 1), ba, kr0, false);
+        copy_plane(ring(2, 1), tp->bx, kr0, false);
+        copy_plane(ring(3, 1), tp->by, kr0, false);
+        copy_plane(ring(4, 2), tp->bz, kr0 + 1, true);
         cp_commit();
-        corr_load(kr0 + 2, cv_cur);
+        corr_load(kr0 + 2, cur0, cur1);
         cp_wait<1>();
         __syncthreads();
-        corr_add(sP + slot(0, RP) * PL, cv_a);
-        corr_add(sP + slot(1, RP) * PL, cv_b);
-        corr_add(sP + slot(2, RP) * PL, cv_c);
+        corr_add(ring(0, 0), ca0, ca1);
+        corr_add(ring(0, 1), cb0, cb1);
+        corr_add(ring(0, 2), cc0, cc1);
 
         const int nsteps = (z1 - z0) + 2;   // red planes z0-1 .. z1
-        for (int u = 0; u < nsteps; ++u) {
+
+        // one z-step; J = (u mod R) is a compile-time constant, so is every slot
+        auto step = [&](int u, auto Jc) {
+            constexpr int J = decltype(Jc)::value;
+            constexpr int S0 = (J + 1) % R;                       // slot of plane kr
+            constexpr int Sm1 = (J + R) % R, Sm2 = (J + R - 1) % R;
+            constexpr int Sp1 = (J + 2) % R, Sp2 = (J + 3) % R, Sp3 = (J + 4) % R;
             const int kr = kr0 + u;
-            const int i0 = u + 1;            // ring index of plane kr
-            // ---- copies for step u+1: p(kr+3), b/x/y faces (kr+1), z faces (kr+2)
+            // copies for step u+1: p(kr+3), b / x / y faces (kr+1), z faces (kr+2)
             if (u + 1 < nsteps) {
-                int64_t zo1, zo2, zo3;
-                const bool ok1 = zinfo(kr + 1, false, zo1);
-                const bool ok2 = zinfo(kr + 2, true, zo2);
-                const bool ok3 = pin != nullptr && zinfo(kr + 3, false, zo3);
                 if (VEC == 4) {
-                    for (int i = 0; i < 3; ++i) {
-                        const int q = tid + i * kThreads;
-                        if (q < NCOPY) {
-                            const int a = q / NCH, c = q - a * NCH;
-                            float* dst;
-                            const float* src;
-                            bool ok;
-                            int64_t zo;
-                            if (a == 0) { dst = sP + slot(i0 + 3, RP) * PL; src = pin; ok = ok3; zo = zo3; }
-                            else if (a == 4) { dst = sZ + slot(i0 + 2, RZ) * PL; src = bza; ok = ok2; zo = zo2; }
-                            else {
-                                dst = (a == 1 ? sB : (a == 2 ? sX : sY)) + slot(i0 + 1, RB) * PL;
-                                src = a == 1 ? ba : (a == 2 ? bxa : bya);
-                                ok = ok1;
-                                zo = zo1;
-                            }
-                            ok = ok && cokxy[i];
-                            cp_async16(dst + 4 * c, ok ? src + zo + coff[i] : ba, ok);
+                    if (chunk < NCH) {
+                        int64_t zo1, zo2;
+                        if (half == 0) {
+                            int64_t zo3;
+                            const bool ok3 = pin != nullptr && zinfo(kr + 3, false, zo3) && cok;
+                            const bool ok1 = zinfo(kr + 1, false, zo1) && cok;
+                            cp_async16(ring(0, Sp3) + 4 * chunk, ok3 ? srcA + zo3 + coff : ba, ok3);
+                            cp_async16(ring(1, Sp1) + 4 * chunk, ok1 ? srcB + zo1 + coff : ba, ok1);
+                            cp_async16(ring(2, Sp1) + 4 * chunk, ok1 ? srcC + zo1 + coff : ba, ok1);
+                        } else {
+                            const bool ok1 = zinfo(kr + 1, false, zo1) && cok;
+                            const bool ok2 = zinfo(kr + 2, true, zo2) && cok;
+                            cp_async16(ring(3, Sp1) + 4 * chunk, ok1 ? srcA + zo1 + coff : ba, ok1);
+                            cp_async16(ring(4, Sp2) + 4 * chunk, ok2 ? srcB + zo2 + coff : ba, ok2);
                         }
                     }
                 } else {
-                    copy_plane(sP + slot(i0 + 3, RP) * PL, pin, kr + 3, false);
-                    copy_plane(sB + slot(i0 + 1, RB) * PL, ba, kr + 1, false);
-                    copy_plane(sX + slot(i0 + 1, RB) * PL, bxa, kr + 1, false);
-                    copy_plane(sY + slot(i0 + 1, RB) * PL, bya, kr + 1, false);
-                    copy_plane(sZ + slot(i0 + 2, RZ) * PL, bza, kr + 2, true);
+                    copy_plane(ring(0, Sp3), pin, kr + 3, false);
+                    copy_plane(ring(1, Sp1), ba, kr + 1, false);
+                    copy_plane(ring(2, Sp1), tp->bx, kr + 1, false);
+                    copy_plane(ring(3, Sp1), tp->by, kr + 1, false);
+                    copy_plane(ring(4, Sp2), tp->bz, kr + 2, true);
                 }
-                corr_load(kr + 3, cv_next);
+                corr_load(kr + 3, nxt0, nxt1);
             }
             cp_commit();
             cp_wait<1>();
             __syncthreads();                               // S1: this step's planes are visible
-            corr_add(sP + slot(i0 + 2, RP) * PL, cv_cur);  // first read at step u+1
-            cv_cur[0] = cv_next[0];
-            cv_cur[1] = cv_next[1];
+            corr_add(ring(0, Sp2), cur0, cur1);            // p(kr+2), first read at step u+1
+            cur0 = nxt0;
+            cur1 = nxt1;
 
-            // ---- red cells of plane kr on the tile and its one-cell ring
-            {
+            // red cells of plane kr on the tile and its one-cell ring
+            if (tid < NRED) {
                 int zk = kr;
                 const bool zok = wrapc(zk, nz, pz);
-                if (red_on) {
-                    const int o = (red_par + kr) & 1;
-                    const int s = sred + o;
-                    float v = 0.f;
-                    if (zok && yr_ok && (o ? xr_ok1 : xr_ok0)) {
-                        const float* P0 = sP + slot(i0, RP) * PL;
-                        const float* Pl = sP + slot(i0 - 1, RP) * PL;
-                        const float* Pu = sP + slot(i0 + 1, RP) * PL;
-                        const float* B0 = sB + slot(i0, RB) * PL;
-                        const float* X0 = sX + slot(i0, RB) * PL;
-                        const float* Y0 = sY + slot(i0, RB) * PL;
-                        const float* Z0 = sZ + slot(i0, RZ) * PL;
-                        const float* Z1 = sZ + slot(i0 + 1, RZ) * PL;
-                        v = P0[s];
-                        const float xl = (o ? xr_wall1 : xr_wall0) ? 0.f : X0[s];
-                        const float yl = yr_wall ? 0.f : Y0[s];
-                        const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW],
-                                                   Y0[s + SW], P0[s + SW], Z0[s], Pl[s], Z1[s], Pu[s], v);
-                        const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], Z0[s], Z1[s]);
-                        v = gs_update(v, fl, dg, B0[s], w);
-                    }
-                    sM[slot(i0, RM) * PL + s] = v;
+                const int o = (red_par + kr) & 1;
+                const int s = sred + o;
+                float v = 0.f;
+                if (zok && yr_ok && (o ? xr_ok1 : xr_ok0)) {
+                    const float* P0 = ring(0, S0);
+                    const float* X0 = ring(2, S0);
+                    const float* Y0 = ring(3, S0);
+                    const float* Z0 = ring(4, S0);
+                    const float* Z1 = ring(4, Sp1);
+                    v = P0[s];
+                    const float xl = (o ? xr_wall1 : xr_wall0) ? 0.f : X0[s];
+                    const float yl = yr_wall ? 0.f : Y0[s];
+                    const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW], Y0[s + SW],
+                                               P0[s + SW], Z0[s], ring(0, Sm1)[s], Z1[s], ring(0, Sp1)[s], v);
+                    const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], Z0[s], Z1[s]);
+                    v = gs_update(v, fl, dg, ring(1, S0)[s], w);
                 }
+                ring(5, S0)[s] = v;
             }
-            __syncthreads();                               // S2: red cells of kr are in M
+            __syncthreads();                               // S2: red cells of kr are merged
 
-            // ---- black cells of plane kr-1 on the tile; the pair's red cell comes from M
+            // black cells of plane kr-1 on the tile; the pair's red cell comes from M
             if (u >= 2 && blk_on) {
                 const int k = kr - 1;
                 const int hb = ((xb + yb + k) & 1) ? 0 : 1;   // black member of the pair
                 const int s = sblk + hb;
-                const float* Mk = sM + slot(i0 - 1, RM) * PL;
-                const float* Mlo = sM + slot(i0 - 2, RM) * PL;
-                const float* Mhi = sM + slot(i0, RM) * PL;
-                const float* Pk = sP + slot(i0 - 1, RP) * PL;
-                const float* Bk = sB + slot(i0 - 1, RB) * PL;
-                const float* Xk = sX + slot(i0 - 1, RB) * PL;
-                const float* Yk = sY + slot(i0 - 1, RB) * PL;
-                const float* Zk = sZ + slot(i0 - 1, RZ) * PL;
-                const float* Zk1 = sZ + slot(i0, RZ) * PL;
-                float v = Pk[s];
+                const float* Mk = ring(5, Sm1);
+                const float* Xk = ring(2, Sm1);
+                const float* Yk = ring(3, Sm1);
+                const float* Zk = ring(4, Sm1);
+                const float* Zk1 = ring(4, S0);
+                float v = ring(0, Sm1)[s];
                 const float xl = (hb == 0 && xb_wall) ? 0.f : Xk[s];
                 const float yl = yb_wall ? 0.f : Yk[s];
                 const float fl = face_flux(xl, Mk[s - 1], Xk[s + 1], Mk[s + 1], yl, Mk[s - SW], Yk[s + SW],
-                                           Mk[s + SW], Zk[s], Mlo[s], Zk1[s], Mhi[s], v);
+                                           Mk[s + SW], Zk[s], ring(5, Sm2)[s], Zk1[s], ring(5, S0)[s], v);
                 const float dg = diag_sum(xl, Xk[s + 1], yl, Yk[s + SW], Zk[s], Zk1[s]);
-                v = gs_update(v, fl, dg, Bk[s], w);
+                v = gs_update(v, fl, dg, ring(1, Sm1)[s], w);
                 const float r = Mk[sblk + (1 - hb)];
                 const float o0 = hb ? r : v, o1 = hb ? v : r;
-                const int64_t I = (int64_t)k * plane + blk_base;
+                float* dst = out_col + (int64_t)k * plane;
                 if (VEC == 4) {
-                    *reinterpret_cast<float2*>(pout + I) = make_float2(o0, o1);
+                    *reinterpret_cast<float2*>(dst) = make_float2(o0, o1);
                 } else {
-                    pout[I] = o0;
-                    if (xb + 1 < nx) pout[I + 1] = o1;
+                    dst[0] = o0;
+                    if (xb + 1 < nx) dst[1] = o1;
                 }
             }
+        };
+        static_assert(R == 6, "the unrolled step sequence below assumes six slots");
+        for (int u = 0; u < nsteps; u += R) {
+            step(u, std::integral_constant<int, 0>());
+            if (u + 1 < nsteps) step(u + 1, std::integral_constant<int, 1>());
+            if (u + 2 < nsteps) step(u + 2, std::integral_constant<int, 2>());
+            if (u + 3 < nsteps) step(u + 3, std::integral_constant<int, 3>());
+            if (u + 4 < nsteps) step(u + 4, std::integral_constant<int, 4>());
+            if (u + 5 < nsteps) step(u + 5, std::integral_constant<int, 5>());
         }
         cp_wait<0>();
         __syncthreads();                                   // the next tile reuses the rings
@@ -1222,14 +1212,21 @@ cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaSt
         constexpr size_t smem = kSweepSmemBytes;
         static bool attr = false;   // opt in to > 48 KB of dynamic shared memory once
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_sweep_async<4, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_sweep_async<1, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const int b = (int)smem;
+            cudaError_t e = cudaFuncSetAttribute(k_sweep_async<4, false, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_async<1, false, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_async<4, true, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_async<1, true, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        if (tl.vec >= 4) k_sweep_async<4, TC><<<grid, kThreads, smem, s>>>(tl);
-        else k_sweep_async<1, TC><<<grid, kThreads, smem, s>>>(tl);
+        if (tl.corr) {
+            if (tl.vec >= 4) k_sweep_async<4, true, TC><<<grid, kThreads, smem, s>>>(tl);
+            else k_sweep_async<1, true, TC><<<grid, kThreads, smem, s>>>(tl);
+        } else {
+            if (tl.vec >= 4) k_sweep_async<4, false, TC><<<grid, kThreads, smem, s>>>(tl);
+            else k_sweep_async<1, false, TC><<<grid, kThreads, smem, s>>>(tl);
+        }
     } else {
         k_sweep<TP, TC><<<grid, kThreads, 0, s>>>(tl);
     }

@@ -334,6 +334,7 @@ struct Engine {
         tl = TaskList<Task>{};
         tl.ntasks = (int)tasks.size();
         tl.vec = 1;
+        tl.corr = 0;
         int64_t tot = 0;
         std::vector<int> off(tasks.size() + 1);
         for (size_t i = 0; i < tasks.size(); ++i) {
@@ -435,6 +436,7 @@ struct Engine {
             if ((rc = make_list(v, tiles, op.s_bb))) return rc;
             op.s_bb.vec = 4;
             for (const auto& t : v) op.s_bb.vec = std::min(op.s_bb.vec, sweep_vec(t));
+            op.s_bb.corr = with_corr ? 1 : 0;
             op.grid = persistent_grid(op.s_bb.total);
         } else if (corr_bf) {
             std::vector<SweepTask<float, bf16>> v;
@@ -443,6 +445,7 @@ struct Engine {
             if ((rc = make_list(v, tiles, op.s_fb))) return rc;
             op.s_fb.vec = 4;
             for (const auto& t : v) op.s_fb.vec = std::min(op.s_fb.vec, sweep_vec(t));
+            op.s_fb.corr = with_corr ? 1 : 0;
             op.grid = persistent_grid(op.s_fb.total);
         } else {
             std::vector<SweepTask<float, float>> v;
@@ -451,6 +454,7 @@ struct Engine {
             if ((rc = make_list(v, tiles, op.s_ff))) return rc;
             op.s_ff.vec = 4;
             for (const auto& t : v) op.s_ff.vec = std::min(op.s_ff.vec, sweep_vec(t));
+            op.s_ff.corr = with_corr ? 1 : 0;
             op.grid = persistent_grid(op.s_ff.total);
         }
         cycle.push_back(op);

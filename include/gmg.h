@@ -232,6 +232,37 @@ int gmg_op_residual_norm(int nx, int ny, int nz, const int* periodic, const floa
                          const float* by, const float* bz, const float* b, const float* p,
                          double* rr, void* stream);
 
+/*
+ * The paper has no counterpart to this entry point; it serves callers that
+ * must not let a library allocate device memory: code recording a CUDA graph
+ * (allocation during stream capture is refused or breaks the capture),
+ * real-time loops that cannot afford the device-wide synchronisation
+ * cudaMalloc / cudaFree may cause, and programs with a device-memory budget
+ * fixed up front.
+ *
+ * Same result as gmg_op_residual_norm (the same kernels, the same summation
+ * order), but its scratch (one FP64 partial sum per 32x4x2-cell tile, plus
+ * the total) lives in a fixed array inside the library image: at most 65536
+ * partial sums, i.e. about 16.7 M cells.  Every GPU that loads the library
+ * holds that array (about 512 KB) until the process exits.  The call
+ * allocates and frees nothing.
+ *
+ * Errors: GMG_ERR_ARG for bad dimensions, a null pointer, or a grid needing
+ * more than 65536 partial sums (message in gmg_last_error(NULL));
+ * GMG_ERR_CUDA if a CUDA call fails.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls on a device share the one array
+ * and each overwrites what the previous call left there: calls that overlap
+ * on the GPU (concurrent streams, or several host threads) race and must be
+ * serialised by the caller.  The call synchronises `stream` before it
+ * returns *rr (host memory).
+ */
+int gmg_op_residual_norm_noalloc(int nx, int ny, int nz, const int* periodic, const float* bx,
+                                 const float* by, const float* bz, const float* b,
+                                 const float* p, double* rr, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

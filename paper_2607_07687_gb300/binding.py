@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
     L.gmg_op_prolong_add.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp]
     L.gmg_op_coarsen_coeffs.argtypes = [c_int, c_int, c_int, ip, ip, vp, vp, vp, vp, vp, vp, vp]
     L.gmg_op_residual_norm.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
+    L.gmg_op_residual_norm_noalloc.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
     _lib = L
     return L
 
@@ -332,6 +333,19 @@ def op_residual_norm(bx, by, bz, b, p, periodic=(False, False, False), stream=No
     rr = ctypes.c_double(0.0)
     rc = lib().gmg_op_residual_norm(*dims, _ivec(periodic), *ptrs, ctypes.byref(rr),
                                     ctypes.c_void_p(_stream(stream)))
+    _check(rc, None)
+    return rr.value
+
+
+def op_residual_norm_noalloc(bx, by, bz, b, p, periodic=(False, False, False), stream=None) -> float:
+    """As op_residual_norm, with the library's fixed scratch array (no allocation)."""
+    import torch
+    dims = _dims_of(b)
+    n = b.numel()
+    ptrs = [_ptr(t, torch.float32, n) for t in (bx, by, bz, b, p)]
+    rr = ctypes.c_double(0.0)
+    rc = lib().gmg_op_residual_norm_noalloc(*dims, _ivec(periodic), *ptrs, ctypes.byref(rr),
+                                            ctypes.c_void_p(_stream(stream)))
     _check(rc, None)
     return rr.value
 

@@ -206,6 +206,9 @@ struct IrTask {
     double* scale;       // device scalar: inner = outer residual * scale
 };
 
+// Message returned by gmg_last_error(NULL) for calls without a handle.
+void set_api_error(const char* msg);
+
 // ---------------------------------------------------------------- launchers
 
 template <class TP, class TC>

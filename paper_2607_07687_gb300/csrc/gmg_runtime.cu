@@ -1082,6 +1082,10 @@ int validate_options(const gmg_options& o, std::string& msg)
 
 }  // namespace
 
+namespace gmg {
+void set_api_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace gmg
+
 struct gmg_solver {
     Engine eng;
 };

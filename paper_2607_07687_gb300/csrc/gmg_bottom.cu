@@ -1,0 +1,217 @@
+// gmg_bottom.cu -- the bottom of the V-cycle in one CTA.
+//
+// The coarse levels of a hierarchy are small (a few thousand cells and
+// below), where one launch per sweep costs more in launch and pipeline
+// latency than in work.  k_bottom runs the whole lower part of the V-cycle
+// (paper Sec. 3: smoothing and coarse-grid correction; Sec. 3.1: the
+// under-relaxed red-black Gauss-Seidel smoother; Sec. 3.2: the iso- or
+// anisotropically coarsened levels) for levels lb .. L-1 of one problem inside
+// one CTA, with every level's iterate, right-hand side and face coefficients
+// in shared memory:
+//   descent  : zero guess, nu1 sweeps, residual summed over the children of
+//              each coarse cell (restriction);
+//   coarsest : right-hand side projected to zero mean over active cells,
+//              nu_c sweeps from zero;
+//   ascent   : p += e[I / c] (prolongation), nu2 sweeps;
+// and writes level lb's result for the finer level's correction.  Colour
+// phases are separated by block barriers; within a colour the cells are
+// independent, so in-place updates are exact Gauss-Seidel.
+#include "gmg_internal.h"
+#include "gmg_device.cuh"
+
+namespace gmg {
+namespace {
+
+using namespace dev;
+
+struct LevelView {
+    Geo g;
+    int n;
+    float* p;
+    float* b;
+    float* x;   // lower faces, walls zeroed
+    float* y;
+    float* z;
+};
+
+__device__ __forceinline__ void decode(const Geo& g, int i, int& x, int& y, int& z)
+{
+    x = i % g.n[0];
+    const int r = i / g.n[0];
+    y = r % g.n[1];
+    z = r / g.n[1];
+}
+
+// neighbour of (x, y, z) along axis d in direction s, or -1 outside a wall
+__device__ __forceinline__ int nbr(const Geo& g, int x, int y, int z, int d, int s)
+{
+    int c[3] = {x, y, z};
+    c[d] += s;
+    if (!wrapc(c[d], g.n[d], g.per[d])) return -1;
+    return (c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
+}
+
+// (A p)_i and the diagonal, from shared memory
+__device__ __forceinline__ float flux_at(const LevelView& L, int i, float& dg)
+{
+    int x, y, z;
+    decode(L.g, i, x, y, z);
+    const int xl = nbr(L.g, x, y, z, 0, -1), xu = nbr(L.g, x, y, z, 0, +1);
+    const int yl = nbr(L.g, x, y, z, 1, -1), yu = nbr(L.g, x, y, z, 1, +1);
+    const int zl = nbr(L.g, x, y, z, 2, -1), zu = nbr(L.g, x, y, z, 2, +1);
+    const float p0 = L.p[i];
+    const float fxu = xu < 0 ? 0.f : L.x[xu], fyu = yu < 0 ? 0.f : L.y[yu], fzu = zu < 0 ? 0.f : L.z[zu];
+    dg = diag_sum(L.x[i], fxu, L.y[i], fyu, L.z[i], fzu);
+    return face_flux(L.x[i], xl < 0 ? p0 : L.p[xl], fxu, xu < 0 ? p0 : L.p[xu], L.y[i],
+                     yl < 0 ? p0 : L.p[yl], fyu, yu < 0 ? p0 : L.p[yu], L.z[i],
+                     zl < 0 ? p0 : L.p[zl], fzu, zu < 0 ? p0 : L.p[zu], p0);
+}
+
+// diagonal (sum of the six face coefficients) of cell i
+__device__ __forceinline__ float diag_at(const LevelView& L, int i)
+{
+    int x, y, z;
+    decode(L.g, i, x, y, z);
+    const int xu = nbr(L.g, x, y, z, 0, +1), yu = nbr(L.g, x, y, z, 1, +1), zu = nbr(L.g, x, y, z, 2, +1);
+    return diag_sum(L.x[i], xu < 0 ? 0.f : L.x[xu], L.y[i], yu < 0 ? 0.f : L.y[yu], L.z[i],
+                    zu < 0 ? 0.f : L.z[zu]);
+}
+
+__device__ void sweeps(const LevelView& L, int count, float w)
+{
+    for (int it = 0; it < count; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+                int x, y, z;
+                decode(L.g, i, x, y, z);
+                if (((x + y + z) & 1) != colour) continue;
+                float dg;
+                const float fl = flux_at(L, i, dg);
+                L.p[i] = gs_update(L.p[i], fl, dg, L.b[i], w);
+            }
+            __syncthreads();
+        }
+}
+
+template <class TP>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>* __restrict__ tasks)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ double red[kBottomThreads / 32];
+    __shared__ double s_mean;
+    const BottomTask<TP>& T = tasks[blockIdx.x];
+    if (T.ctl && T.ctl->done) return;
+    const int nlev = T.nlev;
+    const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
+
+    auto view = [&](int l) {
+        LevelView L;
+        L.g = T.lev[l].g;
+        L.n = L.g.n[0] * L.g.n[1] * L.g.n[2];
+        float* base = sm + T.lev[l].off;
+        L.p = base;
+        L.b = base + L.n;
+        L.x = base + 2 * L.n;
+        L.y = base + 3 * L.n;
+        L.z = base + 4 * L.n;
+        return L;
+    };
+
+    // coefficients of every level (lower faces, walls zeroed) and the top right-hand side
+    for (int l = 0; l < nlev; ++l) {
+        const LevelView L = view(l);
+        const BottomLevel& B = T.lev[l];
+        for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+            int x, y, z;
+            decode(L.g, i, x, y, z);
+            L.x[i] = face_lo(B.bx, L.g, 0, x, y, z);
+            L.y[i] = face_lo(B.by, L.g, 1, x, y, z);
+            L.z[i] = face_lo(B.bz, L.g, 2, x, y, z);
+            if (l == 0) L.b[i] = T.b[i];
+        }
+    }
+    __syncthreads();
+
+    // descent
+    for (int l = 0; l + 1 < nlev; ++l) {
+        const LevelView L = view(l);
+        const LevelView C = view(l + 1);
+        for (int i = threadIdx.x; i < L.n; i += blockDim.x) L.p[i] = 0.f;
+        __syncthreads();
+        sweeps(L, T.nu1, w);
+        const int c0 = T.lev[l].cf[0], c1 = T.lev[l].cf[1], c2 = T.lev[l].cf[2];
+        for (int j = threadIdx.x; j < C.n; j += blockDim.x) {
+            int X, Y, Z;
+            decode(C.g, j, X, Y, Z);
+            float s = 0.f;
+            for (int dz = 0; dz < c2; ++dz)
+                for (int dy = 0; dy < c1; ++dy)
+                    for (int dx = 0; dx < c0; ++dx) {
+                        const int i = ((Z * c2 + dz) * L.g.n[1] + (Y * c1 + dy)) * L.g.n[0] + (X * c0 + dx);
+                        float dg;
+                        s += L.b[i] - flux_at(L, i, dg);
+                    }
+            C.b[j] = s;
+        }
+        __syncthreads();
+    }
+
+    // coarsest: zero-mean projection over active cells, then nu_c sweeps from zero
+    {
+        const LevelView C = view(nlev - 1);
+        double s = 0.0, cnt = 0.0;
+        for (int i = threadIdx.x; i < C.n; i += blockDim.x) {
+            C.p[i] = 0.f;
+            if (diag_at(C, i) > 0.f) {
+                s += (double)C.b[i];
+                cnt += 1.0;
+            }
+        }
+        s = block_sum(s, red);
+        cnt = block_sum(cnt, red);
+        if (threadIdx.x == 0) s_mean = cnt > 0.0 ? s / cnt : 0.0;
+        __syncthreads();
+        const double mean = s_mean;
+        for (int i = threadIdx.x; i < C.n; i += blockDim.x)
+            C.b[i] = diag_at(C, i) > 0.f ? (float)((double)C.b[i] - mean) : 0.f;
+        __syncthreads();
+        sweeps(C, T.nu_c, w);
+    }
+
+    // ascent
+    for (int l = nlev - 2; l >= 0; --l) {
+        const LevelView L = view(l);
+        const LevelView C = view(l + 1);
+        const int c0 = T.lev[l].cf[0], c1 = T.lev[l].cf[1], c2 = T.lev[l].cf[2];
+        for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+            int x, y, z;
+            decode(L.g, i, x, y, z);
+            L.p[i] += C.p[((z / c2) * C.g.n[1] + y / c1) * C.g.n[0] + x / c0];
+        }
+        __syncthreads();
+        sweeps(L, T.nu2, w);
+    }
+
+    const LevelView L = view(0);
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x) stv(T.out, (int64_t)i, L.p[i]);
+}
+
+}  // namespace
+
+template <class TP>
+cudaError_t launch_bottom(const BottomTask<TP>* tasks, int ntasks, size_t smem, cudaStream_t s)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    static size_t opted = 0;   // dynamic shared memory opted in so far
+    if (smem > opted) {
+        cudaError_t e = cudaFuncSetAttribute(k_bottom<TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        opted = smem;
+    }
+    k_bottom<TP><<<ntasks, kBottomThreads, smem, s>>>(tasks);
+    return cudaGetLastError();
+}
+template cudaError_t launch_bottom<float>(const BottomTask<float>*, int, size_t, cudaStream_t);
+template cudaError_t launch_bottom<bf16>(const BottomTask<bf16>*, int, size_t, cudaStream_t);
+
+}  // namespace gmg

@@ -20,7 +20,6 @@
 namespace gmg {
 
 constexpr int kMaxLevels = 32;
-constexpr int kCoarseMaxCells = 2048;   // largest coarsest level solved inside one CTA
 constexpr int kThreads = 256;           // threads per block of the grid kernels
 
 // sweep tile (cells): TX x TY columns marching through a z-chunk
@@ -113,28 +112,37 @@ struct ResTask {
     const Ctl* ctl;
 };
 
-// Coarsest-level solve inside one CTA: project b to zero mean over active
-// cells, then nu_c sweeps from zero.
-template <class TP>
-struct CoarseTask {
-    Geo g;
-    const float* bx;
-    const float* by;
-    const float* bz;
-    float* b;
-    TP* out;
-    int nu_c;
-    const Ctl* ctl;
-};
-
 // Zero-mean projection of one level's right-hand side over its active cells
-// (coarsest levels too large for CoarseTask; their sweeps then run as k_sweep).
+// (coarsest levels too large for the bottom kernel; their sweeps then run as k_sweep).
 struct LevelProjTask {
     Geo g;
     const float* bx;
     const float* by;
     const float* bz;
     float* b;
+    const Ctl* ctl;
+};
+
+// The bottom of the V-cycle (levels lb .. L-1 of one problem) in one CTA.
+constexpr int kBottomThreads = 512;
+constexpr int kBottomMaxCells = 10240;   // 5 floats per cell of shared memory: 200 KB
+
+struct BottomLevel {
+    Geo g;
+    int cf[3];           // coarsening factors to the next level
+    const float* bx;
+    const float* by;
+    const float* bz;
+    int off;             // offset (floats) of the level's block in shared memory
+};
+
+template <class TP>
+struct BottomTask {
+    int nlev;            // levels lb .. L-1; the last one is the coarsest
+    BottomLevel lev[kMaxLevels];
+    const float* b;      // right-hand side of level lb (written by the finer level)
+    TP* out;             // result of level lb (read by the finer level's correction)
+    int nu1, nu2, nu_c;
     const Ctl* ctl;
 };
 
@@ -215,10 +223,11 @@ template <class TP, class TC>
 cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaStream_t s);
 template <class TP>
 cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStream_t s);
-template <class TP>
-cudaError_t launch_coarse(const CoarseTask<TP>* tasks, int ntasks, cudaStream_t s);
 
 cudaError_t launch_project_level(const LevelProjTask* tasks, int ntasks, cudaStream_t s);
+
+template <class TP>
+cudaError_t launch_bottom(const BottomTask<TP>* tasks, int ntasks, size_t smem, cudaStream_t s);
 
 // Reference variant of the sweep: one in-place launch per colour.
 cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const float* bz,

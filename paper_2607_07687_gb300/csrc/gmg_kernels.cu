@@ -27,6 +27,7 @@
 // Reductions are deterministic: per-tile partials in FP64, summed in a fixed
 // order by one block per problem.
 #include "gmg_internal.h"
+#include "gmg_device.cuh"
 
 #include <cmath>
 #include <type_traits>
@@ -34,113 +35,7 @@
 namespace gmg {
 namespace {
 
-// ---------------------------------------------------------------- helpers
-
-// Map a (possibly out-of-range) index onto the grid: periodic axes wrap by
-// any number of periods (tiles and halos can exceed a small periodic level),
-// walled axes report "outside".
-__device__ __forceinline__ bool wrapc(int& i, int n, int per)
-{
-    if (i >= 0 && i < n) return true;
-    if (!per) return false;
-    i %= n;
-    if (i < 0) i += n;
-    return true;
-}
-
-__device__ __forceinline__ int64_t lin(const Geo& g, int x, int y, int z)
-{
-    return ((int64_t)z * g.n[1] + y) * g.n[0] + x;
-}
-
-template <class T>
-__device__ __forceinline__ float ldv(const T* p, int64_t i);
-template <>
-__device__ __forceinline__ float ldv<float>(const float* p, int64_t i) { return __ldg(p + i); }
-template <>
-__device__ __forceinline__ float ldv<bf16>(const bf16* p, int64_t i) { return __bfloat162float(p[i]); }
-
-template <class T>
-__device__ __forceinline__ void stv(T* p, int64_t i, float v);
-template <>
-__device__ __forceinline__ void stv<float>(float* p, int64_t i, float v) { p[i] = v; }
-template <>
-__device__ __forceinline__ void stv<bf16>(bf16* p, int64_t i, float v) { p[i] = __float2bfloat16_rn(v); }
-
-// coefficient of the lower d-face of the cell at (unwrapped) c: 0 on walls and outside
-__device__ __forceinline__ float face_lo(const float* a, const Geo& g, int d, int x, int y, int z)
-{
-    if (!wrapc(x, g.n[0], g.per[0]) || !wrapc(y, g.n[1], g.per[1]) || !wrapc(z, g.n[2], g.per[2]))
-        return 0.f;
-    const int c = d == 0 ? x : (d == 1 ? y : z);
-    if (c == 0 && !g.per[d]) return 0.f;
-    return __ldg(a + lin(g, x, y, z));
-}
-
-// (A p)_I = sum over the six faces of beta_f (p_nb - p_I), in one fixed order
-// (lower/upper x, y, z).  Each difference of two nearby FP32 values is exact,
-// so the rounding error scales with the local differences rather than with
-// |p|; the form nb - diag * p would cancel and lose ~log2(|p| / |A p|) bits.
-__device__ __forceinline__ float face_flux(float bxl, float pxl, float bxu, float pxu, float byl,
-                                           float pyl, float byu, float pyu, float bzl, float pzl,
-                                           float bzu, float pzu, float p)
-{
-    return ((bxl * (pxl - p) + bxu * (pxu - p)) + (byl * (pyl - p) + byu * (pyu - p))) +
-           (bzl * (pzl - p) + bzu * (pzu - p));
-}
-
-__device__ __forceinline__ float diag_sum(float bxl, float bxu, float byl, float byu, float bzl,
-                                          float bzu)
-{
-    return ((bxl + bxu) + (byl + byu)) + (bzl + bzu);
-}
-
-// under-relaxed Gauss-Seidel update of one cell (Sec. 3.1) in correction form:
-// (1 - w) p + w (sum beta p_nb - b) / diag = p + w ((A p)_I - b_I) / diag;
-// isolated cells (diag = 0) keep p
-__device__ __forceinline__ float gs_update(float p, float flux, float dg, float b, float w)
-{
-    if (!(dg > 0.f)) return p;
-    return p + w * ((flux - b) / dg);
-}
-
-template <class Task>
-__device__ __forceinline__ const Task* task_of(const TaskList<Task>& tl, int tile, int& local)
-{
-    if (!tl.tasks) {
-        local = tile;
-        return &tl.single;
-    }
-    int lo = 0, hi = tl.ntasks - 1;
-    while (lo < hi) {   // last t with tile_off[t] <= tile
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(tl.tile_off + mid) <= tile) lo = mid;
-        else hi = mid - 1;
-    }
-    local = tile - __ldg(tl.tile_off + lo);
-    return tl.tasks + lo;
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum over the block, fixed order; result valid in thread 0.  `red` holds one
-// double per warp.  Ends with a barrier so `red` may be reused at once.
-__device__ __forceinline__ double block_sum(double v, double* red)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    __syncthreads();
-    return s;
-}
+using namespace dev;
 
 // ---------------------------------------------------------------- K1: fused sweep
 
@@ -692,88 +587,6 @@ __global__ void __launch_bounds__(kThreads) k_residual(const __grid_constant__ T
     }
 }
 
-// ---------------------------------------------------------------- K4: coarsest level
-
-constexpr int kCoarseSmem = kCoarseMaxCells;
-
-template <class TP>
-__global__ void __launch_bounds__(kThreads) k_coarse(const CoarseTask<TP>* __restrict__ tasks)
-{
-    __shared__ float sp[kCoarseSmem], sb[kCoarseSmem], sx[kCoarseSmem], sy[kCoarseSmem], sz[kCoarseSmem];
-    __shared__ double red[kThreads / 32];
-    __shared__ double s_mean;
-    const CoarseTask<TP>& T = tasks[blockIdx.x];
-    if (T.ctl && T.ctl->done) return;
-    const Geo g = T.g;
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const int N = nx * ny * nz;
-    for (int i = threadIdx.x; i < N; i += kThreads) {
-        const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
-        sx[i] = face_lo(T.bx, g, 0, x, y, z);
-        sy[i] = face_lo(T.by, g, 1, x, y, z);
-        sz[i] = face_lo(T.bz, g, 2, x, y, z);
-        sb[i] = T.b[i];
-        sp[i] = 0.f;
-    }
-    __syncthreads();
-    // neighbour index along d in direction s, or -1
-    auto nbi = [&](int x, int y, int z, int d, int s) -> int {
-        int c[3] = {x, y, z};
-        c[d] += s;
-        if (!wrapc(c[d], g.n[d], g.per[d])) return -1;
-        return (c[2] * ny + c[1]) * nx + c[0];
-    };
-    auto upper = [&](const float* a, int x, int y, int z, int d) -> float {
-        const int j = nbi(x, y, z, d, +1);
-        return j < 0 ? 0.f : a[j];
-    };
-    // projection of b to zero mean over active cells
-    double s = 0.0, cnt = 0.0;
-    for (int i = threadIdx.x; i < N; i += kThreads) {
-        const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
-        const float dg = diag_sum(sx[i], upper(sx, x, y, z, 0), sy[i], upper(sy, x, y, z, 1), sz[i],
-                                  upper(sz, x, y, z, 2));
-        if (dg > 0.f) {
-            s += (double)sb[i];
-            cnt += 1.0;
-        }
-    }
-    s = block_sum(s, red);
-    cnt = block_sum(cnt, red);
-    if (threadIdx.x == 0) s_mean = cnt > 0.0 ? s / cnt : 0.0;
-    __syncthreads();
-    const double mean = s_mean;
-    for (int i = threadIdx.x; i < N; i += kThreads) {
-        const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
-        const float dg = diag_sum(sx[i], upper(sx, x, y, z, 0), sy[i], upper(sy, x, y, z, 1), sz[i],
-                                  upper(sz, x, y, z, 2));
-        sb[i] = dg > 0.f ? (float)((double)sb[i] - mean) : 0.f;
-    }
-    __syncthreads();
-    const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
-    for (int it = 0; it < T.nu_c; ++it) {
-        for (int colour = 0; colour < 2; ++colour) {
-            for (int i = threadIdx.x; i < N; i += kThreads) {
-                const int x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
-                if (((x + y + z) & 1) != colour) continue;
-                const int xl = nbi(x, y, z, 0, -1), xu = nbi(x, y, z, 0, +1);
-                const int yl = nbi(x, y, z, 1, -1), yu = nbi(x, y, z, 1, +1);
-                const int zl = nbi(x, y, z, 2, -1), zu = nbi(x, y, z, 2, +1);
-                const float fxu = xu < 0 ? 0.f : sx[xu], fyu = yu < 0 ? 0.f : sy[yu],
-                            fzu = zu < 0 ? 0.f : sz[zu];
-                const float p0 = sp[i];
-                const float fl = face_flux(sx[i], xl < 0 ? p0 : sp[xl], fxu, xu < 0 ? p0 : sp[xu], sy[i],
-                                           yl < 0 ? p0 : sp[yl], fyu, yu < 0 ? p0 : sp[yu], sz[i],
-                                           zl < 0 ? p0 : sp[zl], fzu, zu < 0 ? p0 : sp[zu], p0);
-                const float dg = diag_sum(sx[i], fxu, sy[i], fyu, sz[i], fzu);
-                sp[i] = gs_update(p0, fl, dg, sb[i], w);
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < N; i += kThreads) stv(T.out, (int64_t)i, sp[i]);
-}
-
 // one block per task: b <- b - mean over active cells (0 on inactive cells)
 __global__ void __launch_bounds__(kThreads) k_project_level(const LevelProjTask* __restrict__ tasks)
 {
@@ -1245,16 +1058,6 @@ cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStrea
 }
 template cudaError_t launch_residual<float>(const TaskList<ResTask<float>>&, int, cudaStream_t);
 template cudaError_t launch_residual<bf16>(const TaskList<ResTask<bf16>>&, int, cudaStream_t);
-
-template <class TP>
-cudaError_t launch_coarse(const CoarseTask<TP>* tasks, int ntasks, cudaStream_t s)
-{
-    if (ntasks <= 0) return cudaSuccess;
-    k_coarse<TP><<<ntasks, kThreads, 0, s>>>(tasks);
-    return cudaGetLastError();
-}
-template cudaError_t launch_coarse<float>(const CoarseTask<float>*, int, cudaStream_t);
-template cudaError_t launch_coarse<bf16>(const CoarseTask<bf16>*, int, cudaStream_t);
 
 cudaError_t launch_project_level(const LevelProjTask* tasks, int ntasks, cudaStream_t s)
 {

@@ -151,7 +151,7 @@ struct ProblemMem {
     int* hist_acc = nullptr;
 };
 
-enum OpKind { kSweepFF, kSweepFB, kSweepBB, kResF, kResB, kCoarseF, kCoarseB, kProjLevel, kControl };
+enum OpKind { kSweepFF, kSweepFB, kSweepBB, kResF, kResB, kBottomF, kBottomB, kProjLevel, kControl };
 
 struct LaunchOp {
     OpKind kind;
@@ -161,8 +161,9 @@ struct LaunchOp {
     TaskList<SweepTask<bf16, bf16>> s_bb{};
     TaskList<ResTask<float>> r_f{};
     TaskList<ResTask<bf16>> r_b{};
-    const CoarseTask<float>* c_f = nullptr;
-    const CoarseTask<bf16>* c_b = nullptr;
+    const BottomTask<float>* bot_f = nullptr;
+    const BottomTask<bf16>* bot_b = nullptr;
+    size_t smem = 0;
     const LevelProjTask* lp = nullptr;
     const CtlTask* ctl = nullptr;
     int n = 0;
@@ -420,6 +421,7 @@ struct Engine {
     }
 
     std::vector<std::vector<int>> coarse_result_;   // [p][l] buffer holding the level's result
+    std::vector<int> stop_;                         // [p] first level not run by grid kernels
 
     int add_sweeps(int l, const std::vector<int>& probs, int in, int out, bool with_corr)
     {
@@ -492,12 +494,30 @@ struct Engine {
         int Lmax = 0;
         for (auto& M : P) Lmax = std::max(Lmax, M.L);
         coarse_result_.assign(nprob, std::vector<int>(kMaxLevels, 0));
+        // per problem: levels from `stop` down run in one CTA (bottom kernel) when
+        // they fit in its shared memory; otherwise only the coarsest level is
+        // special (grid sweeps); a problem that does not coarsen runs sweeps only
+        stop_.assign(nprob, 0);
+        std::vector<int> bottom(nprob, -1);
+        for (int p = 0; p < nprob; ++p) {
+            const ProblemMem& M = P[p];
+            if (M.L == 1) continue;
+            int64_t acc = 0;
+            int lb = -1;
+            for (int l = M.L - 1; l >= 1; --l) {
+                acc += cells(M.lev[l].g);
+                if (acc > kBottomMaxCells) break;
+                lb = l;
+            }
+            bottom[p] = lb;
+            stop_[p] = lb >= 1 ? lb : M.L - 1;
+        }
         std::vector<int> pre(kMaxLevels, 0);   // role/buffer of the pre-smoothed iterate per level
         // descent
         for (int l = 0; l + 1 < Lmax; ++l) {
             std::vector<int> probs;
             for (int p = 0; p < nprob; ++p)
-                if (l < P[p].L - 1) probs.push_back(p);
+                if (l < stop_[p]) probs.push_back(p);
             if (probs.empty()) continue;
             int cur = l == 0 ? 0 : -1;
             for (int s = 0; s < opt.nu1; ++s) {
@@ -510,44 +530,77 @@ struct Engine {
             int rc = add_residual(l, probs, cur, true, false);
             if (rc) return rc;
         }
-        // coarsest levels (one CTA per problem); a problem that does not coarsen at
-        // all runs nu_c sweeps on its only level, continuing from the iterate
         res_role.assign(nprob, 0);
         {
-            std::vector<CoarseTask<float>> cf;
-            std::vector<CoarseTask<bf16>> cb;
+            std::vector<BottomTask<float>> bf;
+            std::vector<BottomTask<bf16>> bb;
+            size_t smem = 0;
             std::vector<int> single;
             std::vector<std::vector<int>> big(kMaxLevels);   // by coarsest level index
             for (int p = 0; p < nprob; ++p) {
-                const int l = P[p].L - 1;
-                const LevelMem& Lm = P[p].lev[l];
-                coarse_result_[p][l] = 0;
-                if (l == 0) {
+                const ProblemMem& M = P[p];
+                if (M.L == 1) {
                     single.push_back(p);
-                } else if (cells(Lm.g) > kCoarseMaxCells) {
-                    big[l].push_back(p);
-                } else if (bf16_coarse) {
-                    cb.push_back(CoarseTask<bf16>{Lm.g, Lm.beta[0], Lm.beta[1], Lm.beta[2], Lm.b,
-                                                  static_cast<bf16*>(Lm.buf[0]), opt.nu_c, P[p].ctl});
+                    continue;
+                }
+                if (bottom[p] < 1) {
+                    big[M.L - 1].push_back(p);
+                    continue;
+                }
+                const int lb = bottom[p];
+                BottomTask<float> t{};
+                t.nlev = M.L - lb;
+                int off = 0;
+                for (int k = 0; k < t.nlev; ++k) {
+                    const LevelMem& Lm = M.lev[lb + k];
+                    BottomLevel& B = t.lev[k];
+                    B.g = Lm.g;
+                    for (int d = 0; d < 3; ++d) B.cf[d] = Lm.cf[d];
+                    B.bx = Lm.beta[0];
+                    B.by = Lm.beta[1];
+                    B.bz = Lm.beta[2];
+                    B.off = off;
+                    off += 5 * (int)cells(Lm.g);
+                }
+                smem = std::max(smem, sizeof(float) * (size_t)off);
+                t.b = M.lev[lb].b;
+                t.nu1 = opt.nu1;
+                t.nu2 = opt.nu2;
+                t.nu_c = opt.nu_c;
+                t.ctl = M.ctl;
+                coarse_result_[p][lb] = 0;
+                if (bf16_coarse) {
+                    BottomTask<bf16> tb{};
+                    tb.nlev = t.nlev;
+                    for (int k = 0; k < t.nlev; ++k) tb.lev[k] = t.lev[k];
+                    tb.b = t.b;
+                    tb.out = static_cast<bf16*>(M.lev[lb].buf[0]);
+                    tb.nu1 = t.nu1;
+                    tb.nu2 = t.nu2;
+                    tb.nu_c = t.nu_c;
+                    tb.ctl = t.ctl;
+                    bb.push_back(tb);
                 } else {
-                    cf.push_back(CoarseTask<float>{Lm.g, Lm.beta[0], Lm.beta[1], Lm.beta[2], Lm.b,
-                                                   static_cast<float*>(Lm.buf[0]), opt.nu_c, P[p].ctl});
+                    t.out = static_cast<float*>(M.lev[lb].buf[0]);
+                    bf.push_back(t);
                 }
             }
-            if (!cf.empty()) {
+            if (!bf.empty()) {
                 LaunchOp op;
-                op.kind = kCoarseF;
-                op.c_f = upload(cf);
-                op.n = (int)cf.size();
-                if (!op.c_f) return fail(GMG_ERR_CUDA, "upload failed");
+                op.kind = kBottomF;
+                op.bot_f = upload(bf);
+                op.n = (int)bf.size();
+                op.smem = smem;
+                if (!op.bot_f) return fail(GMG_ERR_CUDA, "upload failed");
                 cycle.push_back(op);
             }
-            if (!cb.empty()) {
+            if (!bb.empty()) {
                 LaunchOp op;
-                op.kind = kCoarseB;
-                op.c_b = upload(cb);
-                op.n = (int)cb.size();
-                if (!op.c_b) return fail(GMG_ERR_CUDA, "upload failed");
+                op.kind = kBottomB;
+                op.bot_b = upload(bb);
+                op.n = (int)bb.size();
+                op.smem = smem;
+                if (!op.bot_b) return fail(GMG_ERR_CUDA, "upload failed");
                 cycle.push_back(op);
             }
             // coarsest levels too large for one CTA: projection, then nu_c grid sweeps
@@ -588,7 +641,7 @@ struct Engine {
         for (int l = Lmax - 2; l >= 0; --l) {
             std::vector<int> probs;
             for (int p = 0; p < nprob; ++p)
-                if (l < P[p].L - 1) probs.push_back(p);
+                if (l < stop_[p]) probs.push_back(p);
             if (probs.empty()) continue;
             int cur = pre[l];
             for (int s = 0; s < opt.nu2; ++s) {
@@ -634,8 +687,8 @@ struct Engine {
         case kSweepBB: return launch_sweep(op.s_bb, op.grid, stream);
         case kResF: return launch_residual(op.r_f, op.grid, stream);
         case kResB: return launch_residual(op.r_b, op.grid, stream);
-        case kCoarseF: return launch_coarse(op.c_f, op.n, stream);
-        case kCoarseB: return launch_coarse(op.c_b, op.n, stream);
+        case kBottomF: return launch_bottom(op.bot_f, op.n, op.smem, stream);
+        case kBottomB: return launch_bottom(op.bot_b, op.n, op.smem, stream);
         case kProjLevel: return launch_project_level(op.lp, op.n, stream);
         case kControl: return launch_control_cycle(op.ctl, op.n, stream);
         }

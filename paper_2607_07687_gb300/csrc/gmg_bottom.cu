@@ -51,20 +51,32 @@ __device__ __forceinline__ int nbr(const Geo& g, int x, int y, int z, int d, int
     return (c[2] * g.n[1] + c[1]) * g.n[0] + c[0];
 }
 
-// (A p)_i and the diagonal, from shared memory
-__device__ __forceinline__ float flux_at(const LevelView& L, int i, float& dg)
+// (A p)_i and the diagonal at cell i = (x, y, z), from shared memory; interior
+// cells take their neighbours at fixed offsets, boundary cells wrap or drop them
+__device__ __forceinline__ float flux_xyz(const LevelView& L, int i, int x, int y, int z, float& dg)
 {
-    int x, y, z;
-    decode(L.g, i, x, y, z);
-    const int xl = nbr(L.g, x, y, z, 0, -1), xu = nbr(L.g, x, y, z, 0, +1);
-    const int yl = nbr(L.g, x, y, z, 1, -1), yu = nbr(L.g, x, y, z, 1, +1);
-    const int zl = nbr(L.g, x, y, z, 2, -1), zu = nbr(L.g, x, y, z, 2, +1);
+    const int nx = L.g.n[0], nxy = L.g.n[0] * L.g.n[1];
     const float p0 = L.p[i];
+    int xl, xu, yl, yu, zl, zu;
+    if (x > 0 && x < nx - 1 && y > 0 && y < L.g.n[1] - 1 && z > 0 && z < L.g.n[2] - 1) {
+        xl = i - 1; xu = i + 1; yl = i - nx; yu = i + nx; zl = i - nxy; zu = i + nxy;
+    } else {
+        xl = nbr(L.g, x, y, z, 0, -1); xu = nbr(L.g, x, y, z, 0, +1);
+        yl = nbr(L.g, x, y, z, 1, -1); yu = nbr(L.g, x, y, z, 1, +1);
+        zl = nbr(L.g, x, y, z, 2, -1); zu = nbr(L.g, x, y, z, 2, +1);
+    }
     const float fxu = xu < 0 ? 0.f : L.x[xu], fyu = yu < 0 ? 0.f : L.y[yu], fzu = zu < 0 ? 0.f : L.z[zu];
     dg = diag_sum(L.x[i], fxu, L.y[i], fyu, L.z[i], fzu);
     return face_flux(L.x[i], xl < 0 ? p0 : L.p[xl], fxu, xu < 0 ? p0 : L.p[xu], L.y[i],
                      yl < 0 ? p0 : L.p[yl], fyu, yu < 0 ? p0 : L.p[yu], L.z[i],
                      zl < 0 ? p0 : L.p[zl], fzu, zu < 0 ? p0 : L.p[zu], p0);
+}
+
+__device__ __forceinline__ float flux_at(const LevelView& L, int i, float& dg)
+{
+    int x, y, z;
+    decode(L.g, i, x, y, z);
+    return flux_xyz(L, i, x, y, z, dg);
 }
 
 // diagonal (sum of the six face coefficients) of cell i
@@ -77,20 +89,50 @@ __device__ __forceinline__ float diag_at(const LevelView& L, int i)
                     zu < 0 ? 0.f : L.z[zu]);
 }
 
+// Walk cells first, first + stride, ... of a level, keeping (x, y, z) up to date
+// by carries instead of divisions.
+struct CellWalk {
+    int i, x, y, z, dx, dy, dz;
+    __device__ CellWalk(const Geo& g, int first, int stride)
+    {
+        i = first;
+        decode(g, first, x, y, z);
+        decode(g, stride, dx, dy, dz);
+    }
+    __device__ __forceinline__ void next(const Geo& g, int stride)
+    {
+        i += stride;
+        x += dx;
+        int cy = 0;
+        if (x >= g.n[0]) { x -= g.n[0]; cy = 1; }
+        y += dy + cy;
+        int cz = 0;
+        if (y >= g.n[1]) { y -= g.n[1]; cz = 1; }
+        z += dz + cz;
+    }
+};
+
+// nu sweeps; levels of at most 32 * 8 cells run on warp 0 alone (warp barriers)
 __device__ void sweeps(const LevelView& L, int count, float w)
 {
+    const bool small = L.n <= 256;
+    if (small && threadIdx.x >= 32) {
+        __syncthreads();
+        return;
+    }
+    const int stride = small ? 32 : blockDim.x;
     for (int it = 0; it < count; ++it)
         for (int colour = 0; colour < 2; ++colour) {
-            for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-                int x, y, z;
-                decode(L.g, i, x, y, z);
-                if (((x + y + z) & 1) != colour) continue;
+            for (CellWalk c(L.g, threadIdx.x, stride); c.i < L.n; c.next(L.g, stride)) {
+                if (((c.x + c.y + c.z) & 1) != colour) continue;
                 float dg;
-                const float fl = flux_at(L, i, dg);
-                L.p[i] = gs_update(L.p[i], fl, dg, L.b[i], w);
+                const float fl = flux_xyz(L, c.i, c.x, c.y, c.z, dg);
+                L.p[c.i] = gs_update(L.p[c.i], fl, dg, L.b[c.i], w);
             }
-            __syncthreads();
+            if (small) __syncwarp();
+            else __syncthreads();
         }
+    if (small) __syncthreads();
 }
 
 template <class TP>
@@ -183,11 +225,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         const LevelView L = view(l);
         const LevelView C = view(l + 1);
         const int c0 = T.lev[l].cf[0], c1 = T.lev[l].cf[1], c2 = T.lev[l].cf[2];
-        for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-            int x, y, z;
-            decode(L.g, i, x, y, z);
-            L.p[i] += C.p[((z / c2) * C.g.n[1] + y / c1) * C.g.n[0] + x / c0];
-        }
+        for (CellWalk c(L.g, threadIdx.x, blockDim.x); c.i < L.n; c.next(L.g, blockDim.x))
+            L.p[c.i] += C.p[((c.z / c2) * C.g.n[1] + c.y / c1) * C.g.n[0] + c.x / c0];
         __syncthreads();
         sweeps(L, T.nu2, w);
     }

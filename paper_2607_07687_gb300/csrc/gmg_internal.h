@@ -29,6 +29,8 @@ constexpr int kSweepTY = 8;
 // each holding planes kr-2 .. kr+3 of the marching step
 constexpr int kSweepRing = 6;
 constexpr size_t kSweepSmemBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4) * 6 * kSweepRing;
+// the pipelined residual stages the same rings without the merged plane
+constexpr size_t kResidualSmemBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4) * 5 * kSweepRing;
 // residual tile (fine cells)
 constexpr int kResTX = 32;
 constexpr int kResTY = 4;
@@ -108,6 +110,7 @@ struct ResTask {
     float* bc;           // coarse right-hand side, or nullptr (norm only)
     int cf[3];
     int tiles_x, tiles_y, tiles_z;
+    int zchunk;          // marching kernel: cells per z-chunk (tiles_z chunks of 32 x 8 columns)
     double* partials;    // one per tile of this task, or nullptr
     const Ctl* ctl;
 };
@@ -154,6 +157,7 @@ struct TaskList {
     int total;           // total tiles
     int vec;             // 4: every task's rows split into aligned 16-byte chunks
     int corr;            // sweeps: 1 if any task adds a coarse correction
+    int march;           // residuals: 1 = z-marching kernel (tiles of 32 x 8 columns x zchunk)
     Task single;
 };
 

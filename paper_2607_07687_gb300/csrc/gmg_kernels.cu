@@ -495,6 +495,190 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
     }
 }
 
+// ---------------------------------------------------------------- K2: pipelined residual
+//
+// r = b - A p on a TX x TY column marching through a z-chunk, with the planes
+// of p, b and the faces staged by the same asynchronous copies as the sweep.
+// Each of the first TX*TY/2 threads owns a pair of cells of a row; the
+// restriction to the next level sums x-pairs in the thread, y-pairs with the
+// lane 16 apart (rows 2w and 2w+1 share a warp) and z-pairs across two steps,
+// so coarse cells are written without atomics.  Sum r^2 per tile in FP64.
+template <int VEC>
+__global__ void __launch_bounds__(kThreads, 3) k_residual_async(const __grid_constant__ TaskList<ResTask<float>> tl)
+{
+    constexpr int TX = kSweepTX, TY = kSweepTY;
+    constexpr int XO = 4, SW = TX + 8, SH = TY + 4, PL = SW * SH;
+    constexpr int R = kSweepRing;
+    constexpr int CPR = SW / 4, NCH = PL / 4;
+    constexpr int BPR = TX / 2, NPAIR = BPR * TY;
+    static_assert(VEC == 4, "16-byte plane copies only");
+    static_assert(NPAIR <= kThreads && BPR == 16, "pair layout: two rows per warp");
+    extern __shared__ __align__(16) float smem[];
+    __shared__ double red[kThreads / 32];
+    const int tid = threadIdx.x;
+    const int half = tid / (kThreads / 2);
+    const int chunk = tid % (kThreads / 2);
+
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        int local;
+        const ResTask<float>* tp = task_of(tl, tile, local);
+        if (tp->ctl && tp->ctl->done) continue;               // uniform in the block
+        const Geo g = tp->g;
+        const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+        const int px = g.per[0], py = g.per[1], pz = g.per[2];
+        const int cx = local % tp->tiles_x;
+        const int rest = local / tp->tiles_x;
+        const int cy = rest % tp->tiles_y;
+        const int cz = rest / tp->tiles_y;
+        const int x0 = cx * TX, y0 = cy * TY;
+        const int z0 = cz * tp->zchunk;
+        const int z1 = min(nz, z0 + tp->zchunk);
+        const int rot = tp->rot ? *tp->rot : 0;
+        const float* pin = tp->role < 0 ? nullptr : tp->buf[(tp->role + rot) % 3];
+        const float* const ba = tp->b;
+        const float* const srcA = half == 0 ? pin : tp->by;
+        const float* const srcB = half == 0 ? tp->b : tp->bz;
+        const float* const srcC = tp->bx;
+        float* const bc = tp->bc;
+        const int c0 = tp->cf[0], c1 = tp->cf[1], c2 = tp->cf[2];
+        const int64_t plane = (int64_t)nx * ny;
+
+        int coff = 0;
+        bool cok = false;
+        if (chunk < NCH) {
+            const int sy = chunk / CPR, ch = chunk - sy * CPR;
+            int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
+            cok = wrapc(x, nx, px) && wrapc(y, ny, py);
+            coff = cok ? y * nx + x : 0;
+        }
+        const int tyb = tid / BPR, jb = tid - tyb * BPR;
+        const int yb = y0 + tyb, xb = x0 + 2 * jb;
+        const bool pair_on = tid < NPAIR && yb < ny && xb < nx;
+        const int sp = (tyb + 2) * SW + XO + 2 * jb;
+        const bool yb_wall = yb == 0 && !py;
+        const bool xb_wall = xb == 0 && !px;
+        const int gcx = nx / c0, gcy = ny / c1;
+        // coarse cell(s) this thread writes: one x-pair sum (c0 = 2) or two cells
+        const bool writer = pair_on && (c1 == 1 || (tyb & 1) == 0);
+        const int64_t cplane = (int64_t)gcx * gcy;
+        const int64_t crow = (int64_t)(yb / c1) * gcx + xb / c0;
+
+        auto zinfo = [&](int z, bool zface, int64_t& zoff) -> bool {
+            int zw = z;
+            bool ok = wrapc(zw, nz, pz);
+            if (zface && ok && zw == 0 && !pz) ok = false;
+            zoff = (int64_t)zw * plane;
+            return ok;
+        };
+        auto copy_plane = [&](float* dst, const float* a, int z, bool zface) {
+            int64_t zoff;
+            const bool zok = a != nullptr && zinfo(z, zface, zoff);
+            for (int c = tid; c < NCH; c += kThreads) {
+                const int sy = c / CPR, ch = c - sy * CPR;
+                int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
+                const bool ok = zok && wrapc(x, nx, px) && wrapc(y, ny, py);
+                cp_async16(dst + 4 * c, ok ? a + zoff + (int64_t)y * nx + x : ba, ok);
+            }
+        };
+        auto ring = [&](int r, int slot) -> float* { return smem + (r * R + slot) * PL; };
+
+        // plane z in slot (z - z0 + 1) mod R
+        copy_plane(ring(0, 0), pin, z0 - 1, false);
+        copy_plane(ring(0, 1), pin, z0, false);
+        copy_plane(ring(0, 2), pin, z0 + 1, false);
+        copy_plane(ring(4, 1), tp->bz, z0, true);
+        copy_plane(ring(1, 1), ba, z0, false);
+        copy_plane(ring(2, 1), tp->bx, z0, false);
+        copy_plane(ring(3, 1), tp->by, z0, false);
+        copy_plane(ring(4, 2), tp->bz, z0 + 1, true);
+        cp_commit();
+
+        const int nsteps = z1 - z0;
+        double rr = 0.0;
+        float acc0 = 0.f, acc1 = 0.f;
+        auto step = [&](int u, auto Jc) {
+            constexpr int J = decltype(Jc)::value;
+            constexpr int S0 = (J + 1) % R, Sm1 = J % R, Sp1 = (J + 2) % R, Sp2 = (J + 3) % R;
+            const int k = z0 + u;
+            // copies for step u+1: p(k+2), b / x / y faces (k+1), z faces (k+2)
+            if (u + 1 < nsteps && chunk < NCH) {
+                int64_t zo1, zo2;
+                if (half == 0) {
+                    const bool ok2 = pin != nullptr && zinfo(k + 2, false, zo2) && cok;
+                    const bool ok1 = zinfo(k + 1, false, zo1) && cok;
+                    cp_async16(ring(0, Sp2) + 4 * chunk, ok2 ? srcA + zo2 + coff : ba, ok2);
+                    cp_async16(ring(1, Sp1) + 4 * chunk, ok1 ? srcB + zo1 + coff : ba, ok1);
+                    cp_async16(ring(2, Sp1) + 4 * chunk, ok1 ? srcC + zo1 + coff : ba, ok1);
+                } else {
+                    const bool ok1 = zinfo(k + 1, false, zo1) && cok;
+                    const bool ok2 = zinfo(k + 2, true, zo2) && cok;
+                    cp_async16(ring(3, Sp1) + 4 * chunk, ok1 ? srcA + zo1 + coff : ba, ok1);
+                    cp_async16(ring(4, Sp2) + 4 * chunk, ok2 ? srcB + zo2 + coff : ba, ok2);
+                }
+            }
+            cp_commit();
+            cp_wait<1>();
+            __syncthreads();
+            float r0 = 0.f, r1 = 0.f;
+            if (pair_on) {
+                const float* P0 = ring(0, S0);
+                const float* Pl = ring(0, Sm1);
+                const float* Pu = ring(0, Sp1);
+                const float* X0 = ring(2, S0);
+                const float* Y0 = ring(3, S0);
+                const float* Z0 = ring(4, S0);
+                const float* Z1 = ring(4, Sp1);
+                const float* B0 = ring(1, S0);
+                for (int h = 0; h < 2; ++h) {
+                    const int s = sp + h;
+                    const float p0 = P0[s];
+                    const float xl = (h == 0 && xb_wall) ? 0.f : X0[s];
+                    const float yl = yb_wall ? 0.f : Y0[s];
+                    const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW], Y0[s + SW],
+                                               P0[s + SW], Z0[s], Pl[s], Z1[s], Pu[s], p0);
+                    const float r = B0[s] - fl;
+                    if (h == 0) r0 = r; else r1 = (xb + 1 < nx) ? r : 0.f;
+                }
+                rr += (double)r0 * (double)r0 + (double)r1 * (double)r1;
+            }
+            if (bc) {
+                float v0 = c0 == 2 ? r0 + r1 : r0;
+                float v1 = c0 == 2 ? 0.f : r1;
+                if (c1 == 2) {
+                    v0 += __shfl_xor_sync(0xffffffffu, v0, 16);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, 16);
+                }
+                acc0 += v0;
+                acc1 += v1;
+                if (c2 == 1 || (k & 1) == 1) {
+                    if (writer) {
+                        float* dst = bc + (int64_t)(k / c2) * cplane + crow;
+                        dst[0] = acc0;
+                        if (c0 == 1 && xb + 1 < nx) dst[1] = acc1;
+                    }
+                    acc0 = acc1 = 0.f;
+                }
+            }
+        };
+        static_assert(R == 6, "the unrolled step sequence below assumes six slots");
+        for (int u = 0; u < nsteps; u += R) {
+            step(u, std::integral_constant<int, 0>());
+            if (u + 1 < nsteps) step(u + 1, std::integral_constant<int, 1>());
+            if (u + 2 < nsteps) step(u + 2, std::integral_constant<int, 2>());
+            if (u + 3 < nsteps) step(u + 3, std::integral_constant<int, 3>());
+            if (u + 4 < nsteps) step(u + 4, std::integral_constant<int, 4>());
+            if (u + 5 < nsteps) step(u + 5, std::integral_constant<int, 5>());
+        }
+        cp_wait<0>();
+        if (tp->partials) {
+            const double q = block_sum(rr, red);
+            if (tid == 0) tp->partials[local] = q;
+        } else {
+            __syncthreads();
+        }
+    }
+}
+
 // reference sweep: one colour per launch, in place, one thread per cell
 __global__ void k_sweep_colour(Geo g, const float* __restrict__ bx, const float* __restrict__ by,
                                const float* __restrict__ bz, const float* __restrict__ b, float* p,
@@ -1053,6 +1237,20 @@ template <class TP>
 cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStream_t s)
 {
     if (tl.total <= 0) return cudaSuccess;
+    if constexpr (std::is_same<TP, float>::value) {
+        if (tl.march) {
+            constexpr size_t smem = kResidualSmemBytes;
+            static bool attr = false;
+            if (!attr) {
+                cudaError_t e = cudaFuncSetAttribute(k_residual_async<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e != cudaSuccess) return e;
+                attr = true;
+            }
+            k_residual_async<4><<<grid, kThreads, smem, s>>>(tl);
+            return cudaGetLastError();
+        }
+    }
     k_residual<TP><<<grid, kThreads, 0, s>>>(tl);
     return cudaGetLastError();
 }

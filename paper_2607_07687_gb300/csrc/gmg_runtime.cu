@@ -113,13 +113,35 @@ SweepTiling sweep_tiling(const Geo& g)
 
 struct ResTiling {
     int tx, ty, tz;
+    int zchunk;   // marching tiling only
     int64_t tiles() const { return (int64_t)tx * ty * tz; }
 };
 
+// 32 x 4 x 2 cell tiles of the per-cell residual kernel
 ResTiling res_tiling(const Geo& g)
 {
-    return {ceil_div(g.n[0], kResTX), ceil_div(g.n[1], kResTY), ceil_div(g.n[2], kResTZ)};
+    return {ceil_div(g.n[0], kResTX), ceil_div(g.n[1], kResTY), ceil_div(g.n[2], kResTZ), 0};
 }
+
+// FP32 levels with rows of a multiple of 4 cells use the z-marching residual
+bool res_marches(const Geo& g, bool fp32) { return fp32 && g.n[0] % 4 == 0; }
+
+// 32 x 8 columns x z-chunks of even length (coarse z-pairs never straddle chunks)
+ResTiling march_tiling(const Geo& g)
+{
+    ResTiling t;
+    t.tx = ceil_div(g.n[0], kSweepTX);
+    t.ty = ceil_div(g.n[1], kSweepTY);
+    const int64_t cols = (int64_t)t.tx * t.ty;
+    const int want = (int)std::max<int64_t>(1, (kSMs * 6 + cols - 1) / cols);
+    const int nc = std::max(1, std::min(want, g.n[2] / 4));
+    t.zchunk = ceil_div(g.n[2], nc);
+    if (t.zchunk % 2 && t.zchunk < g.n[2]) ++t.zchunk;
+    t.tz = ceil_div(g.n[2], t.zchunk);
+    return t;
+}
+
+ResTiling level_res_tiling(const Geo& g, bool fp32) { return res_marches(g, fp32) ? march_tiling(g) : res_tiling(g); }
 
 // ------------------------------------------------------------ plan structures
 
@@ -281,13 +303,13 @@ struct Engine {
                 }
             }
             if (!(M.mask = dalloc<uint8_t>(M.n0))) return fail(GMG_ERR_CUDA, "out of device memory");
-            M.norm_tiles = (int)res_tiling(M.g0).tiles();
+            M.norm_tiles = (int)level_res_tiling(M.g0, true).tiles();
             M.elem_tiles = ceil_div(M.n0, kElemTile);
             total_norm += M.norm_tiles;
             total_elem += M.elem_tiles;
             if (ir) {
                 if (!(M.b64 = dalloc<double>(M.n0))) return fail(GMG_ERR_CUDA, "out of device memory");
-                if (!(M.ir_part = dalloc<double>(M.norm_tiles)))
+                if (!(M.ir_part = dalloc<double>(res_tiling(M.g0).tiles())))
                     return fail(GMG_ERR_CUDA, "out of device memory");
             }
             const int cap = std::max(1, o.max_cycles);
@@ -411,13 +433,55 @@ struct Engine {
         t.role = role;
         t.bc = restrict_to_next ? M.lev[l + 1].b : nullptr;
         for (int d = 0; d < 3; ++d) t.cf[d] = restrict_to_next ? Lm.cf[d] : 1;
-        const ResTiling rt = res_tiling(Lm.g);
+        const ResTiling rt = level_res_tiling(Lm.g, std::is_same<TP, float>::value);
         t.tiles_x = rt.tx;
         t.tiles_y = rt.ty;
         t.tiles_z = rt.tz;
+        t.zchunk = rt.zchunk;
         t.partials = partials;
         t.ctl = M.ctl;
         return t;
+    }
+
+    // residual launches of level l for `probs`: problems whose level marches and
+    // those that do not go to separate launches
+    int res_ops(int l, const std::vector<int>& probs, const std::vector<int>& role, bool restrict_to_next,
+                bool norm, std::vector<LaunchOp>& ops)
+    {
+        const bool bf = l > 0 && bf16_coarse;
+        for (int m = 0; m < 2; ++m) {
+            std::vector<int> sel;
+            for (size_t i = 0; i < probs.size(); ++i)
+                if ((int)res_marches(P[probs[i]].lev[l].g, !bf) == m) sel.push_back((int)i);
+            if (sel.empty()) continue;
+            LaunchOp op;
+            std::vector<int64_t> tiles;
+            int rc;
+            if (bf) {
+                std::vector<ResTask<bf16>> v;
+                for (int i : sel) {
+                    const int p = probs[i];
+                    v.push_back(res_task<bf16>(p, l, role[i], restrict_to_next, norm ? P[p].norm_part : nullptr));
+                    tiles.push_back(level_res_tiling(P[p].lev[l].g, false).tiles());
+                }
+                op.kind = kResB;
+                if ((rc = make_list(v, tiles, op.r_b))) return rc;
+                op.grid = persistent_grid(op.r_b.total);
+            } else {
+                std::vector<ResTask<float>> v;
+                for (int i : sel) {
+                    const int p = probs[i];
+                    v.push_back(res_task<float>(p, l, role[i], restrict_to_next, norm ? P[p].norm_part : nullptr));
+                    tiles.push_back(level_res_tiling(P[p].lev[l].g, true).tiles());
+                }
+                op.kind = kResF;
+                if ((rc = make_list(v, tiles, op.r_f))) return rc;
+                op.r_f.march = m;
+                op.grid = persistent_grid(op.r_f.total);
+            }
+            ops.push_back(op);
+        }
+        return GMG_OK;
     }
 
     std::vector<std::vector<int>> coarse_result_;   // [p][l] buffer holding the level's result
@@ -463,28 +527,21 @@ struct Engine {
         return GMG_OK;
     }
 
+    int add_residual_roles(const std::vector<int>& probs, const std::vector<int>& roles)
+    {
+        std::vector<LaunchOp> ops;
+        int rc = res_ops(0, probs, roles, false, true, ops);
+        if (rc) return rc;
+        for (auto& op : ops) cycle.push_back(op);
+        return GMG_OK;
+    }
+
     int add_residual(int l, const std::vector<int>& probs, int role, bool restrict_to_next, bool norm)
     {
-        LaunchOp op;
-        std::vector<int64_t> tiles;
-        for (int p : probs) tiles.push_back(res_tiling(P[p].lev[l].g).tiles());
-        int rc;
-        if (l > 0 && bf16_coarse) {
-            std::vector<ResTask<bf16>> v;
-            for (int p : probs)
-                v.push_back(res_task<bf16>(p, l, role, restrict_to_next, norm ? P[p].norm_part : nullptr));
-            op.kind = kResB;
-            if ((rc = make_list(v, tiles, op.r_b))) return rc;
-            op.grid = persistent_grid(op.r_b.total);
-        } else {
-            std::vector<ResTask<float>> v;
-            for (int p : probs)
-                v.push_back(res_task<float>(p, l, role, restrict_to_next, norm ? P[p].norm_part : nullptr));
-            op.kind = kResF;
-            if ((rc = make_list(v, tiles, op.r_f))) return rc;
-            op.grid = persistent_grid(op.r_f.total);
-        }
-        cycle.push_back(op);
+        std::vector<LaunchOp> ops;
+        int rc = res_ops(l, probs, std::vector<int>(probs.size(), role), restrict_to_next, norm, ops);
+        if (rc) return rc;
+        for (auto& op : ops) cycle.push_back(op);
         return GMG_OK;
     }
 
@@ -657,18 +714,10 @@ struct Engine {
         }
         // fine residual norm of the candidate, then the control rule
         {
-            LaunchOp op;
-            std::vector<ResTask<float>> v;
-            std::vector<int64_t> tiles;
-            for (int p = 0; p < nprob; ++p) {
-                v.push_back(res_task<float>(p, 0, res_role[p], false, P[p].norm_part));
-                tiles.push_back(P[p].norm_tiles);
-            }
-            op.kind = kResF;
-            int rc = make_list(v, tiles, op.r_f);
+            std::vector<int> probs(nprob);
+            for (int p = 0; p < nprob; ++p) probs[p] = p;
+            int rc = add_residual_roles(probs, res_role);
             if (rc) return rc;
-            op.grid = persistent_grid(op.r_f.total);
-            cycle.push_back(op);
             LaunchOp c;
             c.kind = kControl;
             c.ctl = cycle_ctl;
@@ -908,22 +957,21 @@ struct Engine {
     {
         std::vector<int> probs(P.size());
         for (size_t p = 0; p < P.size(); ++p) probs[p] = (int)p;
-        std::vector<ResTask<float>> v;
-        std::vector<int64_t> tiles;
-        for (int p : probs) {
-            v.push_back(res_task<float>(p, 0, 0, false, P[p].norm_part));
-            v.back().ctl = nullptr;   // runs before the done flag is meaningful
-            tiles.push_back(P[p].norm_tiles);
-        }
-        TaskList<ResTask<float>> tl;
-        if (make_list(v, tiles, tl)) return cudaErrorMemoryAllocation;
-        launches += 2;
-        cudaError_t e = launch_residual(tl, persistent_grid(tl.total), stream);
+        std::vector<LaunchOp> ops;
+        if (res_ops(0, probs, std::vector<int>(P.size(), 0), false, true, ops)) return cudaErrorMemoryAllocation;
+        cudaError_t e = cudaSuccess;
+        for (const LaunchOp& op : ops)
+            if (e == cudaSuccess) e = launch(op);
+        ++launches;
         if (e == cudaSuccess) e = launch_control_init(init_ctl, (int)P.size(), stream);
-        if (tl.tasks) {
+        bool uploaded = false;
+        for (const LaunchOp& op : ops) uploaded |= op.r_f.tasks != nullptr;
+        if (uploaded) {   // the lists are built per solve: free them once the launches ran
             cudaStreamSynchronize(stream);
-            drop(tl.tasks);
-            drop(tl.tile_off);
+            for (const LaunchOp& op : ops) {
+                if (op.r_f.tasks) drop(op.r_f.tasks);
+                if (op.r_f.tile_off) drop(op.r_f.tile_off);
+            }
         }
         return e;
     }
@@ -1474,10 +1522,13 @@ static int op_residual(int nx, int ny, int nz, const int* periodic, const int* f
     t.role = 0;
     t.bc = b_coarse;
     for (int d = 0; d < 3; ++d) t.cf[d] = b_coarse ? factors[d] : 1;
-    const ResTiling rt = res_tiling(t.g);
+    const bool march = res_marches(t.g, true) && aligned16(bx) && aligned16(by) && aligned16(bz) && aligned16(b) &&
+                       aligned16(p);
+    const ResTiling rt = march ? march_tiling(t.g) : res_tiling(t.g);
     t.tiles_x = rt.tx;
     t.tiles_y = rt.ty;
     t.tiles_z = rt.tz;
+    t.zchunk = rt.zchunk;
     t.ctl = nullptr;
     std::unique_lock<std::mutex> lock(g_op_mutex, std::defer_lock);
     double* out = nullptr;
@@ -1489,6 +1540,7 @@ static int op_residual(int nx, int ny, int nz, const int* periodic, const int* f
     tl.ntasks = 1;
     tl.total = (int)rt.tiles();
     tl.single = t;
+    tl.march = march ? 1 : 0;
     cudaError_t e = launch_residual(tl, persistent_grid(tl.total), s);
     if (e == cudaSuccess && rr) {
         e = launch_sum_partials(t.partials, (int)rt.tiles(), out, s);

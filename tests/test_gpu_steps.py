@@ -58,7 +58,13 @@ def test_sweep_single_launch_equals_two_launches(dims, periodic):
                                                ((34, 9, 12), (0, 0, 1), (2, 1, 2)),
                                                ((33, 20, 8), (0, 1, 0), (1, 2, 2)),
                                                ((40, 8, 6), (0, 0, 0), (2, 2, 1)),
-                                               ((8, 6, 4), (0, 0, 0), (1, 1, 1))])
+                                               ((8, 6, 4), (0, 0, 0), (1, 1, 1)),
+                                               ((64, 18, 14), (1, 1, 1), (2, 2, 2)),
+                                               ((128, 40, 22), (0, 0, 0), (2, 2, 2)),
+                                               ((96, 20, 30), (0, 1, 0), (2, 1, 2)),
+                                               ((36, 12, 9), (0, 0, 0), (1, 2, 1)),
+                                               ((260, 16, 12), (1, 0, 0), (1, 1, 2)),
+                                               ((4, 4, 4), (1, 1, 1), (2, 2, 2))])
 def test_residual_restrict_matches_oracle(O, dims, periodic, fac):
     from paper_2607_07687_gb300 import binding as G
     (bx, by, bz), b, p = random_fields(dims, periodic, seed=7 + sum(dims))

@@ -27,6 +27,7 @@ using namespace dev;
 struct LevelView {
     Geo g;
     int n;
+    double inv_nx, inv_nxy;
     float* p;
     float* b;
     float* x;   // lower faces, walls zeroed
@@ -34,12 +35,18 @@ struct LevelView {
     float* z;
 };
 
-__device__ __forceinline__ void decode(const Geo& g, int i, int& x, int& y, int& z)
+// cell index -> (x, y, z) without integer division.  (i + 1/2) / d lies at
+// least 1/(2d) from the nearest integer, while the FP64 product with the
+// rounded reciprocal is off by at most about 2^-52 (i + 1) / d; for i, d below
+// 2^20 (a bottom level has at most kBottomMaxCells cells) that is far smaller,
+// so the truncation is the exact quotient.
+__device__ __forceinline__ void decode(const LevelView& L, int i, int& x, int& y, int& z)
 {
-    x = i % g.n[0];
-    const int r = i / g.n[0];
-    y = r % g.n[1];
-    z = r / g.n[1];
+    const int nx = L.g.n[0], nxy = L.g.n[0] * L.g.n[1];
+    z = (int)(((double)i + 0.5) * L.inv_nxy);
+    const int r = i - z * nxy;
+    y = (int)(((double)r + 0.5) * L.inv_nx);
+    x = r - y * nx;
 }
 
 // neighbour of (x, y, z) along axis d in direction s, or -1 outside a wall
@@ -75,7 +82,7 @@ __device__ __forceinline__ float flux_xyz(const LevelView& L, int i, int x, int 
 __device__ __forceinline__ float flux_at(const LevelView& L, int i, float& dg)
 {
     int x, y, z;
-    decode(L.g, i, x, y, z);
+    decode(L, i, x, y, z);
     return flux_xyz(L, i, x, y, z, dg);
 }
 
@@ -83,7 +90,7 @@ __device__ __forceinline__ float flux_at(const LevelView& L, int i, float& dg)
 __device__ __forceinline__ float diag_at(const LevelView& L, int i)
 {
     int x, y, z;
-    decode(L.g, i, x, y, z);
+    decode(L, i, x, y, z);
     const int xu = nbr(L.g, x, y, z, 0, +1), yu = nbr(L.g, x, y, z, 1, +1), zu = nbr(L.g, x, y, z, 2, +1);
     return diag_sum(L.x[i], xu < 0 ? 0.f : L.x[xu], L.y[i], yu < 0 ? 0.f : L.y[yu], L.z[i],
                     zu < 0 ? 0.f : L.z[zu]);
@@ -93,11 +100,11 @@ __device__ __forceinline__ float diag_at(const LevelView& L, int i)
 // by carries instead of divisions.
 struct CellWalk {
     int i, x, y, z, dx, dy, dz;
-    __device__ CellWalk(const Geo& g, int first, int stride)
+    __device__ CellWalk(const LevelView& L, int first, int stride)
     {
         i = first;
-        decode(g, first, x, y, z);
-        decode(g, stride, dx, dy, dz);
+        decode(L, first, x, y, z);
+        decode(L, stride, dx, dy, dz);
     }
     __device__ __forceinline__ void next(const Geo& g, int stride)
     {
@@ -112,27 +119,19 @@ struct CellWalk {
     }
 };
 
-// nu sweeps; levels of at most 32 * 8 cells run on warp 0 alone (warp barriers)
+// nu red-black sweeps of one level, every thread of the block
 __device__ void sweeps(const LevelView& L, int count, float w)
 {
-    const bool small = L.n <= 256;
-    if (small && threadIdx.x >= 32) {
-        __syncthreads();
-        return;
-    }
-    const int stride = small ? 32 : blockDim.x;
     for (int it = 0; it < count; ++it)
         for (int colour = 0; colour < 2; ++colour) {
-            for (CellWalk c(L.g, threadIdx.x, stride); c.i < L.n; c.next(L.g, stride)) {
+            for (CellWalk c(L, threadIdx.x, blockDim.x); c.i < L.n; c.next(L.g, blockDim.x)) {
                 if (((c.x + c.y + c.z) & 1) != colour) continue;
                 float dg;
                 const float fl = flux_xyz(L, c.i, c.x, c.y, c.z, dg);
                 L.p[c.i] = gs_update(L.p[c.i], fl, dg, L.b[c.i], w);
             }
-            if (small) __syncwarp();
-            else __syncthreads();
+            __syncthreads();
         }
-    if (small) __syncthreads();
 }
 
 template <class TP>
@@ -150,6 +149,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         LevelView L;
         L.g = T.lev[l].g;
         L.n = L.g.n[0] * L.g.n[1] * L.g.n[2];
+        L.inv_nx = T.lev[l].inv_nx;
+        L.inv_nxy = T.lev[l].inv_nxy;
         float* base = sm + T.lev[l].off;
         L.p = base;
         L.b = base + L.n;
@@ -163,9 +164,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
     for (int l = 0; l < nlev; ++l) {
         const LevelView L = view(l);
         const BottomLevel& B = T.lev[l];
-        for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
-            int x, y, z;
-            decode(L.g, i, x, y, z);
+        for (CellWalk c(L, threadIdx.x, blockDim.x); c.i < L.n; c.next(L.g, blockDim.x)) {
+            const int i = c.i, x = c.x, y = c.y, z = c.z;
             L.x[i] = face_lo(B.bx, L.g, 0, x, y, z);
             L.y[i] = face_lo(B.by, L.g, 1, x, y, z);
             L.z[i] = face_lo(B.bz, L.g, 2, x, y, z);
@@ -182,16 +182,16 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         __syncthreads();
         sweeps(L, T.nu1, w);
         const int c0 = T.lev[l].cf[0], c1 = T.lev[l].cf[1], c2 = T.lev[l].cf[2];
-        for (int j = threadIdx.x; j < C.n; j += blockDim.x) {
-            int X, Y, Z;
-            decode(C.g, j, X, Y, Z);
+        for (CellWalk cw(C, threadIdx.x, blockDim.x); cw.i < C.n; cw.next(C.g, blockDim.x)) {
+            const int j = cw.i, X = cw.x, Y = cw.y, Z = cw.z;
             float s = 0.f;
             for (int dz = 0; dz < c2; ++dz)
                 for (int dy = 0; dy < c1; ++dy)
                     for (int dx = 0; dx < c0; ++dx) {
-                        const int i = ((Z * c2 + dz) * L.g.n[1] + (Y * c1 + dy)) * L.g.n[0] + (X * c0 + dx);
+                        const int x = X * c0 + dx, y = Y * c1 + dy, z = Z * c2 + dz;
+                        const int i = (z * L.g.n[1] + y) * L.g.n[0] + x;
                         float dg;
-                        s += L.b[i] - flux_at(L, i, dg);
+                        s += L.b[i] - flux_xyz(L, i, x, y, z, dg);
                     }
             C.b[j] = s;
         }
@@ -225,8 +225,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         const LevelView L = view(l);
         const LevelView C = view(l + 1);
         const int c0 = T.lev[l].cf[0], c1 = T.lev[l].cf[1], c2 = T.lev[l].cf[2];
-        for (CellWalk c(L.g, threadIdx.x, blockDim.x); c.i < L.n; c.next(L.g, blockDim.x))
-            L.p[c.i] += C.p[((c.z / c2) * C.g.n[1] + c.y / c1) * C.g.n[0] + c.x / c0];
+        for (CellWalk c(L, threadIdx.x, blockDim.x); c.i < L.n; c.next(L.g, blockDim.x))
+            L.p[c.i] += C.p[((c.z >> (c2 - 1)) * C.g.n[1] + (c.y >> (c1 - 1))) * C.g.n[0] + (c.x >> (c0 - 1))];
         __syncthreads();
         sweeps(L, T.nu2, w);
     }

@@ -137,6 +137,8 @@ struct BottomLevel {
     const float* by;
     const float* bz;
     int off;             // offset (floats) of the level's block in shared memory
+    double inv_nx;       // 1 / nx and 1 / (nx ny): cell index -> (x, y, z) by multiplication
+    double inv_nxy;
 };
 
 template <class TP>

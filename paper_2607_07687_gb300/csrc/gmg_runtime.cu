@@ -617,6 +617,8 @@ struct Engine {
                     B.by = Lm.beta[1];
                     B.bz = Lm.beta[2];
                     B.off = off;
+                    B.inv_nx = 1.0 / Lm.g.n[0];
+                    B.inv_nxy = 1.0 / ((double)Lm.g.n[0] * Lm.g.n[1]);
                     off += 5 * (int)cells(Lm.g);
                 }
                 smem = std::max(smem, sizeof(float) * (size_t)off);

@@ -67,6 +67,7 @@ typedef struct {
     int use_graph;      /* replay the V-cycle from a captured CUDA graph (default 1) */
     int cycles_per_sync;/* V-cycles queued before the host reads the status (default 4) */
     double ir_inner_rtol; /* IR modes: inner V-cycles stop at this residual reduction (default 1e-4) */
+    int autotune;       /* time launch shapes at gmg_set_coeffs and keep the fastest (default 1) */
 } gmg_options;
 
 typedef struct {

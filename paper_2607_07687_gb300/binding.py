@@ -32,7 +32,8 @@ class Options(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("omega0", ctypes.c_double),
                 ("omega_min", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("grow", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("cycles_per_sync", ctypes.c_int), ("ir_inner_rtol", ctypes.c_double)]
+                ("cycles_per_sync", ctypes.c_int), ("ir_inner_rtol", ctypes.c_double),
+                ("autotune", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -21,6 +21,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -98,15 +100,49 @@ struct SweepTiling {
     int64_t tiles() const { return (int64_t)tx * ty * nchunks; }
 };
 
-SweepTiling sweep_tiling(const Geo& g)
+// ------------------------------------------------------------ autotuned shapes
+// z-chunk depth per (kernel kind, level geometry), filled by Engine::tune from
+// timed trial launches and shared by every handle of the process.
+enum TuneKind { kTuneSweep = 0, kTuneSweepCorr = 1, kTuneResidual = 2 };
+
+struct TuneKey {
+    int kind, n0, n1, n2, p0, p1, p2;
+    bool operator<(const TuneKey& o) const
+    {
+        const int a[7] = {kind, n0, n1, n2, p0, p1, p2}, b[7] = {o.kind, o.n0, o.n1, o.n2, o.p0, o.p1, o.p2};
+        return std::lexicographical_compare(a, a + 7, b, b + 7);
+    }
+};
+
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tuned_zchunk;
+
+TuneKey tune_key(int kind, const Geo& g) { return {kind, g.n[0], g.n[1], g.n[2], g.per[0], g.per[1], g.per[2]}; }
+
+int tuned_zchunk(int kind, const Geo& g)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned_zchunk.find(tune_key(kind, g));
+    return it == g_tuned_zchunk.end() ? 0 : it->second;
+}
+
+// heuristic depth: enough z-chunks for about six CTAs per SM, chunks of >= 4 planes
+int default_zchunk(const Geo& g)
+{
+    const int64_t cols = (int64_t)ceil_div(g.n[0], kSweepTX) * ceil_div(g.n[1], kSweepTY);
+    const int want = (int)std::max<int64_t>(1, (kSMs * 6 + cols - 1) / cols);
+    const int nc = std::max(1, std::min(want, g.n[2] / 4));
+    return ceil_div(g.n[2], nc);
+}
+
+SweepTiling sweep_tiling(const Geo& g, int kind = kTuneSweep, int zchunk = 0)
 {
     SweepTiling t;
     t.tx = ceil_div(g.n[0], kSweepTX);
     t.ty = ceil_div(g.n[1], kSweepTY);
-    const int64_t cols = (int64_t)t.tx * t.ty;
-    const int want = (int)std::max<int64_t>(1, (kSMs * 6 + cols - 1) / cols);
-    const int nc = std::max(1, std::min(want, g.n[2] / 4));
-    t.zchunk = ceil_div(g.n[2], nc);
+    if (zchunk <= 0) zchunk = tuned_zchunk(kind, g);
+    if (zchunk <= 0) zchunk = default_zchunk(g);
+    t.zchunk = std::min(zchunk, g.n[2]);
     t.nchunks = ceil_div(g.n[2], t.zchunk);
     return t;
 }
@@ -127,15 +163,14 @@ ResTiling res_tiling(const Geo& g)
 bool res_marches(const Geo& g, bool fp32) { return fp32 && g.n[0] % 4 == 0; }
 
 // 32 x 8 columns x z-chunks of even length (coarse z-pairs never straddle chunks)
-ResTiling march_tiling(const Geo& g)
+ResTiling march_tiling(const Geo& g, int zchunk = 0)
 {
     ResTiling t;
     t.tx = ceil_div(g.n[0], kSweepTX);
     t.ty = ceil_div(g.n[1], kSweepTY);
-    const int64_t cols = (int64_t)t.tx * t.ty;
-    const int want = (int)std::max<int64_t>(1, (kSMs * 6 + cols - 1) / cols);
-    const int nc = std::max(1, std::min(want, g.n[2] / 4));
-    t.zchunk = ceil_div(g.n[2], nc);
+    if (zchunk <= 0) zchunk = tuned_zchunk(kTuneResidual, g);
+    if (zchunk <= 0) zchunk = default_zchunk(g);
+    t.zchunk = std::min(zchunk, g.n[2]);
     if (t.zchunk % 2 && t.zchunk < g.n[2]) ++t.zchunk;
     t.tz = ceil_div(g.n[2], t.zchunk);
     return t;
@@ -407,7 +442,7 @@ struct Engine {
             t.corr = static_cast<const TC*>(M.lev[l + 1].buf[coarse_result_[p][l + 1]]);
             for (int d = 0; d < 3; ++d) t.cf[d] = Lm.cf[d];
         }
-        const SweepTiling st = sweep_tiling(Lm.g);
+        const SweepTiling st = sweep_tiling(Lm.g, with_corr ? kTuneSweepCorr : kTuneSweep);
         t.tiles_x = st.tx;
         t.tiles_y = st.ty;
         t.zchunk = st.zchunk;
@@ -486,6 +521,8 @@ struct Engine {
 
     std::vector<std::vector<int>> coarse_result_;   // [p][l] buffer holding the level's result
     std::vector<int> stop_;                         // [p] first level not run by grid kernels
+    int forced_lb_ = 0;                             // tuned start of the one-CTA bottom (0: smallest fit)
+    bool tuned_ = false;
 
     int add_sweeps(int l, const std::vector<int>& probs, int in, int out, bool with_corr)
     {
@@ -493,7 +530,8 @@ struct Engine {
         const bool corr_bf = with_corr && bf16_coarse;   // the correction comes from level l+1 >= 1
         LaunchOp op;
         std::vector<int64_t> tiles;
-        for (int p : probs) tiles.push_back(sweep_tiling(P[p].lev[l].g).tiles());
+        for (int p : probs)
+            tiles.push_back(sweep_tiling(P[p].lev[l].g, with_corr ? kTuneSweepCorr : kTuneSweep).tiles());
         int rc;
         if (coarse_bf) {
             std::vector<SweepTask<bf16, bf16>> v;
@@ -566,6 +604,7 @@ struct Engine {
                 if (acc > kBottomMaxCells) break;
                 lb = l;
             }
+            if (lb >= 1 && forced_lb_ > lb && forced_lb_ < M.L) lb = forced_lb_;
             bottom[p] = lb;
             stop_[p] = lb >= 1 ? lb : M.L - 1;
         }
@@ -829,6 +868,177 @@ struct Engine {
         if (e != cudaSuccess) return fail(GMG_ERR_CUDA, "gmg_set_coeffs (%s): %s", step, cudaGetErrorString(e));
         if (hbad) return fail(GMG_ERR_ARG, "face coefficients must be finite and >= 0");
         coeffs_set = true;
+        if (opt.autotune && !tuned_) {
+            tuned_ = true;
+            const int rc = tune();
+            if (rc != GMG_OK) return rc;
+        }
+        return GMG_OK;
+    }
+
+    // ---------------------------------------------------------------- autotuner
+
+    // mean time of one call of f after two warm-up calls (ms), or a huge value on error
+    float time_ms(const std::function<cudaError_t()>& f, int reps)
+    {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaError_t e = f();
+        if (e == cudaSuccess) e = f();
+        if (e == cudaSuccess) e = cudaEventRecord(a, stream);
+        for (int i = 0; i < reps && e == cudaSuccess; ++i) e = f();
+        if (e == cudaSuccess) e = cudaEventRecord(b, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 1e30f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return e == cudaSuccess ? ms / reps : 1e30f;
+    }
+
+    // free the launch lists of the current cycle plan and its graph
+    void reset_cycle()
+    {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        graph_exec = nullptr;
+        graph = nullptr;
+        for (const LaunchOp& op : cycle) {
+            const void* ptrs[] = {op.s_ff.tasks, op.s_ff.tile_off, op.s_fb.tasks, op.s_fb.tile_off, op.s_bb.tasks,
+                                  op.s_bb.tile_off, op.r_f.tasks, op.r_f.tile_off, op.r_b.tasks, op.r_b.tile_off,
+                                  op.bot_f, op.bot_b, op.lp};
+            for (const void* q : ptrs)
+                if (q) drop(q);
+        }
+        cycle.clear();
+    }
+
+    // a control state under which timed V-cycles never finish: tolerance below
+    // zero, no divergence floor, no cycle limit, no history
+    cudaError_t upload_timing_ctl()
+    {
+        for (size_t p = 0; p < P.size(); ++p) {
+            Ctl c = initial_ctl(P[p], -1.0);
+            c.omega_min = -1.0;
+            c.r_prev = 1.0;
+            c.bnorm = 1.0;
+            c.max_cycles = 1 << 30;
+            c.hist_cap = 0;
+            ctl_host[p] = c;
+        }
+        return cudaMemcpy(ctl_dev, ctl_host, sizeof(Ctl) * P.size(), cudaMemcpyHostToDevice);
+    }
+
+    int tune()
+    {
+        // timed launches run on zeros: right-hand sides and iterates of every level
+        for (auto& M : P)
+            for (int l = 0; l < M.L; ++l) {
+                const size_t n = (size_t)cells(M.lev[l].g);
+                const size_t es = (l > 0 && bf16_coarse) ? sizeof(bf16) : sizeof(float);
+                cudaMemsetAsync(M.lev[l].b, 0, n * sizeof(float), stream);
+                for (int r = 0; r < 3; ++r)
+                    if (M.lev[l].buf[r]) cudaMemsetAsync(M.lev[l].buf[r], 0, n * es, stream);
+            }
+        if (upload_timing_ctl() != cudaSuccess) return fail(GMG_ERR_CUDA, "autotune: control upload failed");
+        // 1) z-chunk depth of each grid-kernel level, per kernel kind
+        for (size_t p = 0; p < P.size(); ++p) {
+            const ProblemMem& M = P[p];
+            for (int l = 0; l < stop_[p]; ++l) {
+                if (l > 0 && bf16_coarse) continue;   // BF16 levels keep the heuristic depth
+                const Geo g = M.lev[l].g;
+                std::vector<int> cand;
+                for (int zc : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+                    if (zc < g.n[2]) cand.push_back(zc);
+                cand.push_back(g.n[2]);
+                const int in = l == 0 ? 0 : 1, out = l == 0 ? 1 : 0;
+                for (int kind : {kTuneSweep, kTuneSweepCorr, kTuneResidual}) {
+                    if (tuned_zchunk(kind, g)) continue;
+                    if (kind == kTuneResidual && !res_marches(g, true)) continue;
+                    float best = 1e30f;
+                    int best_zc = 0;
+                    int last_chunks = -1;
+                    for (int zc : cand) {
+                        const SweepTiling st = sweep_tiling(g, kind, zc);
+                        const int chunks = kind == kTuneResidual ? march_tiling(g, zc).tz : st.nchunks;
+                        if (chunks == last_chunks) continue;   // same launch as the previous candidate
+                        last_chunks = chunks;
+                        float ms;
+                        if (kind == kTuneResidual) {
+                            ResTask<float> t = res_task<float>((int)p, l, in, true, nullptr);
+                            const ResTiling rt = march_tiling(g, zc);
+                            t.tiles_z = rt.tz;
+                            t.zchunk = rt.zchunk;
+                            TaskList<ResTask<float>> tl{};
+                            tl.ntasks = 1;
+                            tl.total = (int)rt.tiles();
+                            tl.single = t;
+                            tl.march = 1;
+                            ms = time_ms([&] { return launch_residual(tl, persistent_grid(tl.total), stream); }, 5);
+                        } else if (kind == kTuneSweepCorr && bf16_coarse) {
+                            SweepTask<float, bf16> t = sweep_task<float, bf16>((int)p, l, in, out, true);
+                            t.zchunk = st.zchunk;
+                            t.nchunks = st.nchunks;
+                            TaskList<SweepTask<float, bf16>> tl{};
+                            tl.ntasks = 1;
+                            tl.total = (int)st.tiles();
+                            tl.single = t;
+                            tl.vec = sweep_vec(t);
+                            tl.corr = 1;
+                            ms = time_ms([&] { return launch_sweep(tl, persistent_grid(tl.total), stream); }, 5);
+                        } else {
+                            SweepTask<float, float> t =
+                                sweep_task<float, float>((int)p, l, in, out, kind == kTuneSweepCorr);
+                            t.zchunk = st.zchunk;
+                            t.nchunks = st.nchunks;
+                            TaskList<SweepTask<float, float>> tl{};
+                            tl.ntasks = 1;
+                            tl.total = (int)st.tiles();
+                            tl.single = t;
+                            tl.vec = sweep_vec(t);
+                            tl.corr = kind == kTuneSweepCorr ? 1 : 0;
+                            ms = time_ms([&] { return launch_sweep(tl, persistent_grid(tl.total), stream); }, 5);
+                        }
+                        if (ms < best) {
+                            best = ms;
+                            best_zc = zc;
+                        }
+                    }
+                    if (best_zc > 0) {
+                        std::lock_guard<std::mutex> lock(g_tune_mutex);
+                        g_tuned_zchunk[tune_key(kind, g)] = best_zc;
+                    }
+                }
+            }
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "autotune (z-chunks)");
+        // 2) where the one-CTA bottom starts (one problem): time whole V-cycle graphs
+        reset_cycle();
+        int rc = build_cycle();
+        if (rc != GMG_OK) return rc;
+        if (P.size() == 1 && P[0].L > 1 && stop_[0] < P[0].L - 1) {
+            const int first = stop_[0];
+            float best = 1e30f;
+            int best_lb = first;
+            for (int lb = first; lb < P[0].L; ++lb) {
+                forced_lb_ = lb;
+                reset_cycle();
+                if ((rc = build_cycle()) != GMG_OK) return rc;
+                if (upload_timing_ctl() != cudaSuccess) return fail(GMG_ERR_CUDA, "autotune: control upload failed");
+                const float ms = time_ms([&] { return run_cycle(); }, 5);
+                if (ms < best) {
+                    best = ms;
+                    best_lb = lb;
+                }
+            }
+            forced_lb_ = best_lb;
+            reset_cycle();
+            if ((rc = build_cycle()) != GMG_OK) return rc;
+        }
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune");
         return GMG_OK;
     }
 
@@ -1215,6 +1425,7 @@ void gmg_default_options(gmg_options* o)
     o->use_graph = 1;
     o->cycles_per_sync = 4;
     o->ir_inner_rtol = 1e-4;
+    o->autotune = 1;
 }
 
 int gmg_create(gmg_handle* h, int nx, int ny, int nz, const int* periodic, const gmg_options* opt,

@@ -196,7 +196,9 @@ struct ProblemMem {
     int64_t n0 = 0;
     int elem_tiles = 0;
     double* norm_part = nullptr;    // fine residual norm partials
-    int norm_tiles = 0;
+    int norm_tiles = 0;              // partials the finest residual writes (current tiling)
+    int norm_cap = 0;                // partials the buffer holds
+    int res_zchunk0 = 0;             // z-chunk depth of the finest residual, fixed per handle
     double* proj_part = nullptr;    // 3 per element tile
     double* bpart = nullptr;        // 1 per element tile
     double* gauge_part = nullptr;   // 1 per element tile
@@ -338,9 +340,10 @@ struct Engine {
                 }
             }
             if (!(M.mask = dalloc<uint8_t>(M.n0))) return fail(GMG_ERR_CUDA, "out of device memory");
-            M.norm_tiles = (int)level_res_tiling(M.g0, true).tiles();
             M.elem_tiles = ceil_div(M.n0, kElemTile);
-            total_norm += M.norm_tiles;
+            // room for the finest tiling any z-chunk depth can give
+            M.norm_cap = (int)std::max<int64_t>(res_tiling(M.g0).tiles(), march_tiling(M.g0, 1).tiles());
+            total_norm += M.norm_cap;
             total_elem += M.elem_tiles;
             if (ir) {
                 if (!(M.b64 = dalloc<double>(M.n0))) return fail(GMG_ERR_CUDA, "out of device memory");
@@ -370,19 +373,40 @@ struct Engine {
             M.bpart = bp + oe;
             M.gauge_part = gp + oe;
             M.ctl = ctl_dev + p;
-            on += M.norm_tiles;
+            on += M.norm_cap;
             oe += M.elem_tiles;
         }
+        if (upload_ctl_tasks() != GMG_OK) return fail(GMG_ERR_CUDA, "upload failed");
+        return build_cycle();
+    }
+
+    // tiling of the finest level's residual, as fixed by upload_ctl_tasks
+    static ResTiling res0_tiling(const ProblemMem& M)
+    {
+        return M.res_zchunk0 > 0 ? march_tiling(M.g0, M.res_zchunk0) : res_tiling(M.g0);
+    }
+
+    // control tasks: how many residual partials each problem's finest level
+    // writes (this follows the tuned tiling)
+    int upload_ctl_tasks()
+    {
+        const int nprob = (int)P.size();
         std::vector<CtlTask> cyc(nprob), ini(nprob), gau(nprob);
         for (int p = 0; p < nprob; ++p) {
             ProblemMem& M = P[p];
+            M.res_zchunk0 = res_marches(M.g0, true) ? march_tiling(M.g0).zchunk : 0;
+            M.norm_tiles = (int)res0_tiling(M).tiles();
+            if (M.norm_tiles > M.norm_cap) return GMG_ERR_CUDA;
             cyc[p] = CtlTask{M.ctl, M.norm_part, M.norm_tiles, nullptr, 0, nullptr, 0};
             ini[p] = CtlTask{M.ctl, M.norm_part, M.norm_tiles, M.bpart, M.elem_tiles, M.proj_part, M.elem_tiles};
             gau[p] = CtlTask{M.ctl, nullptr, 0, nullptr, 0, M.gauge_part, M.elem_tiles};
         }
-        if (!(cycle_ctl = upload(cyc)) || !(init_ctl = upload(ini)) || !(gauge_ctl = upload(gau)))
-            return fail(GMG_ERR_CUDA, "upload failed");
-        return build_cycle();
+        if (cycle_ctl) drop(cycle_ctl);
+        if (init_ctl) drop(init_ctl);
+        if (gauge_ctl) drop(gauge_ctl);
+        cycle_ctl = init_ctl = gauge_ctl = nullptr;
+        if (!(cycle_ctl = upload(cyc)) || !(init_ctl = upload(ini)) || !(gauge_ctl = upload(gau))) return GMG_ERR_CUDA;
+        return GMG_OK;
     }
 
     // device array + prefix of tile counts for a multi-task list
@@ -468,7 +492,8 @@ struct Engine {
         t.role = role;
         t.bc = restrict_to_next ? M.lev[l + 1].b : nullptr;
         for (int d = 0; d < 3; ++d) t.cf[d] = restrict_to_next ? Lm.cf[d] : 1;
-        const ResTiling rt = level_res_tiling(Lm.g, std::is_same<TP, float>::value);
+        const ResTiling rt = (l == 0 && M.res_zchunk0 > 0) ? res0_tiling(M)
+                                                            : level_res_tiling(Lm.g, std::is_same<TP, float>::value);
         t.tiles_x = rt.tx;
         t.tiles_y = rt.ty;
         t.tiles_z = rt.tz;
@@ -507,7 +532,7 @@ struct Engine {
                 for (int i : sel) {
                     const int p = probs[i];
                     v.push_back(res_task<float>(p, l, role[i], restrict_to_next, norm ? P[p].norm_part : nullptr));
-                    tiles.push_back(level_res_tiling(P[p].lev[l].g, true).tiles());
+                    tiles.push_back((int64_t)v.back().tiles_x * v.back().tiles_y * v.back().tiles_z);
                 }
                 op.kind = kResF;
                 if ((rc = make_list(v, tiles, op.r_f))) return rc;
@@ -1016,6 +1041,7 @@ struct Engine {
         if (e != cudaSuccess) return cuda_fail(e, "autotune (z-chunks)");
         // 2) where the one-CTA bottom starts (one problem): time whole V-cycle graphs
         reset_cycle();
+        if (upload_ctl_tasks() != GMG_OK) return fail(GMG_ERR_CUDA, "autotune: control task upload failed");
         int rc = build_cycle();
         if (rc != GMG_OK) return rc;
         if (P.size() == 1 && P[0].L > 1 && stop_[0] < P[0].L - 1) {

@@ -17,6 +17,7 @@ from typing import List, Optional, Sequence
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgmg.so")
 HEADER = os.path.join(HERE, "..", "include", "gmg.h")
+NET_HEADER = os.path.join(HERE, "..", "include", "gmg_net.h")
 
 OK, ERR_ARG, ERR_CUDA, NOT_CONVERGED, DIVERGED, NONFINITE = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {OK: "ok", ERR_ARG: "bad argument", ERR_CUDA: "cuda error",
@@ -91,15 +92,48 @@ def lib() -> ctypes.CDLL:
     L.gmg_op_coarsen_coeffs.argtypes = [c_int, c_int, c_int, ip, ip, vp, vp, vp, vp, vp, vp, vp]
     L.gmg_op_residual_norm.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
     L.gmg_op_residual_norm_noalloc.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
+    _net_signatures(L)
     _lib = L
     return L
 
 
+def _net_signatures(L):
+    vp, c_int, c_float, c_ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "gmg_net_conv3": [c_int, c_int, c_int, vp, c_int, c_int, vp, vp, c_int, c_int, vp, c_int, c_int, vp],
+        "gmg_net_conv3_wgrad": [c_int, c_int, c_int, vp, c_int, c_int, vp, c_int, c_int, vp, vp, vp],
+        "gmg_net_relu_backward": [c_int, c_int, c_int, vp, c_int, vp, c_int, c_int, vp],
+        "gmg_net_pool2": [c_int, c_int, c_int, vp, c_int, c_int, vp, c_int, c_int, vp],
+        "gmg_net_pool2_backward": [c_int, c_int, c_int, vp, c_int, c_int, vp, c_int, vp, c_int, c_int, vp],
+        "gmg_net_up2": [c_int, c_int, c_int, vp, c_int, c_int, vp, c_int, c_int, vp],
+        "gmg_net_up2_backward": [c_int, c_int, c_int, vp, c_int, c_int, c_int, vp, c_int, vp],
+        "gmg_net_pack_input": [c_int, c_int, c_int, vp, vp, vp, vp, vp, ip, vp, vp, vp, vp],
+        "gmg_net_head": [c_int, c_int, c_int, vp, c_int, vp, vp, vp, vp],
+        "gmg_net_loss": [c_int, c_int, c_int, vp, vp, vp, vp, vp, vp, vp],
+        "gmg_net_head_backward": [c_int, c_int, c_int, vp, vp, c_int, vp, vp, vp, vp, vp],
+        "gmg_net_unscale": [c_ll, vp, vp, vp, vp],
+        "gmg_net_adam": [c_ll, vp, vp, vp, vp, c_int, c_float, c_float, c_float, c_float, vp, vp, c_int, c_int, vp],
+        "gmg_net_zero": [c_ll, vp, vp],
+    }
+    for name, args in sig.items():
+        getattr(L, name).argtypes = args
+
+
+def net_call(name: str, *args) -> None:
+    """Call one gmg_net_* entry point; raise on a non-zero status."""
+    rc = getattr(lib(), name)(*args)
+    if rc != 0:
+        raise GmgError(f"{name} failed with status {rc}")
+
+
 def declared_functions() -> List[str]:
-    """Names of the functions declared in include/gmg.h."""
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gmg_\w+)\s*\(", text, flags=re.M)))
+    """Names of the functions declared in include/gmg.h and include/gmg_net.h."""
+    names = set()
+    for path in (HEADER, NET_HEADER):
+        text = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gmg_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
 
 
 def options(coarsen: str = "aniso", precision: str = "fp32", **kw) -> Options:

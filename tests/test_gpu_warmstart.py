@@ -1,0 +1,428 @@
+"""Parity of the warm-start network's kernels (BF16 tensor-core convolutions,
+FP32 sums) with the FP64 network oracle, and the gain of the trained net.
+
+Inputs are rounded to BF16 on the host before both sides see them, so the
+oracle computes exactly on the values the kernels multiply.  Tolerances:
+one BF16 rounding of each output (relative 2^-9, checked as 2^-8) for a
+single kernel; FP32 accumulation error (~1e-4 of the sum of |terms|) for the
+weight gradient; for the whole network a relative L2 error that allows one
+BF16 rounding per layer along the forward and the backward chain.
+"""
+import numpy as np
+import pytest
+
+from oracle import warmstart_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+U_BF16 = 2.0 ** -8
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def bf(a):
+    """Host float64 values of the BF16 rounding of a."""
+    torch = _torch()
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def to_cl(a, cs=None, off=0):
+    """[C][D][H][W] host array -> channels-last BF16 device tensor with cs channels."""
+    torch = _torch()
+    c = a.shape[0]
+    cs = cs or c
+    out = np.zeros((int(np.prod(a.shape[1:])), cs), dtype=np.float32)
+    out[:, off:off + c] = a.reshape(c, -1).T
+    return torch.from_numpy(out).to("cuda:0").to(torch.bfloat16)
+
+
+def from_cl(t, shape, c0=0, c=None):
+    """Channels-last device tensor -> [C][D][H][W] float64 host array."""
+    a = t.float().cpu().numpy().astype(np.float64)
+    c = c or a.shape[1] - c0
+    return np.ascontiguousarray(a[:, c0:c0 + c].T.reshape((c,) + tuple(shape)))
+
+
+def ptr(t, off=0):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr() + off * t.element_size())
+
+
+def stream():
+    import ctypes
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def call(name, *args):
+    from paper_2607_07687_gb300 import binding as G
+    G.net_call(name, *args)
+
+
+def pack_weights(w):
+    """[co][ci][3][3][3] -> FP32 device tensor packed [27][co][ci], its BF16 copy and flipped copy."""
+    torch = _torch()
+    co, ci = w.shape[:2]
+    wp = np.ascontiguousarray(w.reshape(co, ci, 27).transpose(2, 0, 1), dtype=np.float32)
+    w32 = torch.from_numpy(wp.ravel()).to("cuda:0")
+    z = torch.zeros_like(w32)
+    m, v = torch.zeros_like(w32), torch.zeros_like(w32)
+    wb = torch.zeros((27, co, ci), dtype=torch.bfloat16, device="cuda:0")
+    wt = torch.zeros((27, ci, co), dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_adam", w32.numel(), ptr(w32), ptr(z), ptr(m), ptr(v), 1, 0.0, 0.9, 0.999, 1e-8, ptr(wb), ptr(wt),
+         co, ci, stream())
+    return w32, wb, wt
+
+
+def rand_w(rng, co, ci):
+    return bf(rng.standard_normal((co, ci, 3, 3, 3)) * np.sqrt(2.0 / (27 * ci)))
+
+
+# ------------------------------------------------------------------ convolution
+
+@pytest.mark.parametrize("ci,co", [(16, 16), (16, 32), (32, 48), (32, 64), (96, 32), (48, 96), (64, 16)])
+def test_conv3_forward(ci, co):
+    torch = _torch()
+    rng = np.random.default_rng(ci * 100 + co)
+    shape = (3, 6, 40)                         # ragged against the 4 x 32 tile
+    x = bf(rng.standard_normal((ci,) + shape))
+    w = rand_w(rng, co, ci)
+    b = rng.standard_normal(co).astype(np.float32).astype(np.float64)
+    _, wb, _ = pack_weights(w)
+    bias = torch.from_numpy(b.astype(np.float32)).to("cuda:0")
+    xt = to_cl(x)
+    for relu in (0, 1):
+        y = torch.zeros((xt.shape[0], co), dtype=torch.bfloat16, device="cuda:0")
+        call("gmg_net_conv3", shape[0], shape[1], shape[2], ptr(xt), ci, ci, ptr(wb), ptr(bias), co, relu, ptr(y),
+             co, 0, stream())
+        ref = O.conv3(x, w, b)
+        if relu:
+            ref = O.relu(ref)
+        got = from_cl(y, shape)
+        err = np.abs(got - ref)
+        assert np.all(err <= U_BF16 * np.abs(ref) + 1e-5 * np.abs(ref).max()), (relu, err.max())
+
+
+def test_conv3_channel_offsets_and_bias_free():
+    """Input read from channels 16..47 of a 48-channel buffer, output written to
+    channels 16..79 of an 80-channel buffer; the other channels stay untouched."""
+    torch = _torch()
+    rng = np.random.default_rng(7)
+    shape = (4, 5, 33)
+    ci, co = 32, 64
+    x = bf(rng.standard_normal((ci,) + shape))
+    junk = bf(rng.standard_normal((16,) + shape))
+    w = rand_w(rng, co, ci)
+    _, wb, _ = pack_weights(w)
+    xt = to_cl(x, 48, 16)
+    xt[:, :16] = to_cl(junk)
+    y = torch.full((xt.shape[0], 80), 3.0, dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_conv3", *shape, ptr(xt, 16), 48, ci, ptr(wb), None, co, 0, ptr(y), 80, 16, stream())
+    ref = O.conv3(x, w, np.zeros(co))
+    got = from_cl(y, shape, 16, co)
+    assert np.all(np.abs(got - ref) <= U_BF16 * np.abs(ref) + 1e-5 * np.abs(ref).max())
+    yh = y.float().cpu().numpy()
+    assert np.all(yh[:, :16] == 3.0)
+
+
+@pytest.mark.parametrize("ci,co", [(16, 16), (32, 64), (96, 32), (48, 16)])
+def test_conv3_input_gradient(ci, co):
+    """The forward kernel on the flipped transposed weights is the adjoint."""
+    torch = _torch()
+    rng = np.random.default_rng(ci + 7 * co)
+    shape = (5, 7, 36)
+    w = rand_w(rng, co, ci)
+    g = bf(rng.standard_normal((co,) + shape))
+    _, _, wt = pack_weights(w)
+    gt = to_cl(g)
+    gx = torch.zeros((gt.shape[0], ci), dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_conv3", *shape, ptr(gt), co, co, ptr(wt), None, ci, 0, ptr(gx), ci, 0, stream())
+    ref = O.conv3_backward(np.zeros((ci,) + shape), w, g)[0]
+    got = from_cl(gx, shape)
+    assert np.all(np.abs(got - ref) <= U_BF16 * np.abs(ref) + 1e-5 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("ci,co,shape", [(16, 16, (3, 6, 40)), (48, 32, (4, 8, 12)), (96, 64, (2, 4, 20)),
+                                         (32, 32, (16, 16, 16))])
+def test_conv3_weight_gradient(ci, co, shape):
+    torch = _torch()
+    rng = np.random.default_rng(ci * 3 + co)
+    x = bf(rng.standard_normal((ci,) + shape))
+    g = bf(rng.standard_normal((co,) + shape))
+    xt, gt = to_cl(x), to_cl(g)
+    dw = torch.full((27 * co * ci,), 0.5, dtype=torch.float32, device="cuda:0")   # accumulates
+    db = torch.full((co,), 0.25, dtype=torch.float32, device="cuda:0")
+    call("gmg_net_conv3_wgrad", *shape, ptr(xt), ci, ci, ptr(gt), co, co, ptr(dw), ptr(db), stream())
+    _, gw, gb = O.conv3_backward(x, np.zeros((co, ci, 3, 3, 3)), g)
+    _, aw, ab = O.conv3_backward(np.abs(x), np.zeros((co, ci, 3, 3, 3)), np.abs(g))
+    got = dw.cpu().numpy().astype(np.float64).reshape(27, co, ci).transpose(1, 2, 0).reshape(co, ci, 3, 3, 3)
+    assert np.all(np.abs(got - 0.5 - gw) <= 1e-4 * aw + 1e-6)
+    assert np.all(np.abs(db.cpu().numpy() - 0.25 - gb) <= 1e-4 * ab + 1e-6)
+
+
+# ------------------------------------------------------------------ elementwise
+
+def test_pool_upsample_relu_kernels():
+    torch = _torch()
+    rng = np.random.default_rng(11)
+    C, shape = 16, (6, 10, 14)
+    cshape = tuple(s // 2 for s in shape)
+    x = bf(rng.standard_normal((C,) + shape))
+    xt = to_cl(x, 32, 16)
+    # pool into channels 8..23 of a 32-channel coarse buffer
+    y = torch.zeros((int(np.prod(cshape)), 32), dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_pool2", *shape, ptr(xt, 16), 32, C, ptr(y), 32, 8, stream())
+    ref = O.pool2(x)
+    assert np.all(np.abs(from_cl(y, cshape, 8, C) - ref) <= U_BF16 * np.abs(ref) + 1e-7)
+    # up2 (a copy: exact)
+    xc = bf(rng.standard_normal((C,) + cshape))
+    xct = to_cl(xc)
+    yu = torch.zeros((int(np.prod(shape)), 48), dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_up2", *cshape, ptr(xct), C, C, ptr(yu), 48, 32, stream())
+    assert np.array_equal(from_cl(yu, shape, 32, C), O.up2(xc))
+    # up2 backward from channels 16..31 of a 48-channel gradient
+    gy = bf(rng.standard_normal((C,) + shape))
+    gyt = to_cl(gy, 48, 16)
+    gx = torch.zeros((int(np.prod(cshape)), C), dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_up2_backward", *cshape, ptr(gyt), 48, 16, C, ptr(gx), C, stream())
+    ref = O.up2_backward(gy)
+    assert np.all(np.abs(from_cl(gx, cshape) - ref) <= U_BF16 * np.abs(ref) + 1e-6)
+    # pool backward plus a skip gradient taken from channels 32..47
+    gc = bf(rng.standard_normal((C,) + cshape))
+    add = bf(rng.standard_normal((C,) + shape))
+    gct, addt = to_cl(gc), to_cl(add, 48, 32)
+    gf = torch.zeros((int(np.prod(shape)), C), dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_pool2_backward", *shape, ptr(gct), C, C, ptr(gf), C, ptr(addt), 48, 32, stream())
+    ref = O.pool2_backward(gc) + add
+    assert np.all(np.abs(from_cl(gf, shape) - ref) <= U_BF16 * np.abs(ref) + 1e-7)
+    # relu backward against an activation read from channels 16..31
+    act = O.relu(bf(rng.standard_normal((C,) + shape)))
+    actt = to_cl(act, 32, 16)
+    g = bf(rng.standard_normal((C,) + shape))
+    gt = to_cl(g)
+    call("gmg_net_relu_backward", *shape, ptr(gt), C, ptr(actt, 16), 32, C, stream())
+    assert np.array_equal(from_cl(gt, shape), g * (act > 0))
+
+
+def beta_mean(bx, by, bz, periodic):
+    """Mean of each cell's six face coefficients; faces on walls are zero."""
+    out = np.zeros(bx.shape)
+    for axis_arr, ax, per in ((bx, 2, periodic[0]), (by, 1, periodic[1]), (bz, 0, periodic[2])):
+        lo = axis_arr.copy()
+        hi = np.roll(axis_arr, -1, axis=ax)
+        if not per:
+            idx = [slice(None)] * 3
+            idx[ax] = 0
+            lo[tuple(idx)] = 0.0
+            idx[ax] = -1
+            hi[tuple(idx)] = 0.0
+        out += lo + hi
+    return out / 6.0
+
+
+@pytest.mark.parametrize("periodic", [(False, False, False), (True, False, True)])
+def test_pack_input(periodic):
+    import ctypes
+    torch = _torch()
+    rng = np.random.default_rng(5)
+    shape = (4, 6, 8)
+    b = rng.standard_normal(shape).astype(np.float32)
+    pp = rng.standard_normal(shape).astype(np.float32)
+    bx, by, bz = (rng.uniform(0, 1, shape).astype(np.float32) for _ in range(3))
+    T = lambda a: torch.from_numpy(a).to("cuda:0")
+    x0 = torch.full((b.size, 16), 9.0, dtype=torch.bfloat16, device="cuda:0")
+    s = torch.zeros(1, dtype=torch.float32, device="cuda:0")
+    red = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    per = (ctypes.c_int * 3)(*[int(v) for v in periodic])
+    bt, pt, bxt, byt, bzt = T(b), T(pp), T(bx), T(by), T(bz)
+    call("gmg_net_pack_input", *shape, ptr(bt), ptr(pt), ptr(bxt), ptr(byt), ptr(bzt), per, ptr(x0), ptr(s), ptr(red),
+         stream())
+    bm = beta_mean(*(a.astype(np.float64) for a in (bx, by, bz)), periodic)
+    ref, sref = O.features(b.astype(np.float64), bm, pp.astype(np.float64))
+    assert float(s.item()) == pytest.approx(sref, rel=1e-6)
+    got = from_cl(x0, shape)
+    assert np.all(np.abs(got[:3] - ref) <= U_BF16 * np.abs(ref) + 1e-6)
+    assert np.all(got[3:] == 0.0)
+
+
+def test_head_loss_and_head_backward():
+    torch = _torch()
+    rng = np.random.default_rng(9)
+    shape = (4, 8, 8)
+    n = int(np.prod(shape))
+    h = O.relu(bf(rng.standard_normal((16,) + shape)))
+    w = rng.standard_normal(16).astype(np.float32)
+    bb = np.array([0.3], dtype=np.float32)
+    ht = to_cl(h)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda:0")
+    wt, bt = T(w), T(bb)
+    out = torch.zeros(n, dtype=torch.float32, device="cuda:0")
+    call("gmg_net_head", *shape, ptr(ht), 16, ptr(wt), ptr(bt), ptr(out), stream())
+    ref = np.einsum("i,izyx->zyx", w.astype(np.float64), h) + 0.3
+    got = out.cpu().numpy().astype(np.float64).reshape(shape)
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-5)
+    # loss on out against target / s
+    target = rng.standard_normal(shape).astype(np.float32)
+    s = np.float32(2.5)
+    gout = torch.zeros_like(out)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    red = torch.zeros(4, dtype=torch.float64, device="cuda:0")
+    tt, st = T(target), T(np.array([s]))
+    call("gmg_net_loss", *shape, ptr(out), ptr(tt), ptr(st), ptr(gout), ptr(loss), ptr(red), stream())
+    lref, gref = O.loss_and_grad_out(float(s) * got, target.astype(np.float64))
+    assert float(loss.item()) == pytest.approx(lref, rel=1e-5)
+    # d loss / d out = s * d loss / d p0
+    np.testing.assert_allclose(gout.cpu().numpy().reshape(shape), float(s) * gref, rtol=1e-4,
+                               atol=1e-6 * np.abs(gref).max() * float(s))
+    # head backward
+    go = rng.standard_normal(shape).astype(np.float32)
+    gh = torch.zeros((n, 16), dtype=torch.bfloat16, device="cuda:0")
+    dw = torch.zeros(16, dtype=torch.float32, device="cuda:0")
+    db = torch.zeros(1, dtype=torch.float32, device="cuda:0")
+    got_ = T(go)
+    call("gmg_net_head_backward", *shape, ptr(got_), ptr(ht), 16, ptr(wt), ptr(gh), ptr(dw), ptr(db), stream())
+    g64 = go.astype(np.float64)
+    refgh = w.astype(np.float64)[:, None, None, None] * g64[None]
+    assert np.all(np.abs(from_cl(gh, shape) - refgh) <= U_BF16 * np.abs(refgh) + 1e-7)
+    aw = np.einsum("zyx,izyx->i", np.abs(g64), np.abs(h))
+    assert np.all(np.abs(dw.cpu().numpy() - np.einsum("zyx,izyx->i", g64, h)) <= 1e-5 * aw + 1e-6)
+    assert float(db.item()) == pytest.approx(g64.sum(), abs=1e-5 * np.abs(g64).sum())
+
+
+def test_adam_matches_oracle_and_packs():
+    torch = _torch()
+    rng = np.random.default_rng(12)
+    co, ci = 16, 32
+    w0 = rng.standard_normal((27, co, ci)).astype(np.float32)
+    w = torch.from_numpy(w0.ravel().copy()).to("cuda:0")
+    m, v = torch.zeros_like(w), torch.zeros_like(w)
+    wb = torch.zeros((27, co, ci), dtype=torch.bfloat16, device="cuda:0")
+    wt = torch.zeros((27, ci, co), dtype=torch.bfloat16, device="cuda:0")
+    params = {"a": w0.ravel().astype(np.float64)}
+    state = {}
+    for t in range(1, 4):
+        g = rng.standard_normal(w0.size).astype(np.float32)
+        gt = torch.from_numpy(g).to("cuda:0")
+        call("gmg_net_adam", w.numel(), ptr(w), ptr(gt), ptr(m), ptr(v), t, 1e-2, 0.9, 0.999, 1e-8, ptr(wb), ptr(wt),
+             co, ci, stream())
+        O.adam_step(params, {"a": g.astype(np.float64)}, state, lr=1e-2)
+    got = w.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, params["a"], rtol=0, atol=1e-5)
+    wf = got.astype(np.float32).reshape(27, co, ci)
+    assert np.array_equal(wb.float().cpu().numpy(), bf(wf).astype(np.float32))
+    flip = wf[::-1].transpose(0, 2, 1)
+    assert np.array_equal(wt.float().cpu().numpy(), bf(flip).astype(np.float32))
+
+
+# ------------------------------------------------------------------ whole network
+
+def _net_and_inputs(seed=21, dims=(32, 16, 16)):
+    torch = _torch()
+    from paper_2607_07687_gb300.warmstart import WarmStartNet
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    params = O.init_params(seed)
+    for k in params:
+        if k.endswith(".b"):
+            params[k] = rng.standard_normal(params[k].shape) * 0.05
+    net = WarmStartNet(dims, seed=0)
+    net.set_weights(params)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda:0")
+    b = rng.standard_normal(shape)
+    pp = rng.standard_normal(shape)
+    coef = [rng.uniform(0.2, 1.0, shape) for _ in range(3)]
+    target = rng.standard_normal(shape) + 0.5 * pp
+    dev = [T(a) for a in (b, *coef, pp, target)]
+    # the kernels compute with BF16 weights, FP32 biases and head
+    used = {}
+    for k, v in params.items():
+        used[k] = bf(v) if (k.endswith(".w") and not k.startswith("out")) else v.astype(np.float32).astype(np.float64)
+    return net, dev, used, shape
+
+
+def test_network_forward_and_gradients_match_oracle():
+    net, (b, bx, by, bz, pp, target), used, shape = _net_and_inputs()
+    net.pack(b, bx, by, bz, pp)
+    net.forward()
+    x0 = from_cl(net.a["x0"], shape)[:3]
+    out_ref, cache = O.forward(used, x0)
+    out = net.out.cpu().numpy().astype(np.float64).reshape(shape)
+    fwd = np.linalg.norm(out - out_ref) / np.linalg.norm(out_ref)
+    assert fwd <= 3e-2, fwd
+    net.loss(target)
+    s = float(net.s.item())
+    # the oracle's loss gradient at the oracle's own output (same target / s)
+    _, gref = O.loss_and_grad_out(out_ref, target.cpu().numpy().astype(np.float64) / s)
+    net.backward()
+    grads = net.gradients()
+    ref = O.backward(used, cache, gref)
+    worst = {}
+    for k in ref:
+        a, r = grads[k].ravel(), ref[k].ravel()
+        rel = np.linalg.norm(a - r) / max(np.linalg.norm(r), 1e-30)
+        cos = float(a @ r / max(np.linalg.norm(a) * np.linalg.norm(r), 1e-30))
+        worst[k] = (rel, cos)
+    bad = {k: v for k, v in worst.items() if not (v[0] <= 0.1 and v[1] >= 0.995)}
+    assert not bad, bad
+
+
+def test_training_lowers_the_loss():
+    """Adam steps on one (input, target) pair drive the loss down."""
+    net, (b, bx, by, bz, pp, target), _, _ = _net_and_inputs(seed=22)
+    losses = [net.train_step(b, bx, by, bz, pp, target) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+def test_warm_start_gain_on_vortex_sequence():
+    """A net trained on GMG solves of one vortex sequence (seed 31) gives a
+    held-out sequence (seed 4) initial guesses that save V-cycles against the
+    zero guess, at the same tolerance."""
+    torch = _torch()
+    from paper_2607_07687_gb300 import binding as G
+    from paper_2607_07687_gb300 import inputs as I
+    from paper_2607_07687_gb300.warmstart import WarmStartNet
+    geo = dict(nx=64, ny=32, nz=32, radius=4.0, center_x=16.0, blob_sigma=3.0)
+    tol = 1e-5
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda:0")
+
+    def frames(seed, count):
+        seq = I.VortexSequence(seed=seed, **geo)
+        out = []
+        for _ in range(count):
+            out.append(seq.problem())
+            seq.advance()
+        return out
+
+    train = frames(31, 24)
+    held = frames(4, 8)
+    dims = train[0].dims
+    solver = G.Solver(dims, (False, False, False), precision="fp32", autotune=0)
+    p0 = train[0]
+    coef = [T(a) for a in (p0.bx, p0.by, p0.bz)]
+    solver.set_coeffs(*coef)
+
+    def solve(prob, guess):
+        p = guess.clone()
+        info = solver.solve(T(prob.b), p, tol)
+        assert info.status == 0
+        return p, info.cycles
+
+    sols = [solve(pr, torch.zeros(pr.cells, device="cuda:0"))[0] for pr in train]
+    net = WarmStartNet(dims, seed=0, lr=2e-3)
+    for epoch in range(12):
+        for t in range(1, len(train)):
+            net.train_step(T(train[t].b), *coef, sols[t - 1], sols[t])
+    zero_c, net_c = [], []
+    prev = solve(held[0], torch.zeros(held[0].cells, device="cuda:0"))[0]
+    for pr in held[1:]:
+        z = solve(pr, torch.zeros(pr.cells, device="cuda:0"))
+        guess = net.infer(T(pr.b), *coef, prev).clone()
+        w = solve(pr, guess)
+        zero_c.append(z[1])
+        net_c.append(w[1])
+        prev = z[0]
+    solver.close()
+    assert np.mean(net_c) < np.mean(zero_c), (zero_c, net_c)

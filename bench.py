@@ -215,6 +215,167 @@ def kernel_only(args):
     return 0
 
 
+# per-layer (input channels actually used, output channels, level) of the warm-start network
+NET_LAYERS = [(3, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 64, 2), (96, 32, 1), (32, 32, 1),
+              (48, 16, 0), (16, 16, 0)]
+
+
+def net_forward_flops(cells):
+    """Algorithmic FLOPs of one forward pass: 2 x cells x 27 x ci x co per 3x3x3 convolution
+    (unpadded input channels), plus the 1x1x1 head."""
+    return sum(2.0 * cells / 8 ** lv * 27 * ci * co for ci, co, lv in NET_LAYERS) + 2.0 * cells * 16
+
+
+def warmstart_bench(args):
+    """Learned warm start on the advected-vortex sphere channel (192 x 64 x 64,
+    sphere r = 8 at x = 48, three Gaussian vortex blobs of width 6 moving +1
+    cell per step): the net is trained on GMG solves of sequences with seeds
+    disjoint from the evaluation seed 4, then each of the evaluation steps is
+    solved to 1e-6 from the zero guess, the previous step's pressure and the
+    net's prediction; V-cycles and wall times (CUDA events) are compared."""
+    import numpy as np
+    from paper_2607_07687_gb300 import inputs as I
+    geo = dict(nx=192, ny=64, nz=64)
+    workers = max(1, min(16, len(os.sched_getaffinity(0))))
+    t0 = time.perf_counter()
+    train_seeds = [int(x) for x in args.train_seeds.split(",")]
+    train_rhs = []
+    walls = None
+    for sd in train_seeds:
+        walls, rhs = I.vortex_frames(args.train_frames, workers=workers, seed=sd, **geo)
+        train_rhs.append(rhs)
+    walls, eval_rhs = I.vortex_frames(args.frames, workers=workers, seed=4, **geo)
+    gen_s = time.perf_counter() - t0
+
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    from paper_2607_07687_gb300.warmstart import WarmStartNet
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nz, ny, nx = walls[0].shape
+    dims = (nx, ny, nz)
+    cells = nx * ny * nz
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev).reshape(-1)
+    coef = [f32(a) for a in walls]
+    solver = G.Solver(dims, (False, False, False), precision="ir64_fp32")
+    solver.set_coeffs(*coef)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def solve(b64, guess64):
+        p = guess64.clone()
+        torch.cuda.synchronize()
+        ev0.record()
+        info = solver.solve(b64, p, TOL)
+        ev1.record()
+        torch.cuda.synchronize()
+        if info.status != 0:
+            raise RuntimeError(f"solve status {info.status}")
+        return p, info.cycles, ev0.elapsed_time(ev1)
+
+    # training pairs: (sigma_t, p*_{t-1}, p*_t) from GMG solves of the training sequences
+    t0 = time.perf_counter()
+    samples = []
+    for rhs in train_rhs:
+        p = torch.zeros(cells, dtype=torch.float64, device=dev)
+        prev32 = None
+        for b in rhs:
+            b32 = f32(b)
+            p, _, _ = solve(b32.double(), p)
+            p32 = p.float()
+            if prev32 is not None:
+                samples.append((b32, prev32, p32))
+            prev32 = p32
+    targets_s = time.perf_counter() - t0
+
+    net = WarmStartNet(dims, seed=0, lr=args.lr)
+    rng = np.random.default_rng(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 0
+    for _ in range(args.epochs):
+        for i in rng.permutation(len(samples)):
+            b32, prev32, p32 = samples[i]
+            net.pack(b32, *coef, prev32)
+            net.forward()
+            net.loss(p32, prev32)
+            net.backward()
+            net.step()
+            steps += 1
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    losses = []
+    for b32, prev32, p32 in samples[:: max(1, len(samples) // 32)]:
+        net.pack(b32, *coef, prev32)
+        net.forward()
+        net.loss(p32, prev32)
+        losses.append(float(net.loss_dev.item()))
+
+    # forward throughput (tensor-core contraction) on one evaluation input
+    b32 = f32(eval_rhs[0])
+    z32 = torch.zeros(cells, dtype=torch.float32, device=dev)
+    net.pack(b32, *coef, z32)
+    for _ in range(3):
+        net.forward()
+    reps = 20
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        net.forward()
+    ev1.record()
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / reps
+    ev0.record()
+    for _ in range(reps):
+        net.train_step(b32, *coef, z32, z32)
+    ev1.record()
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1) / reps
+
+    # evaluation: zero, previous-step and learned initial guesses
+    rec = {"zero": ([], []), "previous": ([], []), "net": ([], [])}
+    infer_ms = []
+    zero64 = torch.zeros(cells, dtype=torch.float64, device=dev)
+    prev64, _, _ = solve(f32(eval_rhs[0]).double(), zero64)
+    for b in eval_rhs[1:]:
+        b32 = f32(b)
+        b64 = b32.double()
+        pz, cz, tz = solve(b64, zero64)
+        _, cp, tp = solve(b64, prev64)
+        prev32 = prev64.float()
+        torch.cuda.synchronize()
+        ev0.record()
+        guess = net.infer(b32, *coef, prev32)
+        g64 = guess.double()
+        ev1.record()
+        torch.cuda.synchronize()
+        ti = ev0.elapsed_time(ev1)
+        _, cn, tn = solve(b64, g64)
+        for k, c, t in (("zero", cz, tz), ("previous", cp, tp), ("net", cn, tn + ti)):
+            rec[k][0].append(c)
+            rec[k][1].append(t)
+        infer_ms.append(ti)
+        prev64 = pz
+    solver.close()
+    mean = lambda v: float(np.mean(v))
+    gflop = net_forward_flops(cells) / 1e9
+    line = {"metric": "learned warm start: V-cycles and time to 1e-6 vs zero / previous-step guess",
+            "workload": f"vortex_sphere_channel_{nx}x{ny}x{nz}", "eval_seed": 4, "eval_steps": len(eval_rhs) - 1,
+            "tol": TOL, "precision": "ir64_fp32 solves; BF16 network, FP32 accumulate",
+            "cycles_mean": {k: mean(v[0]) for k, v in rec.items()},
+            "solve_ms_mean": {k: mean(v[1]) for k, v in rec.items()},
+            "net_infer_ms_mean": mean(infer_ms),
+            "cycles_hist": {k: {str(c): int(n) for c, n in zip(*np.unique(v[0], return_counts=True))}
+                            for k, v in rec.items()},
+            "train": {"seeds": train_seeds, "frames_per_seed": args.train_frames, "samples": len(samples),
+                      "epochs": args.epochs, "steps": steps, "lr": args.lr, "seconds": train_s,
+                      "loss_mean_after": mean(losses), "ms_per_step": train_ms},
+            "forward": {"ms": fwd_ms, "gflop": gflop, "tflops": gflop / fwd_ms,
+                        "train_step_tflops": 3 * gflop / train_ms},
+            "setup_seconds": {"sources_cpu": gen_s, "training_targets_gpu": targets_s}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,9 +387,18 @@ def main():
                     help="only launch one kernel --reps times on a --grid (for profiler captures)")
     ap.add_argument("--grid", default="512,256,128", help="nx,ny,nz of the --kernel grid")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmstart", action="store_true",
+                    help="run the learned warm-start experiment instead of the solve benchmark")
+    ap.add_argument("--frames", type=int, default=200, help="evaluation steps of the vortex sequence")
+    ap.add_argument("--train-seeds", default="101,102")
+    ap.add_argument("--train-frames", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--lr", type=float, default=1e-3)
     args = ap.parse_args()
     if args.kernel:
         return kernel_only(args)
+    if args.warmstart:
+        return warmstart_bench(args)
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)

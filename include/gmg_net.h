@@ -84,19 +84,21 @@ int gmg_net_head(int D, int H, int W, const gmg_bf16* h, int ch, const float* w,
                  void* stream);
 
 /*
- * Loss |(out - mean out) - (t - mean t)|^2 / |t - mean t|^2 with t = target / s
- * (target FP32, s device float); writes the loss to *loss (device double) and
- * d(loss)/d(out) to gout.  Uses scratch red (device double[4]).
+ * Loss of the prediction q = out + p_prev / s against t = target / s:
+ * |(q - mean q) - (t - mean t)|^2 / |t - mean t|^2 (target and p_prev FP32,
+ * p_prev may be NULL: zero; s device float).  Writes the loss to *loss
+ * (device double) and d(loss)/d(out) to gout.  Uses scratch red (device double[4]).
  */
-int gmg_net_loss(int D, int H, int W, const float* out, const float* target, const float* s, float* gout,
-                 double* loss, double* red, void* stream);
+int gmg_net_loss(int D, int H, int W, const float* out, const float* target, const float* p_prev, const float* s,
+                 float* gout, double* loss, double* red, void* stream);
 
 /* Head backward: gh[c] = w[c] gout, dw[c] += sum gout h[c], db[0] += sum gout. */
 int gmg_net_head_backward(int D, int H, int W, const float* gout, const gmg_bf16* h, int ch, const float* w,
                           gmg_bf16* gh, float* dw, float* db, void* stream);
 
-/* p0 = s * out (the scaled prediction, FP32). */
-int gmg_net_unscale(long long n, const float* out, const float* s, float* p0, void* stream);
+/* p0 = s * out + p_prev (the prediction: the network gives the increment over
+ * the previous pressure in units of s; p_prev may be NULL: zero). */
+int gmg_net_unscale(long long n, const float* out, const float* s, const float* p_prev, float* p0, void* stream);
 
 /*
  * Adam on n FP32 parameters (step number t >= 1, bias-corrected moments).

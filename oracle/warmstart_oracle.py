@@ -15,6 +15,8 @@ definitions, in FP64, on arrays laid out [C][D][H][W] (z, y, x):
     relu:     max(v, 0)
     pool:     mean of each 2 x 2 x 2 block
     upsample: each value copied to its 2 x 2 x 2 block
+    output:   p0 = s * net(x0) + p_prev  (the net predicts the increment over
+              the previous pressure, in units of s)
     loss:     |(p0 - mean p0) - (p* - mean p*)|^2 / |p* - mean p*|^2
 
 Backward passes are the adjoints of these maps, written out term by term.
@@ -191,6 +193,13 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         mh = m / (1 - b1 ** t)
         vh = v / (1 - b2 ** t)
         params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+def predict(params, b, beta_mean, p_prev):
+    """Initial guess p0 = s * net(x0) + p_prev, with the network's cache and s."""
+    x0, s = features(b, beta_mean, p_prev)
+    out, cache = forward(params, x0)
+    return s * out + p_prev, cache, s
 
 
 def features(b, beta_mean, p_prev):

@@ -67,11 +67,13 @@ __device__ __forceinline__ float diag_sum(float bxl, float bxu, float byl, float
 
 // under-relaxed Gauss-Seidel update of one cell (Sec. 3.1) in correction form:
 // (1 - w) p + w (sum beta p_nb - b) / diag = p + w ((A p)_I - b_I) / diag;
-// isolated cells (diag = 0) keep p
+// isolated cells (diag = 0) keep p.  The quotient is the fast approximate one
+// (2 ulp): a smoother step needs no correctly rounded division, and the
+// residual that decides convergence is computed without it.
 __device__ __forceinline__ float gs_update(float p, float flux, float dg, float b, float w)
 {
     if (!(dg > 0.f)) return p;
-    return p + w * ((flux - b) / dg);
+    return p + w * __fdividef(flux - b, dg);
 }
 
 template <class Task>

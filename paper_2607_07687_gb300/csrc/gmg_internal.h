@@ -13,6 +13,7 @@
 // copying the grid.  Coarse levels use rot == nullptr (fixed roles).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -45,6 +46,15 @@ using bf16 = __nv_bfloat16;
 struct Geo {
     int n[3];      // nx, ny, nz
     int per[3];    // periodic flags
+};
+
+// Tensor maps of one FP32 level for the tensor-memory-accelerator plane
+// copies of the pipelined sweep and residual: 3-D maps (x, y, z) with a box of
+// one (kSweepTX + 8) x (kSweepTY + 4) plane, zero fill outside the grid.
+// Lives in device memory; p[r] maps iterate buffer r.
+struct TmaPlanes {
+    CUtensorMap p[3];
+    CUtensorMap b, x, y, z;
 };
 
 // Per-problem solve state, resident in device memory.
@@ -94,6 +104,7 @@ struct SweepTask {
     int tiles_x, tiles_y, zchunk, nchunks;
     float omega;         // used when ctl == nullptr
     const Ctl* ctl;
+    const TmaPlanes* tma;  // plane copies by TMA (FP32, 16-byte rows), or nullptr
 };
 
 // Residual of one level, restricted to the next level and/or summed in squares.
@@ -113,6 +124,7 @@ struct ResTask {
     int zchunk;          // marching kernel: cells per z-chunk (tiles_z chunks of 32 x 8 columns)
     double* partials;    // one per tile of this task, or nullptr
     const Ctl* ctl;
+    const TmaPlanes* tma;  // plane copies by TMA (marching kernel), or nullptr
 };
 
 // Zero-mean projection of one level's right-hand side over its active cells
@@ -227,6 +239,17 @@ void set_api_error(const char* msg);
 
 template <class TP, class TC>
 cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaStream_t s);
+
+// Host: tensor maps of the seven arrays of an FP32 level (null pointers get an
+// unused zero map); false if the driver refuses one (the kernels then copy planes
+// with per-thread asynchronous copies).  The geometry needs rows of a multiple of
+// 4 cells and 16-byte aligned arrays.
+bool encode_tma_planes(TmaPlanes* out, const Geo& g, const float* const p[3], const float* b, const float* bx,
+                       const float* by, const float* bz);
+
+// Device flag set when a pipelined kernel gave up waiting for its plane copies
+// (the kernel then drained its copies and returned); 0 otherwise.
+int* wait_fault_flag();
 template <class TP>
 cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStream_t s);
 

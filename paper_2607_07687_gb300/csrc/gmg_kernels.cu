@@ -226,12 +226,78 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Whole-plane copies by the tensor memory accelerator: one thread issues a box
+// copy per plane (tensor map with a (TX + 8) x (TY + 4) box, zeros outside the
+// grid) that completes on an mbarrier of the ring step; every wait is bounded.
+constexpr uint32_t kPlaneBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4);
+constexpr int kWaitTries = 1 << 22;
+
+__device__ int g_wait_fault = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count = 1)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// false once kWaitTries rounds of try_wait (each may suspend the thread) have passed
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    for (int i = 0; i < kWaitTries; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tma_plane(float* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// after a failed wait: record it, then wait (bounded) for the copies still in flight
+__device__ __noinline__ void drain_after_fault(uint64_t* bars, uint32_t phase, int first, int count, int ring)
+{
+    if (threadIdx.x == 0) atomicExch(&g_wait_fault, 1);
+    for (int d = 0; d < count; ++d) {
+        const int j = (first + d) % ring;
+        mbar_wait(&bars[j], (phase >> j) & 1u);
+    }
+}
+
 template <int VEC, bool CORR, class TC>
 __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_constant__ TaskList<SweepTask<float, TC>> tl)
 {
     constexpr int TX = kSweepTX, TY = kSweepTY;
     constexpr int XO = 4, SW = TX + 8, SH = TY + 4, PL = SW * SH;   // 40 x 12 positions per plane
     constexpr int R = kSweepRing;               // planes per ring, every array
+    constexpr int LA = CORR ? 2 : 3;            // copy lookahead in z-steps
+    constexpr int PA = CORR ? 1 : 0;            // p planes arrive PA further ahead (correction)
+    static_assert(3 + LA + PA <= R && 3 + LA <= R, "ring depth vs lookahead");
     constexpr int CPR = SW / 4;                 // 16-byte chunks per row
     constexpr int NCH = PL / 4;                 // chunks per plane (120)
     constexpr int RPR = (TX + 2) / 2;           // red cells per ring row
@@ -240,11 +306,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
     constexpr int NBLK = BPR * TY;
     static_assert(NCH <= kThreads / 2 && NRED <= kThreads && PL <= 2 * kThreads, "thread budget");
     // rings: 0 = p, 1 = b, 2 = lower x faces, 3 = lower y faces, 4 = lower z faces, 5 = merged red plane
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t s_mbar[R];
     const int tid = threadIdx.x;
     const int half = tid / (kThreads / 2);      // copy duty: 0 -> p, b, x faces; 1 -> y, z faces
     const int chunk = tid % (kThreads / 2);
 
+    if (VEC == 4) {
+        if (tid == 0) {
+            for (int j = 0; j < R; ++j) mbar_init(&s_mbar[j]);
+            fence_mbar_init();
+        }
+        __syncthreads();
+    }
+    uint32_t phase = 0;                         // bit j: parity of the next completion of s_mbar[j]
+    bool dead = false;                          // a plane-copy wait gave up
     for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
         int local;
         const SweepTask<float, TC>* tp = task_of(tl, tile, local);
@@ -359,74 +435,140 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
             if (tid + kThreads < PL) dst[tid + kThreads] += c1;
         };
 
-        // ---- prologue: p planes kr0-1 .. kr0+1 and z faces of kr0, then step 0's group;
-        // plane z lives in slot (z - kr0 + 1) mod R
+        // ---- copy groups.  Group G(v) holds b / x / y faces of plane kr0+v+LA, z faces of
+        // kr0+v+1+LA and p of kr0+v+1+LA+PA: everything step v+LA reads for the first time
+        // (p one step earlier when PA = 1, so its coarse correction can be added a step
+        // before the plane is read).  Step u waits for G(u-LA), then issues G(u) after its
+        // first barrier; the prologue issues G0 (p planes kr0-1 .. kr0+PA, z faces of kr0)
+        // and G(-LA) .. G(-1).  Plane z lives in slot (z - kr0 + 1) mod R.
+        // Copies go by TMA (G(v) completing on s_mbar[(v + LA) mod R], G0 with G(-LA))
+        // when the tile's box needs no periodic wrap in x or y; otherwise, and for a zero
+        // input, every thread issues 16-byte asynchronous copies (cp.async groups).
         const int kr0 = z0 - 1;
-        copy_plane(ring(0, 0), pin, kr0 - 1, false);
-        copy_plane(ring(0, 1), pin, kr0, false);
-        copy_plane(ring(0, 2), pin, kr0 + 1, false);
-        copy_plane(ring(4, 1), tp->bz, kr0, true);
-        cp_commit();
-        float ca0, ca1, cb0, cb1, cc0, cc1, cur0, cur1, nxt0, nxt1;
-        corr_load(kr0 - 1, ca0, ca1);
-        corr_load(kr0, cb0, cb1);
-        corr_load(kr0 + 1, cc0, cc1);
-        copy_plane(ring(0, 3), pin, kr0 + 2, false);
-        copy_plane(ring(1, 1), ba, kr0, false);
-        copy_plane(ring(2, 1), tp->bx, kr0, false);
-        copy_plane(ring(3, 1), tp->by, kr0, false);
-        copy_plane(ring(4, 2), tp->bz, kr0 + 1, true);
-        cp_commit();
-        corr_load(kr0 + 2, cur0, cur1);
-        cp_wait<1>();
-        __syncthreads();
-        corr_add(ring(0, 0), ca0, ca1);
-        corr_add(ring(0, 1), cb0, cb1);
-        corr_add(ring(0, 2), cc0, cc1);
-
         const int nsteps = (z1 - z0) + 2;   // red planes z0-1 .. z1
+        const TmaPlanes* tm = VEC == 4 ? tp->tma : nullptr;
+        const bool use_tma = tm != nullptr && pin != nullptr && !(px && (x0 - XO < 0 || x0 + TX + XO > nx)) &&
+                             !(py && (y0 - 2 < 0 || y0 + TY + 2 > ny));
+        const CUtensorMap* pmap = use_tma ? &tm->p[(tp->in_role + rot) % 3] : nullptr;
+        auto tplane = [&](float* dst, const CUtensorMap* map, int z, uint64_t* bar) {
+            if (pz) {
+                z %= nz;
+                if (z < 0) z += nz;
+            }
+            tma_plane(dst, map, x0 - XO, y0 - 2, z, bar);   // x0 - 4: 16-byte aligned (x0 is a multiple of 32)
+        };
+        auto issue_group = [&](int v, uint64_t* bar) {
+            const int kb = kr0 + v + LA;
+            const int sb = (v + LA + 1 + R * 4) % R, sz = (v + LA + 2 + R * 4) % R, sp = (v + LA + PA + 2 + R * 4) % R;
+            if (bar) {
+                tplane(ring(1, sb), &tm->b, kb, bar);
+                tplane(ring(2, sb), &tm->x, kb, bar);
+                tplane(ring(3, sb), &tm->y, kb, bar);
+                tplane(ring(4, sz), &tm->z, kb + 1, bar);
+                tplane(ring(0, sp), pmap, kb + 1 + PA, bar);
+            } else {
+                copy_plane(ring(1, sb), ba, kb, false);
+                copy_plane(ring(2, sb), tp->bx, kb, false);
+                copy_plane(ring(3, sb), tp->by, kb, false);
+                copy_plane(ring(4, sz), tp->bz, kb + 1, true);
+                copy_plane(ring(0, sp), pin, kb + 1 + PA, false);
+            }
+        };
+        if (use_tma) {
+            if (tid == 0) {
+                fence_proxy_async();                       // earlier generic writes to the rings come first
+                mbar_expect_tx(&s_mbar[0], kPlaneBytes * (5 + (2 + PA) + 1));
+                for (int z = kr0 - 1; z <= kr0 + PA; ++z) tplane(ring(0, (z - kr0 + 1 + R) % R), pmap, z, &s_mbar[0]);
+                tplane(ring(4, 1), &tm->z, kr0, &s_mbar[0]);
+                issue_group(-LA, &s_mbar[0]);
+                for (int v = -LA + 1; v < 0 && v + LA < nsteps; ++v) {   // only groups a step will wait for
+                    mbar_expect_tx(&s_mbar[v + LA], 5 * kPlaneBytes);
+                    issue_group(v, &s_mbar[v + LA]);
+                }
+            }
+        } else {
+            for (int z = kr0 - 1; z <= kr0 + PA; ++z) copy_plane(ring(0, (z - kr0 + 1 + R) % R), pin, z, false);
+            copy_plane(ring(4, 1), tp->bz, kr0, true);
+            cp_commit();
+            for (int v = -LA; v < 0; ++v) {
+                issue_group(v, nullptr);
+                cp_commit();
+            }
+        }
+        float cur0 = 0.f, cur1 = 0.f, nxt0 = 0.f, nxt1 = 0.f;
+        if (CORR) {
+            float c[3][2];
+            for (int j = 0; j < 3; ++j) corr_load(kr0 - 1 + j, c[j][0], c[j][1]);
+            corr_load(kr0 + 2, cur0, cur1);
+            bool ok = true;
+            if (use_tma) ok = mbar_wait(&s_mbar[0], phase & 1u);   // G0: p planes kr0-1 .. kr0+1 (phase kept)
+            else cp_wait<LA>();
+            if (__syncthreads_or(!ok)) {
+                drain_after_fault(s_mbar, phase, 0, LA, R);
+                return;
+            }
+            for (int j = 0; j < 3; ++j) corr_add(ring(0, j), c[j][0], c[j][1]);
+        }
 
         // one z-step; J = (u mod R) is a compile-time constant, so is every slot
         auto step = [&](int u, auto Jc) {
             constexpr int J = decltype(Jc)::value;
             constexpr int S0 = (J + 1) % R;                       // slot of plane kr
             constexpr int Sm1 = (J + R) % R, Sm2 = (J + R - 1) % R;
-            constexpr int Sp1 = (J + 2) % R, Sp2 = (J + 3) % R, Sp3 = (J + 4) % R;
+            constexpr int Sp1 = (J + 2) % R, Sp2 = (J + 3) % R;
+            constexpr int SB = (J + 1 + LA) % R, SZ = (J + 2 + LA) % R, SP = (J + 2 + LA + PA) % R;
+            if (dead) return;
             const int kr = kr0 + u;
-            // copies for step u+1: p(kr+3), b / x / y faces (kr+1), z faces (kr+2)
-            if (u + 1 < nsteps) {
-                if (VEC == 4) {
+            bool ok = true;
+            if (use_tma) ok = mbar_wait(&s_mbar[J], (phase >> J) & 1u);
+            else cp_wait<LA - 1>();
+            if (__syncthreads_or(!ok)) {                  // S1: G(u-LA) visible, step u-1 done everywhere
+                drain_after_fault(s_mbar, phase, J, min(LA, nsteps - u), R);
+                dead = true;
+                return;
+            }
+            if (use_tma) phase ^= 1u << J;
+            // G(u): written slots hold planes every thread finished with in step u-1
+            if (u + LA < nsteps) {
+                if (use_tma) {
+                    if (tid == 0) {
+                        fence_proxy_async();
+                        uint64_t* bar = &s_mbar[(J + LA) % R];
+                        mbar_expect_tx(bar, 5 * kPlaneBytes);
+                        tplane(ring(0, SP), pmap, kr + 1 + LA + PA, bar);
+                        tplane(ring(1, SB), &tm->b, kr + LA, bar);
+                        tplane(ring(2, SB), &tm->x, kr + LA, bar);
+                        tplane(ring(3, SB), &tm->y, kr + LA, bar);
+                        tplane(ring(4, SZ), &tm->z, kr + 1 + LA, bar);
+                    }
+                } else if (VEC == 4) {
                     if (chunk < NCH) {
                         int64_t zo1, zo2;
                         if (half == 0) {
                             int64_t zo3;
-                            const bool ok3 = pin != nullptr && zinfo(kr + 3, false, zo3) && cok;
-                            const bool ok1 = zinfo(kr + 1, false, zo1) && cok;
-                            cp_async16(ring(0, Sp3) + 4 * chunk, ok3 ? srcA + zo3 + coff : ba, ok3);
-                            cp_async16(ring(1, Sp1) + 4 * chunk, ok1 ? srcB + zo1 + coff : ba, ok1);
-                            cp_async16(ring(2, Sp1) + 4 * chunk, ok1 ? srcC + zo1 + coff : ba, ok1);
+                            const bool ok3 = pin != nullptr && zinfo(kr + 1 + LA + PA, false, zo3) && cok;
+                            const bool ok1 = zinfo(kr + LA, false, zo1) && cok;
+                            cp_async16(ring(0, SP) + 4 * chunk, ok3 ? srcA + zo3 + coff : ba, ok3);
+                            cp_async16(ring(1, SB) + 4 * chunk, ok1 ? srcB + zo1 + coff : ba, ok1);
+                            cp_async16(ring(2, SB) + 4 * chunk, ok1 ? srcC + zo1 + coff : ba, ok1);
                         } else {
-                            const bool ok1 = zinfo(kr + 1, false, zo1) && cok;
-                            const bool ok2 = zinfo(kr + 2, true, zo2) && cok;
-                            cp_async16(ring(3, Sp1) + 4 * chunk, ok1 ? srcA + zo1 + coff : ba, ok1);
-                            cp_async16(ring(4, Sp2) + 4 * chunk, ok2 ? srcB + zo2 + coff : ba, ok2);
+                            const bool ok1 = zinfo(kr + LA, false, zo1) && cok;
+                            const bool ok2 = zinfo(kr + 1 + LA, true, zo2) && cok;
+                            cp_async16(ring(3, SB) + 4 * chunk, ok1 ? srcA + zo1 + coff : ba, ok1);
+                            cp_async16(ring(4, SZ) + 4 * chunk, ok2 ? srcB + zo2 + coff : ba, ok2);
                         }
                     }
                 } else {
-                    copy_plane(ring(0, Sp3), pin, kr + 3, false);
-                    copy_plane(ring(1, Sp1), ba, kr + 1, false);
-                    copy_plane(ring(2, Sp1), tp->bx, kr + 1, false);
-                    copy_plane(ring(3, Sp1), tp->by, kr + 1, false);
-                    copy_plane(ring(4, Sp2), tp->bz, kr + 2, true);
+                    issue_group(u, nullptr);
                 }
                 corr_load(kr + 3, nxt0, nxt1);
             }
             cp_commit();
-            cp_wait<1>();
-            __syncthreads();                               // S1: this step's planes are visible
-            corr_add(ring(0, Sp2), cur0, cur1);            // p(kr+2), first read at step u+1
-            cur0 = nxt0;
-            cur1 = nxt1;
+            if (CORR) {
+                corr_add(ring(0, Sp2), cur0, cur1);        // p(kr+2): landed in G(u-LA-1), first read at step u+1
+                cur0 = nxt0;
+                cur1 = nxt1;
+            }
 
             // red cells of plane kr on the tile and its one-cell ring
             if (tid < NRED) {
@@ -444,9 +586,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
                     v = P0[s];
                     const float xl = (o ? xr_wall1 : xr_wall0) ? 0.f : X0[s];
                     const float yl = yr_wall ? 0.f : Y0[s];
+                    const float zl = (kr == 0 && !pz) ? 0.f : Z0[s];
                     const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW], Y0[s + SW],
-                                               P0[s + SW], Z0[s], ring(0, Sm1)[s], Z1[s], ring(0, Sp1)[s], v);
-                    const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], Z0[s], Z1[s]);
+                                               P0[s + SW], zl, ring(0, Sm1)[s], Z1[s], ring(0, Sp1)[s], v);
+                    const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], zl, Z1[s]);
                     v = gs_update(v, fl, dg, ring(1, S0)[s], w);
                 }
                 ring(5, S0)[s] = v;
@@ -466,9 +609,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
                 float v = ring(0, Sm1)[s];
                 const float xl = (hb == 0 && xb_wall) ? 0.f : Xk[s];
                 const float yl = yb_wall ? 0.f : Yk[s];
+                const float zl = (k == 0 && !pz) ? 0.f : Zk[s];
                 const float fl = face_flux(xl, Mk[s - 1], Xk[s + 1], Mk[s + 1], yl, Mk[s - SW], Yk[s + SW],
-                                           Mk[s + SW], Zk[s], ring(5, Sm2)[s], Zk1[s], ring(5, S0)[s], v);
-                const float dg = diag_sum(xl, Xk[s + 1], yl, Yk[s + SW], Zk[s], Zk1[s]);
+                                           Mk[s + SW], zl, ring(5, Sm2)[s], Zk1[s], ring(5, S0)[s], v);
+                const float dg = diag_sum(xl, Xk[s + 1], yl, Yk[s + SW], zl, Zk1[s]);
                 v = gs_update(v, fl, dg, ring(1, Sm1)[s], w);
                 const float r = Mk[sblk + (1 - hb)];
                 const float o0 = hb ? r : v, o1 = hb ? v : r;
@@ -490,6 +634,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
             if (u + 4 < nsteps) step(u + 4, std::integral_constant<int, 4>());
             if (u + 5 < nsteps) step(u + 5, std::integral_constant<int, 5>());
         }
+        if (dead) return;
         cp_wait<0>();
         __syncthreads();                                   // the next tile reuses the rings
     }
@@ -497,150 +642,554 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
 
 // ---------------------------------------------------------------- K2: pipelined residual
 //
-// r = b - A p on a TX x TY column marching through a z-chunk, with the planes
-// of p, b and the faces staged by the same asynchronous copies as the sweep.
-// Each of the first TX*TY/2 threads owns a pair of cells of a row; the
-// restriction to the next level sums x-pairs in the thread, y-pairs with the
-// lane 16 apart (rows 2w and 2w+1 share a warp) and z-pairs across two steps,
-// so coarse cells are written without atomics.  Sum r^2 per tile in FP64.
-template <int VEC>
-__global__ void __launch_bounds__(kThreads, 3) k_residual_async(const __grid_constant__ TaskList<ResTask<float>> tl)
+// r = b - A p on a TX x TY column marching through a z-chunk, restricted to the
+// next level and summed in squares (FP64, one partial per tile).  Warp-
+// specialised: warps 0-3 (consumers) each own two tile rows, one x-pair of
+// cells per thread; warp 4 (producer) streams whole planes of p, b and the
+// three face arrays into a ring of R plane slots.  Group H(g) (the g-th plane
+// this block streams, over all its tiles) lands in slot g mod R and completes
+// on full[g mod R]: by TMA (one box per array, zeros outside the grid) when the
+// box needs no periodic wrap in x or y, else by 16-byte asynchronous copies of
+// the producer's lanes.  The consumers release a slot on empty[] once no later
+// step reads it; the producer waits for that release before refilling the
+// slot.  Restriction: x-pairs in the thread, y-pairs with the lane 16 apart,
+// z-pairs across two steps, so coarse cells are written without atomics.
+constexpr int kResConsumers = 128;
+constexpr int kResBlock = kResConsumers + 32;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// arrive-on triggered by the completion of this thread's earlier cp.async copies
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait that also gives up once another warp of the block recorded a fault
+__device__ __forceinline__ bool mbar_wait_live(uint64_t* bar, uint32_t parity, const volatile int* dead)
+{
+    for (int i = 0; i < kWaitTries; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && *dead) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int wrap_plane(int z, int nz, int pz)
+{
+    if (pz) z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+    return z;
+}
+
+// ---------------------------------------------------------------- K1: warp-specialised sweep
+//
+// The pipelined sweep (same arithmetic as k_sweep_async, bit-identical) with a
+// producer warp streaming the planes of p, b and the three face arrays into a
+// ring of R plane slots while 8 consumer warps compute.  Group H(g), the g-th
+// plane this block streams over all its tiles, lands in slot g mod R and
+// completes on full[g mod R] (TMA boxes with zero fill when the tile's box
+// needs no periodic wrap in x or y, else 16-byte asynchronous copies of the
+// producer's lanes); the consumers release it on empty[] when no later step
+// reads it.  Step u of a tile (red cells of plane kr = z0 - 1 + u on the tile
+// and its one-cell ring, then black cells of plane kr - 1 on the tile) reads
+// H(u) .. H(u + 2) = planes kr - 1 .. kr + 1; with a coarse correction it also
+// waits for H(u + 3) and adds the correction to that p plane, which the next
+// step reads first.  The red results go to a consumer-only ring (M); one named
+// barrier per step separates the red and black phases.
+constexpr int kSweepConsumers = 256;
+constexpr int kSweepBlock = kSweepConsumers + 32;
+
+template <bool CORR, class TC>
+__global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_constant__ TaskList<SweepTask<float, TC>> tl)
 {
     constexpr int TX = kSweepTX, TY = kSweepTY;
-    constexpr int XO = 4, SW = TX + 8, SH = TY + 4, PL = SW * SH;
+    constexpr int XO = 4, SW = TX + 8, PL = SW * (TY + 4);
     constexpr int R = kSweepRing;
     constexpr int CPR = SW / 4, NCH = PL / 4;
-    constexpr int BPR = TX / 2, NPAIR = BPR * TY;
-    static_assert(VEC == 4, "16-byte plane copies only");
-    static_assert(NPAIR <= kThreads && BPR == 16, "pair layout: two rows per warp");
-    extern __shared__ __align__(16) float smem[];
-    __shared__ double red[kThreads / 32];
+    constexpr int RPR = (TX + 2) / 2, NRED = RPR * (TY + 2);   // red cells of the tile and its ring
+    constexpr int BPR = TX / 2, NBLK = BPR * TY;               // black cells of the tile (x-pairs)
+    constexpr int BLK0 = kSweepConsumers - NBLK;               // black duty: the last NBLK consumers
+    constexpr int AHEAD = CORR ? 3 : 2;                        // a step waits for H(u + AHEAD)
+    static_assert(NRED <= kSweepConsumers && BLK0 >= 0 && AHEAD + 2 <= R && PL <= 2 * kSweepConsumers,
+                  "thread and ring budget");
+    extern __shared__ __align__(128) float smem[];             // rings 0 p, 1 b, 2-4 faces, 5 merged red (M)
+    __shared__ __align__(8) uint64_t full[R];
+    __shared__ __align__(8) uint64_t empty[R];
+    __shared__ int s_dead;
     const int tid = threadIdx.x;
-    const int half = tid / (kThreads / 2);
-    const int chunk = tid % (kThreads / 2);
+    const int lane = tid & 31;
+    if (tid == 0) {
+        for (int j = 0; j < R; ++j) {
+            mbar_init(&full[j], 1);
+            mbar_init(&empty[j], kSweepConsumers / 32);
+        }
+        s_dead = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    volatile int* dead = &s_dead;
+    auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
 
+    if (tid >= kSweepConsumers) {
+        // ------------------------------------------------ producer warp
+        uint32_t g = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < tl.total && ok; tile += gridDim.x) {
+            int local;
+            const SweepTask<float, TC>* tp = task_of(tl, tile, local);
+            if (tp->ctl && tp->ctl->done) continue;
+            const int nx = tp->g.n[0], ny = tp->g.n[1], nz = tp->g.n[2];
+            const int px = tp->g.per[0], py = tp->g.per[1], pz = tp->g.per[2];
+            const int cx = local % tp->tiles_x, rest = local / tp->tiles_x;
+            const int x0 = cx * TX, y0 = (rest % tp->tiles_y) * TY, z0 = (rest / tp->tiles_y) * tp->zchunk;
+            const int z1 = min(nz, z0 + tp->zchunk);
+            const int rot = tp->rot ? *tp->rot : 0;
+            const int pidx = tp->in_role < 0 ? 0 : (tp->in_role + rot) % 3;
+            const float* pin = tp->in_role < 0 ? nullptr : tp->buf[pidx];
+            const TmaPlanes* tm = tp->tma;
+            const bool use_tma = tm != nullptr && pin != nullptr && !(px && (x0 - XO < 0 || x0 + TX + XO > nx)) &&
+                                 !(py && (y0 - 2 < 0 || y0 + TY + 2 > ny));
+            const float* src[5] = {pin, tp->b, tp->bx, tp->by, tp->bz};
+            const int64_t plane = (int64_t)nx * ny;
+            constexpr int CPL = (NCH + 31) / 32;
+            int coff[CPL];
+            bool cok[CPL];
+            if (!use_tma) {
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int c = lane + 32 * i;
+                    const int sy = c / CPR, ch = c - sy * CPR;
+                    int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
+                    cok[i] = c < NCH && wrapc(x, nx, px) && wrapc(y, ny, py);
+                    coff[i] = cok[i] ? y * nx + x : 0;
+                }
+            }
+            const int nh = (z1 - z0) + 4;                      // planes z0-2 .. z1+1
+            for (int m = 0; m < nh; ++m, ++g) {
+                if (g >= (uint32_t)R && !mbar_wait_live(&empty[g % R], ((g / R) - 1) & 1u, dead)) {
+                    ok = false;
+                    break;
+                }
+                uint64_t* bar = &full[g % R];
+                const int z = z0 - 2 + m;
+                if (use_tma) {
+                    if (lane == 0) {
+                        const int zw = wrap_plane(z, nz, pz);
+                        mbar_expect_tx(bar, 5 * kPlaneBytes);
+                        tma_plane(ring(0, g), &tm->p[pidx], x0 - XO, y0 - 2, zw, bar);
+                        tma_plane(ring(1, g), &tm->b, x0 - XO, y0 - 2, zw, bar);
+                        tma_plane(ring(2, g), &tm->x, x0 - XO, y0 - 2, zw, bar);
+                        tma_plane(ring(3, g), &tm->y, x0 - XO, y0 - 2, zw, bar);
+                        tma_plane(ring(4, g), &tm->z, x0 - XO, y0 - 2, zw, bar);
+                    }
+                } else {
+                    int zw = z;
+                    const bool zok = wrapc(zw, nz, pz);
+                    const int64_t zoff = (int64_t)zw * plane;
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        const int c = lane + 32 * i;
+                        if (c < NCH) {
+#pragma unroll
+                            for (int a = 0; a < 5; ++a) {
+                                const bool okc = zok && cok[i] && src[a] != nullptr;
+                                cp_async16(ring(a, g) + 4 * c, okc ? src[a] + zoff + coff[i] : tp->b, okc);
+                            }
+                        }
+                    }
+                    cp_async_mbar_arrive(bar);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar);
+                }
+            }
+        }
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(&g_wait_fault, 1);
+                s_dead = 1;
+            }
+            for (uint32_t q = g > (uint32_t)R ? g - R : 0; q < g; ++q) mbar_wait(&full[q % R], (q / R) & 1u);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------- consumer warps
+    uint32_t g = 0;                             // first group of the current tile
     for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
         int local;
-        const ResTask<float>* tp = task_of(tl, tile, local);
-        if (tp->ctl && tp->ctl->done) continue;               // uniform in the block
-        const Geo g = tp->g;
-        const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-        const int px = g.per[0], py = g.per[1], pz = g.per[2];
-        const int cx = local % tp->tiles_x;
-        const int rest = local / tp->tiles_x;
-        const int cy = rest % tp->tiles_y;
-        const int cz = rest / tp->tiles_y;
-        const int x0 = cx * TX, y0 = cy * TY;
-        const int z0 = cz * tp->zchunk;
+        const SweepTask<float, TC>* tp = task_of(tl, tile, local);
+        const Ctl* ctl = tp->ctl;
+        if (ctl && ctl->done) continue;
+        const int nx = tp->g.n[0], ny = tp->g.n[1], nz = tp->g.n[2];
+        const int px = tp->g.per[0], py = tp->g.per[1], pz = tp->g.per[2];
+        const int cx = local % tp->tiles_x, rest = local / tp->tiles_x;
+        const int x0 = cx * TX, y0 = (rest % tp->tiles_y) * TY, z0 = (rest / tp->tiles_y) * tp->zchunk;
         const int z1 = min(nz, z0 + tp->zchunk);
         const int rot = tp->rot ? *tp->rot : 0;
-        const float* pin = tp->role < 0 ? nullptr : tp->buf[(tp->role + rot) % 3];
-        const float* const ba = tp->b;
-        const float* const srcA = half == 0 ? pin : tp->by;
-        const float* const srcB = half == 0 ? tp->b : tp->bz;
-        const float* const srcC = tp->bx;
-        float* const bc = tp->bc;
-        const int c0 = tp->cf[0], c1 = tp->cf[1], c2 = tp->cf[2];
+        float* pout = tp->buf[(tp->out_role + rot) % 3];
+        const float w = ctl ? (float)ctl->omega : tp->omega;
+
+        // red duty: one red cell of the tile or its ring per thread (tid < NRED)
+        const int ey = tid / RPR, jr = tid - ey * RPR;
+        int yr = y0 - 1 + ey;
+        const bool yr_ok = tid < NRED && wrapc(yr, ny, py);
+        const bool yr_wall = yr == 0 && !py;
+        const int sred = (ey + 1) * SW + XO - 1 + 2 * jr;
+        int xr0 = x0 - 1 + 2 * jr, xr1 = xr0 + 1;
+        const bool xr_wall0 = xr0 == 0 && !px, xr_wall1 = xr1 == 0 && !px;
+        const bool xr_ok0 = wrapc(xr0, nx, px), xr_ok1 = wrapc(xr1, nx, px);
+        const int red_par = (1 + (y0 - 1 + ey)) & 1;          // red member: (red_par + kr) & 1
+        // black duty: one x-pair of a tile row (tid >= BLK0)
+        const int bi = tid - BLK0;
+        const int tyb = bi / BPR, jb = bi - tyb * BPR;
+        const int yb = y0 + tyb, xb = x0 + 2 * jb;
+        const bool blk_on = bi >= 0 && yb < ny && xb < nx;
+        const int sblk = (tyb + 2) * SW + XO + 2 * jb;
+        const bool yb_wall = yb == 0 && !py;
+        const bool xb_wall = xb == 0 && !px;
+        float* const out_col = pout + ((int64_t)(blk_on ? yb : 0) * nx + (blk_on ? xb : 0));
         const int64_t plane = (int64_t)nx * ny;
 
-        int coff = 0;
-        bool cok = false;
-        if (chunk < NCH) {
-            const int sy = chunk / CPR, ch = chunk - sy * CPR;
-            int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
-            cok = wrapc(x, nx, px) && wrapc(y, ny, py);
-            coff = cok ? y * nx + x : 0;
+        // coarse correction of p planes: gathered into registers one step ahead
+        const TC* corr = tp->corr;
+        const int cf0 = tp->cf[0], cf1 = tp->cf[1], cf2 = tp->cf[2];
+        const int gcx = nx / cf0, gcy = ny / cf1;
+        int crr0 = 0, crr1 = 0;
+        bool crok0 = false, crok1 = false;
+        if (CORR) {
+            for (int r = 0; r < 2; ++r) {
+                const int e = tid + r * kSweepConsumers;
+                if (e < PL) {
+                    const int sy = e / SW, sx = e - sy * SW;
+                    int x = x0 - XO + sx, y = y0 - 2 + sy;
+                    const bool okp = wrapc(x, nx, px) && wrapc(y, ny, py);
+                    const int off = okp ? (y / cf1) * gcx + x / cf0 : 0;
+                    if (r == 0) { crok0 = okp; crr0 = off; } else { crok1 = okp; crr1 = off; }
+                }
+            }
         }
-        const int tyb = tid / BPR, jb = tid - tyb * BPR;
-        const int yb = y0 + tyb, xb = x0 + 2 * jb;
-        const bool pair_on = tid < NPAIR && yb < ny && xb < nx;
+        auto corr_load = [&](int z, float& c0, float& c1) {
+            c0 = c1 = 0.f;
+            if (!CORR) return;
+            int zw = z;
+            if (!wrapc(zw, nz, pz)) return;
+            const int64_t zoff = (int64_t)(zw / cf2) * gcx * gcy;
+            if (crok0) c0 = ldv(corr, zoff + crr0);
+            if (crok1) c1 = ldv(corr, zoff + crr1);
+        };
+        auto corr_add = [&](float* dst, float c0, float c1) {
+            if (!CORR) return;
+            dst[tid] += c0;
+            if (tid + kSweepConsumers < PL) dst[tid + kSweepConsumers] += c1;
+        };
+
+        const int kr0 = z0 - 1;
+        const int nsteps = (z1 - z0) + 2;                      // red planes z0-1 .. z1
+        const int nh = nsteps + 2;                             // H(m): plane kr0 - 1 + m
+        bool live = true;
+        for (int m = 0; m < AHEAD && live; ++m)
+            live = mbar_wait_live(&full[(g + m) % R], ((g + m) / R) & 1u, dead);
+        float cur0 = 0.f, cur1 = 0.f;
+        if (CORR) {
+            if (live) {
+                for (int m = 0; m < 3; ++m) {
+                    float c0, c1;
+                    corr_load(kr0 - 1 + m, c0, c1);
+                    corr_add(ring(0, g + m), c0, c1);
+                }
+                corr_load(kr0 + 2, cur0, cur1);
+            }
+        }
+        // every consumer warp agrees that the tile's first planes arrived (and were corrected)
+        {
+            int any;
+            asm volatile("{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+                         : "=r"(any) : "r"((int)!live), "n"(kSweepConsumers) : "memory");
+            live = !any;
+        }
+        for (int u = 0; u < nsteps && live; ++u) {
+            const uint32_t hl = g + u, h0 = hl + 1, hu = hl + 2;   // planes kr-1, kr, kr+1
+            const int kr = kr0 + u;
+            bool ok = true;
+            if (u + AHEAD <= nh - 1) ok = mbar_wait_live(&full[(hl + AHEAD) % R], ((hl + AHEAD) / R) & 1u, dead);
+            if (CORR && ok && u + 3 <= nh - 1) {
+                float nxt0, nxt1;
+                corr_load(kr + 3, nxt0, nxt1);
+                corr_add(ring(0, hl + 3), cur0, cur1);       // p(kr+2), first read in step u+1
+                cur0 = nxt0;
+                cur1 = nxt1;
+            }
+            // red cells of plane kr
+            if (ok && tid < NRED) {
+                int zk = kr;
+                const bool zok = wrapc(zk, nz, pz);
+                const int o = (red_par + kr) & 1;
+                const int s = sred + o;
+                float v = 0.f;
+                if (zok && yr_ok && (o ? xr_ok1 : xr_ok0)) {
+                    const float* P0 = ring(0, h0);
+                    const float* X0 = ring(2, h0);
+                    const float* Y0 = ring(3, h0);
+                    const float* Z0 = ring(4, h0);
+                    const float* Z1 = ring(4, hu);
+                    v = P0[s];
+                    const float xl = (o ? xr_wall1 : xr_wall0) ? 0.f : X0[s];
+                    const float yl = yr_wall ? 0.f : Y0[s];
+                    const float zl = (kr == 0 && !pz) ? 0.f : Z0[s];
+                    const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW], Y0[s + SW],
+                                               P0[s + SW], zl, ring(0, hl)[s], Z1[s], ring(0, hu)[s], v);
+                    const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], zl, Z1[s]);
+                    v = gs_update(v, fl, dg, ring(1, h0)[s], w);
+                }
+                ring(5, h0)[s] = v;
+            }
+            // S2: red cells of kr merged (and corrections visible), faults agreed
+            {
+                int any;
+                asm volatile("{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+                             : "=r"(any) : "r"((int)!ok), "n"(kSweepConsumers) : "memory");
+                if (any) {
+                    live = false;
+                    break;
+                }
+            }
+            // black cells of plane kr-1; the pair's red cell comes from M
+            if (u >= 2 && blk_on) {
+                const int k = kr - 1;
+                const int hb = ((xb + yb + k) & 1) ? 0 : 1;   // black member of the pair
+                const int s = sblk + hb;
+                const float* Mk = ring(5, hl);
+                const float* Xk = ring(2, hl);
+                const float* Yk = ring(3, hl);
+                const float* Zk = ring(4, hl);
+                const float* Zk1 = ring(4, h0);
+                float v = ring(0, hl)[s];
+                const float xl = (hb == 0 && xb_wall) ? 0.f : Xk[s];
+                const float yl = yb_wall ? 0.f : Yk[s];
+                const float zl = (k == 0 && !pz) ? 0.f : Zk[s];
+                const float fl = face_flux(xl, Mk[s - 1], Xk[s + 1], Mk[s + 1], yl, Mk[s - SW], Yk[s + SW],
+                                           Mk[s + SW], zl, ring(5, hl + R - 1)[s], Zk1[s], ring(5, h0)[s], v);
+                const float dg = diag_sum(xl, Xk[s + 1], yl, Yk[s + SW], zl, Zk1[s]);
+                v = gs_update(v, fl, dg, ring(1, hl)[s], w);
+                const float r = Mk[sblk + (1 - hb)];
+                const float o0 = hb ? r : v, o1 = hb ? v : r;
+                *reinterpret_cast<float2*>(out_col + (int64_t)k * plane) = make_float2(o0, o1);
+            }
+            // plane kr-1 (H(u)) is no longer read by this tile's later steps
+            if (CORR) fence_proxy_async();                 // corrected p planes: generic writes before refills
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[hl % R]);
+        }
+        if (!live) {
+            if (tid == 0) {
+                atomicExch(&g_wait_fault, 1);
+                s_dead = 1;
+            }
+            return;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&empty[(g + nsteps) % R]);
+            mbar_arrive(&empty[(g + nsteps + 1) % R]);
+        }
+        g += nh;
+    }
+}
+
+struct ResTile {
+    const ResTask<float>* tp;
+    int local, x0, y0, z0, z1;
+    int pidx;                                   // buffer holding the iterate
+    const float* pin;
+};
+
+__device__ __forceinline__ bool res_tile(const TaskList<ResTask<float>>& tl, int tile, ResTile& t)
+{
+    t.tp = task_of(tl, tile, t.local);
+    if (t.tp->ctl && t.tp->ctl->done) return false;
+    const int cx = t.local % t.tp->tiles_x;
+    const int rest = t.local / t.tp->tiles_x;
+    const int cy = rest % t.tp->tiles_y;
+    const int cz = rest / t.tp->tiles_y;
+    t.x0 = cx * kSweepTX;
+    t.y0 = cy * kSweepTY;
+    t.z0 = cz * t.tp->zchunk;
+    t.z1 = min(t.tp->g.n[2], t.z0 + t.tp->zchunk);
+    const int rot = t.tp->rot ? *t.tp->rot : 0;
+    t.pidx = t.tp->role < 0 ? 0 : (t.tp->role + rot) % 3;
+    t.pin = t.tp->role < 0 ? nullptr : t.tp->buf[t.pidx];
+    return true;
+}
+
+__global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_constant__ TaskList<ResTask<float>> tl)
+{
+    constexpr int TX = kSweepTX, TY = kSweepTY;
+    constexpr int XO = 4, SW = TX + 8, PL = SW * (TY + 4);
+    constexpr int R = kSweepRing;
+    constexpr int CPR = SW / 4, NCH = PL / 4;
+    constexpr int BPR = TX / 2;
+    static_assert(BPR * TY == kResConsumers && BPR == 16, "one x-pair per consumer thread, two rows per warp");
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t full[R];
+    __shared__ __align__(8) uint64_t empty[R];
+    __shared__ double red[kResConsumers / 32];
+    __shared__ int s_dead;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    if (tid == 0) {
+        for (int j = 0; j < R; ++j) {
+            mbar_init(&full[j], 1);
+            mbar_init(&empty[j], kResConsumers / 32);
+        }
+        s_dead = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    volatile int* dead = &s_dead;
+    auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
+
+    if (tid >= kResConsumers) {
+        // ------------------------------------------------ producer warp
+        uint32_t g = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < tl.total && ok; tile += gridDim.x) {
+            ResTile t;
+            if (!res_tile(tl, tile, t)) continue;
+            const ResTask<float>* tp = t.tp;
+            const int nx = tp->g.n[0], ny = tp->g.n[1], nz = tp->g.n[2];
+            const int px = tp->g.per[0], py = tp->g.per[1], pz = tp->g.per[2];
+            const TmaPlanes* tm = tp->tma;
+            const bool use_tma = tm != nullptr && t.pin != nullptr &&
+                                 !(px && (t.x0 - XO < 0 || t.x0 + TX + XO > nx)) &&
+                                 !(py && (t.y0 - 2 < 0 || t.y0 + TY + 2 > ny));
+            const CUtensorMap* pmap = use_tma ? &tm->p[t.pidx] : nullptr;
+            const float* src[5] = {t.pin, tp->b, tp->bx, tp->by, tp->bz};
+            const int64_t plane = (int64_t)nx * ny;
+            const int nh = (t.z1 - t.z0) + 2;                  // planes z0-1 .. z1
+            // per-thread copies: this lane's 16-byte chunks (c = lane + 32 i) of a plane, fixed for the tile
+            constexpr int CPL = (NCH + 31) / 32;
+            int coff[CPL];
+            bool cok[CPL];
+            if (!use_tma) {
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int c = lane + 32 * i;
+                    const int sy = c / CPR, ch = c - sy * CPR;
+                    int x = t.x0 - XO + 4 * ch, y = t.y0 - 2 + sy;
+                    cok[i] = c < NCH && wrapc(x, nx, px) && wrapc(y, ny, py);
+                    coff[i] = cok[i] ? y * nx + x : 0;
+                }
+            }
+            for (int m = 0; m < nh; ++m, ++g) {
+                if (g >= (uint32_t)R && !mbar_wait_live(&empty[g % R], ((g / R) - 1) & 1u, dead)) {
+                    ok = false;
+                    break;
+                }
+                uint64_t* bar = &full[g % R];
+                const int z = t.z0 - 1 + m;
+                if (use_tma) {
+                    if (lane == 0) {
+                        const int zw = wrap_plane(z, nz, pz);
+                        mbar_expect_tx(bar, 5 * kPlaneBytes);
+                        tma_plane(ring(0, g), pmap, t.x0 - XO, t.y0 - 2, zw, bar);
+                        tma_plane(ring(1, g), &tm->b, t.x0 - XO, t.y0 - 2, zw, bar);
+                        tma_plane(ring(2, g), &tm->x, t.x0 - XO, t.y0 - 2, zw, bar);
+                        tma_plane(ring(3, g), &tm->y, t.x0 - XO, t.y0 - 2, zw, bar);
+                        tma_plane(ring(4, g), &tm->z, t.x0 - XO, t.y0 - 2, zw, bar);
+                    }
+                } else {
+                    int zw = z;
+                    const bool zok = wrapc(zw, nz, pz);
+                    const int64_t zoff = (int64_t)zw * plane;
+#pragma unroll
+                    for (int i = 0; i < CPL; ++i) {
+                        const int c = lane + 32 * i;
+                        if (c < NCH) {
+#pragma unroll
+                            for (int a = 0; a < 5; ++a) {
+                                const bool okc = zok && cok[i] && src[a] != nullptr;
+                                cp_async16(ring(a, g) + 4 * c, okc ? src[a] + zoff + coff[i] : tp->b, okc);
+                            }
+                        }
+                    }
+                    cp_async_mbar_arrive(bar);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar);
+                }
+            }
+        }
+        if (!ok) {
+            // record the fault, then wait (bounded) for the copies still in flight
+            if (lane == 0) {
+                atomicExch(&g_wait_fault, 1);
+                s_dead = 1;
+            }
+            for (uint32_t q = g > (uint32_t)R ? g - R : 0; q < g; ++q) mbar_wait(&full[q % R], (q / R) & 1u);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------- consumer warps
+    const int tyb = tid / BPR, jb = tid - tyb * BPR;
+    uint32_t g = 0;                             // first group of the current tile
+    for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
+        ResTile t;
+        if (!res_tile(tl, tile, t)) continue;
+        const ResTask<float>* tp = t.tp;
+        const int nx = tp->g.n[0], ny = tp->g.n[1];
+        const int px = tp->g.per[0], py = tp->g.per[1], pz = tp->g.per[2];
+        float* const bc = tp->bc;
+        const int c0 = tp->cf[0], c1 = tp->cf[1], c2 = tp->cf[2];
+        const int yb = t.y0 + tyb, xb = t.x0 + 2 * jb;
+        const bool pair_on = yb < ny && xb < nx;
         const int sp = (tyb + 2) * SW + XO + 2 * jb;
         const bool yb_wall = yb == 0 && !py;
         const bool xb_wall = xb == 0 && !px;
         const int gcx = nx / c0, gcy = ny / c1;
-        // coarse cell(s) this thread writes: one x-pair sum (c0 = 2) or two cells
         const bool writer = pair_on && (c1 == 1 || (tyb & 1) == 0);
         const int64_t cplane = (int64_t)gcx * gcy;
         const int64_t crow = (int64_t)(yb / c1) * gcx + xb / c0;
-
-        auto zinfo = [&](int z, bool zface, int64_t& zoff) -> bool {
-            int zw = z;
-            bool ok = wrapc(zw, nz, pz);
-            if (zface && ok && zw == 0 && !pz) ok = false;
-            zoff = (int64_t)zw * plane;
-            return ok;
-        };
-        auto copy_plane = [&](float* dst, const float* a, int z, bool zface) {
-            int64_t zoff;
-            const bool zok = a != nullptr && zinfo(z, zface, zoff);
-            for (int c = tid; c < NCH; c += kThreads) {
-                const int sy = c / CPR, ch = c - sy * CPR;
-                int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
-                const bool ok = zok && wrapc(x, nx, px) && wrapc(y, ny, py);
-                cp_async16(dst + 4 * c, ok ? a + zoff + (int64_t)y * nx + x : ba, ok);
-            }
-        };
-        auto ring = [&](int r, int slot) -> float* { return smem + (r * R + slot) * PL; };
-
-        // plane z in slot (z - z0 + 1) mod R
-        copy_plane(ring(0, 0), pin, z0 - 1, false);
-        copy_plane(ring(0, 1), pin, z0, false);
-        copy_plane(ring(0, 2), pin, z0 + 1, false);
-        copy_plane(ring(4, 1), tp->bz, z0, true);
-        copy_plane(ring(1, 1), ba, z0, false);
-        copy_plane(ring(2, 1), tp->bx, z0, false);
-        copy_plane(ring(3, 1), tp->by, z0, false);
-        copy_plane(ring(4, 2), tp->bz, z0 + 1, true);
-        cp_commit();
-
-        const int nsteps = z1 - z0;
+        const int nsteps = t.z1 - t.z0;
         double rr = 0.0;
         float acc0 = 0.f, acc1 = 0.f;
-        auto step = [&](int u, auto Jc) {
-            constexpr int J = decltype(Jc)::value;
-            constexpr int S0 = (J + 1) % R, Sm1 = J % R, Sp1 = (J + 2) % R, Sp2 = (J + 3) % R;
-            const int k = z0 + u;
-            // copies for step u+1: p(k+2), b / x / y faces (k+1), z faces (k+2)
-            if (u + 1 < nsteps && chunk < NCH) {
-                int64_t zo1, zo2;
-                if (half == 0) {
-                    const bool ok2 = pin != nullptr && zinfo(k + 2, false, zo2) && cok;
-                    const bool ok1 = zinfo(k + 1, false, zo1) && cok;
-                    cp_async16(ring(0, Sp2) + 4 * chunk, ok2 ? srcA + zo2 + coff : ba, ok2);
-                    cp_async16(ring(1, Sp1) + 4 * chunk, ok1 ? srcB + zo1 + coff : ba, ok1);
-                    cp_async16(ring(2, Sp1) + 4 * chunk, ok1 ? srcC + zo1 + coff : ba, ok1);
-                } else {
-                    const bool ok1 = zinfo(k + 1, false, zo1) && cok;
-                    const bool ok2 = zinfo(k + 2, true, zo2) && cok;
-                    cp_async16(ring(3, Sp1) + 4 * chunk, ok1 ? srcA + zo1 + coff : ba, ok1);
-                    cp_async16(ring(4, Sp2) + 4 * chunk, ok2 ? srcB + zo2 + coff : ba, ok2);
-                }
+        bool live = mbar_wait_live(&full[g % R], (g / R) & 1u, dead) &&
+                    mbar_wait_live(&full[(g + 1) % R], ((g + 1) / R) & 1u, dead);
+        for (int u = 0; u < nsteps && live; ++u) {
+            const uint32_t hl = g + u, h0 = hl + 1, hu = hl + 2;   // planes k-1, k, k+1
+            if (!mbar_wait_live(&full[hu % R], (hu / R) & 1u, dead)) {
+                live = false;
+                break;
             }
-            cp_commit();
-            cp_wait<1>();
-            __syncthreads();
+            const int k = t.z0 + u;
             float r0 = 0.f, r1 = 0.f;
             if (pair_on) {
-                const float* P0 = ring(0, S0);
-                const float* Pl = ring(0, Sm1);
-                const float* Pu = ring(0, Sp1);
-                const float* X0 = ring(2, S0);
-                const float* Y0 = ring(3, S0);
-                const float* Z0 = ring(4, S0);
-                const float* Z1 = ring(4, Sp1);
-                const float* B0 = ring(1, S0);
+                const float* P0 = ring(0, h0);
+                const float* Pl = ring(0, hl);
+                const float* Pu = ring(0, hu);
+                const float* B0 = ring(1, h0);
+                const float* X0 = ring(2, h0);
+                const float* Y0 = ring(3, h0);
+                const float* Z0 = ring(4, h0);
+                const float* Z1 = ring(4, hu);
                 for (int h = 0; h < 2; ++h) {
                     const int s = sp + h;
                     const float p0 = P0[s];
                     const float xl = (h == 0 && xb_wall) ? 0.f : X0[s];
                     const float yl = yb_wall ? 0.f : Y0[s];
+                    const float zl = (k == 0 && !pz) ? 0.f : Z0[s];
                     const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW], Y0[s + SW],
-                                               P0[s + SW], Z0[s], Pl[s], Z1[s], Pu[s], p0);
+                                               P0[s + SW], zl, Pl[s], Z1[s], Pu[s], p0);
                     const float r = B0[s] - fl;
                     if (h == 0) r0 = r; else r1 = (xb + 1 < nx) ? r : 0.f;
                 }
                 rr += (double)r0 * (double)r0 + (double)r1 * (double)r1;
             }
+            // plane k-1 is no longer read
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[hl % R]);
             if (bc) {
                 float v0 = c0 == 2 ? r0 + r1 : r0;
                 float v1 = c0 == 2 ? 0.f : r1;
@@ -659,22 +1208,39 @@ __global__ void __launch_bounds__(kThreads, 3) k_residual_async(const __grid_con
                     acc0 = acc1 = 0.f;
                 }
             }
-        };
-        static_assert(R == 6, "the unrolled step sequence below assumes six slots");
-        for (int u = 0; u < nsteps; u += R) {
-            step(u, std::integral_constant<int, 0>());
-            if (u + 1 < nsteps) step(u + 1, std::integral_constant<int, 1>());
-            if (u + 2 < nsteps) step(u + 2, std::integral_constant<int, 2>());
-            if (u + 3 < nsteps) step(u + 3, std::integral_constant<int, 3>());
-            if (u + 4 < nsteps) step(u + 4, std::integral_constant<int, 4>());
-            if (u + 5 < nsteps) step(u + 5, std::integral_constant<int, 5>());
         }
-        cp_wait<0>();
+        if (live) {
+            // planes z1-1 and z1 (the last two groups of the tile) are released too
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[(g + nsteps) % R]);
+                mbar_arrive(&empty[(g + nsteps + 1) % R]);
+            }
+        }
+        g += nsteps + 2;
+        // all consumer warps agree on faults before the tile's norm partial
+        int any_dead;
+        asm volatile("{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+                     : "=r"(any_dead)
+                     : "r"((int)!live), "n"(kResConsumers)
+                     : "memory");
+        if (any_dead) {
+            if (tid == 0) {
+                atomicExch(&g_wait_fault, 1);
+                s_dead = 1;
+            }
+            return;
+        }
         if (tp->partials) {
-            const double q = block_sum(rr, red);
-            if (tid == 0) tp->partials[local] = q;
-        } else {
-            __syncthreads();
+            const double q = warp_sum(rr);
+            if (lane == 0) red[tid >> 5] = q;
+            asm volatile("bar.sync 1, %0;\n" ::"n"(kResConsumers) : "memory");
+            if (tid == 0) {
+                double s = 0.0;
+                for (int i = 0; i < kResConsumers / 32; ++i) s += red[i];
+                tp->partials[t.local] = s;
+            }
+            asm volatile("bar.sync 1, %0;\n" ::"n"(kResConsumers) : "memory");
         }
     }
 }
@@ -1210,18 +1776,18 @@ cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaSt
         static bool attr = false;   // opt in to > 48 KB of dynamic shared memory once
         if (!attr) {
             const int b = (int)smem;
-            cudaError_t e = cudaFuncSetAttribute(k_sweep_async<4, false, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+            cudaError_t e = cudaFuncSetAttribute(k_sweep_ws<false, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_async<1, false, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_async<4, true, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_ws<true, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sweep_async<1, true, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
             if (e != cudaSuccess) return e;
             attr = true;
         }
         if (tl.corr) {
-            if (tl.vec >= 4) k_sweep_async<4, true, TC><<<grid, kThreads, smem, s>>>(tl);
+            if (tl.vec >= 4) k_sweep_ws<true, TC><<<grid, kSweepBlock, smem, s>>>(tl);
             else k_sweep_async<1, true, TC><<<grid, kThreads, smem, s>>>(tl);
         } else {
-            if (tl.vec >= 4) k_sweep_async<4, false, TC><<<grid, kThreads, smem, s>>>(tl);
+            if (tl.vec >= 4) k_sweep_ws<false, TC><<<grid, kSweepBlock, smem, s>>>(tl);
             else k_sweep_async<1, false, TC><<<grid, kThreads, smem, s>>>(tl);
         }
     } else {
@@ -1242,12 +1808,12 @@ cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStrea
             constexpr size_t smem = kResidualSmemBytes;
             static bool attr = false;
             if (!attr) {
-                cudaError_t e = cudaFuncSetAttribute(k_residual_async<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                cudaError_t e = cudaFuncSetAttribute(k_residual_ws, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                      (int)smem);
                 if (e != cudaSuccess) return e;
                 attr = true;
             }
-            k_residual_async<4><<<grid, kThreads, smem, s>>>(tl);
+            k_residual_ws<<<grid, kResBlock, smem, s>>>(tl);
             return cudaGetLastError();
         }
     }
@@ -1382,6 +1948,12 @@ cudaError_t launch_ir_update(const IrTask& t, cudaStream_t s)
     const int64_t N = (int64_t)t.g.n[0] * t.g.n[1] * t.g.n[2];
     k_ir_update<<<grid_for(N), kThreads, 0, s>>>(t.g, t.p64, t.ebuf[0], t.ebuf[1], t.ebuf[2], t.rot);
     return cudaGetLastError();
+}
+
+int* wait_fault_flag()
+{
+    int* p = nullptr;
+    return cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_wait_fault) == cudaSuccess ? p : nullptr;
 }
 
 }  // namespace gmg

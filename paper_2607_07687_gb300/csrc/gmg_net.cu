@@ -411,19 +411,26 @@ __global__ void k_head(int64_t n, const bf16* h, int ch, const float* w, const f
     }
 }
 
-// red[0] = sum out, red[1] = sum t, (second pass) red[2] = sum (t - mt)^2, red[3] = sum diff^2
-__global__ void k_loss_sums(int64_t n, const float* out, const float* target, const float* s, double* red, int pass)
+// prediction q = out + p_prev / s in units of s
+__device__ __forceinline__ double pred(const float* out, const float* p_prev, double inv, int64_t i)
 {
-    const float inv = 1.f / *s;
+    return p_prev ? (double)out[i] + (double)p_prev[i] * inv : (double)out[i];
+}
+
+// red[0] = sum q, red[1] = sum t, (second pass) red[2] = sum (t - mt)^2, red[3] = sum diff^2
+__global__ void k_loss_sums(int64_t n, const float* out, const float* target, const float* p_prev, const float* s,
+                            double* red, int pass)
+{
+    const double inv = 1.0 / (double)*s;
     const double mo = pass ? red[0] / (double)n : 0.0, mt = pass ? red[1] / (double)n : 0.0;
     double a = 0.0, c = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double t = (double)target[i] * inv;
         if (pass == 0) {
-            a += out[i];
+            a += pred(out, p_prev, inv, i);
             c += t;
         } else {
-            const double tc = t - mt, d = ((double)out[i] - mo) - tc;
+            const double tc = t - mt, d = (pred(out, p_prev, inv, i) - mo) - tc;
             a += tc * tc;
             c += d * d;
         }
@@ -438,14 +445,14 @@ __global__ void k_loss_sums(int64_t n, const float* out, const float* target, co
     }
 }
 
-__global__ void k_loss_grad(int64_t n, const float* out, const float* target, const float* s, const double* red,
-                            float* gout, double* loss)
+__global__ void k_loss_grad(int64_t n, const float* out, const float* target, const float* p_prev, const float* s,
+                            const double* red, float* gout, double* loss)
 {
-    const float inv = 1.f / *s;
+    const double inv = 1.0 / (double)*s;
     const double mo = red[0] / (double)n, mt = red[1] / (double)n, den = red[2] > 0.0 ? red[2] : 1.0;
     if (blockIdx.x == 0 && threadIdx.x == 0) *loss = red[3] / den;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double d = ((double)out[i] - mo) - ((double)target[i] * inv - mt);
+        const double d = (pred(out, p_prev, inv, i) - mo) - ((double)target[i] * inv - mt);
         gout[i] = (float)(2.0 * d / den);
     }
 }
@@ -474,11 +481,11 @@ __global__ void k_head_backward(int64_t n, const float* gout, const bf16* h, int
     }
 }
 
-__global__ void k_unscale(int64_t n, const float* out, const float* s, float* p0)
+__global__ void k_unscale(int64_t n, const float* out, const float* s, const float* p_prev, float* p0)
 {
     const float sc = *s;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        p0[i] = sc * out[i];
+        p0[i] = p_prev ? fmaf(sc, out[i], p_prev[i]) : sc * out[i];
 }
 
 // Adam; weights packed [27][co][ci] also land as BF16 and, flipped and
@@ -629,17 +636,17 @@ int gmg_net_head(int D, int H, int W, const gmg_bf16* h, int ch, const float* w,
     return status(cudaGetLastError());
 }
 
-int gmg_net_loss(int D, int H, int W, const float* out, const float* target, const float* s, float* gout,
-                 double* loss, double* red, void* stream)
+int gmg_net_loss(int D, int H, int W, const float* out, const float* target, const float* p_prev, const float* s,
+                 float* gout, double* loss, double* red, void* stream)
 {
     if (!out || !target || !s || !gout || !loss || !red) return 1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t n = (int64_t)D * H * W;
     cudaError_t e = cudaMemsetAsync(red, 0, 4 * sizeof(double), st);
     if (e != cudaSuccess) return 2;
-    k_loss_sums<<<grid_of(n), 256, 0, st>>>(n, out, target, s, red, 0);
-    k_loss_sums<<<grid_of(n), 256, 0, st>>>(n, out, target, s, red, 1);
-    k_loss_grad<<<grid_of(n), 256, 0, st>>>(n, out, target, s, red, gout, loss);
+    k_loss_sums<<<grid_of(n), 256, 0, st>>>(n, out, target, p_prev, s, red, 0);
+    k_loss_sums<<<grid_of(n), 256, 0, st>>>(n, out, target, p_prev, s, red, 1);
+    k_loss_grad<<<grid_of(n), 256, 0, st>>>(n, out, target, p_prev, s, red, gout, loss);
     return status(cudaGetLastError());
 }
 
@@ -653,10 +660,10 @@ int gmg_net_head_backward(int D, int H, int W, const float* gout, const gmg_bf16
     return status(cudaGetLastError());
 }
 
-int gmg_net_unscale(long long n, const float* out, const float* s, float* p0, void* stream)
+int gmg_net_unscale(long long n, const float* out, const float* s, const float* p_prev, float* p0, void* stream)
 {
     if (!out || !s || !p0 || n < 0) return 1;
-    k_unscale<<<grid_of(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, out, s, p0);
+    k_unscale<<<grid_of(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, out, s, p_prev, p0);
     return status(cudaGetLastError());
 }
 

@@ -38,6 +38,25 @@ thread_local std::string g_create_error;
 
 int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// tensor maps of one call's arrays in stream-ordered device memory (freed by the
+// caller after its launch), or nullptr when the plane copies stay per-thread
+TmaPlanes* op_tensor_maps(const Geo& g, const float* p, const float* b, const float* bx, const float* by,
+                          const float* bz, bool vec4, cudaStream_t s)
+{
+    if (!vec4) return nullptr;
+    TmaPlanes h;
+    const float* pb[3] = {p, nullptr, nullptr};
+    if (!encode_tma_planes(&h, g, pb, b, bx, by, bz)) return nullptr;
+    TmaPlanes* d = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(h), s) != cudaSuccess) return nullptr;
+    // pageable source: the copy is staged before the call returns
+    if (cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaFreeAsync(d, s);
+        return nullptr;
+    }
+    return d;
+}
+
 int persistent_grid(int64_t tiles)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)kSMs * kResident));
@@ -116,6 +135,9 @@ struct TuneKey {
 
 std::mutex g_tune_mutex;
 std::map<TuneKey, int> g_tuned_zchunk;
+// tuned start of the one-CTA bottom per (fine geometry, hierarchy options): every
+// handle of the same problem shape then runs the same cycle, bit for bit
+std::map<std::vector<int>, int> g_tuned_lb;
 
 TuneKey tune_key(int kind, const Geo& g) { return {kind, g.n[0], g.n[1], g.n[2], g.per[0], g.per[1], g.per[2]}; }
 
@@ -126,13 +148,25 @@ int tuned_zchunk(int kind, const Geo& g)
     return it == g_tuned_zchunk.end() ? 0 : it->second;
 }
 
-// heuristic depth: enough z-chunks for about six CTAs per SM, chunks of >= 4 planes
+// heuristic depth: the chunk count that minimises rounds x (chunk + 3 planes of
+// pipeline fill), a round being one tile on each of the 3 CTA slots per SM the
+// pipelined kernels occupy; chunks of >= 4 planes
 int default_zchunk(const Geo& g)
 {
     const int64_t cols = (int64_t)ceil_div(g.n[0], kSweepTX) * ceil_div(g.n[1], kSweepTY);
-    const int want = (int)std::max<int64_t>(1, (kSMs * 6 + cols - 1) / cols);
-    const int nc = std::max(1, std::min(want, g.n[2] / 4));
-    return ceil_div(g.n[2], nc);
+    const int64_t slots = (int64_t)kSMs * 3;
+    int best_zc = g.n[2];
+    double best = 1e300;
+    for (int nc = 1; nc <= std::max(1, g.n[2] / 4); ++nc) {
+        const int zc = ceil_div(g.n[2], nc);
+        const int64_t tiles = cols * ceil_div(g.n[2], zc);
+        const double cost = (double)((tiles + slots - 1) / slots) * (zc + 3);
+        if (cost < best * 0.999) {
+            best = cost;
+            best_zc = zc;
+        }
+    }
+    return best_zc;
 }
 
 SweepTiling sweep_tiling(const Geo& g, int kind = kTuneSweep, int zchunk = 0)
@@ -186,6 +220,7 @@ struct LevelMem {
     float* beta[3] = {nullptr, nullptr, nullptr};
     float* b = nullptr;
     void* buf[3] = {nullptr, nullptr, nullptr};
+    TmaPlanes* tma = nullptr;     // device tensor maps of the FP32 arrays, or nullptr
 };
 
 struct ProblemMem {
@@ -243,6 +278,8 @@ struct Engine {
     cudaGraphExec_t graph_exec = nullptr;
     Ctl* ctl_dev = nullptr;         // nprob
     Ctl* ctl_host = nullptr;        // pinned mirror
+    int* fault_host = nullptr;      // pinned copy of the plane-copy wait fault flag
+    int* fault_dev = nullptr;
     CtlTask* cycle_ctl = nullptr;   // device: per-cycle control tasks
     CtlTask* init_ctl = nullptr;    // device: init / projection / gauge tasks
     CtlTask* gauge_ctl = nullptr;
@@ -263,6 +300,8 @@ struct Engine {
         allocs.clear();
         if (ctl_host) cudaFreeHost(ctl_host);
         ctl_host = nullptr;
+        if (fault_host) cudaFreeHost(fault_host);
+        fault_host = nullptr;
     }
 
     int fail(int code, const char* fmt, ...)
@@ -338,6 +377,16 @@ struct Engine {
                     if (!q) return fail(GMG_ERR_CUDA, "out of device memory");
                     Lm.buf[r] = q;
                 }
+                if (!(l > 0 && bf16_coarse)) {
+                    TmaPlanes h;
+                    const float* pb[3] = {static_cast<const float*>(Lm.buf[0]), static_cast<const float*>(Lm.buf[1]),
+                                          static_cast<const float*>(Lm.buf[2])};
+                    if (encode_tma_planes(&h, Lm.g, pb, Lm.b, Lm.beta[0], Lm.beta[1], Lm.beta[2])) {
+                        if (!(Lm.tma = dalloc<TmaPlanes>(1))) return fail(GMG_ERR_CUDA, "out of device memory");
+                        if (cudaMemcpy(Lm.tma, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess)
+                            return fail(GMG_ERR_CUDA, "tensor map upload failed");
+                    }
+                }
             }
             if (!(M.mask = dalloc<uint8_t>(M.n0))) return fail(GMG_ERR_CUDA, "out of device memory");
             M.elem_tiles = ceil_div(M.n0, kElemTile);
@@ -364,6 +413,10 @@ struct Engine {
         if (!norm || !proj || !bp || !gp || !ctl_dev) return fail(GMG_ERR_CUDA, "out of device memory");
         if (cudaMallocHost(&ctl_host, sizeof(Ctl) * nprob) != cudaSuccess)
             return fail(GMG_ERR_CUDA, "out of pinned host memory");
+        if (cudaMallocHost(&fault_host, sizeof(int)) != cudaSuccess)
+            return fail(GMG_ERR_CUDA, "out of pinned host memory");
+        *fault_host = 0;
+        fault_dev = wait_fault_flag();
         std::memset(ctl_host, 0, sizeof(Ctl) * nprob);
         int64_t on = 0, oe = 0;
         for (int p = 0; p < nprob; ++p) {
@@ -473,6 +526,7 @@ struct Engine {
         t.nchunks = st.nchunks;
         t.omega = 1.0f;
         t.ctl = M.ctl;
+        t.tma = std::is_same<TP, float>::value ? Lm.tma : nullptr;
         return t;
     }
 
@@ -500,6 +554,7 @@ struct Engine {
         t.zchunk = rt.zchunk;
         t.partials = partials;
         t.ctl = M.ctl;
+        t.tma = std::is_same<TP, float>::value ? Lm.tma : nullptr;
         return t;
     }
 
@@ -1044,7 +1099,19 @@ struct Engine {
         if (upload_ctl_tasks() != GMG_OK) return fail(GMG_ERR_CUDA, "autotune: control task upload failed");
         int rc = build_cycle();
         if (rc != GMG_OK) return rc;
-        if (P.size() == 1 && P[0].L > 1 && stop_[0] < P[0].L - 1) {
+        const std::vector<int> lb_key = {P[0].g0.n[0], P[0].g0.n[1], P[0].g0.n[2], P[0].g0.per[0], P[0].g0.per[1],
+                                         P[0].g0.per[2], opt.coarsen, opt.n_min, opt.precision, opt.nu_c};
+        int cached_lb = 0;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            auto it = g_tuned_lb.find(lb_key);
+            if (it != g_tuned_lb.end()) cached_lb = it->second;
+        }
+        if (P.size() == 1 && cached_lb > 0) {
+            forced_lb_ = cached_lb;
+            reset_cycle();
+            if ((rc = build_cycle()) != GMG_OK) return rc;
+        } else if (P.size() == 1 && P[0].L > 1 && stop_[0] < P[0].L - 1) {
             const int first = stop_[0];
             float best = 1e30f;
             int best_lb = first;
@@ -1060,6 +1127,10 @@ struct Engine {
                 }
             }
             forced_lb_ = best_lb;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                g_tuned_lb[lb_key] = best_lb;
+            }
             reset_cycle();
             if ((rc = build_cycle()) != GMG_OK) return rc;
         }
@@ -1090,10 +1161,19 @@ struct Engine {
         return c;
     }
 
+    // control blocks to the host; a pipelined kernel that gave up waiting for its
+    // plane copies turns into cudaErrorLaunchTimeout
     cudaError_t read_ctl()
     {
         cudaError_t e = cudaMemcpyAsync(ctl_host, ctl_dev, sizeof(Ctl) * P.size(), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess && fault_dev)
+            e = cudaMemcpyAsync(fault_host, fault_dev, sizeof(int), cudaMemcpyDeviceToHost, stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess && fault_dev && *fault_host) {
+            *fault_host = 0;
+            cudaMemsetAsync(fault_dev, 0, sizeof(int), stream);   // reported once
+            e = cudaErrorLaunchTimeout;
+        }
         return e;
     }
 
@@ -1691,11 +1771,14 @@ int gmg_op_sweep(int nx, int ny, int nz, const int* periodic, const float* bx, c
     TaskList<SweepTask<float, float>> tl{};
     tl.ntasks = 1;
     tl.total = (int)st.tiles();
-    tl.single = t;
     tl.vec = sweep_vec(t);
-    return launch_sweep(tl, persistent_grid(tl.total), static_cast<cudaStream_t>(stream)) == cudaSuccess
-               ? GMG_OK
-               : GMG_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TmaPlanes* dmap = op_tensor_maps(t.g, p_in, b, bx, by, bz, tl.vec == 4, s);
+    t.tma = dmap;
+    tl.single = t;
+    cudaError_t e = launch_sweep(tl, persistent_grid(tl.total), s);
+    if (dmap) cudaFreeAsync(dmap, s);
+    return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
 int gmg_op_sweep_reference(int nx, int ny, int nz, const int* periodic, const float* bx,
@@ -1778,9 +1861,12 @@ static int op_residual(int nx, int ny, int nz, const int* periodic, const int* f
     TaskList<ResTask<float>> tl{};
     tl.ntasks = 1;
     tl.total = (int)rt.tiles();
-    tl.single = t;
     tl.march = march ? 1 : 0;
+    TmaPlanes* dmap = op_tensor_maps(t.g, p, b, bx, by, bz, march, s);
+    t.tma = dmap;
+    tl.single = t;
     cudaError_t e = launch_residual(tl, persistent_grid(tl.total), s);
+    if (dmap) cudaFreeAsync(dmap, s);
     if (e == cudaSuccess && rr) {
         e = launch_sum_partials(t.partials, (int)rt.tiles(), out, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(rr, out, sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -370,3 +370,26 @@ def random_small_problem(dims, periodic, seed: int, zero_blocks: bool = True) ->
     bx, by, bz = apply_walls(bx, by, bz, periodic)
     b = rng.standard_normal(shape)
     return Problem(shape, tuple(periodic), b, bx, by, bz, [], f"random_{nx}x{ny}x{nz}")
+
+
+def _vortex_rhs(job):
+    shape, bodies, centers, axes, gamma, sigma, u_inf = job
+    return solenoidal_rhs(shape, bodies, VortexBlobs(centers, axes, gamma, sigma), u_inf).astype(np.float32)
+
+
+def vortex_frames(count: int, workers: int = 1, **kw):
+    """Coefficients and the right-hand sides (float32) of `count` consecutive
+    steps of VortexSequence(**kw); the sources are computed in a spawn pool
+    of `workers` processes when workers > 1."""
+    seq = VortexSequence(**kw)
+    jobs = []
+    for _ in range(count):
+        jobs.append((seq.shape, seq.bodies, seq.centers.copy(), seq.axes.copy(), seq.gamma.copy(), seq.s, seq.u_inf))
+        seq.advance()
+    if workers > 1 and count > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, count)) as pool:
+            rhs = pool.map(_vortex_rhs, jobs, chunksize=max(1, count // (4 * workers)))
+    else:
+        rhs = [_vortex_rhs(j) for j in jobs]
+    return seq.walls, rhs

@@ -1,7 +1,8 @@
 """Learned warm start: a small 3D U-Net that predicts a solve's initial guess.
 
 Inputs per cell: sigma / s, the mean of the cell's six face coefficients and
-the previous pressure / s (s = RMS of sigma); output p0 = s * net(...).  The
+the previous pressure / s (s = RMS of sigma); output p0 = s * net(...) + p_prev,
+so the network predicts the increment over the previous pressure.  The
 solver then iterates from p0 to its usual tolerance, so a poor prediction
 costs V-cycles but never accuracy.  Architecture (3x3x3 convolutions with
 zero padding, ReLU after each): 16-16 | pool | 32-32 | pool | 64-64 | up,
@@ -166,7 +167,8 @@ class WarmStartNet:
         """Predicted initial guess p0 (FP32 device tensor of the grid's cells)."""
         self.pack(b, bx, by, bz, p_prev)
         self.forward()
-        G.net_call("gmg_net_unscale", self.ncell[0], self._p(self.out), self._p(self.s), self._p(self.p0), self._st())
+        G.net_call("gmg_net_unscale", self.ncell[0], self._p(self.out), self._p(self.s),
+                   self._p(p_prev) if p_prev is not None else None, self._p(self.p0), self._st())
         return self.p0
 
     # ------------------------------------------------------------------ backward
@@ -239,10 +241,11 @@ class WarmStartNet:
         self._relu_b(0, gr["l0a"], 16, a["e0a"], 16, 0, 16)
         self._wgrad("e0a", 0, a["x0"], 16, 0, gr["l0a"], 16)
 
-    def loss(self, p_target):
-        """Loss against the converged pressure (and d loss / d out in self.gout)."""
+    def loss(self, p_target, p_prev=None):
+        """Loss of the prediction against the converged pressure (d loss / d out in self.gout)."""
         D, H, W = self._dims(0)
-        G.net_call("gmg_net_loss", D, H, W, self._p(self.out), self._p(p_target), self._p(self.s),
+        G.net_call("gmg_net_loss", D, H, W, self._p(self.out), self._p(p_target),
+                   self._p(p_prev) if p_prev is not None else None, self._p(self.s),
                    self._p(self.gout), self._p(self.loss_dev), self._p(self.red), self._st())
 
     def step(self):
@@ -258,7 +261,7 @@ class WarmStartNet:
         """Forward, loss, backward and Adam on one (input, converged pressure) pair."""
         self.pack(b, bx, by, bz, p_prev)
         self.forward()
-        self.loss(p_target)
+        self.loss(p_target, p_prev)
         self.backward()
         self.step()
         loss = float(self.loss_dev.item())

@@ -96,3 +96,33 @@ def test_adam_first_step_closed_form():
     W.adam_step(params, grads, state, lr=0.01)
     np.testing.assert_allclose(params["a"], np.array([1.0, -2.0, 0.5]) - 0.01 * grads["a"] / (np.abs(grads["a"]) + 1e-8),
                                rtol=1e-12)
+
+
+def test_predict_increment_map():
+    """p0 = s * net + p_prev: a zeroed network returns p_prev exactly, and the
+    parameter gradient of loss(p0) is backward(s * d loss / d p0), checked by
+    central differences on one weight tensor."""
+    rng = np.random.default_rng(6)
+    shape = (8, 8, 8)
+    b = rng.standard_normal(shape)
+    bm = rng.uniform(0, 1, shape)
+    pp = rng.standard_normal(shape)
+    pt = pp + 0.3 * rng.standard_normal(shape)
+    params = W.init_params(7)
+    zero = {k: np.zeros_like(v) for k, v in params.items()}
+    p0, _, s = W.predict(zero, b, bm, pp)
+    assert np.array_equal(p0, pp) and s == pytest.approx(np.sqrt(np.mean(b * b)))
+    p0, cache, s = W.predict(params, b, bm, pp)
+    _, g = W.loss_and_grad_out(p0, pt)
+    grads = W.backward(params, cache, s * g)
+    d = rng.standard_normal(params["d1a.w"].shape)
+
+    def f(w):
+        q = dict(params)
+        q["d1a.w"] = w
+        return W.loss_and_grad_out(W.predict(q, b, bm, pp)[0], pt)[0]
+    errs = []
+    for eps in (1e-7, 3e-8):
+        fd = (f(params["d1a.w"] + eps * d) - f(params["d1a.w"] - eps * d)) / (2 * eps)
+        errs.append(abs(float(np.sum(grads["d1a.w"] * d)) - fd) / abs(fd))
+    assert min(errs) <= 1e-5, errs

@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: the tests and the smoke check use it; the solver
 package never imports it.
 
 The network predicts the initial guess p0 of a pressure-Poisson solve from
-(sigma, mean face coefficient, previous pressure).  It is a small 3-level
+(sigma, mean face coefficient, previous pressure, residual of the previous
+pressure).  It is a small 3-level
 U-Net of 3x3x3 convolutions (16 / 32 / 64 channels) with 2x average pooling,
 nearest 2x upsampling and channel concatenation of the encoder features,
 finished by a 1x1x1 convolution.  Everything here is written from the
@@ -15,8 +16,10 @@ definitions, in FP64, on arrays laid out [C][D][H][W] (z, y, x):
     relu:     max(v, 0)
     pool:     mean of each 2 x 2 x 2 block
     upsample: each value copied to its 2 x 2 x 2 block
-    output:   p0 = s * net(x0) + p_prev  (the net predicts the increment over
-              the previous pressure, in units of s)
+    input:    x0 = (b / s, mean face coefficient, p_prev / s, r / s_r) with
+              r = b - A p_prev, s = RMS(b), s_r = RMS(r)
+    output:   p0 = p_prev + s_r * net(x0)  (the net predicts the increment
+              over the previous pressure, which solves A dp = r, in units of s_r)
     loss:     |(p0 - mean p0) - (p* - mean p*)|^2 / |p* - mean p*|^2
 
 Backward passes are the adjoints of these maps, written out term by term.
@@ -27,7 +30,7 @@ import numpy as np
 
 # (name, input channels, output channels, level)
 LAYERS = [
-    ("e0a", 3, 16, 0), ("e0b", 16, 16, 0),
+    ("e0a", 4, 16, 0), ("e0b", 16, 16, 0),
     ("e1a", 16, 32, 1), ("e1b", 32, 32, 1),
     ("e2a", 32, 64, 2), ("e2b", 64, 64, 2),
     ("d1a", 96, 32, 1), ("d1b", 32, 32, 1),
@@ -104,7 +107,7 @@ def up2_backward(g):
 
 
 def forward(params, x0):
-    """x0 [3][D][H][W] -> (out [D][H][W], cache of activations)."""
+    """x0 [4][D][H][W] -> (out [D][H][W], cache of activations)."""
     cache = {"x0": x0}
     h = x0
     for name in ("e0a", "e0b"):
@@ -195,15 +198,19 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
 
 
-def predict(params, b, beta_mean, p_prev):
-    """Initial guess p0 = s * net(x0) + p_prev, with the network's cache and s."""
-    x0, s = features(b, beta_mean, p_prev)
+def predict(params, b, beta_mean, p_prev, r):
+    """Initial guess p0 = p_prev + s_r * net(x0), with the network's cache and s_r."""
+    x0, s, s_r = features(b, beta_mean, p_prev, r)
     out, cache = forward(params, x0)
-    return s * out + p_prev, cache, s
+    return p_prev + s_r * out, cache, s_r
 
 
-def features(b, beta_mean, p_prev):
-    """Network input [3][D][H][W] and the scale s = RMS(b)."""
-    s = float(np.sqrt(np.mean(b * b)))
-    s = s if s > 0 else 1.0
-    return np.stack([b / s, beta_mean, p_prev / s]), s
+def _rms(a):
+    v = float(np.sqrt(np.mean(a * a)))
+    return v if v > 0 else 1.0
+
+
+def features(b, beta_mean, p_prev, r):
+    """Network input [4][D][H][W] and the scales s = RMS(b), s_r = RMS(r)."""
+    s, s_r = _rms(b), _rms(r)
+    return np.stack([b / s, beta_mean, p_prev / s, r / s_r]), s, s_r

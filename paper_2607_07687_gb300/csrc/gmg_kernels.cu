@@ -279,16 +279,6 @@ __device__ __forceinline__ void tma_plane(float* dst, const CUtensorMap* map, in
         : "memory");
 }
 
-// after a failed wait: record it, then wait (bounded) for the copies still in flight
-__device__ __noinline__ void drain_after_fault(uint64_t* bars, uint32_t phase, int first, int count, int ring)
-{
-    if (threadIdx.x == 0) atomicExch(&g_wait_fault, 1);
-    for (int d = 0; d < count; ++d) {
-        const int j = (first + d) % ring;
-        mbar_wait(&bars[j], (phase >> j) & 1u);
-    }
-}
-
 template <int VEC, bool CORR, class TC>
 __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_constant__ TaskList<SweepTask<float, TC>> tl)
 {
@@ -307,20 +297,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
     static_assert(NCH <= kThreads / 2 && NRED <= kThreads && PL <= 2 * kThreads, "thread budget");
     // rings: 0 = p, 1 = b, 2 = lower x faces, 3 = lower y faces, 4 = lower z faces, 5 = merged red plane
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t s_mbar[R];
     const int tid = threadIdx.x;
     const int half = tid / (kThreads / 2);      // copy duty: 0 -> p, b, x faces; 1 -> y, z faces
     const int chunk = tid % (kThreads / 2);
 
-    if (VEC == 4) {
-        if (tid == 0) {
-            for (int j = 0; j < R; ++j) mbar_init(&s_mbar[j]);
-            fence_mbar_init();
-        }
-        __syncthreads();
-    }
-    uint32_t phase = 0;                         // bit j: parity of the next completion of s_mbar[j]
-    bool dead = false;                          // a plane-copy wait gave up
     for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
         int local;
         const SweepTask<float, TC>* tp = task_of(tl, tile, local);
@@ -441,72 +421,31 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
         // before the plane is read).  Step u waits for G(u-LA), then issues G(u) after its
         // first barrier; the prologue issues G0 (p planes kr0-1 .. kr0+PA, z faces of kr0)
         // and G(-LA) .. G(-1).  Plane z lives in slot (z - kr0 + 1) mod R.
-        // Copies go by TMA (G(v) completing on s_mbar[(v + LA) mod R], G0 with G(-LA))
-        // when the tile's box needs no periodic wrap in x or y; otherwise, and for a zero
-        // input, every thread issues 16-byte asynchronous copies (cp.async groups).
         const int kr0 = z0 - 1;
         const int nsteps = (z1 - z0) + 2;   // red planes z0-1 .. z1
-        const TmaPlanes* tm = VEC == 4 ? tp->tma : nullptr;
-        const bool use_tma = tm != nullptr && pin != nullptr && !(px && (x0 - XO < 0 || x0 + TX + XO > nx)) &&
-                             !(py && (y0 - 2 < 0 || y0 + TY + 2 > ny));
-        const CUtensorMap* pmap = use_tma ? &tm->p[(tp->in_role + rot) % 3] : nullptr;
-        auto tplane = [&](float* dst, const CUtensorMap* map, int z, uint64_t* bar) {
-            if (pz) {
-                z %= nz;
-                if (z < 0) z += nz;
-            }
-            tma_plane(dst, map, x0 - XO, y0 - 2, z, bar);   // x0 - 4: 16-byte aligned (x0 is a multiple of 32)
-        };
-        auto issue_group = [&](int v, uint64_t* bar) {
+        auto issue_group = [&](int v) {
             const int kb = kr0 + v + LA;
             const int sb = (v + LA + 1 + R * 4) % R, sz = (v + LA + 2 + R * 4) % R, sp = (v + LA + PA + 2 + R * 4) % R;
-            if (bar) {
-                tplane(ring(1, sb), &tm->b, kb, bar);
-                tplane(ring(2, sb), &tm->x, kb, bar);
-                tplane(ring(3, sb), &tm->y, kb, bar);
-                tplane(ring(4, sz), &tm->z, kb + 1, bar);
-                tplane(ring(0, sp), pmap, kb + 1 + PA, bar);
-            } else {
-                copy_plane(ring(1, sb), ba, kb, false);
-                copy_plane(ring(2, sb), tp->bx, kb, false);
-                copy_plane(ring(3, sb), tp->by, kb, false);
-                copy_plane(ring(4, sz), tp->bz, kb + 1, true);
-                copy_plane(ring(0, sp), pin, kb + 1 + PA, false);
-            }
+            copy_plane(ring(1, sb), ba, kb, false);
+            copy_plane(ring(2, sb), tp->bx, kb, false);
+            copy_plane(ring(3, sb), tp->by, kb, false);
+            copy_plane(ring(4, sz), tp->bz, kb + 1, true);
+            copy_plane(ring(0, sp), pin, kb + 1 + PA, false);
         };
-        if (use_tma) {
-            if (tid == 0) {
-                fence_proxy_async();                       // earlier generic writes to the rings come first
-                mbar_expect_tx(&s_mbar[0], kPlaneBytes * (5 + (2 + PA) + 1));
-                for (int z = kr0 - 1; z <= kr0 + PA; ++z) tplane(ring(0, (z - kr0 + 1 + R) % R), pmap, z, &s_mbar[0]);
-                tplane(ring(4, 1), &tm->z, kr0, &s_mbar[0]);
-                issue_group(-LA, &s_mbar[0]);
-                for (int v = -LA + 1; v < 0 && v + LA < nsteps; ++v) {   // only groups a step will wait for
-                    mbar_expect_tx(&s_mbar[v + LA], 5 * kPlaneBytes);
-                    issue_group(v, &s_mbar[v + LA]);
-                }
-            }
-        } else {
-            for (int z = kr0 - 1; z <= kr0 + PA; ++z) copy_plane(ring(0, (z - kr0 + 1 + R) % R), pin, z, false);
-            copy_plane(ring(4, 1), tp->bz, kr0, true);
+        for (int z = kr0 - 1; z <= kr0 + PA; ++z) copy_plane(ring(0, (z - kr0 + 1 + R) % R), pin, z, false);
+        copy_plane(ring(4, 1), tp->bz, kr0, true);
+        cp_commit();
+        for (int v = -LA; v < 0; ++v) {
+            issue_group(v);
             cp_commit();
-            for (int v = -LA; v < 0; ++v) {
-                issue_group(v, nullptr);
-                cp_commit();
-            }
         }
         float cur0 = 0.f, cur1 = 0.f, nxt0 = 0.f, nxt1 = 0.f;
         if (CORR) {
             float c[3][2];
             for (int j = 0; j < 3; ++j) corr_load(kr0 - 1 + j, c[j][0], c[j][1]);
             corr_load(kr0 + 2, cur0, cur1);
-            bool ok = true;
-            if (use_tma) ok = mbar_wait(&s_mbar[0], phase & 1u);   // G0: p planes kr0-1 .. kr0+1 (phase kept)
-            else cp_wait<LA>();
-            if (__syncthreads_or(!ok)) {
-                drain_after_fault(s_mbar, phase, 0, LA, R);
-                return;
-            }
+            cp_wait<LA>();
+            __syncthreads();
             for (int j = 0; j < 3; ++j) corr_add(ring(0, j), c[j][0], c[j][1]);
         }
 
@@ -517,31 +456,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
             constexpr int Sm1 = (J + R) % R, Sm2 = (J + R - 1) % R;
             constexpr int Sp1 = (J + 2) % R, Sp2 = (J + 3) % R;
             constexpr int SB = (J + 1 + LA) % R, SZ = (J + 2 + LA) % R, SP = (J + 2 + LA + PA) % R;
-            if (dead) return;
             const int kr = kr0 + u;
-            bool ok = true;
-            if (use_tma) ok = mbar_wait(&s_mbar[J], (phase >> J) & 1u);
-            else cp_wait<LA - 1>();
-            if (__syncthreads_or(!ok)) {                  // S1: G(u-LA) visible, step u-1 done everywhere
-                drain_after_fault(s_mbar, phase, J, min(LA, nsteps - u), R);
-                dead = true;
-                return;
-            }
-            if (use_tma) phase ^= 1u << J;
+            cp_wait<LA - 1>();
+            __syncthreads();                               // S1: G(u-LA) visible, step u-1 done everywhere
             // G(u): written slots hold planes every thread finished with in step u-1
             if (u + LA < nsteps) {
-                if (use_tma) {
-                    if (tid == 0) {
-                        fence_proxy_async();
-                        uint64_t* bar = &s_mbar[(J + LA) % R];
-                        mbar_expect_tx(bar, 5 * kPlaneBytes);
-                        tplane(ring(0, SP), pmap, kr + 1 + LA + PA, bar);
-                        tplane(ring(1, SB), &tm->b, kr + LA, bar);
-                        tplane(ring(2, SB), &tm->x, kr + LA, bar);
-                        tplane(ring(3, SB), &tm->y, kr + LA, bar);
-                        tplane(ring(4, SZ), &tm->z, kr + 1 + LA, bar);
-                    }
-                } else if (VEC == 4) {
+                if (VEC == 4) {
                     if (chunk < NCH) {
                         int64_t zo1, zo2;
                         if (half == 0) {
@@ -559,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
                         }
                     }
                 } else {
-                    issue_group(u, nullptr);
+                    issue_group(u);
                 }
                 corr_load(kr + 3, nxt0, nxt1);
             }
@@ -634,7 +554,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
             if (u + 4 < nsteps) step(u + 4, std::integral_constant<int, 4>());
             if (u + 5 < nsteps) step(u + 5, std::integral_constant<int, 5>());
         }
-        if (dead) return;
         cp_wait<0>();
         __syncthreads();                                   // the next tile reuses the rings
     }

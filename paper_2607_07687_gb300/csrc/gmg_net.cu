@@ -351,21 +351,6 @@ namespace {
 
 // ---------------------------------------------------------------- input, head, loss, optimiser
 
-__global__ void k_sumsq(int64_t n, const float* __restrict__ b, double* red)
-{
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += (double)b[i] * b[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(red, s);
-}
-
-__global__ void k_scale_from(const double* red, int64_t n, float* s)
-{
-    const double v = sqrt(red[0] / (double)n);
-    *s = v > 0.0 ? (float)v : 1.f;
-}
-
 // lower face coefficient of cell (x, y, z) along d, 0 on walls
 __device__ __forceinline__ float face_lo(const float* a, int D, int H, int W, const int* per, int d, int x, int y,
                                          int z)
@@ -382,23 +367,94 @@ __device__ __forceinline__ float face_lo(const float* a, int D, int H, int W, co
     return a[((int64_t)c[2] * H + c[1]) * W + c[0]];
 }
 
-__global__ void k_pack_input(int D, int H, int W, const float* b, const float* p_prev, const float* bx,
-                             const float* by, const float* bz, int px, int py, int pz, const float* s, bf16* x0)
+// p at (x, y, z) with periodic wrap; 0 outside a wall (its face is 0 there)
+__device__ __forceinline__ float p_at(const float* p, int D, int H, int W, const int* per, int x, int y, int z)
+{
+    int c[3] = {x, y, z};
+    const int n[3] = {W, H, D};
+    for (int e = 0; e < 3; ++e) {
+        if (c[e] < 0 || c[e] >= n[e]) {
+            if (!per[e]) return 0.f;
+            c[e] = (c[e] % n[e] + n[e]) % n[e];
+        }
+    }
+    return p[((int64_t)c[2] * H + c[1]) * W + c[0]];
+}
+
+struct PackCell {
+    float b, r, mean;
+};
+
+// b, the residual b - A p_prev (difference form, FP32) and the mean of the six faces of one cell
+__device__ __forceinline__ PackCell pack_cell(int D, int H, int W, const float* b, const float* pp, const float* bx,
+                                              const float* by, const float* bz, const int* per, int64_t i)
+{
+    const int x = (int)(i % W), y = (int)((i / W) % H), z = (int)(i / ((int64_t)W * H));
+    const float fx0 = face_lo(bx, D, H, W, per, 0, x, y, z), fx1 = face_lo(bx, D, H, W, per, 0, x + 1, y, z);
+    const float fy0 = face_lo(by, D, H, W, per, 1, x, y, z), fy1 = face_lo(by, D, H, W, per, 1, x, y + 1, z);
+    const float fz0 = face_lo(bz, D, H, W, per, 2, x, y, z), fz1 = face_lo(bz, D, H, W, per, 2, x, y, z + 1);
+    PackCell c;
+    c.b = b[i];
+    c.mean = (fx0 + fx1 + fy0 + fy1 + fz0 + fz1) / 6.f;
+    c.r = c.b;
+    if (pp) {
+        const float p = pp[i];
+        const float flux = ((fx0 * (p_at(pp, D, H, W, per, x - 1, y, z) - p) +
+                             fx1 * (p_at(pp, D, H, W, per, x + 1, y, z) - p)) +
+                            (fy0 * (p_at(pp, D, H, W, per, x, y - 1, z) - p) +
+                             fy1 * (p_at(pp, D, H, W, per, x, y + 1, z) - p))) +
+                           (fz0 * (p_at(pp, D, H, W, per, x, y, z - 1) - p) +
+                            fz1 * (p_at(pp, D, H, W, per, x, y, z + 1) - p));
+        c.r = c.b - flux;
+    }
+    return c;
+}
+
+// red[0] += sum b^2, red[1] += sum r^2
+__global__ void k_pack_sums(int D, int H, int W, const float* b, const float* pp, const float* bx, const float* by,
+                            const float* bz, int px, int py, int pz, double* red)
 {
     const int per[3] = {px, py, pz};
     const int64_t n = (int64_t)D * H * W;
-    const float inv = 1.f / *s;
+    double sb = 0.0, sr = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % W), y = (int)((i / W) % H), z = (int)(i / ((int64_t)W * H));
-        const float mean = (face_lo(bx, D, H, W, per, 0, x, y, z) + face_lo(bx, D, H, W, per, 0, x + 1, y, z) +
-                            face_lo(by, D, H, W, per, 1, x, y, z) + face_lo(by, D, H, W, per, 1, x, y + 1, z) +
-                            face_lo(bz, D, H, W, per, 2, x, y, z) + face_lo(bz, D, H, W, per, 2, x, y, z + 1)) /
-                           6.f;
+        const PackCell c = pack_cell(D, H, W, b, pp, bx, by, bz, per, i);
+        sb += (double)c.b * c.b;
+        sr += (double)c.r * c.r;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(red, sb);
+        atomicAdd(red + 1, sr);
+    }
+}
+
+// s[0] = RMS(b), s[1] = RMS(r) (1 where zero)
+__global__ void k_scales(const double* red, int64_t n, float* s)
+{
+    for (int k = 0; k < 2; ++k) {
+        const double v = sqrt(red[k] / (double)n);
+        s[k] = v > 0.0 ? (float)v : 1.f;
+    }
+}
+
+__global__ void k_pack_input(int D, int H, int W, const float* b, const float* pp, const float* bx, const float* by,
+                             const float* bz, int px, int py, int pz, const float* s, bf16* x0)
+{
+    const int per[3] = {px, py, pz};
+    const int64_t n = (int64_t)D * H * W;
+    const float inv = 1.f / s[0], invr = 1.f / s[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const PackCell c = pack_cell(D, H, W, b, pp, bx, by, bz, per, i);
         bf16* o = x0 + i * 16;
-        o[0] = __float2bfloat16_rn(b[i] * inv);
-        o[1] = __float2bfloat16_rn(mean);
-        o[2] = __float2bfloat16_rn(p_prev ? p_prev[i] * inv : 0.f);
-        for (int c = 3; c < 16; ++c) o[c] = __float2bfloat16_rn(0.f);
+        o[0] = __float2bfloat16_rn(c.b * inv);
+        o[1] = __float2bfloat16_rn(c.mean);
+        o[2] = __float2bfloat16_rn(pp ? pp[i] * inv : 0.f);
+        o[3] = __float2bfloat16_rn(c.r * invr);
+        for (int k = 4; k < 16; ++k) o[k] = __float2bfloat16_rn(0.f);
     }
 }
 
@@ -615,12 +671,12 @@ int gmg_net_pack_input(int D, int H, int W, const float* b, const float* p_prev,
     if (!b || !bx || !by || !bz || !x0 || !s_out || !red) return 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t n = (int64_t)D * H * W;
-    cudaError_t e = cudaMemsetAsync(red, 0, sizeof(double), s);
+    cudaError_t e = cudaMemsetAsync(red, 0, 2 * sizeof(double), s);
     if (e != cudaSuccess) return 2;
-    k_sumsq<<<grid_of(n), 256, 0, s>>>(n, b, red);
-    k_scale_from<<<1, 1, 0, s>>>(red, n, s_out);
     const int px = periodic ? periodic[0] != 0 : 0, py = periodic ? periodic[1] != 0 : 0,
               pz = periodic ? periodic[2] != 0 : 0;
+    k_pack_sums<<<grid_of(n), 256, 0, s>>>(D, H, W, b, p_prev, bx, by, bz, px, py, pz, red);
+    k_scales<<<1, 1, 0, s>>>(red, n, s_out);
     k_pack_input<<<grid_of(n), 256, 0, s>>>(D, H, W, b, p_prev, bx, by, bz, px, py, pz, s_out,
                                             reinterpret_cast<bf16*>(x0));
     return status(cudaGetLastError());

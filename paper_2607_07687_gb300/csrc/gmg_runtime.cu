@@ -38,22 +38,51 @@ thread_local std::string g_create_error;
 
 int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
-// tensor maps of one call's arrays in stream-ordered device memory (freed by the
-// caller after its launch), or nullptr when the plane copies stay per-thread
+// Tensor maps of one call's arrays (single-step ops), or nullptr when the plane
+// copies stay per-thread.  Maps live in device memory in a small cache keyed by
+// geometry and pointers, so repeated calls on the same arrays upload nothing;
+// an evicted entry is released with cudaFree, which waits for kernels using it.
+std::mutex g_map_mutex;
+struct MapEntry {
+    std::vector<uintptr_t> key;
+    TmaPlanes* dev;
+    uint64_t used;
+};
+std::vector<MapEntry> g_map_cache;
+uint64_t g_map_clock = 0;
+constexpr size_t kMapCacheEntries = 16;
+
 TmaPlanes* op_tensor_maps(const Geo& g, const float* p, const float* b, const float* bx, const float* by,
                           const float* bz, bool vec4, cudaStream_t s)
 {
     if (!vec4) return nullptr;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const std::vector<uintptr_t> key = {(uintptr_t)dev, (uintptr_t)g.n[0], (uintptr_t)g.n[1], (uintptr_t)g.n[2],
+                                        (uintptr_t)p, (uintptr_t)b, (uintptr_t)bx, (uintptr_t)by, (uintptr_t)bz};
+    std::lock_guard<std::mutex> lock(g_map_mutex);
+    for (MapEntry& m : g_map_cache)
+        if (m.key == key) {
+            m.used = ++g_map_clock;
+            return m.dev;
+        }
     TmaPlanes h;
     const float* pb[3] = {p, nullptr, nullptr};
     if (!encode_tma_planes(&h, g, pb, b, bx, by, bz)) return nullptr;
+    if (g_map_cache.size() >= kMapCacheEntries) {
+        auto it = std::min_element(g_map_cache.begin(), g_map_cache.end(),
+                                   [](const MapEntry& a, const MapEntry& c) { return a.used < c.used; });
+        cudaFree(it->dev);
+        g_map_cache.erase(it);
+    }
     TmaPlanes* d = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(h), s) != cudaSuccess) return nullptr;
-    // pageable source: the copy is staged before the call returns
-    if (cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        cudaFreeAsync(d, s);
+    if (cudaMalloc(reinterpret_cast<void**>(&d), sizeof(h)) != cudaSuccess) return nullptr;
+    if (cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaFree(d);
         return nullptr;
     }
+    g_map_cache.push_back({key, d, ++g_map_clock});
     return d;
 }
 
@@ -1777,7 +1806,6 @@ int gmg_op_sweep(int nx, int ny, int nz, const int* periodic, const float* bx, c
     t.tma = dmap;
     tl.single = t;
     cudaError_t e = launch_sweep(tl, persistent_grid(tl.total), s);
-    if (dmap) cudaFreeAsync(dmap, s);
     return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
@@ -1866,7 +1894,6 @@ static int op_residual(int nx, int ny, int nz, const int* periodic, const int* f
     t.tma = dmap;
     tl.single = t;
     cudaError_t e = launch_residual(tl, persistent_grid(tl.total), s);
-    if (dmap) cudaFreeAsync(dmap, s);
     if (e == cudaSuccess && rr) {
         e = launch_sum_partials(t.partials, (int)rt.tiles(), out, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(rr, out, sizeof(double), cudaMemcpyDeviceToHost, s);

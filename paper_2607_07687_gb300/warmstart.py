@@ -1,8 +1,10 @@
 """Learned warm start: a small 3D U-Net that predicts a solve's initial guess.
 
-Inputs per cell: sigma / s, the mean of the cell's six face coefficients and
-the previous pressure / s (s = RMS of sigma); output p0 = s * net(...) + p_prev,
-so the network predicts the increment over the previous pressure.  The
+Inputs per cell: sigma / s, the mean of the cell's six face coefficients, the
+previous pressure / s and its residual r = sigma - A p_prev over s_r (s, s_r
+the RMS values of sigma and r); output p0 = p_prev + s_r * net(...), so the
+network predicts the increment over the previous pressure (the solution of
+A dp = r).  The
 solver then iterates from p0 to its usual tolerance, so a poor prediction
 costs V-cycles but never accuracy.  Architecture (3x3x3 convolutions with
 zero padding, ReLU after each): 16-16 | pool | 32-32 | pool | 64-64 | up,
@@ -24,7 +26,7 @@ from . import binding as G
 
 # (name, input channels, output channels, level)
 LAYERS = [
-    ("e0a", 3, 16, 0), ("e0b", 16, 16, 0),
+    ("e0a", 4, 16, 0), ("e0b", 16, 16, 0),
     ("e1a", 16, 32, 1), ("e1b", 32, 32, 1),
     ("e2a", 32, 64, 2), ("e2b", 64, 64, 2),
     ("d1a", 96, 32, 1), ("d1b", 32, 32, 1),
@@ -80,7 +82,7 @@ class WarmStartNet:
         self.out = torch.zeros(self.ncell[0], dtype=torch.float32, device=dev)
         self.gout = torch.zeros_like(self.out)
         self.p0 = torch.zeros_like(self.out)
-        self.s = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.s = torch.zeros(2, dtype=torch.float32, device=dev)   # RMS of sigma, RMS of the residual
         self.red = torch.zeros(4, dtype=torch.float64, device=dev)
         self.loss_dev = torch.zeros(1, dtype=torch.float64, device=dev)
 
@@ -167,7 +169,7 @@ class WarmStartNet:
         """Predicted initial guess p0 (FP32 device tensor of the grid's cells)."""
         self.pack(b, bx, by, bz, p_prev)
         self.forward()
-        G.net_call("gmg_net_unscale", self.ncell[0], self._p(self.out), self._p(self.s),
+        G.net_call("gmg_net_unscale", self.ncell[0], self._p(self.out), self._p(self.s, 1),
                    self._p(p_prev) if p_prev is not None else None, self._p(self.p0), self._st())
         return self.p0
 
@@ -245,7 +247,7 @@ class WarmStartNet:
         """Loss of the prediction against the converged pressure (d loss / d out in self.gout)."""
         D, H, W = self._dims(0)
         G.net_call("gmg_net_loss", D, H, W, self._p(self.out), self._p(p_target),
-                   self._p(p_prev) if p_prev is not None else None, self._p(self.s),
+                   self._p(p_prev) if p_prev is not None else None, self._p(self.s, 1),
                    self._p(self.gout), self._p(self.loss_dev), self._p(self.red), self._st())
 
     def step(self):

@@ -225,28 +225,35 @@ def beta_mean(bx, by, bz, periodic):
 
 
 @pytest.mark.parametrize("periodic", [(False, False, False), (True, False, True)])
-def test_pack_input(periodic):
+@pytest.mark.parametrize("with_prev", [True, False])
+def test_pack_input(periodic, with_prev, oracle):
+    """Input channels against the oracle's features, with the residual
+    r = b - A p_prev from the FP64 solver oracle's operator."""
     import ctypes
     torch = _torch()
     rng = np.random.default_rng(5)
     shape = (4, 6, 8)
     b = rng.standard_normal(shape).astype(np.float32)
-    pp = rng.standard_normal(shape).astype(np.float32)
+    pp = rng.standard_normal(shape).astype(np.float32) if with_prev else np.zeros(shape, np.float32)
     bx, by, bz = (rng.uniform(0, 1, shape).astype(np.float32) for _ in range(3))
     T = lambda a: torch.from_numpy(a).to("cuda:0")
     x0 = torch.full((b.size, 16), 9.0, dtype=torch.bfloat16, device="cuda:0")
-    s = torch.zeros(1, dtype=torch.float32, device="cuda:0")
+    s = torch.zeros(2, dtype=torch.float32, device="cuda:0")
     red = torch.zeros(2, dtype=torch.float64, device="cuda:0")
     per = (ctypes.c_int * 3)(*[int(v) for v in periodic])
     bt, pt, bxt, byt, bzt = T(b), T(pp), T(bx), T(by), T(bz)
-    call("gmg_net_pack_input", *shape, ptr(bt), ptr(pt), ptr(bxt), ptr(byt), ptr(bzt), per, ptr(x0), ptr(s), ptr(red),
-         stream())
-    bm = beta_mean(*(a.astype(np.float64) for a in (bx, by, bz)), periodic)
-    ref, sref = O.features(b.astype(np.float64), bm, pp.astype(np.float64))
-    assert float(s.item()) == pytest.approx(sref, rel=1e-6)
+    call("gmg_net_pack_input", *shape, ptr(bt), ptr(pt) if with_prev else None, ptr(bxt), ptr(byt), ptr(bzt), per,
+         ptr(x0), ptr(s), ptr(red), stream())
+    f64 = [a.astype(np.float64) for a in (b, pp, bx, by, bz)]
+    bm = beta_mean(*f64[2:], periodic)
+    r = f64[0] - oracle.apply_A(f64[1], *f64[2:], periodic=periodic)
+    ref, sref, srref = O.features(f64[0], bm, f64[1], r)
+    sh = s.cpu().numpy()
+    assert float(sh[0]) == pytest.approx(sref, rel=1e-6)
+    assert float(sh[1]) == pytest.approx(srref, rel=1e-5)
     got = from_cl(x0, shape)
-    assert np.all(np.abs(got[:3] - ref) <= U_BF16 * np.abs(ref) + 1e-6)
-    assert np.all(got[3:] == 0.0)
+    assert np.all(np.abs(got[:4] - ref) <= U_BF16 * np.abs(ref) + 1e-5)
+    assert np.all(got[4:] == 0.0)
 
 
 def test_head_loss_and_head_backward():
@@ -357,16 +364,16 @@ def test_network_forward_and_gradients_match_oracle():
     net, (b, bx, by, bz, pp, target), used, shape = _net_and_inputs()
     net.pack(b, bx, by, bz, pp)
     net.forward()
-    x0 = from_cl(net.a["x0"], shape)[:3]
+    x0 = from_cl(net.a["x0"], shape)[:4]
     out_ref, cache = O.forward(used, x0)
     out = net.out.cpu().numpy().astype(np.float64).reshape(shape)
     fwd = np.linalg.norm(out - out_ref) / np.linalg.norm(out_ref)
     assert fwd <= 3e-2, fwd
     net.loss(target, pp)
-    s = float(net.s.item())
-    # the oracle's loss gradient at the oracle's own prediction, in units of s
-    pq = pp.cpu().numpy().astype(np.float64).reshape(shape) / s
-    _, gref = O.loss_and_grad_out(out_ref + pq, target.cpu().numpy().astype(np.float64).reshape(shape) / s)
+    s_r = float(net.s[1].item())
+    # the oracle's loss gradient at the oracle's own prediction, in units of s_r
+    pq = pp.cpu().numpy().astype(np.float64).reshape(shape) / s_r
+    _, gref = O.loss_and_grad_out(out_ref + pq, target.cpu().numpy().astype(np.float64).reshape(shape) / s_r)
     net.backward()
     grads = net.gradients()
     ref = O.backward(used, cache, gref)

@@ -63,7 +63,7 @@ def test_network_gradient_finite_differences():
     for k in params:
         if k.endswith(".b"):
             params[k] = rng.standard_normal(params[k].shape) * 0.1
-    x0 = rng.standard_normal((3, 8, 8, 8))
+    x0 = rng.standard_normal((4, 8, 8, 8))
     pt = rng.standard_normal((8, 8, 8))
 
     def f(p):
@@ -99,28 +99,33 @@ def test_adam_first_step_closed_form():
 
 
 def test_predict_increment_map():
-    """p0 = s * net + p_prev: a zeroed network returns p_prev exactly, and the
-    parameter gradient of loss(p0) is backward(s * d loss / d p0), checked by
-    central differences on one weight tensor."""
+    """p0 = p_prev + s_r * net: a zeroed network returns p_prev exactly, the
+    scales are the RMS values, and the parameter gradient of loss(p0) is
+    backward(s_r * d loss / d p0), checked by central differences on one
+    weight tensor."""
     rng = np.random.default_rng(6)
     shape = (8, 8, 8)
     b = rng.standard_normal(shape)
     bm = rng.uniform(0, 1, shape)
     pp = rng.standard_normal(shape)
+    r = 0.01 * rng.standard_normal(shape)
     pt = pp + 0.3 * rng.standard_normal(shape)
     params = W.init_params(7)
     zero = {k: np.zeros_like(v) for k, v in params.items()}
-    p0, _, s = W.predict(zero, b, bm, pp)
-    assert np.array_equal(p0, pp) and s == pytest.approx(np.sqrt(np.mean(b * b)))
-    p0, cache, s = W.predict(params, b, bm, pp)
+    p0, _, s_r = W.predict(zero, b, bm, pp, r)
+    assert np.array_equal(p0, pp) and s_r == pytest.approx(np.sqrt(np.mean(r * r)))
+    x0, s, _ = W.features(b, bm, pp, r)
+    assert s == pytest.approx(np.sqrt(np.mean(b * b)))
+    np.testing.assert_allclose(x0[3] * s_r, r)
+    p0, cache, s_r = W.predict(params, b, bm, pp, r)
     _, g = W.loss_and_grad_out(p0, pt)
-    grads = W.backward(params, cache, s * g)
+    grads = W.backward(params, cache, s_r * g)
     d = rng.standard_normal(params["d1a.w"].shape)
 
     def f(w):
         q = dict(params)
         q["d1a.w"] = w
-        return W.loss_and_grad_out(W.predict(q, b, bm, pp)[0], pt)[0]
+        return W.loss_and_grad_out(W.predict(q, b, bm, pp, r)[0], pt)[0]
     errs = []
     for eps in (1e-7, 3e-8):
         fd = (f(params["d1a.w"] + eps * d) - f(params["d1a.w"] - eps * d)) / (2 * eps)

@@ -309,12 +309,15 @@ def warmstart_bench(args):
             steps += 1
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    losses = []
+    losses, losses_prev = [], []
     for b32, prev32, p32 in samples[:: max(1, len(samples) // 32)]:
         net.pack(b32, *coef, prev32)
         net.forward()
         net.loss(p32, prev32)
         losses.append(float(net.loss_dev.item()))
+        net.out.zero_()                                   # the previous-step guess itself
+        net.loss(p32, prev32)
+        losses_prev.append(float(net.loss_dev.item()))
 
     # forward throughput (tensor-core contraction) on one evaluation input
     b32 = f32(eval_rhs[0])
@@ -340,6 +343,12 @@ def warmstart_bench(args):
     # evaluation: zero, previous-step and learned initial guesses
     rec = {"zero": ([], []), "previous": ([], []), "net": ([], [])}
     infer_ms = []
+    r0 = {"previous": [], "net": []}                      # initial relative residuals
+    shp = (nz, ny, nx)
+
+    def rel_res(b32, guess32):
+        rr = G.op_residual_norm(*(c.view(shp) for c in coef), b32.view(shp), guess32.view(shp))
+        return float(np.sqrt(rr)) / float(torch.linalg.vector_norm(b32.double()).item())
     zero64 = torch.zeros(cells, dtype=torch.float64, device=dev)
     prev64, _, _ = solve(f32(eval_rhs[0]).double(), zero64)
     for b in eval_rhs[1:]:
@@ -356,6 +365,8 @@ def warmstart_bench(args):
         torch.cuda.synchronize()
         ti = ev0.elapsed_time(ev1)
         _, cn, tn = solve(b64, g64)
+        r0["previous"].append(rel_res(b32, prev32))
+        r0["net"].append(rel_res(b32, guess))
         for k, c, t in (("zero", cz, tz), ("previous", cp, tp), ("net", cn, tn + ti)):
             rec[k][0].append(c)
             rec[k][1].append(t)
@@ -370,11 +381,13 @@ def warmstart_bench(args):
             "cycles_mean": {k: mean(v[0]) for k, v in rec.items()},
             "solve_ms_mean": {k: mean(v[1]) for k, v in rec.items()},
             "net_infer_ms_mean": mean(infer_ms),
+            "initial_rel_residual_geomean": {k: float(np.exp(np.mean(np.log(v)))) for k, v in r0.items()},
             "cycles_hist": {k: {str(c): int(n) for c, n in zip(*np.unique(v[0], return_counts=True))}
                             for k, v in rec.items()},
             "train": {"seeds": train_seeds, "frames_per_seed": args.train_frames, "samples": len(samples),
                       "epochs": args.epochs, "steps": steps, "lr": args.lr, "seconds": train_s,
-                      "loss_mean_after": mean(losses), "ms_per_step": train_ms},
+                      "loss_mean_after": mean(losses), "loss_mean_previous_guess": mean(losses_prev),
+                      "ms_per_step": train_ms},
             "forward": {"ms": fwd_ms, "gflop": gflop, "tflops": gflop / fwd_ms,
                         "train_step_tflops": 3 * gflop / train_ms},
             "setup_seconds": {"sources_cpu": gen_s, "training_targets_gpu": targets_s}}

@@ -70,10 +70,10 @@ int gmg_net_up2_backward(int D, int H, int W, const gmg_bf16* gy, int cgy, int g
 
 /*
  * Network input, 16 channels: (b / s, mean of the six face coefficients,
- * p_prev / s, r / s_r, 0, ...) with r = b - A p_prev the residual of the
- * previous pressure (difference form of the solver's operator, FP32),
- * s = RMS of b and s_r = RMS of r (1 where zero), written to s_out[0] and
- * s_out[1] (device float[2]).  b, p_prev (may be NULL: zero, then r = b), bx,
+ * p_prev / s, r / s, 0, ...) with r = b - A p_prev the residual of the
+ * previous pressure (difference form of the solver's operator, FP32) and
+ * s = RMS of b, written to s_out[0]; s_out[1] receives RMS of r (device
+ * float[2]; each 1 where zero).  b, p_prev (may be NULL: zero, then r = b), bx,
  * by, bz are FP32 [D][H][W] arrays in the solver's layout; periodic: host array
  * of 3 flags for (x, y, z) (NULL: walls).  Uses the scratch `red` (device
  * double[2]).
@@ -89,7 +89,7 @@ int gmg_net_head(int D, int H, int W, const gmg_bf16* h, int ch, const float* w,
 /*
  * Loss of the prediction q = out + p_prev / s against t = target / s:
  * |(q - mean q) - (t - mean t)|^2 / |t - mean t|^2 (target and p_prev FP32,
- * p_prev may be NULL: zero; s device float, the output scale: s_r of
+ * p_prev may be NULL: zero; s device float, the output scale: s_out[0] of
  * gmg_net_pack_input).  Writes the loss to *loss (device double) and
  * d(loss)/d(out) to gout.  Uses scratch red (device double[4]).
  */
@@ -101,7 +101,7 @@ int gmg_net_head_backward(int D, int H, int W, const float* gout, const gmg_bf16
                           gmg_bf16* gh, float* dw, float* db, void* stream);
 
 /* p0 = s * out + p_prev (the prediction: the network gives the increment over
- * the previous pressure in units of the output scale s, the s_r of
+ * the previous pressure in units of the output scale s, s_out[0] of
  * gmg_net_pack_input; p_prev may be NULL: zero). */
 int gmg_net_unscale(long long n, const float* out, const float* s, const float* p_prev, float* p0, void* stream);
 

@@ -16,10 +16,10 @@ definitions, in FP64, on arrays laid out [C][D][H][W] (z, y, x):
     relu:     max(v, 0)
     pool:     mean of each 2 x 2 x 2 block
     upsample: each value copied to its 2 x 2 x 2 block
-    input:    x0 = (b / s, mean face coefficient, p_prev / s, r / s_r) with
-              r = b - A p_prev, s = RMS(b), s_r = RMS(r)
-    output:   p0 = p_prev + s_r * net(x0)  (the net predicts the increment
-              over the previous pressure, which solves A dp = r, in units of s_r)
+    input:    x0 = (b / s, mean face coefficient, p_prev / s, r / s) with
+              r = b - A p_prev and s = RMS(b)
+    output:   p0 = p_prev + s * net(x0)  (the net predicts the increment over
+              the previous pressure, which solves A dp = r, in units of s)
     loss:     |(p0 - mean p0) - (p* - mean p*)|^2 / |p* - mean p*|^2
 
 Backward passes are the adjoints of these maps, written out term by term.
@@ -199,18 +199,14 @@ def adam_step(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def predict(params, b, beta_mean, p_prev, r):
-    """Initial guess p0 = p_prev + s_r * net(x0), with the network's cache and s_r."""
-    x0, s, s_r = features(b, beta_mean, p_prev, r)
+    """Initial guess p0 = p_prev + s * net(x0), with the network's cache and s."""
+    x0, s = features(b, beta_mean, p_prev, r)
     out, cache = forward(params, x0)
-    return p_prev + s_r * out, cache, s_r
-
-
-def _rms(a):
-    v = float(np.sqrt(np.mean(a * a)))
-    return v if v > 0 else 1.0
+    return p_prev + s * out, cache, s
 
 
 def features(b, beta_mean, p_prev, r):
-    """Network input [4][D][H][W] and the scales s = RMS(b), s_r = RMS(r)."""
-    s, s_r = _rms(b), _rms(r)
-    return np.stack([b / s, beta_mean, p_prev / s, r / s_r]), s, s_r
+    """Network input [4][D][H][W] and the scale s = RMS(b) (1 if b = 0)."""
+    s = float(np.sqrt(np.mean(b * b)))
+    s = s if s > 0 else 1.0
+    return np.stack([b / s, beta_mean, p_prev / s, r / s]), s

@@ -14,6 +14,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <initializer_list>
+
+namespace gmgnet {
+// tcgen05 convolution (gmg_net_tc.cu): 0 done, 1 shapes not supported, 2 CUDA error
+int conv3_tc(int D, int H, int W, const void* x, int cx, int ci, const void* w, const float* bias, int co, int relu,
+             void* y, int cy, int yoff, cudaStream_t s);
+}
 
 namespace {
 
@@ -335,6 +342,139 @@ __global__ void k_up2_backward(int d, int h, int w, const bf16* gy, int cgy, int
     }
 }
 
+// ---- the same elementwise kernels on 8-channel chunks (16-byte loads and stores),
+// for channel counts, strides and offsets that are multiples of 8; identical sums
+
+__device__ __forceinline__ void unpack8(const uint4& v, float* f)
+{
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 pack8(const float* f)
+{
+    uint4 v;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    return v;
+}
+
+__device__ __forceinline__ const uint4& ld8(const bf16* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ uint4& st8(bf16* p) { return *reinterpret_cast<uint4*>(p); }
+
+__global__ void k_relu_backward_v(int64_t ncell, bf16* g, int cg, const bf16* y, int cy, int C)
+{
+    const int nq = C / 8;
+    const int64_t n = ncell * nq;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = e / nq;
+        const int q = (int)(e - cell * nq);
+        float gv[8], yv[8];
+        unpack8(ld8(g + cell * cg + 8 * q), gv);
+        unpack8(ld8(y + cell * cy + 8 * q), yv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (!(yv[j] > 0.f)) gv[j] = 0.f;
+        st8(g + cell * cg + 8 * q) = pack8(gv);
+    }
+}
+
+__global__ void k_pool2_v(int d, int h, int w, const bf16* x, int cx, int C, bf16* y, int cy, int yoff)
+{
+    const int nq = C / 8;
+    const int64_t n = (int64_t)d * h * w * nq;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = e / nq;
+        const int q = (int)(e - cell * nq);
+        const int X = (int)(cell % w), Y = (int)((cell / w) % h), Z = (int)(cell / ((int64_t)w * h));
+        float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < 8; ++k) {
+            const int fx = 2 * X + (k & 1), fy = 2 * Y + ((k >> 1) & 1), fz = 2 * Z + (k >> 2);
+            float v[8];
+            unpack8(ld8(x + ((int64_t)(fz * 2 * h + fy) * 2 * w + fx) * cx + 8 * q), v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sum[j] += v[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sum[j] *= 0.125f;
+        st8(y + cell * cy + yoff + 8 * q) = pack8(sum);
+    }
+}
+
+__global__ void k_pool2_backward_v(int D, int H, int W, const bf16* gy, int cgy, int C, bf16* gx, int cgx,
+                                   const bf16* add, int cadd, int addoff)
+{
+    const int nq = C / 8;
+    const int64_t n = (int64_t)D * H * W * nq;
+    const int h = H / 2, w = W / 2;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = e / nq;
+        const int q = (int)(e - cell * nq);
+        const int xx = (int)(cell % W), yy = (int)((cell / W) % H), zz = (int)(cell / ((int64_t)W * H));
+        float v[8];
+        unpack8(ld8(gy + ((int64_t)((zz / 2) * h + yy / 2) * w + xx / 2) * cgy + 8 * q), v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] *= 0.125f;
+        if (add) {
+            float a[8];
+            unpack8(ld8(add + cell * cadd + addoff + 8 * q), a);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] += a[j];
+        }
+        st8(gx + cell * cgx + 8 * q) = pack8(v);
+    }
+}
+
+__global__ void k_up2_v(int d, int h, int w, const bf16* x, int cx, int C, bf16* y, int cy, int yoff)
+{
+    const int nq = C / 8;
+    const int64_t n = (int64_t)8 * d * h * w * nq;
+    const int H = 2 * h, W = 2 * w;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = e / nq;
+        const int q = (int)(e - cell * nq);
+        const int xx = (int)(cell % W), yy = (int)((cell / W) % H), zz = (int)(cell / ((int64_t)W * H));
+        st8(y + cell * cy + yoff + 8 * q) = ld8(x + ((int64_t)((zz / 2) * h + yy / 2) * w + xx / 2) * cx + 8 * q);
+    }
+}
+
+__global__ void k_up2_backward_v(int d, int h, int w, const bf16* gy, int cgy, int goff, int C, bf16* gx, int cgx)
+{
+    const int nq = C / 8;
+    const int64_t n = (int64_t)d * h * w * nq;
+    const int H = 2 * h, W = 2 * w;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cell = e / nq;
+        const int q = (int)(e - cell * nq);
+        const int X = (int)(cell % w), Y = (int)((cell / w) % h), Z = (int)(cell / ((int64_t)w * h));
+        float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < 8; ++k) {
+            const int fx = 2 * X + (k & 1), fy = 2 * Y + ((k >> 1) & 1), fz = 2 * Z + (k >> 2);
+            float v[8];
+            unpack8(ld8(gy + ((int64_t)(fz * H + fy) * W + fx) * cgy + goff + 8 * q), v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sum[j] += v[j];
+        }
+        st8(gx + cell * cgx + 8 * q) = pack8(sum);
+    }
+}
+
+// 16-byte chunks apply: channel counts, strides and offsets multiples of 8, aligned pointers
+bool chunked(std::initializer_list<long long> counts, std::initializer_list<const void*> ptrs)
+{
+    for (long long c : counts)
+        if (c % 8) return false;
+    for (const void* p : ptrs)
+        if (p && ((uintptr_t)p & 15)) return false;
+    return true;
+}
+
 int grid_of(int64_t n, int threads = 256)
 {
     int64_t b = (n + threads - 1) / threads;
@@ -446,14 +586,14 @@ __global__ void k_pack_input(int D, int H, int W, const float* b, const float* p
 {
     const int per[3] = {px, py, pz};
     const int64_t n = (int64_t)D * H * W;
-    const float inv = 1.f / s[0], invr = 1.f / s[1];
+    const float inv = 1.f / s[0];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const PackCell c = pack_cell(D, H, W, b, pp, bx, by, bz, per, i);
         bf16* o = x0 + i * 16;
         o[0] = __float2bfloat16_rn(c.b * inv);
         o[1] = __float2bfloat16_rn(c.mean);
         o[2] = __float2bfloat16_rn(pp ? pp[i] * inv : 0.f);
-        o[3] = __float2bfloat16_rn(c.r * invr);
+        o[3] = __float2bfloat16_rn(c.r * inv);
         for (int k = 4; k < 16; ++k) o[k] = __float2bfloat16_rn(0.f);
     }
 }
@@ -585,9 +725,11 @@ int gmg_net_conv3(int D, int H, int W, const gmg_bf16* x, int cx, int ci, const 
     if (D < 1 || H < 1 || W < 1 || !x || !w || !y || ci < 16 || ci % 16 || co < 16 || co % 16 || co > 96 ||
         cx < ci || cx % 8 || cy % 2 || yoff % 2 || cy < yoff + co)
         return 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int tc = gmgnet::conv3_tc(D, H, W, x, cx, ci, w, bias, co, relu, y, cy, yoff, s);
+    if (tc != 1) return tc;
     ConvArgs a{D, H, W, reinterpret_cast<const bf16*>(x), cx, ci, reinterpret_cast<const bf16*>(w), bias, relu,
                reinterpret_cast<bf16*>(y), cy, yoff};
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     switch (co / 8) {
     case 2: return status(launch_conv3<2>(a, s));
     case 4: return status(launch_conv3<4>(a, s));
@@ -625,6 +767,11 @@ int gmg_net_relu_backward(int D, int H, int W, gmg_bf16* g, int cg, const gmg_bf
 {
     if (!g || !y || C < 1) return 1;
     const int64_t n = (int64_t)D * H * W;
+    if (chunked({cg, cy, C}, {g, y})) {
+        k_relu_backward_v<<<grid_of(n * C / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            n, reinterpret_cast<bf16*>(g), cg, reinterpret_cast<const bf16*>(y), cy, C);
+        return status(cudaGetLastError());
+    }
     k_relu_backward<<<grid_of(n * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         n, reinterpret_cast<bf16*>(g), cg, reinterpret_cast<const bf16*>(y), cy, C);
     return status(cudaGetLastError());
@@ -633,6 +780,11 @@ int gmg_net_relu_backward(int D, int H, int W, gmg_bf16* g, int cg, const gmg_bf
 int gmg_net_pool2(int D, int H, int W, const gmg_bf16* x, int cx, int C, gmg_bf16* y, int cy, int yoff, void* stream)
 {
     if (!x || !y || D % 2 || H % 2 || W % 2 || C < 1) return 1;
+    if (chunked({cx, cy, yoff, C}, {x, y})) {
+        k_pool2_v<<<grid_of((int64_t)D * H * W * C / 64), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            D / 2, H / 2, W / 2, reinterpret_cast<const bf16*>(x), cx, C, reinterpret_cast<bf16*>(y), cy, yoff);
+        return status(cudaGetLastError());
+    }
     k_pool2<<<grid_of((int64_t)D * H * W * C / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         D / 2, H / 2, W / 2, reinterpret_cast<const bf16*>(x), cx, C, reinterpret_cast<bf16*>(y), cy, yoff);
     return status(cudaGetLastError());
@@ -642,6 +794,12 @@ int gmg_net_pool2_backward(int D, int H, int W, const gmg_bf16* gy, int cgy, int
                            const gmg_bf16* add, int cadd, int addoff, void* stream)
 {
     if (!gy || !gx || D % 2 || H % 2 || W % 2 || C < 1) return 1;
+    if (chunked({cgy, cgx, C, add ? cadd : 0, add ? addoff : 0}, {gy, gx, add})) {
+        k_pool2_backward_v<<<grid_of((int64_t)D * H * W * C / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            D, H, W, reinterpret_cast<const bf16*>(gy), cgy, C, reinterpret_cast<bf16*>(gx), cgx,
+            reinterpret_cast<const bf16*>(add), cadd, addoff);
+        return status(cudaGetLastError());
+    }
     k_pool2_backward<<<grid_of((int64_t)D * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         D, H, W, reinterpret_cast<const bf16*>(gy), cgy, C, reinterpret_cast<bf16*>(gx), cgx,
         reinterpret_cast<const bf16*>(add), cadd, addoff);
@@ -651,6 +809,11 @@ int gmg_net_pool2_backward(int D, int H, int W, const gmg_bf16* gy, int cgy, int
 int gmg_net_up2(int D, int H, int W, const gmg_bf16* x, int cx, int C, gmg_bf16* y, int cy, int yoff, void* stream)
 {
     if (!x || !y || C < 1) return 1;
+    if (chunked({cx, cy, yoff, C}, {x, y})) {
+        k_up2_v<<<grid_of((int64_t)D * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            D, H, W, reinterpret_cast<const bf16*>(x), cx, C, reinterpret_cast<bf16*>(y), cy, yoff);
+        return status(cudaGetLastError());
+    }
     k_up2<<<grid_of((int64_t)8 * D * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         D, H, W, reinterpret_cast<const bf16*>(x), cx, C, reinterpret_cast<bf16*>(y), cy, yoff);
     return status(cudaGetLastError());
@@ -660,6 +823,11 @@ int gmg_net_up2_backward(int D, int H, int W, const gmg_bf16* gy, int cgy, int g
                          void* stream)
 {
     if (!gy || !gx || C < 1) return 1;
+    if (chunked({cgy, goff, cgx, C}, {gy, gx})) {
+        k_up2_backward_v<<<grid_of((int64_t)D * H * W * C / 8), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            D, H, W, reinterpret_cast<const bf16*>(gy), cgy, goff, C, reinterpret_cast<bf16*>(gx), cgx);
+        return status(cudaGetLastError());
+    }
     k_up2_backward<<<grid_of((int64_t)D * H * W * C), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         D, H, W, reinterpret_cast<const bf16*>(gy), cgy, goff, C, reinterpret_cast<bf16*>(gx), cgx);
     return status(cudaGetLastError());

@@ -1,10 +1,9 @@
 """Learned warm start: a small 3D U-Net that predicts a solve's initial guess.
 
 Inputs per cell: sigma / s, the mean of the cell's six face coefficients, the
-previous pressure / s and its residual r = sigma - A p_prev over s_r (s, s_r
-the RMS values of sigma and r); output p0 = p_prev + s_r * net(...), so the
-network predicts the increment over the previous pressure (the solution of
-A dp = r).  The
+previous pressure / s and its residual r = sigma - A p_prev over s (s = RMS of
+sigma); output p0 = p_prev + s * net(...), so the network predicts the
+increment over the previous pressure (the solution of A dp = r).  The
 solver then iterates from p0 to its usual tolerance, so a poor prediction
 costs V-cycles but never accuracy.  Architecture (3x3x3 convolutions with
 zero padding, ReLU after each): 16-16 | pool | 32-32 | pool | 64-64 | up,
@@ -100,8 +99,9 @@ class WarmStartNet:
             p.w.copy_(torch.from_numpy(w.ravel()))
             self.params[name] = p
             self.bias[name] = _Param(torch, dev, co)
+        # the head starts at zero: an untrained net returns the previous pressure,
+        # and training only adds the learned increment
         self.head = _Param(torch, dev, 16)
-        self.head.w.copy_(torch.from_numpy((rng.standard_normal(16) / 4.0).astype(np.float32)))
         self.head_b = _Param(torch, dev, 1)
         # BF16 copies: an Adam step with a zero gradient and lr 0 leaves w unchanged
         for name, _, co, _ in LAYERS:
@@ -169,7 +169,7 @@ class WarmStartNet:
         """Predicted initial guess p0 (FP32 device tensor of the grid's cells)."""
         self.pack(b, bx, by, bz, p_prev)
         self.forward()
-        G.net_call("gmg_net_unscale", self.ncell[0], self._p(self.out), self._p(self.s, 1),
+        G.net_call("gmg_net_unscale", self.ncell[0], self._p(self.out), self._p(self.s),
                    self._p(p_prev) if p_prev is not None else None, self._p(self.p0), self._st())
         return self.p0
 
@@ -247,7 +247,7 @@ class WarmStartNet:
         """Loss of the prediction against the converged pressure (d loss / d out in self.gout)."""
         D, H, W = self._dims(0)
         G.net_call("gmg_net_loss", D, H, W, self._p(self.out), self._p(p_target),
-                   self._p(p_prev) if p_prev is not None else None, self._p(self.s, 1),
+                   self._p(p_prev) if p_prev is not None else None, self._p(self.s),
                    self._p(self.gout), self._p(self.loss_dev), self._p(self.red), self._st())
 
     def step(self):

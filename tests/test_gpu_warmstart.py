@@ -247,10 +247,10 @@ def test_pack_input(periodic, with_prev, oracle):
     f64 = [a.astype(np.float64) for a in (b, pp, bx, by, bz)]
     bm = beta_mean(*f64[2:], periodic)
     r = f64[0] - oracle.apply_A(f64[1], *f64[2:], periodic=periodic)
-    ref, sref, srref = O.features(f64[0], bm, f64[1], r)
+    ref, sref = O.features(f64[0], bm, f64[1], r)
     sh = s.cpu().numpy()
     assert float(sh[0]) == pytest.approx(sref, rel=1e-6)
-    assert float(sh[1]) == pytest.approx(srref, rel=1e-5)
+    assert float(sh[1]) == pytest.approx(float(np.sqrt(np.mean(r * r))), rel=1e-5)
     got = from_cl(x0, shape)
     assert np.all(np.abs(got[:4] - ref) <= U_BF16 * np.abs(ref) + 1e-5)
     assert np.all(got[4:] == 0.0)
@@ -370,10 +370,10 @@ def test_network_forward_and_gradients_match_oracle():
     fwd = np.linalg.norm(out - out_ref) / np.linalg.norm(out_ref)
     assert fwd <= 3e-2, fwd
     net.loss(target, pp)
-    s_r = float(net.s[1].item())
-    # the oracle's loss gradient at the oracle's own prediction, in units of s_r
-    pq = pp.cpu().numpy().astype(np.float64).reshape(shape) / s_r
-    _, gref = O.loss_and_grad_out(out_ref + pq, target.cpu().numpy().astype(np.float64).reshape(shape) / s_r)
+    s = float(net.s[0].item())
+    # the oracle's loss gradient at the oracle's own prediction, in units of s
+    pq = pp.cpu().numpy().astype(np.float64).reshape(shape) / s
+    _, gref = O.loss_and_grad_out(out_ref + pq, target.cpu().numpy().astype(np.float64).reshape(shape) / s)
     net.backward()
     grads = net.gradients()
     ref = O.backward(used, cache, gref)

@@ -99,10 +99,9 @@ def test_adam_first_step_closed_form():
 
 
 def test_predict_increment_map():
-    """p0 = p_prev + s_r * net: a zeroed network returns p_prev exactly, the
-    scales are the RMS values, and the parameter gradient of loss(p0) is
-    backward(s_r * d loss / d p0), checked by central differences on one
-    weight tensor."""
+    """p0 = p_prev + s * net: a zeroed network returns p_prev exactly, s is the
+    RMS of b, and the parameter gradient of loss(p0) is backward(s * d loss /
+    d p0), checked by central differences on one weight tensor."""
     rng = np.random.default_rng(6)
     shape = (8, 8, 8)
     b = rng.standard_normal(shape)
@@ -112,14 +111,14 @@ def test_predict_increment_map():
     pt = pp + 0.3 * rng.standard_normal(shape)
     params = W.init_params(7)
     zero = {k: np.zeros_like(v) for k, v in params.items()}
-    p0, _, s_r = W.predict(zero, b, bm, pp, r)
-    assert np.array_equal(p0, pp) and s_r == pytest.approx(np.sqrt(np.mean(r * r)))
-    x0, s, _ = W.features(b, bm, pp, r)
-    assert s == pytest.approx(np.sqrt(np.mean(b * b)))
-    np.testing.assert_allclose(x0[3] * s_r, r)
-    p0, cache, s_r = W.predict(params, b, bm, pp, r)
+    p0, _, s = W.predict(zero, b, bm, pp, r)
+    assert np.array_equal(p0, pp) and s == pytest.approx(np.sqrt(np.mean(b * b)))
+    x0, s = W.features(b, bm, pp, r)
+    np.testing.assert_allclose(x0[3] * s, r)
+    np.testing.assert_allclose(x0[2] * s, pp)
+    p0, cache, s = W.predict(params, b, bm, pp, r)
     _, g = W.loss_and_grad_out(p0, pt)
-    grads = W.backward(params, cache, s_r * g)
+    grads = W.backward(params, cache, s * g)
     d = rng.standard_normal(params["d1a.w"].shape)
 
     def f(w):

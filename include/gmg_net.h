@@ -96,6 +96,19 @@ int gmg_net_head(int D, int H, int W, const gmg_bf16* h, int ch, const float* w,
 int gmg_net_loss(int D, int H, int W, const float* out, const float* target, const float* p_prev, const float* s,
                  float* gout, double* loss, double* red, void* stream);
 
+/*
+ * Residual loss of the prediction p0 = p_prev + s out (s the output scale,
+ * device float; p_prev may be NULL: zero) against the source b:
+ * L = |b - A p0|^2 / |b|^2 with A the solver's operator (difference form,
+ * FP32; walls or periodic axes as in gmg_net_pack_input; periodic is a host
+ * array or NULL), written to *loss (device double), and
+ * d(L)/d(out) = s * (-2 A (b - A p0) / |b|^2) to gout (A is symmetric).
+ * work: device scratch of 2 D H W floats; red: device double[2].
+ */
+int gmg_net_residual_loss(int D, int H, int W, const float* out, const float* p_prev, const float* s, const float* b,
+                          const float* bx, const float* by, const float* bz, const int* periodic, float* work,
+                          float* gout, double* loss, double* red, void* stream);
+
 /* Head backward: gh[c] = w[c] gout, dw[c] += sum gout h[c], db[0] += sum gout. */
 int gmg_net_head_backward(int D, int H, int W, const float* gout, const gmg_bf16* h, int ch, const float* w,
                           gmg_bf16* gh, float* dw, float* db, void* stream);

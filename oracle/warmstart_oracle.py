@@ -20,7 +20,9 @@ definitions, in FP64, on arrays laid out [C][D][H][W] (z, y, x):
               r = b - A p_prev and s = RMS(b)
     output:   p0 = p_prev + s * net(x0)  (the net predicts the increment over
               the previous pressure, which solves A dp = r, in units of s)
-    loss:     |(p0 - mean p0) - (p* - mean p*)|^2 / |p* - mean p*|^2
+    loss:     |(p0 - mean p0) - (p* - mean p*)|^2 / |p* - mean p*|^2, or the
+              squared relative residual |b - A p0|^2 / |b|^2 (the quantity the
+              solver's stopping test measures)
 
 Backward passes are the adjoints of these maps, written out term by term.
 """
@@ -146,6 +148,14 @@ def loss_and_grad_out(p0, ptarget):
     loss = float(np.sum(diff * diff)) / den
     g = 2.0 * diff / den
     return loss, g - g.mean()
+
+
+def residual_loss_and_grad(p0, b, apply_A):
+    """|b - A p0|^2 / |b|^2 and its gradient -2 A^T (b - A p0) / |b|^2 w.r.t. p0.
+    apply_A is the (symmetric) operator; A^T = A."""
+    r = b - apply_A(p0)
+    den = float(np.sum(b * b))
+    return float(np.sum(r * r)) / den, -2.0 * apply_A(r) / den
 
 
 def backward(params, cache, gout):

@@ -111,6 +111,7 @@ def _net_signatures(L):
         "gmg_net_pack_input": [c_int, c_int, c_int, vp, vp, vp, vp, vp, ip, vp, vp, vp, vp],
         "gmg_net_head": [c_int, c_int, c_int, vp, c_int, vp, vp, vp, vp],
         "gmg_net_loss": [c_int, c_int, c_int, vp, vp, vp, vp, vp, vp, vp, vp],
+        "gmg_net_residual_loss": [c_int, c_int, c_int, vp, vp, vp, vp, vp, vp, vp, ip, vp, vp, vp, vp, vp],
         "gmg_net_head_backward": [c_int, c_int, c_int, vp, vp, c_int, vp, vp, vp, vp, vp],
         "gmg_net_unscale": [c_ll, vp, vp, vp, vp, vp],
         "gmg_net_adam": [c_ll, vp, vp, vp, vp, c_int, c_float, c_float, c_float, c_float, vp, vp, c_int, c_int, vp],

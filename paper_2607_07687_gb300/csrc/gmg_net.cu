@@ -598,6 +598,64 @@ __global__ void k_pack_input(int D, int H, int W, const float* b, const float* p
     }
 }
 
+// flux sum_f beta_f (v_nb - v_c) of the solver's operator at cell i (difference form)
+__device__ __forceinline__ float flux_of(const float* v, int D, int H, int W, const float* bx, const float* by,
+                                         const float* bz, const int* per, int64_t i)
+{
+    const int x = (int)(i % W), y = (int)((i / W) % H), z = (int)(i / ((int64_t)W * H));
+    const float c = v[i];
+    return ((face_lo(bx, D, H, W, per, 0, x, y, z) * (p_at(v, D, H, W, per, x - 1, y, z) - c) +
+             face_lo(bx, D, H, W, per, 0, x + 1, y, z) * (p_at(v, D, H, W, per, x + 1, y, z) - c)) +
+            (face_lo(by, D, H, W, per, 1, x, y, z) * (p_at(v, D, H, W, per, x, y - 1, z) - c) +
+             face_lo(by, D, H, W, per, 1, x, y + 1, z) * (p_at(v, D, H, W, per, x, y + 1, z) - c))) +
+           (face_lo(bz, D, H, W, per, 2, x, y, z) * (p_at(v, D, H, W, per, x, y, z - 1) - c) +
+            face_lo(bz, D, H, W, per, 2, x, y, z + 1) * (p_at(v, D, H, W, per, x, y, z + 1) - c));
+}
+
+// p0 = p_prev + s out
+__global__ void k_rloss_p0(int64_t n, const float* out, const float* pp, const float* s, float* p0)
+{
+    const float sc = *s;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p0[i] = pp ? fmaf(sc, out[i], pp[i]) : sc * out[i];
+}
+
+// r = b - A p0; red[0] += sum r^2, red[1] += sum b^2
+__global__ void k_rloss_r(int D, int H, int W, const float* p0, const float* b, const float* bx, const float* by,
+                          const float* bz, int px, int py, int pz, float* r, double* red)
+{
+    const int per[3] = {px, py, pz};
+    const int64_t n = (int64_t)D * H * W;
+    double sr = 0.0, sb = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = b[i] - flux_of(p0, D, H, W, bx, by, bz, per, i);
+        r[i] = v;
+        sr += (double)v * v;
+        sb += (double)b[i] * b[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(red, sr);
+        atomicAdd(red + 1, sb);
+    }
+}
+
+// gout = s (-2 A r / |b|^2); loss = |r|^2 / |b|^2
+__global__ void k_rloss_grad(int D, int H, int W, const float* r, const float* bx, const float* by, const float* bz,
+                             int px, int py, int pz, const float* s, const double* red, float* gout, double* loss)
+{
+    const int per[3] = {px, py, pz};
+    const int64_t n = (int64_t)D * H * W;
+    const double den = red[1] > 0.0 ? red[1] : 1.0;
+    const float scale = (float)(-2.0 * (double)*s / den);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *loss = red[0] / den;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        gout[i] = scale * flux_of(r, D, H, W, bx, by, bz, per, i);
+}
+
 __global__ void k_head(int64_t n, const bf16* h, int ch, const float* w, const float* b, float* out)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -871,6 +929,25 @@ int gmg_net_loss(int D, int H, int W, const float* out, const float* target, con
     k_loss_sums<<<grid_of(n), 256, 0, st>>>(n, out, target, p_prev, s, red, 0);
     k_loss_sums<<<grid_of(n), 256, 0, st>>>(n, out, target, p_prev, s, red, 1);
     k_loss_grad<<<grid_of(n), 256, 0, st>>>(n, out, target, p_prev, s, red, gout, loss);
+    return status(cudaGetLastError());
+}
+
+int gmg_net_residual_loss(int D, int H, int W, const float* out, const float* p_prev, const float* s, const float* b,
+                          const float* bx, const float* by, const float* bz, const int* periodic, float* work,
+                          float* gout, double* loss, double* red, void* stream)
+{
+    if (!out || !s || !b || !bx || !by || !bz || !work || !gout || !loss || !red) return 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = (int64_t)D * H * W;
+    const int px = periodic ? periodic[0] != 0 : 0, py = periodic ? periodic[1] != 0 : 0,
+              pz = periodic ? periodic[2] != 0 : 0;
+    cudaError_t e = cudaMemsetAsync(red, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return 2;
+    float* p0 = work;
+    float* r = work + n;
+    k_rloss_p0<<<grid_of(n), 256, 0, st>>>(n, out, p_prev, s, p0);
+    k_rloss_r<<<grid_of(n), 256, 0, st>>>(D, H, W, p0, b, bx, by, bz, px, py, pz, r, red);
+    k_rloss_grad<<<grid_of(n), 256, 0, st>>>(D, H, W, r, bx, by, bz, px, py, pz, s, red, gout, loss);
     return status(cudaGetLastError());
 }
 

@@ -50,7 +50,8 @@ class _Param:
 
 
 class WarmStartNet:
-    def __init__(self, dims, periodic=(False, False, False), seed: int = 0, lr: float = 1e-3, stream=None):
+    def __init__(self, dims, periodic=(False, False, False), seed: int = 0, lr: float = 1e-3, stream=None,
+                 loss: str = "mse"):
         import torch
         self.torch = torch
         nx, ny, nz = (int(d) for d in dims)
@@ -61,6 +62,9 @@ class WarmStartNet:
         self.dev = torch.device("cuda", torch.cuda.current_device())
         self.stream = G._stream(stream)
         self.lr = lr
+        if loss not in ("mse", "residual"):
+            raise ValueError("loss: 'mse' (against the converged pressure) or 'residual' (|b - A p0| / |b|)")
+        self.loss_kind = loss
         self.t = 0
         self.loss_history = []
         dev = self.dev
@@ -84,6 +88,7 @@ class WarmStartNet:
         self.s = torch.zeros(2, dtype=torch.float32, device=dev)   # RMS of sigma, RMS of the residual
         self.red = torch.zeros(4, dtype=torch.float64, device=dev)
         self.loss_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.work = torch.zeros(2 * self.ncell[0], dtype=torch.float32, device=dev) if loss == "residual" else None
 
         # parameters, initialised on the host (He normal, zero biases) and packed
         rng = np.random.default_rng(seed)
@@ -250,6 +255,17 @@ class WarmStartNet:
                    self._p(p_prev) if p_prev is not None else None, self._p(self.s),
                    self._p(self.gout), self._p(self.loss_dev), self._p(self.red), self._st())
 
+    def residual_loss(self, b, bx, by, bz, p_prev=None):
+        """Squared relative residual |b - A p0|^2 / |b|^2 of the prediction (d loss / d out in self.gout)."""
+        D, H, W = self._dims(0)
+        if self.work is None:
+            self.work = self.torch.zeros(2 * self.ncell[0], dtype=self.torch.float32, device=self.dev)
+        per = (ctypes.c_int * 3)(*[int(v) for v in self.periodic])
+        G.net_call("gmg_net_residual_loss", D, H, W, self._p(self.out),
+                   self._p(p_prev) if p_prev is not None else None, self._p(self.s), self._p(b), self._p(bx),
+                   self._p(by), self._p(bz), per, self._p(self.work), self._p(self.gout), self._p(self.loss_dev),
+                   self._p(self.red), self._st())
+
     def step(self):
         """One Adam update of every parameter."""
         self.t += 1
@@ -259,11 +275,14 @@ class WarmStartNet:
         self._adam(self.head, self.t, self.lr)
         self._adam(self.head_b, self.t, self.lr)
 
-    def train_step(self, b, bx, by, bz, p_prev, p_target) -> float:
-        """Forward, loss, backward and Adam on one (input, converged pressure) pair."""
+    def train_step(self, b, bx, by, bz, p_prev, p_target=None) -> float:
+        """Forward, loss, backward and Adam on one input (and its converged pressure for the MSE loss)."""
         self.pack(b, bx, by, bz, p_prev)
         self.forward()
-        self.loss(p_target, p_prev)
+        if self.loss_kind == "residual":
+            self.residual_loss(b, bx, by, bz, p_prev)
+        else:
+            self.loss(p_target, p_prev)
         self.backward()
         self.step()
         loss = float(self.loss_dev.item())

@@ -308,6 +308,37 @@ def test_head_loss_and_head_backward():
     assert float(db.item()) == pytest.approx(g64.sum(), abs=1e-5 * np.abs(g64).sum())
 
 
+@pytest.mark.parametrize("periodic", [(False, False, False), (True, True, False)])
+def test_residual_loss_kernel(periodic, oracle):
+    """Loss and gradient of the residual loss against the oracle (FP64 operator)
+    on the same FP32 inputs; r is O(b) here, so FP32 keeps ~1e-6 relative."""
+    import ctypes
+    torch = _torch()
+    rng = np.random.default_rng(13)
+    shape = (4, 6, 8)
+    n = int(np.prod(shape))
+    f = lambda a: a.astype(np.float32)
+    b, out, pp = f(rng.standard_normal(shape)), f(rng.standard_normal(shape)), f(rng.standard_normal(shape))
+    bx, by, bz = (f(rng.uniform(0.1, 1.0, shape)) for _ in range(3))
+    sc = np.float32(0.7)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to("cuda:0")
+    ts = [T(a) for a in (b, out, pp, bx, by, bz, np.array([sc]))]
+    work = torch.zeros(2 * n, dtype=torch.float32, device="cuda:0")
+    gout = torch.zeros(n, dtype=torch.float32, device="cuda:0")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    red = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+    per = (ctypes.c_int * 3)(*[int(v) for v in periodic])
+    call("gmg_net_residual_loss", *shape, ptr(ts[1]), ptr(ts[2]), ptr(ts[6]), ptr(ts[0]), ptr(ts[3]), ptr(ts[4]),
+         ptr(ts[5]), per, ptr(work), ptr(gout), ptr(loss), ptr(red), stream())
+    f64 = [a.astype(np.float64) for a in (b, out, pp, bx, by, bz)]
+    A = lambda v: oracle.apply_A(v, *f64[3:], periodic=periodic)
+    p0 = f64[2] + float(sc) * f64[1]
+    lref, gref = O.residual_loss_and_grad(p0, f64[0], A)
+    assert float(loss.item()) == pytest.approx(lref, rel=1e-5)
+    g = gout.cpu().numpy().astype(np.float64).reshape(shape)
+    np.testing.assert_allclose(g, float(sc) * gref, rtol=1e-4, atol=1e-5 * np.abs(gref).max())
+
+
 def test_adam_matches_oracle_and_packs():
     torch = _torch()
     rng = np.random.default_rng(12)

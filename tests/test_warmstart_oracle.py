@@ -130,3 +130,24 @@ def test_predict_increment_map():
         fd = (f(params["d1a.w"] + eps * d) - f(params["d1a.w"] - eps * d)) / (2 * eps)
         errs.append(abs(float(np.sum(grads["d1a.w"] * d)) - fd) / abs(fd))
     assert min(errs) <= 1e-5, errs
+
+
+def test_residual_loss_gradient(oracle):
+    """The residual loss's gradient: central differences, and equality with
+    -2 A^T r / |b|^2 from the dense assembly of the operator (A^T = A)."""
+    rng = np.random.default_rng(8)
+    shape = (4, 4, 6)
+    per = (False, True, False)
+    bx, by, bz = (rng.uniform(0.1, 1.0, shape) for _ in range(3))
+    A = lambda v: oracle.apply_A(v, bx, by, bz, periodic=per)
+    b = rng.standard_normal(shape)
+    p0 = rng.standard_normal(shape)
+    loss, g = W.residual_loss_and_grad(p0, b, A)
+    M = oracle.dense_operator(bx, by, bz, periodic=per)
+    r = b.ravel() - M @ p0.ravel()
+    np.testing.assert_allclose(loss, r @ r / (b.ravel() @ b.ravel()), rtol=1e-12)
+    np.testing.assert_allclose(g.ravel(), -2.0 * M.T @ r / (b.ravel() @ b.ravel()), rtol=1e-10, atol=1e-14)
+    d = rng.standard_normal(shape)
+    eps = 1e-6
+    fd = (W.residual_loss_and_grad(p0 + eps * d, b, A)[0] - W.residual_loss_and_grad(p0 - eps * d, b, A)[0]) / (2 * eps)
+    assert float(np.sum(g * d)) == pytest.approx(fd, rel=1e-7)

@@ -397,6 +397,116 @@ def warmstart_bench(args):
     return 0
 
 
+def suite(args):
+    """Time to tolerance of each solver form on the paper-shaped workloads
+    (one JSON line per workload): the Taylor-Green cube 32^3 (FP32, 1e-6), the
+    sphere channel 256x96x96 (FP64 refinement around FP32 or BF16-coarse
+    V-cycles, 1e-6), the Taylor-Green cube 512^3 (1e-10, FP32 and BF16-coarse
+    V-cycles inside FP64 refinement) and the batch of 64 uneven problems (one
+    batched solve against 64 separate solves, FP32).  Median of the timed
+    solves, each from a zero guess, CUDA events, inputs resident."""
+    import numpy as np
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    from paper_2607_07687_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps, warm):
+        for _ in range(warm):
+            fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev0.record()
+            out = fn()
+            ev1.record()
+            torch.cuda.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+        return float(np.median(ts)), out
+
+    def single(prob, precision, tol, coarsen, reps, warm):
+        s = G.Solver(prob.dims, prob.periodic, precision=precision, coarsen=coarsen)
+        s.set_coeffs(f32(prob.bx), f32(prob.by), f32(prob.bz))
+        fp64 = s.fp64
+        b = torch.from_numpy(np.asarray(prob.b, dtype=np.float32).astype(np.float64 if fp64 else np.float32)).to(dev)
+        p = torch.zeros_like(b)
+
+        def run():
+            p.zero_()
+            return s.solve(b, p, tol)
+        ms, info = timed(run, reps, warm)
+        s.close()
+        cells = prob.cells
+        return {"precision": precision, "ms": ms, "v_cycles": info.cycles, "refinement_steps": info.outer,
+                "rel_res": info.rel_res, "status": info.status,
+                "gcell_updates_per_s": cells * info.cycles / (ms * 1e-3) / 1e9}
+
+    lines = []
+    prob = I.taylor_green_problem(32, seed=0)
+    lines.append({"workload": "taylor_green_32^3_iso", "tol": 1e-6,
+                  "forms": [single(prob, "fp32", 1e-6, "iso", 10, 3)]})
+    prob = I.sphere_channel_problem(*DIMS, seed=1)
+    lines.append({"workload": "sphere_channel_256x96x96_aniso", "tol": 1e-6,
+                  "forms": [single(prob, "ir64_fp32", 1e-6, "aniso", 10, 3),
+                            single(prob, "ir64", 1e-6, "aniso", 10, 3)]})
+    del prob
+    if not args.no_large:
+        prob = I.taylor_green_problem(512, seed=2)
+        lines.append({"workload": "taylor_green_512^3_iso", "tol": 1e-10,
+                      "forms": [single(prob, "ir64_fp32", 1e-10, "iso", 3, 1),
+                                single(prob, "ir64", 1e-10, "iso", 3, 1)]})
+        del prob
+    probs = I.batch_problems(64, seed=3)
+    tol = 1e-6
+    cells = sum(pr.cells for pr in probs)
+    entry = {"workload": "batch_64_uneven_walls_bodies", "tol": tol, "cells": cells, "forms": []}
+    for precision in ("fp32", "ir64_fp32"):
+        fp64 = precision == "ir64_fp32"
+        rhs = [torch.from_numpy(np.asarray(pr.b, dtype=np.float32).astype(np.float64 if fp64 else np.float32)).to(dev)
+               for pr in probs]
+        bs = G.BatchSolver([pr.dims for pr in probs], precision=precision)
+        bs.set_coeffs([f32(pr.bx) for pr in probs], [f32(pr.by) for pr in probs], [f32(pr.bz) for pr in probs])
+        pp = [torch.zeros_like(x) for x in rhs]
+
+        def run_batch():
+            for x in pp:
+                x.zero_()
+            return bs.solve(rhs, pp, tol)
+        batch_ms, infos = timed(run_batch, 5, 2)
+        bs.close()
+        sols = []
+        for pr, b in zip(probs, rhs):
+            s1 = G.Solver(pr.dims, pr.periodic, precision=precision)
+            s1.set_coeffs(f32(pr.bx), f32(pr.by), f32(pr.bz))
+            sols.append((s1, b, torch.zeros_like(b)))
+
+        def run_each():
+            out = []
+            for s1, b, p in sols:
+                p.zero_()
+                out.append(s1.solve(b, p, tol))
+            return out
+        each_ms, einfos = timed(run_each, 5, 2)
+        for s1, _, _ in sols:
+            s1.close()
+        entry["forms"].append({
+            "precision": precision,
+            "batched": {"ms": batch_ms, "v_cycles_max": max(i.cycles for i in infos),
+                        "converged": sum(int(i.status) == 0 for i in infos),
+                        "worst_rel_res": max(i.rel_res for i in infos)},
+            "separate": {"ms": each_ms, "v_cycles_max": max(i.cycles for i in einfos),
+                         "converged": sum(int(i.status) == 0 for i in einfos)},
+            "speedup": each_ms / batch_ms})
+        del rhs, pp, sols
+    lines.append(entry)
+    for ln in lines:
+        print(json.dumps(ln), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,6 +519,9 @@ def main():
     ap.add_argument("--grid", default="512,256,128", help="nx,ny,nz of the --kernel grid")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--walls", action="store_true", help="--kernel grid with walls instead of periodic axes")
+    ap.add_argument("--suite", action="store_true",
+                    help="time to tolerance of every solver form on the paper-shaped workloads")
+    ap.add_argument("--no-large", action="store_true", help="--suite without the 512^3 cube")
     ap.add_argument("--warmstart", action="store_true",
                     help="run the learned warm-start experiment instead of the solve benchmark")
     ap.add_argument("--frames", type=int, default=200, help="evaluation steps of the vortex sequence")
@@ -423,6 +536,8 @@ def main():
         return kernel_only(args)
     if args.warmstart:
         return warmstart_bench(args)
+    if args.suite:
+        return suite(args)
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)

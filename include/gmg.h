@@ -152,8 +152,9 @@ const char* gmg_last_error(gmg_handle h);
 
 /*
  * dims: nprob x 3 ints (nx, ny, nz); periodic: nprob x 3 flags (or NULL for
- * all walls); opt shared by all problems (precision must be GMG_FP32 or
- * GMG_FP32_BF16).
+ * all walls); opt shared by all problems (any precision: the FP64 refinement
+ * modes run their outer steps per problem and the V-cycles of all unfinished
+ * problems together).
  */
 int gmg_batch_create(gmg_batch* b, int nprob, const int* dims, const int* periodic,
                      const gmg_options* opt, void* stream);
@@ -163,11 +164,12 @@ int gmg_batch_set_coeffs(gmg_batch b, const float* const* bx, const float* const
                          const float* const* bz);
 
 /*
- * sigma, p: host arrays of nprob device pointers (float).  infos: host array
- * of nprob gmg_info (may be NULL).  Returns GMG_OK if every problem
- * converged, else the first failing problem's status.
+ * sigma, p: host arrays of nprob device pointers, to float arrays (GMG_FP32,
+ * GMG_FP32_BF16) or double arrays (GMG_IR64, GMG_IR64_FP32), as for gmg_solve.
+ * infos: host array of nprob gmg_info (may be NULL).  Returns GMG_OK if every
+ * problem converged, else the first failing problem's status.
  */
-int gmg_batch_solve(gmg_batch b, const float* const* sigma, float* const* p, double tol,
+int gmg_batch_solve(gmg_batch b, const void* const* sigma, void* const* p, double tol,
                     gmg_info* infos);
 
 int gmg_batch_destroy(gmg_batch b);

@@ -312,10 +312,11 @@ class BatchSolver:
                self.h, batch=True)
 
     def solve(self, sigma, p, tol: float = 1e-6) -> List[Info]:
+        """sigma, p: lists of device tensors, float32 (or float64 in the FP64 refinement modes)."""
         import torch
+        dt = torch.float64 if self.opts.precision in (IR64, IR64_FP32) else torch.float32
         infos = (Info * self.n)()
-        rc = lib().gmg_batch_solve(self.h, self._arr(sigma, torch.float32), self._arr(p, torch.float32),
-                                   float(tol), infos)
+        rc = lib().gmg_batch_solve(self.h, self._arr(sigma, dt), self._arr(p, dt), float(tol), infos)
         _check(rc, self.h, batch=True, ok=SOLVE_STATUSES)
         return list(infos)
 

@@ -1386,103 +1386,141 @@ struct Engine {
         return worst;
     }
 
-    int solve64(const double* sigma, double* p, double tol, gmg_info* info)
+    // FP64 iterative refinement (Sec. 3 cycles inside an FP64 outer loop) for every
+    // problem of the engine: each outer step computes r64 = b64 - A p64, runs the
+    // FP32 (or BF16-coarse) V-cycles of all unfinished problems together on it,
+    // and adds the correction; a problem leaves the loop when its outer residual
+    // meets tol (or its inner solve diverged).
+    int solve64(const double* const* sigma, double* const* p, double tol, gmg_info* infos)
     {
         if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_solve");
-        ProblemMem& M = P[0];
+        const size_t N = P.size();
         launches = 0;
         cudaError_t e = upload_ctl(tol);
-        const double* sg[1] = {sigma};
-        const double* pi[1] = {p};
-        double* pd[1] = {p};
-        if (e == cudaSuccess) e = project<double>(sg, pi, true, pd);
+        if (e == cudaSuccess) e = project<double>(sigma, (const double* const*)p, true, p);
         // |b64| -> bnorm (partials = nullptr: the residual equals b here)
         if (e == cudaSuccess) {
-            CtlTask t{M.ctl, nullptr, 0, M.bpart, M.elem_tiles, M.proj_part, M.elem_tiles};
-            std::vector<CtlTask> tv{t};
+            std::vector<CtlTask> tv(N);
+            for (size_t q = 0; q < N; ++q)
+                tv[q] = CtlTask{P[q].ctl, nullptr, 0, P[q].bpart, P[q].elem_tiles, P[q].proj_part, P[q].elem_tiles};
             CtlTask* d = upload(tv);
             if (!d) return fail(GMG_ERR_CUDA, "upload failed");
-            e = launch_control_init(d, 1, stream);
+            e = launch_control_init(d, (int)N, stream);
             ++launches;
             if (e == cudaSuccess) e = read_ctl();
             drop(d);
         }
         if (e != cudaSuccess) return cuda_fail(e, "gmg_solve");
-        Ctl& c = ctl_host[0];
-        int outer = 0;
-        int status = c.status;
-        if (!c.done) {
-            // the outer |b| lives in outer_bnorm
-            c.outer_bnorm = c.bnorm;
+        std::vector<int> outer(N, 0), status(N, kRunning);
+        std::vector<char> finished(N, 0);
+        std::vector<IrTask> t(N);
+        std::vector<ResTiling> rt(N);
+        for (size_t q = 0; q < N; ++q) {
+            Ctl& c = ctl_host[q];
+            ProblemMem& M = P[q];
+            if (c.done) {            // zero or non-finite source: settled by the control kernel
+                finished[q] = 1;
+                status[q] = c.status;
+                continue;
+            }
+            c.outer_bnorm = c.bnorm;   // the outer |b| lives in outer_bnorm
             c.outer_r = 0.0;
-            e = cudaMemcpyAsync(M.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, stream);
-            IrTask t{};
-            t.g = M.g0;
-            t.bx = M.lev[0].beta[0];
-            t.by = M.lev[0].beta[1];
-            t.bz = M.lev[0].beta[2];
-            t.b64 = M.b64;
-            t.p64 = p;
-            t.b32 = M.lev[0].b;
-            for (int r = 0; r < 3; ++r) t.ebuf[r] = static_cast<float*>(M.lev[0].buf[r]);
-            t.rot = &M.ctl->rot;
-            t.partials = M.ir_part;
-            const ResTiling rt = res_tiling(M.g0);
-            t.tiles_x = rt.tx;
-            t.tiles_y = rt.ty;
-            t.tiles_z = rt.tz;
-            t.ctl = M.ctl;
-            t.scale = nullptr;
-            status = kRunning;
-            for (;;) {
-                launches += 2;
-                if (e == cudaSuccess) e = launch_ir_residual(t, persistent_grid(rt.tiles()), stream);
-                if (e == cudaSuccess)
-                    e = launch_ir_begin_inner(t, (int)rt.tiles(), tol, opt.ir_inner_rtol, opt.max_cycles, stream);
-                if (e == cudaSuccess) e = read_ctl();
-                if (e != cudaSuccess) break;
-                if (c.done) {
-                    status = c.outer_status;
-                    break;
-                }
-                ++outer;
-                e = iterate();
-                ++launches;
-                if (e == cudaSuccess) e = launch_ir_update(t, stream);
-                if (e == cudaSuccess) e = read_ctl();
-                if (e != cudaSuccess) break;
-                if (c.status == kDiverged) {
-                    // keep the refinement so far and report the inner divergence
-                    launches += 2;
-                    e = launch_ir_residual(t, persistent_grid(rt.tiles()), stream);
-                    if (e == cudaSuccess)
-                        e = launch_ir_begin_inner(t, (int)rt.tiles(), tol, opt.ir_inner_rtol, opt.max_cycles, stream);
-                    if (e == cudaSuccess) e = read_ctl();
-                    status = c.outer_status == kOk ? kOk : kDiverged;
-                    break;
+            IrTask& ti = t[q];
+            ti = IrTask{};
+            ti.g = M.g0;
+            ti.bx = M.lev[0].beta[0];
+            ti.by = M.lev[0].beta[1];
+            ti.bz = M.lev[0].beta[2];
+            ti.b64 = M.b64;
+            ti.p64 = p[q];
+            ti.b32 = M.lev[0].b;
+            for (int r = 0; r < 3; ++r) ti.ebuf[r] = static_cast<float*>(M.lev[0].buf[r]);
+            ti.rot = &M.ctl->rot;
+            ti.partials = M.ir_part;
+            rt[q] = res_tiling(M.g0);
+            ti.tiles_x = rt[q].tx;
+            ti.tiles_y = rt[q].ty;
+            ti.tiles_z = rt[q].tz;
+            ti.ctl = M.ctl;
+            ti.scale = nullptr;
+        }
+        e = cudaMemcpyAsync(ctl_dev, ctl_host, sizeof(Ctl) * N, cudaMemcpyHostToDevice, stream);
+        auto outer_residual = [&](size_t q) {
+            launches += 2;
+            cudaError_t r = launch_ir_residual(t[q], persistent_grid(rt[q].tiles()), stream);
+            if (r == cudaSuccess)
+                r = launch_ir_begin_inner(t[q], (int)rt[q].tiles(), tol, opt.ir_inner_rtol, opt.max_cycles, stream);
+            return r;
+        };
+        for (;;) {
+            // outer residual and the next inner right-hand side of every unfinished problem
+            for (size_t q = 0; q < N && e == cudaSuccess; ++q)
+                if (!finished[q]) e = outer_residual(q);
+            if (e == cudaSuccess) e = read_ctl();
+            if (e != cudaSuccess) break;
+            bool any = false;
+            for (size_t q = 0; q < N; ++q) {
+                if (finished[q]) continue;
+                if (ctl_host[q].done) {
+                    finished[q] = 1;
+                    status[q] = ctl_host[q].outer_status;
+                } else {
+                    ++outer[q];
+                    any = true;
                 }
             }
-            if (e != cudaSuccess) return cuda_fail(e, "gmg_solve (refinement)");
-        }
-        if (status != kNonFinite) {
-            double* dst[1] = {p};
-            e = gauge<double, double>(dst, true);
+            if (!any) break;
+            e = iterate();
+            for (size_t q = 0; q < N && e == cudaSuccess; ++q)
+                if (!finished[q]) {
+                    ++launches;
+                    e = launch_ir_update(t[q], stream);
+                }
             if (e == cudaSuccess) e = read_ctl();
-            if (e != cudaSuccess) return cuda_fail(e, "gmg_solve (gauge)");
+            if (e != cudaSuccess) break;
+            for (size_t q = 0; q < N && e == cudaSuccess; ++q) {
+                if (finished[q] || ctl_host[q].status != kDiverged) continue;
+                // keep the refinement so far and report the inner divergence
+                e = outer_residual(q);
+                if (e == cudaSuccess) e = read_ctl();
+                status[q] = ctl_host[q].outer_status == kOk ? kOk : kDiverged;
+                finished[q] = 1;
+            }
+            if (e != cudaSuccess) break;
         }
-        const int st = status == kRunning ? kNotConverged : status;
-        if (info) {
-            info->cycles = c.total_cycles;
-            info->status = st;
-            info->levels = M.L;
-            info->outer = outer;
-            info->launches = (int)launches;
-            info->rel_res = c.outer_bnorm > 0.0 ? c.outer_r / c.outer_bnorm : 0.0;
-            info->omega = c.omega;
-            info->bnorm = c.outer_bnorm;
+        if (e != cudaSuccess) return cuda_fail(e, "gmg_solve (refinement)");
+        {
+            std::vector<double*> dst;
+            bool any_finite = false;
+            for (size_t q = 0; q < N; ++q) {
+                dst.push_back(p[q]);
+                any_finite |= status[q] != kNonFinite;
+            }
+            if (any_finite) {
+                e = gauge<double, double>(dst.data(), true);
+                if (e == cudaSuccess) e = read_ctl();
+                if (e != cudaSuccess) return cuda_fail(e, "gmg_solve (gauge)");
+            }
         }
-        last_cycles = c.total_cycles;
-        return st;
+        int first_bad = GMG_OK;
+        for (size_t q = 0; q < N; ++q) {
+            const Ctl& c = ctl_host[q];
+            const int st = status[q] == kRunning ? kNotConverged : status[q];
+            if (st != kOk && first_bad == GMG_OK) first_bad = st;
+            if (infos) {
+                gmg_info& info = infos[q];
+                info.cycles = c.total_cycles;
+                info.status = st;
+                info.levels = P[q].L;
+                info.outer = outer[q];
+                info.launches = (int)launches;
+                info.rel_res = c.outer_bnorm > 0.0 ? c.outer_r / c.outer_bnorm : 0.0;
+                info.omega = c.omega;
+                info.bnorm = c.outer_bnorm;
+            }
+        }
+        last_cycles = ctl_host[0].total_cycles;
+        return first_bad;
     }
 };
 
@@ -1608,7 +1646,11 @@ int gmg_solve(gmg_handle h, const void* sigma, void* p, double tol, gmg_info* in
     Engine& E = h->eng;
     if (!sigma || !p) return E.fail(GMG_ERR_ARG, "null sigma or p");
     if (!(tol > 0.0)) return E.fail(GMG_ERR_ARG, "tol must be > 0");
-    if (E.ir) return E.solve64(static_cast<const double*>(sigma), static_cast<double*>(p), tol, info);
+    if (E.ir) {
+        const double* sg[1] = {static_cast<const double*>(sigma)};
+        double* pp[1] = {static_cast<double*>(p)};
+        return E.solve64(sg, pp, tol, info);
+    }
     const float* s[1] = {static_cast<const float*>(sigma)};
     float* q[1] = {static_cast<float*>(p)};
     return E.solve32(s, q, tol, info);
@@ -1695,10 +1737,6 @@ int gmg_batch_create(gmg_batch* b, int nprob, const int* dims, const int* period
     if (opt) o = *opt;
     int rc = validate_options(o, g_create_error);
     if (rc != GMG_OK) return rc;
-    if (o.precision != GMG_FP32 && o.precision != GMG_FP32_BF16) {
-        g_create_error = "batched solves support GMG_FP32 and GMG_FP32_BF16";
-        return GMG_ERR_ARG;
-    }
     for (int p = 0; p < nprob; ++p) {
         rc = validate_geometry(dims[3 * p], dims[3 * p + 1], dims[3 * p + 2], periodic ? periodic + 3 * p : nullptr,
                                g_create_error);
@@ -1724,14 +1762,30 @@ int gmg_batch_set_coeffs(gmg_batch b, const float* const* bx, const float* const
     return b->eng.set_coeffs(bx, by, bz);
 }
 
-int gmg_batch_solve(gmg_batch b, const float* const* sigma, float* const* p, double tol, gmg_info* infos)
+int gmg_batch_solve(gmg_batch b, const void* const* sigma, void* const* p, double tol, gmg_info* infos)
 {
     if (!b) return GMG_ERR_ARG;
     if (!sigma || !p) return b->eng.fail(GMG_ERR_ARG, "null sigma or p array");
     if (!(tol > 0.0)) return b->eng.fail(GMG_ERR_ARG, "tol must be > 0");
-    for (size_t q = 0; q < b->eng.P.size(); ++q)
+    const size_t n = b->eng.P.size();
+    for (size_t q = 0; q < n; ++q)
         if (!sigma[q] || !p[q]) return b->eng.fail(GMG_ERR_ARG, "null sigma or p (problem %zu)", q);
-    return b->eng.solve32(sigma, p, tol, infos);
+    if (b->eng.ir) {
+        std::vector<const double*> s(n);
+        std::vector<double*> q(n);
+        for (size_t k = 0; k < n; ++k) {
+            s[k] = static_cast<const double*>(sigma[k]);
+            q[k] = static_cast<double*>(p[k]);
+        }
+        return b->eng.solve64(s.data(), q.data(), tol, infos);
+    }
+    std::vector<const float*> s(n);
+    std::vector<float*> q(n);
+    for (size_t k = 0; k < n; ++k) {
+        s[k] = static_cast<const float*>(sigma[k]);
+        q[k] = static_cast<float*>(p[k]);
+    }
+    return b->eng.solve32(s.data(), q.data(), tol, infos);
 }
 
 int gmg_batch_destroy(gmg_batch b)

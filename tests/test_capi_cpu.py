@@ -64,9 +64,9 @@ def test_batch_create_rejects(L):
     dims = G._ivec([8, 8, 8])
     o = G.options()
     assert L.gmg_batch_create(ctypes.byref(b), 0, dims, None, ctypes.byref(o), None) == G.ERR_ARG
-    o = G.options(precision="ir64")
-    assert L.gmg_batch_create(ctypes.byref(b), 1, dims, None, ctypes.byref(o), None) == G.ERR_ARG
-    assert "batched" in L.gmg_batch_last_error(None).decode()
+    odd = G._ivec([7, 8, 8])                  # an odd periodic axis, checked before any allocation
+    assert L.gmg_batch_create(ctypes.byref(b), 1, odd, G._ivec([1, 0, 0]), ctypes.byref(o), None) == G.ERR_ARG
+    assert L.gmg_batch_last_error(None).decode()
 
 
 def test_ops_reject_bad_arguments(L):

@@ -246,3 +246,25 @@ def test_autotuned_shapes_agree(O):
     b, ib, _ = gpu_solve(prob, 1e-5, autotune=0)
     assert ia.cycles == ib.cycles and ia.status == ib.status == 0
     assert rel_l2(a, b) <= 1e-6
+
+
+@pytest.mark.gpu
+def test_batch_fp64_refinement_equals_single():
+    """Batched FP64 refinement (the outer loop per problem, the V-cycles of all
+    unfinished problems together): every problem reaches 1e-6 and equals its
+    own single solve bit for bit."""
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    probs = I.batch_problems(5, seed=3)
+    bs = G.BatchSolver([p.dims for p in probs], precision="ir64_fp32")
+    bs.set_coeffs([t32(p.bx) for p in probs], [t32(p.by) for p in probs], [t32(p.bz) for p in probs])
+    sig = [t64(f32(p.b)) for p in probs]
+    out = [torch.zeros_like(s) for s in sig]
+    infos = bs.solve(sig, out, 1e-6)
+    torch.cuda.synchronize()
+    bs.close()
+    for prob, o, inf in zip(probs, out, infos):
+        assert inf.status == 0 and inf.rel_res <= 1e-6, (prob.name, inf.as_dict())
+        single, si, _ = gpu_solve(prob, 1e-6, autotune=0, precision="ir64_fp32")
+        assert inf.cycles == si.cycles and inf.outer == si.outer
+        assert np.array_equal(host(o), single)

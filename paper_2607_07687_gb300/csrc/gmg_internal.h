@@ -26,8 +26,8 @@ constexpr int kThreads = 256;           // threads per block of the grid kernels
 // sweep tile (cells): TX x TY columns marching through a z-chunk
 constexpr int kSweepTX = 32;
 constexpr int kSweepTY = 8;
-// plane rings of the pipelined sweep (p, b, x/y/z faces, merged red plane),
-// each holding planes kr-2 .. kr+3 of the marching step
+// plane rings of the pipelined sweeps (p, b, x/y/z faces, merged red plane),
+// R plane slots each
 constexpr int kSweepRing = 6;
 constexpr size_t kSweepSmemBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4) * 6 * kSweepRing;
 // the pipelined residual stages the same rings without the merged plane

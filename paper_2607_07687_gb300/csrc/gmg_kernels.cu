@@ -191,21 +191,17 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const __grid_constant__ Task
     }
 }
 
-// ---------------------------------------------------------------- K1: pipelined sweep
+// ---------------------------------------------------------------- K1: pipelined sweep, per-thread copies
 //
 // The same sweep as k_sweep (same arithmetic, bit-identical results) with the
-// z-planes staged by asynchronous global->shared copies.  Ring buffers of
-// planes over the tile plus halo (x: 4 columns each side so rows split into
-// 16-byte chunks; y: 2 rows each side):
-//   P  input p (+ coarse correction)     planes kr .. kr+3   (4 slots)
-//   B, X, Y  b and lower x/y faces       planes kr-1 .. kr+1 (4 slots)
-//   Z  lower z faces                     planes kr-1 .. kr+2 (5 slots)
-//   M  merged plane (red new, black old) planes kr-2 .. kr   (3 slots)
-// At step u (red plane kr = z0 - 1 + u, black plane kr - 1) the copies for
-// step u+1 are issued first, then the step waits for its own group.  The
-// coarse correction of a P plane is added two steps before the plane is read,
-// so it needs no extra barrier.  VEC = 4 copies 16-byte chunks (rows of a
-// multiple of 4 cells, 16-byte aligned arrays), VEC = 1 copies single floats.
+// z-planes staged by asynchronous global->shared copies of every thread.  It
+// serves FP32 levels whose rows are not 16-byte chunks (VEC = 1: single-float
+// copies); levels with rows of a multiple of 4 cells run k_sweep_ws below.
+// Ring buffers of R planes over the tile plus halo (x: 4 columns each side so
+// rows split into 16-byte chunks; y: 2 rows each side) for p, b, the x/y/z
+// faces and the merged plane M (red new, black old).  Group G(v) holds what
+// step v + LA reads first; step u waits for G(u - LA), then issues G(u); the
+// coarse correction of a p plane is added one step before the plane is read.
 
 __device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc, bool ok)
 {

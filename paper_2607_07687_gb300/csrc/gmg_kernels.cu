@@ -825,15 +825,20 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
                          : "=r"(any) : "r"((int)!live), "n"(kSweepConsumers) : "memory");
             live = !any;
         }
+        // ring slots advance by one per step: sl holds H(u) (plane kr-1); sw and pw are the
+        // slot and phase parity of H(u + AHEAD), the group this step waits for
+        auto rs = [&](int arr, uint32_t slot) -> float* { return smem + (arr * R + (int)slot) * PL; };
+        uint32_t sl = g % R, sw = (g + AHEAD) % R, pw = ((g + AHEAD) / R) & 1u;
         for (int u = 0; u < nsteps && live; ++u) {
-            const uint32_t hl = g + u, h0 = hl + 1, hu = hl + 2;   // planes kr-1, kr, kr+1
+            const uint32_t s0 = sl + 1 == R ? 0 : sl + 1, su = s0 + 1 == R ? 0 : s0 + 1;   // kr, kr+1
+            const uint32_t sm = sl == 0 ? R - 1 : sl - 1;                                 // kr-2
             const int kr = kr0 + u;
             bool ok = true;
-            if (u + AHEAD <= nh - 1) ok = mbar_wait_live(&full[(hl + AHEAD) % R], ((hl + AHEAD) / R) & 1u, dead);
+            if (u + AHEAD <= nh - 1) ok = mbar_wait_live(&full[sw], pw, dead);
             if (CORR && ok && u + 3 <= nh - 1) {
                 float nxt0, nxt1;
                 corr_load(kr + 3, nxt0, nxt1);
-                corr_add(ring(0, hl + 3), cur0, cur1);       // p(kr+2), first read in step u+1
+                corr_add(rs(0, su + 1 == R ? 0 : su + 1), cur0, cur1);   // p(kr+2), first read in step u+1
                 cur0 = nxt0;
                 cur1 = nxt1;
             }
@@ -845,21 +850,21 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
                 const int s = sred + o;
                 float v = 0.f;
                 if (zok && yr_ok && (o ? xr_ok1 : xr_ok0)) {
-                    const float* P0 = ring(0, h0);
-                    const float* X0 = ring(2, h0);
-                    const float* Y0 = ring(3, h0);
-                    const float* Z0 = ring(4, h0);
-                    const float* Z1 = ring(4, hu);
+                    const float* P0 = rs(0, s0);
+                    const float* X0 = rs(2, s0);
+                    const float* Y0 = rs(3, s0);
+                    const float* Z0 = rs(4, s0);
+                    const float* Z1 = rs(4, su);
                     v = P0[s];
                     const float xl = (o ? xr_wall1 : xr_wall0) ? 0.f : X0[s];
                     const float yl = yr_wall ? 0.f : Y0[s];
                     const float zl = (kr == 0 && !pz) ? 0.f : Z0[s];
                     const float fl = face_flux(xl, P0[s - 1], X0[s + 1], P0[s + 1], yl, P0[s - SW], Y0[s + SW],
-                                               P0[s + SW], zl, ring(0, hl)[s], Z1[s], ring(0, hu)[s], v);
+                                               P0[s + SW], zl, rs(0, sl)[s], Z1[s], rs(0, su)[s], v);
                     const float dg = diag_sum(xl, X0[s + 1], yl, Y0[s + SW], zl, Z1[s]);
-                    v = gs_update(v, fl, dg, ring(1, h0)[s], w);
+                    v = gs_update(v, fl, dg, rs(1, s0)[s], w);
                 }
-                ring(5, h0)[s] = v;
+                rs(5, s0)[s] = v;
             }
             // S2: red cells of kr merged (and corrections visible), faults agreed
             {
@@ -876,19 +881,19 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
                 const int k = kr - 1;
                 const int hb = ((xb + yb + k) & 1) ? 0 : 1;   // black member of the pair
                 const int s = sblk + hb;
-                const float* Mk = ring(5, hl);
-                const float* Xk = ring(2, hl);
-                const float* Yk = ring(3, hl);
-                const float* Zk = ring(4, hl);
-                const float* Zk1 = ring(4, h0);
-                float v = ring(0, hl)[s];
+                const float* Mk = rs(5, sl);
+                const float* Xk = rs(2, sl);
+                const float* Yk = rs(3, sl);
+                const float* Zk = rs(4, sl);
+                const float* Zk1 = rs(4, s0);
+                float v = rs(0, sl)[s];
                 const float xl = (hb == 0 && xb_wall) ? 0.f : Xk[s];
                 const float yl = yb_wall ? 0.f : Yk[s];
                 const float zl = (k == 0 && !pz) ? 0.f : Zk[s];
                 const float fl = face_flux(xl, Mk[s - 1], Xk[s + 1], Mk[s + 1], yl, Mk[s - SW], Yk[s + SW],
-                                           Mk[s + SW], zl, ring(5, hl + R - 1)[s], Zk1[s], ring(5, h0)[s], v);
+                                           Mk[s + SW], zl, rs(5, sm)[s], Zk1[s], rs(5, s0)[s], v);
                 const float dg = diag_sum(xl, Xk[s + 1], yl, Yk[s + SW], zl, Zk1[s]);
-                v = gs_update(v, fl, dg, ring(1, hl)[s], w);
+                v = gs_update(v, fl, dg, rs(1, sl)[s], w);
                 const float r = Mk[sblk + (1 - hb)];
                 const float o0 = hb ? r : v, o1 = hb ? v : r;
                 *reinterpret_cast<float2*>(out_col + (int64_t)k * plane) = make_float2(o0, o1);
@@ -896,7 +901,12 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
             // plane kr-1 (H(u)) is no longer read by this tile's later steps
             if (CORR) fence_proxy_async();                 // corrected p planes: generic writes before refills
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[hl % R]);
+            if (lane == 0) mbar_arrive(&empty[sl]);
+            sl = s0;
+            if (++sw == R) {
+                sw = 0;
+                pw ^= 1u;
+            }
         }
         if (!live) {
             if (tid == 0) {
@@ -1072,23 +1082,25 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
         float acc0 = 0.f, acc1 = 0.f;
         bool live = mbar_wait_live(&full[g % R], (g / R) & 1u, dead) &&
                     mbar_wait_live(&full[(g + 1) % R], ((g + 1) / R) & 1u, dead);
+        auto rs = [&](int arr, uint32_t slot) -> float* { return smem + (arr * R + (int)slot) * PL; };
+        uint32_t sl = g % R, sw = (g + 2) % R, pw = ((g + 2) / R) & 1u;   // H(u); H(u+2) and its parity
         for (int u = 0; u < nsteps && live; ++u) {
-            const uint32_t hl = g + u, h0 = hl + 1, hu = hl + 2;   // planes k-1, k, k+1
-            if (!mbar_wait_live(&full[hu % R], (hu / R) & 1u, dead)) {
+            const uint32_t s0 = sl + 1 == R ? 0 : sl + 1, su = sw;      // planes k, k+1
+            if (!mbar_wait_live(&full[sw], pw, dead)) {
                 live = false;
                 break;
             }
             const int k = t.z0 + u;
             float r0 = 0.f, r1 = 0.f;
             if (pair_on) {
-                const float* P0 = ring(0, h0);
-                const float* Pl = ring(0, hl);
-                const float* Pu = ring(0, hu);
-                const float* B0 = ring(1, h0);
-                const float* X0 = ring(2, h0);
-                const float* Y0 = ring(3, h0);
-                const float* Z0 = ring(4, h0);
-                const float* Z1 = ring(4, hu);
+                const float* P0 = rs(0, s0);
+                const float* Pl = rs(0, sl);
+                const float* Pu = rs(0, su);
+                const float* B0 = rs(1, s0);
+                const float* X0 = rs(2, s0);
+                const float* Y0 = rs(3, s0);
+                const float* Z0 = rs(4, s0);
+                const float* Z1 = rs(4, su);
                 for (int h = 0; h < 2; ++h) {
                     const int s = sp + h;
                     const float p0 = P0[s];
@@ -1104,7 +1116,12 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
             }
             // plane k-1 is no longer read
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[hl % R]);
+            if (lane == 0) mbar_arrive(&empty[sl]);
+            sl = s0;
+            if (++sw == R) {
+                sw = 0;
+                pw ^= 1u;
+            }
             if (bc) {
                 float v0 = c0 == 2 ? r0 + r1 : r0;
                 float v1 = c0 == 2 ? 0.f : r1;

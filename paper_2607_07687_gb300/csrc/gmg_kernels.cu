@@ -560,17 +560,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
 // r = b - A p on a TX x TY column marching through a z-chunk, restricted to the
 // next level and summed in squares (FP64, one partial per tile).  Warp-
 // specialised: warps 0-3 (consumers) each own two tile rows, one x-pair of
-// cells per thread; warp 4 (producer) streams whole planes of p, b and the
+// cells per thread; warps 4-5 (producers) stream whole planes of p, b and the
 // three face arrays into a ring of R plane slots.  Group H(g) (the g-th plane
 // this block streams, over all its tiles) lands in slot g mod R and completes
 // on full[g mod R]: by TMA (one box per array, zeros outside the grid) when the
 // box needs no periodic wrap in x or y, else by 16-byte asynchronous copies of
-// the producer's lanes.  The consumers release a slot on empty[] once no later
+// the producers' lanes.  The consumers release a slot on empty[] once no later
 // step reads it; the producer waits for that release before refilling the
 // slot.  Restriction: x-pairs in the thread, y-pairs with the lane 16 apart,
 // z-pairs across two steps, so coarse cells are written without atomics.
+constexpr int kProducers = 64;                  // producer warps of the warp-specialised kernels: two
 constexpr int kResConsumers = 128;
-constexpr int kResBlock = kResConsumers + 32;
+constexpr int kResBlock = kResConsumers + kProducers;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -601,8 +602,8 @@ __device__ __forceinline__ int wrap_plane(int z, int nz, int pz)
 
 // ---------------------------------------------------------------- K1: warp-specialised sweep
 //
-// The pipelined sweep (same arithmetic as k_sweep_async, bit-identical) with a
-// producer warp streaming the planes of p, b and the three face arrays into a
+// The pipelined sweep (same arithmetic as k_sweep_async, bit-identical) with two
+// producer warps streaming the planes of p, b and the three face arrays into a
 // ring of R plane slots while 8 consumer warps compute.  Group H(g), the g-th
 // plane this block streams over all its tiles, lands in slot g mod R and
 // completes on full[g mod R] (TMA boxes with zero fill when the tile's box
@@ -615,7 +616,7 @@ __device__ __forceinline__ int wrap_plane(int z, int nz, int pz)
 // step reads first.  The red results go to a consumer-only ring (M); one named
 // barrier per step separates the red and black phases.
 constexpr int kSweepConsumers = 256;
-constexpr int kSweepBlock = kSweepConsumers + 32;
+constexpr int kSweepBlock = kSweepConsumers + kProducers;
 
 template <bool CORR, class TC>
 __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_constant__ TaskList<SweepTask<float, TC>> tl)
@@ -638,7 +639,7 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
     const int lane = tid & 31;
     if (tid == 0) {
         for (int j = 0; j < R; ++j) {
-            mbar_init(&full[j], 1);
+            mbar_init(&full[j], kProducers / 32);   // one arrival per producer warp
             mbar_init(&empty[j], kSweepConsumers / 32);
         }
         s_dead = 0;
@@ -649,7 +650,8 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
     auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
 
     if (tid >= kSweepConsumers) {
-        // ------------------------------------------------ producer warp
+        // ------------------------------------------------ producer warps
+        const int pt = tid - kSweepConsumers;                 // producer thread 0 .. kProducers-1
         uint32_t g = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < tl.total && ok; tile += gridDim.x) {
@@ -669,13 +671,13 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
                                  !(py && (y0 - 2 < 0 || y0 + TY + 2 > ny));
             const float* src[5] = {pin, tp->b, tp->bx, tp->by, tp->bz};
             const int64_t plane = (int64_t)nx * ny;
-            constexpr int CPL = (NCH + 31) / 32;
+            constexpr int CPL = (NCH + kProducers - 1) / kProducers;
             int coff[CPL];
             bool cok[CPL];
             if (!use_tma) {
 #pragma unroll
                 for (int i = 0; i < CPL; ++i) {
-                    const int c = lane + 32 * i;
+                    const int c = pt + kProducers * i;
                     const int sy = c / CPR, ch = c - sy * CPR;
                     int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
                     cok[i] = c < NCH && wrapc(x, nx, px) && wrapc(y, ny, py);
@@ -691,7 +693,8 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
                 uint64_t* bar = &full[g % R];
                 const int z = z0 - 2 + m;
                 if (use_tma) {
-                    if (lane == 0) {
+                    if (pt == 32) mbar_arrive(bar);            // the second producer warp's arrival
+                    if (pt == 0) {
                         const int zw = wrap_plane(z, nz, pz);
                         mbar_expect_tx(bar, 5 * kPlaneBytes);
                         tma_plane(ring(0, g), &tm->p[pidx], x0 - XO, y0 - 2, zw, bar);
@@ -706,7 +709,7 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
                     const int64_t zoff = (int64_t)zw * plane;
 #pragma unroll
                     for (int i = 0; i < CPL; ++i) {
-                        const int c = lane + 32 * i;
+                        const int c = pt + kProducers * i;
                         if (c < NCH) {
 #pragma unroll
                             for (int a = 0; a < 5; ++a) {
@@ -966,7 +969,7 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
     const int lane = tid & 31;
     if (tid == 0) {
         for (int j = 0; j < R; ++j) {
-            mbar_init(&full[j], 1);
+            mbar_init(&full[j], kProducers / 32);   // one arrival per producer warp
             mbar_init(&empty[j], kResConsumers / 32);
         }
         s_dead = 0;
@@ -977,7 +980,8 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
     auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
 
     if (tid >= kResConsumers) {
-        // ------------------------------------------------ producer warp
+        // ------------------------------------------------ producer warps
+        const int pt = tid - kResConsumers;                 // producer thread 0 .. kProducers-1
         uint32_t g = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < tl.total && ok; tile += gridDim.x) {
@@ -995,13 +999,13 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
             const int64_t plane = (int64_t)nx * ny;
             const int nh = (t.z1 - t.z0) + 2;                  // planes z0-1 .. z1
             // per-thread copies: this lane's 16-byte chunks (c = lane + 32 i) of a plane, fixed for the tile
-            constexpr int CPL = (NCH + 31) / 32;
+            constexpr int CPL = (NCH + kProducers - 1) / kProducers;
             int coff[CPL];
             bool cok[CPL];
             if (!use_tma) {
 #pragma unroll
                 for (int i = 0; i < CPL; ++i) {
-                    const int c = lane + 32 * i;
+                    const int c = pt + kProducers * i;
                     const int sy = c / CPR, ch = c - sy * CPR;
                     int x = t.x0 - XO + 4 * ch, y = t.y0 - 2 + sy;
                     cok[i] = c < NCH && wrapc(x, nx, px) && wrapc(y, ny, py);
@@ -1016,7 +1020,8 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
                 uint64_t* bar = &full[g % R];
                 const int z = t.z0 - 1 + m;
                 if (use_tma) {
-                    if (lane == 0) {
+                    if (pt == 32) mbar_arrive(bar);            // the second producer warp's arrival
+                    if (pt == 0) {
                         const int zw = wrap_plane(z, nz, pz);
                         mbar_expect_tx(bar, 5 * kPlaneBytes);
                         tma_plane(ring(0, g), pmap, t.x0 - XO, t.y0 - 2, zw, bar);
@@ -1031,7 +1036,7 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
                     const int64_t zoff = (int64_t)zw * plane;
 #pragma unroll
                     for (int i = 0; i < CPL; ++i) {
-                        const int c = lane + 32 * i;
+                        const int c = pt + kProducers * i;
                         if (c < NCH) {
 #pragma unroll
                             for (int a = 0; a < 5; ++a) {

@@ -134,11 +134,51 @@ __device__ void sweeps(const LevelView& L, int count, float w)
         }
 }
 
+// The same sweeps on a level of at most blockDim.x cells, one cell per thread: the
+// cell's neighbour indices, face coefficients, diagonal and right-hand side stay in
+// registers across the sweeps, so a half-sweep is six shared loads and one store.
+// Same operands and operation order as sweeps(): bit-identical results.
+__device__ void sweeps_small(const LevelView& L, int count, float w)
+{
+    const int i = threadIdx.x;
+    const bool on = i < L.n;
+    int nb[6] = {0, 0, 0, 0, 0, 0};
+    float cf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float bi = 0.f, dg = 0.f;
+    int colour = -1;
+    if (on) {
+        int x, y, z;
+        decode(L, i, x, y, z);
+        colour = (x + y + z) & 1;
+        for (int d = 0; d < 3; ++d) {
+            const int lo = nbr(L.g, x, y, z, d, -1), up = nbr(L.g, x, y, z, d, +1);
+            const float* f = d == 0 ? L.x : (d == 1 ? L.y : L.z);
+            nb[2 * d] = lo < 0 ? i : lo;            // a missing neighbour contributes p - p = 0
+            nb[2 * d + 1] = up < 0 ? i : up;
+            cf[2 * d] = f[i];
+            cf[2 * d + 1] = up < 0 ? 0.f : f[up];
+        }
+        dg = diag_sum(cf[0], cf[1], cf[2], cf[3], cf[4], cf[5]);
+        bi = L.b[i];
+    }
+    for (int it = 0; it < count; ++it)
+        for (int c = 0; c < 2; ++c) {
+            if (colour == c) {
+                const float p0 = L.p[i];
+                const float fl = face_flux(cf[0], L.p[nb[0]], cf[1], L.p[nb[1]], cf[2], L.p[nb[2]], cf[3],
+                                           L.p[nb[3]], cf[4], L.p[nb[4]], cf[5], L.p[nb[5]], p0);
+                L.p[i] = gs_update(p0, fl, dg, bi, w);
+            }
+            __syncthreads();
+        }
+}
+
 template <class TP>
 __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>* __restrict__ tasks)
 {
     extern __shared__ __align__(16) float sm[];
     __shared__ double red[kBottomThreads / 32];
+    __shared__ double red2[kBottomThreads / 32];
     __shared__ double s_mean;
     const BottomTask<TP>& T = tasks[blockIdx.x];
     if (T.ctl && T.ctl->done) return;
@@ -164,6 +204,15 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
     for (int l = 0; l < nlev; ++l) {
         const LevelView L = view(l);
         const BottomLevel& B = T.lev[l];
+        if (B.walls_zeroed) {                      // straight copies: independent loads in flight
+            for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
+                L.x[i] = __ldg(B.bx + i);
+                L.y[i] = __ldg(B.by + i);
+                L.z[i] = __ldg(B.bz + i);
+                if (l == 0) L.b[i] = T.b[i];
+            }
+            continue;
+        }
         for (CellWalk c(L, threadIdx.x, blockDim.x); c.i < L.n; c.next(L.g, blockDim.x)) {
             const int i = c.i, x = c.x, y = c.y, z = c.z;
             L.x[i] = face_lo(B.bx, L.g, 0, x, y, z);
@@ -180,7 +229,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         const LevelView C = view(l + 1);
         for (int i = threadIdx.x; i < L.n; i += blockDim.x) L.p[i] = 0.f;
         __syncthreads();
-        sweeps(L, T.nu1, w);
+        if (L.n <= (int)blockDim.x) sweeps_small(L, T.nu1, w);
+        else sweeps(L, T.nu1, w);
         const int c0 = T.lev[l].cf[0], c1 = T.lev[l].cf[1], c2 = T.lev[l].cf[2];
         for (CellWalk cw(C, threadIdx.x, blockDim.x); cw.i < C.n; cw.next(C.g, blockDim.x)) {
             const int j = cw.i, X = cw.x, Y = cw.y, Z = cw.z;
@@ -209,15 +259,29 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
                 cnt += 1.0;
             }
         }
-        s = block_sum(s, red);
-        cnt = block_sum(cnt, red);
-        if (threadIdx.x == 0) s_mean = cnt > 0.0 ? s / cnt : 0.0;
+        // both sums in one block reduction (the same per-warp and cross-warp order as block_sum)
+        s = warp_sum(s);
+        cnt = warp_sum(cnt);
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = s;
+            red2[threadIdx.x >> 5] = cnt;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double ts = 0.0, tc = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                ts += red[k];
+                tc += red2[k];
+            }
+            s_mean = tc > 0.0 ? ts / tc : 0.0;
+        }
         __syncthreads();
         const double mean = s_mean;
         for (int i = threadIdx.x; i < C.n; i += blockDim.x)
             C.b[i] = diag_at(C, i) > 0.f ? (float)((double)C.b[i] - mean) : 0.f;
         __syncthreads();
-        sweeps(C, T.nu_c, w);
+        if (C.n <= (int)blockDim.x) sweeps_small(C, T.nu_c, w);
+        else sweeps(C, T.nu_c, w);
     }
 
     // ascent
@@ -228,7 +292,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         for (CellWalk c(L, threadIdx.x, blockDim.x); c.i < L.n; c.next(L.g, blockDim.x))
             L.p[c.i] += C.p[((c.z >> (c2 - 1)) * C.g.n[1] + (c.y >> (c1 - 1))) * C.g.n[0] + (c.x >> (c0 - 1))];
         __syncthreads();
-        sweeps(L, T.nu2, w);
+        if (L.n <= (int)blockDim.x) sweeps_small(L, T.nu2, w);
+        else sweeps(L, T.nu2, w);
     }
 
     const LevelView L = view(0);

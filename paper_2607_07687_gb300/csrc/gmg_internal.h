@@ -149,6 +149,7 @@ struct BottomLevel {
     const float* by;
     const float* bz;
     int off;             // offset (floats) of the level's block in shared memory
+    int walls_zeroed;    // 1: the stored faces already read 0 on walls (coarse levels)
     double inv_nx;       // 1 / nx and 1 / (nx ny): cell index -> (x, y, z) by multiplication
     double inv_nxy;
 };

@@ -283,14 +283,15 @@ def warmstart_bench(args):
     samples = []
     for rhs in train_rhs:
         p = torch.zeros(cells, dtype=torch.float64, device=dev)
-        prev32 = None
+        prev32 = prev2_32 = None
         for b in rhs:
             b32 = f32(b)
             p, _, _ = solve(b32.double(), p)
             p32 = p.float()
             if prev32 is not None:
-                samples.append((b32, prev32, p32))
-            prev32 = p32
+                base = prev32 if (args.base == "previous" or prev2_32 is None) else 2.0 * prev32 - prev2_32
+                samples.append((b32, base, p32))
+            prev2_32, prev32 = prev32, p32
     targets_s = time.perf_counter() - t0
 
     net = WarmStartNet(dims, seed=0, lr=args.lr, loss=args.loss)
@@ -343,9 +344,9 @@ def warmstart_bench(args):
     del scratch
 
     # evaluation: zero, previous-step and learned initial guesses
-    rec = {"zero": ([], []), "previous": ([], []), "net": ([], [])}
+    rec = {"zero": ([], []), "previous": ([], []), "extrapolated": ([], []), "net": ([], [])}
     infer_ms = []
-    r0 = {"previous": [], "net": []}                      # initial relative residuals
+    r0 = {"previous": [], "extrapolated": [], "net": []}  # initial relative residuals
     shp = (nz, ny, nx)
 
     def rel_res(b32, guess32):
@@ -353,27 +354,32 @@ def warmstart_bench(args):
         return float(np.sqrt(rr)) / float(torch.linalg.vector_norm(b32.double()).item())
     zero64 = torch.zeros(cells, dtype=torch.float64, device=dev)
     prev64, _, _ = solve(f32(eval_rhs[0]).double(), zero64)
+    prev2_64 = None
     for b in eval_rhs[1:]:
         b32 = f32(b)
         b64 = b32.double()
         pz, cz, tz = solve(b64, zero64)
         _, cp, tp = solve(b64, prev64)
-        prev32 = prev64.float()
+        # linear extrapolation in time, 2 p_{t-1} - p_{t-2} (the previous step at t = 1)
+        ex64 = prev64 if prev2_64 is None else 2.0 * prev64 - prev2_64
+        _, ce, te = solve(b64, ex64)
+        base32 = (prev64 if args.base == "previous" else ex64).float()
         torch.cuda.synchronize()
         ev0.record()
-        guess = net.infer(b32, *coef, prev32)
+        guess = net.infer(b32, *coef, base32)
         g64 = guess.double()
         ev1.record()
         torch.cuda.synchronize()
         ti = ev0.elapsed_time(ev1)
         _, cn, tn = solve(b64, g64)
-        r0["previous"].append(rel_res(b32, prev32))
+        r0["previous"].append(rel_res(b32, prev64.float()))
+        r0["extrapolated"].append(rel_res(b32, ex64.float()))
         r0["net"].append(rel_res(b32, guess))
-        for k, c, t in (("zero", cz, tz), ("previous", cp, tp), ("net", cn, tn + ti)):
+        for k, c, t in (("zero", cz, tz), ("previous", cp, tp), ("extrapolated", ce, te), ("net", cn, tn + ti)):
             rec[k][0].append(c)
             rec[k][1].append(t)
         infer_ms.append(ti)
-        prev64 = pz
+        prev2_64, prev64 = prev64, pz
     solver.close()
     mean = lambda v: float(np.mean(v))
     gflop = net_forward_flops(cells) / 1e9
@@ -386,7 +392,7 @@ def warmstart_bench(args):
             "initial_rel_residual_geomean": {k: float(np.exp(np.mean(np.log(v)))) for k, v in r0.items()},
             "cycles_hist": {k: {str(c): int(n) for c, n in zip(*np.unique(v[0], return_counts=True))}
                             for k, v in rec.items()},
-            "train": {"loss": args.loss, "seeds": train_seeds, "frames_per_seed": args.train_frames, "samples": len(samples),
+            "train": {"loss": args.loss, "base": args.base, "seeds": train_seeds, "frames_per_seed": args.train_frames, "samples": len(samples),
                       "epochs": args.epochs, "steps": steps, "lr": args.lr, "seconds": train_s,
                       "loss_mean_after": mean(losses), "loss_mean_previous_guess": mean(losses_prev),
                       "ms_per_step": train_ms},
@@ -507,6 +513,37 @@ def suite(args):
     return 0
 
 
+def net_forward(args):
+    """Forward passes of the warm-start network on a 192 x 64 x 64 grid of random
+    inputs (for timing and profiler captures of its convolutions)."""
+    import torch
+    from paper_2607_07687_gb300 import build as B
+    B.build()
+    from paper_2607_07687_gb300.warmstart import WarmStartNet
+    torch.cuda.set_device(0)
+    dims = (192, 64, 64)
+    n = dims[0] * dims[1] * dims[2]
+    net = WarmStartNet(dims, seed=0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    b = torch.randn(n, device="cuda", generator=g)
+    coef = [torch.rand(n, device="cuda", generator=g) for _ in range(3)]
+    pp = torch.randn(n, device="cuda", generator=g)
+    net.pack(b, *coef, pp)
+    for _ in range(3):
+        net.forward()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        net.forward()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    gflop = net_forward_flops(n) / 1e9
+    print(json.dumps({"net_forward_ms": ms, "gflop": gflop, "tflops": gflop / ms, "grid": list(dims)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,6 +556,7 @@ def main():
     ap.add_argument("--grid", default="512,256,128", help="nx,ny,nz of the --kernel grid")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--walls", action="store_true", help="--kernel grid with walls instead of periodic axes")
+    ap.add_argument("--net", action="store_true", help="time --reps forward passes of the warm-start network")
     ap.add_argument("--suite", action="store_true",
                     help="time to tolerance of every solver form on the paper-shaped workloads")
     ap.add_argument("--no-large", action="store_true", help="--suite without the 512^3 cube")
@@ -529,6 +567,8 @@ def main():
     ap.add_argument("--train-frames", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--base", choices=["previous", "extrapolated"], default="extrapolated",
+                    help="guess the warm-start net corrects (its p_prev input and skip)")
     ap.add_argument("--loss", choices=["mse", "residual"], default="residual",
                     help="warm-start training loss: MSE against the converged pressure or the relative residual")
     args = ap.parse_args()
@@ -538,6 +578,8 @@ def main():
         return warmstart_bench(args)
     if args.suite:
         return suite(args)
+    if args.net:
+        return net_forward(args)
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return reference_arm(args)

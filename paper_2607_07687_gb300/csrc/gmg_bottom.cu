@@ -27,7 +27,7 @@ using namespace dev;
 struct LevelView {
     Geo g;
     int n;
-    double inv_nx, inv_nxy;
+    float inv_nx, inv_nxy;
     float* p;
     float* b;
     float* x;   // lower faces, walls zeroed
@@ -35,17 +35,26 @@ struct LevelView {
     float* z;
 };
 
-// cell index -> (x, y, z) without integer division.  (i + 1/2) / d lies at
-// least 1/(2d) from the nearest integer, while the FP64 product with the
-// rounded reciprocal is off by at most about 2^-52 (i + 1) / d; for i, d below
-// 2^20 (a bottom level has at most kBottomMaxCells cells) that is far smaller,
-// so the truncation is the exact quotient.
+// i / d for 0 <= i < 2^23: an FP32 estimate (FP64 runs at 1/64 of the FP32 rate
+// on this part) corrected by one step.  The estimate's absolute error is below
+// (i + 1/2) / d * 2^-23 < 1, so it is the quotient or off by one, and the
+// remainder's sign and size tell which.
+__device__ __forceinline__ int quot(int i, int d, float inv_d)
+{
+    int q = (int)(((float)i + 0.5f) * inv_d);
+    const int r = i - q * d;
+    if (r < 0) --q;
+    else if (r >= d) ++q;
+    return q;
+}
+
+// cell index -> (x, y, z) (a bottom level has at most kBottomMaxCells cells)
 __device__ __forceinline__ void decode(const LevelView& L, int i, int& x, int& y, int& z)
 {
     const int nx = L.g.n[0], nxy = L.g.n[0] * L.g.n[1];
-    z = (int)(((double)i + 0.5) * L.inv_nxy);
+    z = quot(i, nxy, L.inv_nxy);
     const int r = i - z * nxy;
-    y = (int)(((double)r + 0.5) * L.inv_nx);
+    y = quot(r, nx, L.inv_nx);
     x = r - y * nx;
 }
 

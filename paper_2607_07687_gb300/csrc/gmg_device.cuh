@@ -114,5 +114,23 @@ __device__ __forceinline__ double block_sum(double v, double* red)
     return s;
 }
 
+// Sum of r * r over the block, result valid in thread 0: FP32 within each warp (a
+// fixed five-level tree of 32 non-negative terms, relative error below 5 * 2^-24),
+// FP64 across warps.  FP64 arithmetic runs at 1/64 of the FP32 rate on this part,
+// so a per-cell FP64 reduction would bound a memory-bound kernel.
+__device__ __forceinline__ double block_sum_sq(float r, double* red)
+{
+    float v = r * r;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
 }  // namespace dev
 }  // namespace gmg

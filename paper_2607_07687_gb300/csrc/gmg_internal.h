@@ -141,6 +141,7 @@ struct LevelProjTask {
 // The bottom of the V-cycle (levels lb .. L-1 of one problem) in one CTA.
 constexpr int kBottomThreads = 512;
 constexpr int kBottomMaxCells = 10240;   // 5 floats per cell of shared memory: 200 KB
+static_assert(kBottomMaxCells < (1 << 23), "bottom cell indices are decoded with an FP32 estimate");
 
 struct BottomLevel {
     Geo g;
@@ -150,8 +151,8 @@ struct BottomLevel {
     const float* bz;
     int off;             // offset (floats) of the level's block in shared memory
     int walls_zeroed;    // 1: the stored faces already read 0 on walls (coarse levels)
-    double inv_nx;       // 1 / nx and 1 / (nx ny): cell index -> (x, y, z) by multiplication
-    double inv_nxy;
+    float inv_nx;        // 1 / nx and 1 / (nx ny): cell index -> (x, y, z) by multiplication
+    float inv_nxy;
 };
 
 template <class TP>

@@ -25,7 +25,9 @@
 //   k_project_*, k_gauge_*  right-hand-side projection, exit gauge.
 //
 // Reductions are deterministic: per-tile partials in FP64, summed in a fixed
-// order by one block per problem.
+// order by one block per problem.  Residual norms of the FP32 levels sum r^2 in
+// FP32 over a few cells per thread (or a warp) before the FP64 partial, because
+// FP64 arithmetic runs at 1/64 of the FP32 rate on this part.
 #include "gmg_internal.h"
 #include "gmg_device.cuh"
 
@@ -1083,7 +1085,14 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
         const int64_t cplane = (int64_t)gcx * gcy;
         const int64_t crow = (int64_t)(yb / c1) * gcx + xb / c0;
         const int nsteps = t.z1 - t.z0;
+        // r^2 is summed in FP32 over at most kNormFold planes (2 * kNormFold terms), then
+        // added into an FP64 total: FP64 arithmetic runs at 1/64 of the FP32 rate here, and
+        // one FP64 add per 2 * kNormFold cells keeps it off the critical path.  The FP32
+        // partial's relative error is below 2 * kNormFold * 2^-24 (< 1e-6).
+        constexpr int kNormFold = 8;
         double rr = 0.0;
+        float rr32 = 0.f;
+        int fold = kNormFold;
         float acc0 = 0.f, acc1 = 0.f;
         bool live = mbar_wait_live(&full[g % R], (g / R) & 1u, dead) &&
                     mbar_wait_live(&full[(g + 1) % R], ((g + 1) / R) & 1u, dead);
@@ -1117,7 +1126,12 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
                     const float r = B0[s] - fl;
                     if (h == 0) r0 = r; else r1 = (xb + 1 < nx) ? r : 0.f;
                 }
-                rr += (double)r0 * (double)r0 + (double)r1 * (double)r1;
+                rr32 = fmaf(r1, r1, fmaf(r0, r0, rr32));
+                if (--fold == 0) {
+                    rr += (double)rr32;
+                    rr32 = 0.f;
+                    fold = kNormFold;
+                }
             }
             // plane k-1 is no longer read
             __syncwarp();
@@ -1169,7 +1183,7 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
             return;
         }
         if (tp->partials) {
-            const double q = warp_sum(rr);
+            const double q = warp_sum(rr + (double)rr32);
             if (lane == 0) red[tid >> 5] = q;
             asm volatile("bar.sync 1, %0;\n" ::"n"(kResConsumers) : "memory");
             if (tid == 0) {
@@ -1268,7 +1282,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const __grid_constant__ T
             __syncthreads();
         }
         if (tp->partials) {
-            const double q = block_sum((double)r * (double)r, red);
+            const double q = block_sum_sq(r, red);
             if (threadIdx.x == 0) tp->partials[local] = q;
         }
     }
@@ -1553,7 +1567,7 @@ __global__ void k_control_init(const CtlTask* __restrict__ tasks)
             if (C.hist_cap >= 0) C.hist_res[0] = 0.0;
         } else {
             C.r_prev = sqrt(rr);
-            C.hist_res[0] = C.r_prev / C.bnorm;
+            C.hist_res[0] = C.r_prev * C.hist_scale;   // the same rounding as every later entry
             if (C.r_prev / C.bnorm <= C.tol) {
                 C.status = kOk;
                 C.done = 1;
@@ -1653,7 +1667,7 @@ __global__ void k_ir_begin_inner(Ctl* ctl, const double* __restrict__ part, int 
         const double prev = C.outer_r;
         C.outer_r = rn;
         if (C.total_cycles == 0 && C.hist_cap >= 0)
-            C.hist_res[0] = C.outer_bnorm > 0.0 ? rn / C.outer_bnorm : 0.0;
+            C.hist_res[0] = C.outer_bnorm > 0.0 ? rn * (1.0 / C.outer_bnorm) : 0.0;   // as hist_scale
         if (!(rn == rn)) {
             C.outer_status = kDiverged;
             C.done = 1;

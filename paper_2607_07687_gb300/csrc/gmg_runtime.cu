@@ -766,8 +766,8 @@ struct Engine {
                     B.bz = Lm.beta[2];
                     B.off = off;
                     B.walls_zeroed = lb + k > 0;   // coarse faces are built with walls read as 0
-                    B.inv_nx = 1.0 / Lm.g.n[0];
-                    B.inv_nxy = 1.0 / ((double)Lm.g.n[0] * Lm.g.n[1]);
+                    B.inv_nx = 1.0f / (float)Lm.g.n[0];
+                    B.inv_nxy = 1.0f / (float)(Lm.g.n[0] * Lm.g.n[1]);
                     off += 5 * (int)cells(Lm.g);
                 }
                 smem = std::max(smem, sizeof(float) * (size_t)off);

@@ -51,12 +51,17 @@ __device__ __forceinline__ float face_lo(const float* a, const Geo& g, int d, in
 // (lower/upper x, y, z).  Each difference of two nearby FP32 values is exact,
 // so the rounding error scales with the local differences rather than with
 // |p|; the form nb - diag * p would cancel and lose ~log2(|p| / |A p|) bits.
+// The roundings are spelled out (one product and one fused multiply-add per
+// axis, then two adds) so that no kernel's compiled contraction choices change
+// them: every kernel that evaluates the operator rounds identically.
 __device__ __forceinline__ float face_flux(float bxl, float pxl, float bxu, float pxu, float byl,
                                            float pyl, float byu, float pyu, float bzl, float pzl,
                                            float bzu, float pzu, float p)
 {
-    return ((bxl * (pxl - p) + bxu * (pxu - p)) + (byl * (pyl - p) + byu * (pyu - p))) +
-           (bzl * (pzl - p) + bzu * (pzu - p));
+    const float ax = __fmaf_rn(bxu, __fsub_rn(pxu, p), __fmul_rn(bxl, __fsub_rn(pxl, p)));
+    const float ay = __fmaf_rn(byu, __fsub_rn(pyu, p), __fmul_rn(byl, __fsub_rn(pyl, p)));
+    const float az = __fmaf_rn(bzu, __fsub_rn(pzu, p), __fmul_rn(bzl, __fsub_rn(pzl, p)));
+    return __fadd_rn(__fadd_rn(ax, ay), az);
 }
 
 __device__ __forceinline__ float diag_sum(float bxl, float bxu, float byl, float byu, float bzl,
@@ -73,7 +78,7 @@ __device__ __forceinline__ float diag_sum(float bxl, float bxu, float byl, float
 __device__ __forceinline__ float gs_update(float p, float flux, float dg, float b, float w)
 {
     if (!(dg > 0.f)) return p;
-    return p + w * __fdividef(flux - b, dg);
+    return __fmaf_rn(w, __fdividef(__fsub_rn(flux, b), dg), p);
 }
 
 template <class Task>

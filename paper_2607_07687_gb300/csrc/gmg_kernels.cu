@@ -245,18 +245,23 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
                  : "memory");
 }
 
+// One round of waiting: the thread may stay suspended (issuing nothing) until the
+// phase completes or about kSuspendNs have passed.
+constexpr uint32_t kSuspendNs = 500;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
+        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\n selp.u32 %0, 1, 0, q;\n}\n"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "n"(kSuspendNs)
         : "memory");
     return done != 0;
 }
 
-// false once kWaitTries rounds of try_wait (each may suspend the thread) have passed
+// false once kWaitTries rounds of try_wait (each may suspend the thread for up to
+// kSuspendNs: about two seconds in all) have passed
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 {
     for (int i = 0; i < kWaitTries; ++i)
@@ -602,6 +607,104 @@ __device__ __forceinline__ int wrap_plane(int z, int nz, int pz)
     return z;
 }
 
+// Producer warps of the warp-specialised sweeps: stream the planes z0 - 2 .. z1 + 1
+// of every tile of this block (p, b and the three face arrays) into the ring of
+// R plane slots.  Group g, the g-th plane streamed, lands in slot g mod R and
+// completes on full[g mod R] (TMA boxes with zero fill when the tile's box needs
+// no periodic wrap in x or y, else 16-byte asynchronous copies of the producers'
+// lanes), once the consumers have released the slot's previous group on empty[].
+// pt: producer thread 0 .. kProducers - 1.
+template <class TC>
+__device__ __forceinline__ void sweep_produce(const TaskList<SweepTask<float, TC>>& tl, float* smem, uint64_t* full,
+                                              uint64_t* empty, volatile int* dead, int pt)
+{
+    constexpr int TX = kSweepTX, TY = kSweepTY;
+    constexpr int XO = 4, SW = TX + 8, PL = SW * (TY + 4);
+    constexpr int R = kSweepRing;
+    constexpr int CPR = SW / 4, NCH = PL / 4;
+    const int lane = pt & 31;
+    auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
+    uint32_t g = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < tl.total && ok; tile += gridDim.x) {
+        int local;
+        const SweepTask<float, TC>* tp = task_of(tl, tile, local);
+        if (tp->ctl && tp->ctl->done) continue;
+        const int nx = tp->g.n[0], ny = tp->g.n[1], nz = tp->g.n[2];
+        const int px = tp->g.per[0], py = tp->g.per[1], pz = tp->g.per[2];
+        const int cx = local % tp->tiles_x, rest = local / tp->tiles_x;
+        const int x0 = cx * TX, y0 = (rest % tp->tiles_y) * TY, z0 = (rest / tp->tiles_y) * tp->zchunk;
+        const int z1 = min(nz, z0 + tp->zchunk);
+        const int rot = tp->rot ? *tp->rot : 0;
+        const int pidx = tp->in_role < 0 ? 0 : (tp->in_role + rot) % 3;
+        const float* pin = tp->in_role < 0 ? nullptr : tp->buf[pidx];
+        const TmaPlanes* tm = tp->tma;
+        const bool use_tma = tm != nullptr && pin != nullptr && !(px && (x0 - XO < 0 || x0 + TX + XO > nx)) &&
+                             !(py && (y0 - 2 < 0 || y0 + TY + 2 > ny));
+        const float* src[5] = {pin, tp->b, tp->bx, tp->by, tp->bz};
+        const int64_t plane = (int64_t)nx * ny;
+        constexpr int CPL = (NCH + kProducers - 1) / kProducers;
+        int coff[CPL];
+        bool cok[CPL];
+        if (!use_tma) {
+#pragma unroll
+            for (int i = 0; i < CPL; ++i) {
+                const int c = pt + kProducers * i;
+                const int sy = c / CPR, ch = c - sy * CPR;
+                int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
+                cok[i] = c < NCH && wrapc(x, nx, px) && wrapc(y, ny, py);
+                coff[i] = cok[i] ? y * nx + x : 0;
+            }
+        }
+        const int nh = (z1 - z0) + 4;                      // planes z0-2 .. z1+1
+        for (int m = 0; m < nh; ++m, ++g) {
+            if (g >= (uint32_t)R && !mbar_wait_live(&empty[g % R], ((g / R) - 1) & 1u, dead)) {
+                ok = false;
+                break;
+            }
+            uint64_t* bar = &full[g % R];
+            const int z = z0 - 2 + m;
+            if (use_tma) {
+                if (pt == 32) mbar_arrive(bar);            // the second producer warp's arrival
+                if (pt == 0) {
+                    const int zw = wrap_plane(z, nz, pz);
+                    mbar_expect_tx(bar, 5 * kPlaneBytes);
+                    tma_plane(ring(0, g), &tm->p[pidx], x0 - XO, y0 - 2, zw, bar);
+                    tma_plane(ring(1, g), &tm->b, x0 - XO, y0 - 2, zw, bar);
+                    tma_plane(ring(2, g), &tm->x, x0 - XO, y0 - 2, zw, bar);
+                    tma_plane(ring(3, g), &tm->y, x0 - XO, y0 - 2, zw, bar);
+                    tma_plane(ring(4, g), &tm->z, x0 - XO, y0 - 2, zw, bar);
+                }
+            } else {
+                int zw = z;
+                const bool zok = wrapc(zw, nz, pz);
+                const int64_t zoff = (int64_t)zw * plane;
+#pragma unroll
+                for (int i = 0; i < CPL; ++i) {
+                    const int c = pt + kProducers * i;
+                    if (c < NCH) {
+#pragma unroll
+                        for (int a = 0; a < 5; ++a) {
+                            const bool okc = zok && cok[i] && src[a] != nullptr;
+                            cp_async16(ring(a, g) + 4 * c, okc ? src[a] + zoff + coff[i] : tp->b, okc);
+                        }
+                    }
+                }
+                cp_async_mbar_arrive(bar);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar);
+            }
+        }
+    }
+    if (!ok) {
+        if (lane == 0) {
+            atomicExch(&g_wait_fault, 1);
+            *dead = 1;
+        }
+        for (uint32_t q = g > (uint32_t)R ? g - R : 0; q < g; ++q) mbar_wait(&full[q % R], (q / R) & 1u);
+    }
+}
+
 // ---------------------------------------------------------------- K1: warp-specialised sweep
 //
 // The pipelined sweep (same arithmetic as k_sweep_async, bit-identical) with two
@@ -652,87 +755,7 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
     auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
 
     if (tid >= kSweepConsumers) {
-        // ------------------------------------------------ producer warps
-        const int pt = tid - kSweepConsumers;                 // producer thread 0 .. kProducers-1
-        uint32_t g = 0;
-        bool ok = true;
-        for (int tile = blockIdx.x; tile < tl.total && ok; tile += gridDim.x) {
-            int local;
-            const SweepTask<float, TC>* tp = task_of(tl, tile, local);
-            if (tp->ctl && tp->ctl->done) continue;
-            const int nx = tp->g.n[0], ny = tp->g.n[1], nz = tp->g.n[2];
-            const int px = tp->g.per[0], py = tp->g.per[1], pz = tp->g.per[2];
-            const int cx = local % tp->tiles_x, rest = local / tp->tiles_x;
-            const int x0 = cx * TX, y0 = (rest % tp->tiles_y) * TY, z0 = (rest / tp->tiles_y) * tp->zchunk;
-            const int z1 = min(nz, z0 + tp->zchunk);
-            const int rot = tp->rot ? *tp->rot : 0;
-            const int pidx = tp->in_role < 0 ? 0 : (tp->in_role + rot) % 3;
-            const float* pin = tp->in_role < 0 ? nullptr : tp->buf[pidx];
-            const TmaPlanes* tm = tp->tma;
-            const bool use_tma = tm != nullptr && pin != nullptr && !(px && (x0 - XO < 0 || x0 + TX + XO > nx)) &&
-                                 !(py && (y0 - 2 < 0 || y0 + TY + 2 > ny));
-            const float* src[5] = {pin, tp->b, tp->bx, tp->by, tp->bz};
-            const int64_t plane = (int64_t)nx * ny;
-            constexpr int CPL = (NCH + kProducers - 1) / kProducers;
-            int coff[CPL];
-            bool cok[CPL];
-            if (!use_tma) {
-#pragma unroll
-                for (int i = 0; i < CPL; ++i) {
-                    const int c = pt + kProducers * i;
-                    const int sy = c / CPR, ch = c - sy * CPR;
-                    int x = x0 - XO + 4 * ch, y = y0 - 2 + sy;
-                    cok[i] = c < NCH && wrapc(x, nx, px) && wrapc(y, ny, py);
-                    coff[i] = cok[i] ? y * nx + x : 0;
-                }
-            }
-            const int nh = (z1 - z0) + 4;                      // planes z0-2 .. z1+1
-            for (int m = 0; m < nh; ++m, ++g) {
-                if (g >= (uint32_t)R && !mbar_wait_live(&empty[g % R], ((g / R) - 1) & 1u, dead)) {
-                    ok = false;
-                    break;
-                }
-                uint64_t* bar = &full[g % R];
-                const int z = z0 - 2 + m;
-                if (use_tma) {
-                    if (pt == 32) mbar_arrive(bar);            // the second producer warp's arrival
-                    if (pt == 0) {
-                        const int zw = wrap_plane(z, nz, pz);
-                        mbar_expect_tx(bar, 5 * kPlaneBytes);
-                        tma_plane(ring(0, g), &tm->p[pidx], x0 - XO, y0 - 2, zw, bar);
-                        tma_plane(ring(1, g), &tm->b, x0 - XO, y0 - 2, zw, bar);
-                        tma_plane(ring(2, g), &tm->x, x0 - XO, y0 - 2, zw, bar);
-                        tma_plane(ring(3, g), &tm->y, x0 - XO, y0 - 2, zw, bar);
-                        tma_plane(ring(4, g), &tm->z, x0 - XO, y0 - 2, zw, bar);
-                    }
-                } else {
-                    int zw = z;
-                    const bool zok = wrapc(zw, nz, pz);
-                    const int64_t zoff = (int64_t)zw * plane;
-#pragma unroll
-                    for (int i = 0; i < CPL; ++i) {
-                        const int c = pt + kProducers * i;
-                        if (c < NCH) {
-#pragma unroll
-                            for (int a = 0; a < 5; ++a) {
-                                const bool okc = zok && cok[i] && src[a] != nullptr;
-                                cp_async16(ring(a, g) + 4 * c, okc ? src[a] + zoff + coff[i] : tp->b, okc);
-                            }
-                        }
-                    }
-                    cp_async_mbar_arrive(bar);
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(bar);
-                }
-            }
-        }
-        if (!ok) {
-            if (lane == 0) {
-                atomicExch(&g_wait_fault, 1);
-                s_dead = 1;
-            }
-            for (uint32_t q = g > (uint32_t)R ? g - R : 0; q < g; ++q) mbar_wait(&full[q % R], (q / R) & 1u);
-        }
+        sweep_produce<TC>(tl, smem, full, empty, dead, tid - kSweepConsumers);
         return;
     }
 

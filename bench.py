@@ -556,6 +556,9 @@ def main():
     ap.add_argument("--grid", default="512,256,128", help="nx,ny,nz of the --kernel grid")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--walls", action="store_true", help="--kernel grid with walls instead of periodic axes")
+    ap.add_argument("--tune-file", default=None,
+                    help="autotuner table: loaded when the file exists (no timing of launch shapes), "
+                         "else written after the run; a profiler run then launches what a plain run tuned")
     ap.add_argument("--net", action="store_true", help="time --reps forward passes of the warm-start network")
     ap.add_argument("--suite", action="store_true",
                     help="time to tolerance of every solver form on the paper-shaped workloads")
@@ -598,6 +601,11 @@ def main():
     from paper_2607_07687_gb300 import build as B
     B.build()
     from paper_2607_07687_gb300 import binding as G
+
+    tune_loaded = False
+    if args.tune_file and os.path.exists(args.tune_file):
+        G.tune_import(open(args.tune_file).read())     # the launch shapes of an earlier run
+        tune_loaded = True
 
     prob = workload()       # replicas only: every rank solves its own copy
     cells = prob.cells
@@ -714,6 +722,10 @@ def main():
                                 "sample": f"one full FP64 oracle solve of the workload to {TOL} "
                                           f"({res.cycles} V-cycles, {dt:.1f} s)"}
     solver.close()
+    if args.tune_file and not tune_loaded and rank == 0:
+        with open(args.tune_file, "w") as f:
+            f.write(G.tune_export())
+    line["config"]["tuning"] = "loaded from an earlier run" if tune_loaded else "timed in this run"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

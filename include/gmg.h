@@ -143,6 +143,29 @@ int gmg_destroy(gmg_handle h);
 /* Message of the last error on this handle (or of the last failed create when h is NULL). */
 const char* gmg_last_error(gmg_handle h);
 
+/*
+ * The autotuner's results, process-wide (no counterpart in the paper: launch
+ * shapes are a property of this implementation).  gmg_set_coeffs with
+ * autotune = 1 times the z-chunk depth of each pipelined kernel per level
+ * geometry and where the one-CTA bottom of a single problem starts, and keeps
+ * them in a table that later handles of the same shapes reuse without timing.
+ *
+ * gmg_tune_export writes the table as text: one line per entry,
+ *   "z kind nx ny nz px py pz zchunk"   (kind 0 sweep, 1 sweep with correction,
+ *                                        2 residual)
+ *   "b nx ny nz px py pz coarsen n_min precision nu_c level"
+ * into buf (host, capacity cap bytes, NUL-terminated) and its length without
+ * the NUL into *len.  buf == NULL only reports the length.  GMG_ERR_ARG when
+ * cap is too small (nothing written).
+ *
+ * gmg_tune_import merges such text into the table (entries of the same key
+ * are replaced), so that a later process reuses an earlier one's launch
+ * shapes: same shapes, same launches, same results bit for bit.  GMG_ERR_ARG,
+ * with the table unchanged, on a malformed line.  Neither call touches the GPU.
+ */
+int gmg_tune_export(char* buf, size_t cap, size_t* len);
+int gmg_tune_import(const char* text);
+
 /* ----------------------------------------------------------------------------
  * Batched solves: many independent problems of uneven sizes, one launch per
  * multigrid phase for all of them (levels of equal depth are smoothed,

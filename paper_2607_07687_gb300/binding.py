@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.gmg_op_coarsen_coeffs.argtypes = [c_int, c_int, c_int, ip, ip, vp, vp, vp, vp, vp, vp, vp]
     L.gmg_op_residual_norm.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
     L.gmg_op_residual_norm_noalloc.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
+    L.gmg_tune_export.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.gmg_tune_import.argtypes = [ctypes.c_char_p]
     _net_signatures(L)
     _lib = L
     return L
@@ -135,6 +137,24 @@ def declared_functions() -> List[str]:
         text = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
         names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(gmg_\w+)\s*\(", text, flags=re.M))
     return sorted(names)
+
+
+def tune_export() -> str:
+    """The autotuner's table (launch shapes per level geometry) as text (gmg_tune_export)."""
+    L = lib()
+    n = ctypes.c_size_t(0)
+    if L.gmg_tune_export(None, 0, ctypes.byref(n)) != OK:
+        raise GmgError("gmg_tune_export failed")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    if L.gmg_tune_export(buf, n.value + 1, ctypes.byref(n)) != OK:
+        raise GmgError("gmg_tune_export failed")
+    return buf.value.decode()
+
+
+def tune_import(text: str) -> None:
+    """Merge an exported tuning table into this process's (gmg_tune_import)."""
+    if lib().gmg_tune_import(text.encode()) != OK:
+        raise GmgError("gmg_tune_import: malformed tuning table")
 
 
 def options(coarsen: str = "aniso", precision: str = "fp32", **kw) -> Options:

@@ -24,6 +24,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -1721,6 +1722,63 @@ const char* gmg_last_error(gmg_handle h)
 {
     if (!h) return g_create_error.c_str();
     return h->eng.err.c_str();
+}
+
+// ---------------------------------------------------------------- tuning table
+
+int gmg_tune_export(char* buf, size_t cap, size_t* len)
+{
+    std::string t;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (const auto& kv : g_tuned_zchunk) {
+            const TuneKey& k = kv.first;
+            t += "z " + std::to_string(k.kind) + " " + std::to_string(k.n0) + " " + std::to_string(k.n1) + " " +
+                 std::to_string(k.n2) + " " + std::to_string(k.p0) + " " + std::to_string(k.p1) + " " +
+                 std::to_string(k.p2) + " " + std::to_string(kv.second) + "\n";
+        }
+        for (const auto& kv : g_tuned_lb) {
+            t += "b";
+            for (int v : kv.first) t += " " + std::to_string(v);
+            t += " " + std::to_string(kv.second) + "\n";
+        }
+    }
+    if (len) *len = t.size();
+    if (!buf) return GMG_OK;
+    if (cap < t.size() + 1) return GMG_ERR_ARG;
+    std::memcpy(buf, t.c_str(), t.size() + 1);
+    return GMG_OK;
+}
+
+int gmg_tune_import(const char* text)
+{
+    if (!text) return GMG_ERR_ARG;
+    std::map<TuneKey, int> zs;
+    std::map<std::vector<int>, int> bs;
+    std::istringstream in(text);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        std::string tag;
+        if (!(ls >> tag)) continue;                     // blank line
+        std::vector<long> v;
+        long x;
+        while (ls >> x) v.push_back(x);
+        if (!ls.eof()) return GMG_ERR_ARG;              // a token that is not an integer
+        for (long a : v)
+            if (a < 0 || a > (1L << 30)) return GMG_ERR_ARG;
+        if (tag == "z" && v.size() == 8 && v[7] > 0) {
+            zs[TuneKey{(int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5], (int)v[6]}] = (int)v[7];
+        } else if (tag == "b" && v.size() == 11 && v[10] > 0) {
+            bs[std::vector<int>(v.begin(), v.begin() + 10)] = (int)v[10];
+        } else {
+            return GMG_ERR_ARG;
+        }
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (const auto& kv : zs) g_tuned_zchunk[kv.first] = kv.second;
+    for (const auto& kv : bs) g_tuned_lb[kv.first] = kv.second;
+    return GMG_OK;
 }
 
 // ---------------------------------------------------------------- batch

@@ -86,3 +86,32 @@ def test_ops_reject_bad_arguments(L):
     assert L.gmg_op_residual_norm(8, 8, 8, per, fake, fake, fake, fake, fake, None, None) == G.ERR_ARG
     assert L.gmg_op_residual_restrict(8, 8, 8, per, G._ivec((2, 2, 2)), fake, fake, fake, fake, fake,
                                       None, None, None) == G.ERR_ARG
+
+
+def test_tune_table_round_trip(L):
+    """The autotuner's table exports as text and imports back unchanged (no GPU involved)."""
+    text = ("z 0 256 96 96 0 0 0 8\n"
+            "z 2 128 48 48 0 0 0 12\n"
+            "b 256 96 96 0 0 0 1 4 0 16 3\n")
+    G.tune_import(text)
+    out = G.tune_export()
+    for line in text.splitlines():
+        assert line in out.splitlines()
+    # a replaced entry keeps one line per key
+    G.tune_import("z 0 256 96 96 0 0 0 16\n")
+    lines = G.tune_export().splitlines()
+    assert "z 0 256 96 96 0 0 0 16" in lines and "z 0 256 96 96 0 0 0 8" not in lines
+    # too small a buffer is refused and reports the length
+    n = ctypes.c_size_t(0)
+    buf = ctypes.create_string_buffer(4)
+    assert L.gmg_tune_export(buf, 4, ctypes.byref(n)) == G.ERR_ARG
+    assert n.value == len(G.tune_export())
+
+
+@pytest.mark.parametrize("bad", ["z 0 1 2\n", "q 1 2 3\n", "z 0 8 8 8 0 0 0 x\n", "b 1 2 3\n", "z 0 8 8 8 0 0 0 -4\n",
+                                 "z 0 8 8 8 0 0 0 0\n"])
+def test_tune_import_rejects_malformed(L, bad):
+    before = G.tune_export()
+    with pytest.raises(G.GmgError):
+        G.tune_import("z 1 64 64 64 0 0 0 4\n" + bad)
+    assert G.tune_export() == before              # nothing merged from a rejected table

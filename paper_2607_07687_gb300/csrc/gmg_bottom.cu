@@ -128,16 +128,38 @@ struct CellWalk {
     }
 };
 
-// nu red-black sweeps of one level, every thread of the block
+// nu red-black sweeps of one level, every thread of the block.  A half-sweep walks
+// only the cells of its colour: cell j of row (y, z) in the half-index space is
+// x = 2j + ((colour + y + z) & 1) (x = nx is skipped when nx is odd).  Cells of one
+// colour are independent, so the order of the walk does not change the result.
 __device__ void sweeps(const LevelView& L, int count, float w)
 {
+    const int nx = L.g.n[0], ny = L.g.n[1], nz = L.g.n[2];
+    const int hx = (nx + 1) >> 1;
+    const int nh = hx * ny * nz;
+    const int step = blockDim.x;
+    // start (j, y, z) of this thread and the stride (dj, dy, dz), by carries afterwards
+    const int j0 = threadIdx.x % hx, r0 = threadIdx.x / hx;
+    const int dj = step % hx, dr = step / hx;
+    const int y0 = r0 % ny, z0 = r0 / ny, dy = dr % ny, dz = dr / ny;
     for (int it = 0; it < count; ++it)
         for (int colour = 0; colour < 2; ++colour) {
-            for (CellWalk c(L, threadIdx.x, blockDim.x); c.i < L.n; c.next(L.g, blockDim.x)) {
-                if (((c.x + c.y + c.z) & 1) != colour) continue;
-                float dg;
-                const float fl = flux_xyz(L, c.i, c.x, c.y, c.z, dg);
-                L.p[c.i] = gs_update(L.p[c.i], fl, dg, L.b[c.i], w);
+            int j = j0, y = y0, z = z0;
+            for (int t = threadIdx.x; t < nh; t += step) {
+                const int x = 2 * j + ((colour + y + z) & 1);
+                if (x < nx) {
+                    const int i = (z * ny + y) * nx + x;
+                    float dg;
+                    const float fl = flux_xyz(L, i, x, y, z, dg);
+                    L.p[i] = gs_update(L.p[i], fl, dg, L.b[i], w);
+                }
+                j += dj;
+                int cy = 0;
+                if (j >= hx) { j -= hx; cy = 1; }
+                y += dy + cy;
+                int cz = 0;
+                if (y >= ny) { y -= ny; cz = 1; }
+                z += dz + cz;
             }
             __syncthreads();
         }
@@ -189,7 +211,16 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
     __shared__ double red[kBottomThreads / 32];
     __shared__ double red2[kBottomThreads / 32];
     __shared__ double s_mean;
-    const BottomTask<TP>& T = tasks[blockIdx.x];
+    // the task (level geometries, offsets, sweep counts) in shared memory: the level
+    // views are rebuilt before every phase
+    __shared__ __align__(16) BottomTask<TP> T;
+    static_assert(sizeof(BottomTask<TP>) % 4 == 0, "task copied in words");
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(tasks + blockIdx.x);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
+        for (int k = threadIdx.x; k < (int)(sizeof(BottomTask<TP>) / 4); k += blockDim.x) dst[k] = __ldg(src + k);
+        __syncthreads();
+    }
     if (T.ctl && T.ctl->done) return;
     const int nlev = T.nlev;
     const float w = T.ctl ? (float)T.ctl->omega : 1.0f;

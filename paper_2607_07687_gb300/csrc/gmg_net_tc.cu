@@ -122,22 +122,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int nrow = 3 * WR;                                   // window rows (z, y)
     for (int s = 0; s < slices && ok; ++s) {
         const uint32_t par = (uint32_t)s & 1u;
-        // window: position p of window row (rz, ry), chunk c -> sA + c kChunkA + ((rz WR + ry) 130 + p) 16
-        for (int e = tid; e < 2 * nrow * 2; e += kTcThreads) {   // (chunk, row, half of the row's positions)
-            const int half = e & 1, rowc = e >> 1;
-            const int c = rowc / nrow, row = rowc - c * nrow;
-            const int rz = row / WR, ry = row - rz * WR;
-            const int gz = z0 - 1 + rz, gy = y0 - 1 + ry;
-            const bool rok = gz >= 0 && gz < D && gy >= 0 && gy < H;
-            const bf16* src = x + (((int64_t)(rok ? gz : 0) * H + (rok ? gy : 0)) * W) * cx + s * 16 + c * 8;
-            unsigned char* dst = sA + c * kChunkA + (size_t)row * kTcHX * 16;
-            for (int p = half; p < kTcHX; p += 2) {
-                const int gx = x0 - 1 + p;
-                const bool okp = rok && gx >= 0 && gx < W;
-                const unsigned sa = su32(dst + p * 16);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa),
-                             "l"(okp ? src + (int64_t)gx * cx : x), "r"(okp ? 16 : 0)
+        // window: position p of window row (rz, ry), chunk c -> sA + c kChunkA + ((rz WR + ry) 130 + p) 16.
+        // The 2 x nrow x 130 copies are spread evenly over the block: thread tid takes
+        // items tid, tid + 128, ... of the (row, position) sequence for both chunks,
+        // advancing (row, p) by carries.
+        {
+            int row = tid / kTcHX, p = tid - row * kTcHX;
+            constexpr int drow = kTcThreads / kTcHX, dp = kTcThreads % kTcHX;
+            for (; row < nrow;) {
+                const int rz = row / WR, ry = row - rz * WR;
+                const int gz = z0 - 1 + rz, gy = y0 - 1 + ry, gx = x0 - 1 + p;
+                const bool okp = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                const bf16* src = okp ? x + (((int64_t)gz * H + gy) * W + gx) * cx + s * 16 : x;
+                const unsigned sa = su32(sA + ((size_t)row * kTcHX + p) * 16);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(okp ? 16 : 0)
                              : "memory");
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa + kChunkA),
+                             "l"(okp ? src + 8 : x), "r"(okp ? 16 : 0)
+                             : "memory");
+                p += dp;
+                row += drow;
+                if (p >= kTcHX) {
+                    p -= kTcHX;
+                    ++row;
+                }
             }
         }
         // weights of the slice: [chunk][tap][o][8 channels]

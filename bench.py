@@ -7,7 +7,8 @@ seeded solenoidal source) with anisotropic coarsening: FP32 V-cycles with the
 adaptive under-relaxed red-black Gauss-Seidel smoother inside an FP64
 refinement loop (the FP32 storage floor of p on this workload is ~5e-6, above
 the 1e-6 target).  Inputs are resident in HBM; L2 (129 MB, larger than the
-~90 MB working set) is flushed with a 512 MB write before every timed step.
+~90 MB working set) is flushed with a 512 MB write (then read, so that no dirty
+lines are left to write back) before every timed step.
 
 value = fine cells x V-cycles / time to tolerance (Gcell-updates/s).
 roofline: the fused sweep kernel on the fine level, timed with CUDA events on
@@ -39,6 +40,14 @@ TOL = 1e-6
 DIMS = (256, 96, 96)
 BYTES_PER_CELL_SWEEP = 24          # read p, b, bx, by, bz; write p (FP32)
 L2_FLUSH_BYTES = 512 << 20
+
+
+def flush_l2(buf):
+    """Evict L2 before a timed launch: write a buffer four times its size, then read
+    it back.  The read leaves clean lines, so the timed kernel does not pay for
+    writing back the flush buffer's dirty lines when it evicts them."""
+    buf.fill_(1.0)
+    buf.sum()
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -50,7 +59,7 @@ def workload():
 def config(extra=None):
     c = {"workload": "sphere_channel_256x96x96_aniso", "grid": list(DIMS), "tol": TOL,
          "coarsening": "anisotropic, n_min 4", "cycle": "V(2,2), 16 coarsest sweeps",
-         "precision": "fp32 V-cycles, fp64 outer residual/update", "l2": "flushed (512 MB write) before every timed step",
+         "precision": "fp32 V-cycles, fp64 outer residual/update", "l2": "flushed (512 MB write, then read) before every timed step",
          "seed": 1}
     if extra:
         c.update(extra)
@@ -185,8 +194,9 @@ def reference_arm(args):
 
 def kernel_only(args):
     """Launch one kernel of the fine level --reps times on a grid of random
-    values (a small, bounded case for ncu); L2 is flushed (512 MB write) before
-    every launch, as for the roofline figure, and each launch is timed alone."""
+    values (a small, bounded case for ncu) after two untimed calls; L2 is flushed
+    (512 MB write, then read) before every launch, as for the roofline figure, and
+    each launch is timed alone."""
     import numpy as np
     import torch
     from paper_2607_07687_gb300 import build as B
@@ -202,20 +212,25 @@ def kernel_only(args):
     coarse = torch.zeros((nz // 2, ny // 2, nx // 2), device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     per = (False, False, False) if args.walls else (True, True, True)
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    total = 0.0
-    for i in range(args.reps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0.record()
+    def launch(i):
         if args.kernel == "sweep":
             G.op_sweep(*beta, b, pa if i % 2 == 0 else pb, pb if i % 2 == 0 else pa, 1.0, per)
         else:
             G.op_residual_restrict(*beta, b, pa, coarse, (2, 2, 2), per)
-        t1.record()
-        torch.cuda.synchronize()
-        total += t0.elapsed_time(t1)
-    ms = total / args.reps
+
+    for i in range(2):          # first calls: tensor maps encoded and cached, attributes set
+        launch(i)
+    torch.cuda.synchronize()
+    # the flush keeps the GPU busy while the host enqueues the launch, so the events
+    # bracket the kernel alone
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.reps)]
+    for i in range(args.reps):
+        flush_l2(flush)
+        ev[i][0].record()
+        launch(i)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in ev) / args.reps
     print(json.dumps({"kernel": args.kernel, "grid": [nx, ny, nz], "periodic": not args.walls, "reps": args.reps,
                       "ms_per_launch": ms, "l2": "flushed before each launch"}))
     return 0
@@ -627,7 +642,7 @@ def main():
             pg.barrier()
 
     for _ in range(args.warmup):
-        flush.fill_(1.0)
+        flush_l2(flush)
         info = step()
     barrier()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -635,7 +650,7 @@ def main():
     infos = []
     with Clocks(local) as clk:
         for i in range(args.steps):
-            flush.fill_(1.0)
+            flush_l2(flush)
             starts[i].record(stream)
             infos.append(step())
             ends[i].record(stream)
@@ -658,7 +673,7 @@ def main():
     barrier()
     t_e2e = []
     for _ in range(args.steps):
-        flush.fill_(1.0)
+        flush_l2(flush)
         torch.cuda.synchronize()
         p_h.zero_()
         t0 = time.perf_counter()
@@ -681,7 +696,7 @@ def main():
     reps = 20
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     for i in range(reps):
-        flush.fill_(1.0)
+        flush_l2(flush)
         ev[i][0].record(stream)
         G.op_sweep(*beta, b32, pa if i % 2 == 0 else pb, pb if i % 2 == 0 else pa, 1.0, prob.periodic)
         ev[i][1].record(stream)

@@ -46,6 +46,14 @@ typedef enum {
 
 enum { GMG_COARSEN_ISO = 0, GMG_COARSEN_ANISO = 1 };
 
+/*
+ * Precision modes.  The FP32 V-cycle levels sum squared residuals in FP32 over
+ * a few cells per thread before the FP64 tile partials, so their norms keep
+ * full relative precision while per-cell residuals lie between about 1e-19 and
+ * 1e19 (squares within FP32's normal range).  The IR modes scale the inner
+ * right-hand side to unit norm, and their outer FP64 residual is summed in
+ * FP64, so they have no such range limit.
+ */
 enum {
     GMG_FP32 = 0,       /* FP32 storage and arithmetic throughout */
     GMG_FP32_BF16 = 1,  /* FP32, with BF16 storage of the corrections on levels >= 1 */

@@ -1056,7 +1056,10 @@ struct Engine {
         // 1) z-chunk depth of each grid-kernel level, per kernel kind
         for (size_t p = 0; p < P.size(); ++p) {
             const ProblemMem& M = P[p];
-            for (int l = 0; l < stop_[p]; ++l) {
+            // a single problem may move the bottom's start down (step 2), which turns
+            // the levels above it into grid levels: tune every level but the coarsest
+            const int grid_levels = P.size() == 1 ? std::max(stop_[p], M.L - 1) : stop_[p];
+            for (int l = 0; l < grid_levels; ++l) {
                 if (l > 0 && bf16_coarse) continue;   // BF16 levels keep the heuristic depth
                 const Geo g = M.lev[l].g;
                 std::vector<int> cand;

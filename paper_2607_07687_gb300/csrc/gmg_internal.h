@@ -139,7 +139,7 @@ struct LevelProjTask {
 };
 
 // The bottom of the V-cycle (levels lb .. L-1 of one problem) in one CTA.
-constexpr int kBottomThreads = 512;
+constexpr int kBottomThreads = 1024;
 constexpr int kBottomMaxCells = 10240;   // 5 floats per cell of shared memory: 200 KB
 static_assert(kBottomMaxCells < (1 << 23), "bottom cell indices are decoded with an FP32 estimate");
 

@@ -268,3 +268,26 @@ def test_batch_fp64_refinement_equals_single():
         single, si, _ = gpu_solve(prob, 1e-6, autotune=0, precision="ir64_fp32")
         assert inf.cycles == si.cycles and inf.outer == si.outer
         assert np.array_equal(host(o), single)
+
+
+def test_tuning_table_import_is_used():
+    """The autotuner's table, edited and imported, decides the launch shapes of the next
+    handle of the same shape (no re-timing), and the solve still converges to the same answer."""
+    from paper_2607_07687_gb300 import binding as G
+    prob = problem(("sphere",))
+    a, ia, _ = gpu_solve(prob, 1e-5)
+    table = G.tune_export()
+    nx, ny, nz = prob.dims
+    fine = [ln for ln in table.splitlines() if ln.startswith("z ") and ln.split()[2:5] == [str(nx), str(ny), str(nz)]]
+    assert fine, table                      # the solve tuned its finest level
+    try:
+        edited = "\n".join(" ".join(ln.split()[:-1] + ["1"]) for ln in table.splitlines() if ln.startswith("z "))
+        G.tune_import(edited + "\n")
+        b, ib, _ = gpu_solve(prob, 1e-5)
+        after = G.tune_export().splitlines()
+        for ln in fine:
+            assert " ".join(ln.split()[:-1] + ["1"]) in after   # kept, not re-tuned
+        assert abs(ia.cycles - ib.cycles) <= 1
+        assert rel_l2(b, a) <= 1e-5
+    finally:
+        G.tune_import(table)

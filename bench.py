@@ -418,6 +418,54 @@ def warmstart_bench(args):
     return 0
 
 
+def fig2(args):
+    """Isotropic against anisotropic coarsening over domain aspect ratios (the
+    setting of the paper's Fig. 2, Sec. 3.2): V-cycles and time to 1e-6 from a
+    zero guess (an impulsive start has no earlier pressure) for the 2D flow past
+    a circular cylinder (64N x 64 x 1), a spanwise-periodic cylinder
+    (64N x 64 x 32, z periodic) and a sphere (64N x 64 x 64), N = 1, 2, 4, 8;
+    body radius 8 cells at x = 32; sources by the solenoidal-divergence recipe.
+    FP32 V-cycles inside FP64 refinement; one JSON line per geometry."""
+    import numpy as np
+    import torch
+    from paper_2607_07687_gb300 import build as B
+    B.build()
+    from paper_2607_07687_gb300 import binding as G
+    from paper_2607_07687_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    geoms = [("cylinder_2d", lambda n: I.cylinder_channel_problem(64 * n, 64, 1, 5, 8.0, 32.0)),
+             ("cylinder_spanwise_periodic", lambda n: I.cylinder_channel_problem(64 * n, 64, 32, 5, 8.0, 32.0, True)),
+             ("sphere", lambda n: I.sphere_channel_problem(64 * n, 64, 64, 1, 8.0, 32.0))]
+    for name, make in geoms:
+        rows = []
+        for n in (1, 2, 4, 8):
+            prob = make(n)
+            b = torch.from_numpy(np.asarray(prob.b, dtype=np.float32).astype(np.float64)).to(dev)
+            beta = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (prob.bx, prob.by, prob.bz)]
+            row = {"aspect_ratio": n, "dims": list(prob.dims)}
+            for coarsen in ("iso", "aniso"):
+                s = G.Solver(prob.dims, prob.periodic, precision="ir64_fp32", coarsen=coarsen, max_cycles=1000)
+                s.set_coeffs(*beta)
+                p = torch.zeros_like(b)
+                s.solve(b, p, TOL)                       # warm-up (graph capture)
+                p.zero_()
+                torch.cuda.synchronize()
+                ev0.record()
+                info = s.solve(b, p, TOL)
+                ev1.record()
+                torch.cuda.synchronize()
+                row[coarsen] = {"v_cycles": int(info.cycles), "levels": int(info.levels), "status": int(info.status),
+                                "ms": ev0.elapsed_time(ev1), "rel_res": float(info.rel_res)}
+                s.close()
+            row["cycle_ratio_iso_over_aniso"] = row["iso"]["v_cycles"] / max(1, row["aniso"]["v_cycles"])
+            rows.append(row)
+        print(json.dumps({"experiment": "iso vs aniso coarsening over aspect ratio", "geometry": name, "tol": TOL,
+                          "guess": "zero", "precision": "FP32 V-cycles in FP64 refinement", "rows": rows}), flush=True)
+    return 0
+
+
 def suite(args):
     """Time to tolerance of each solver form on the paper-shaped workloads
     (one JSON line per workload): the Taylor-Green cube 32^3 (FP32, 1e-6), the
@@ -575,6 +623,9 @@ def main():
                     help="autotuner table: loaded when the file exists (no timing of launch shapes), "
                          "else written after the run; a profiler run then launches what a plain run tuned")
     ap.add_argument("--net", action="store_true", help="time --reps forward passes of the warm-start network")
+    ap.add_argument("--fig2", action="store_true",
+                    help="iso vs aniso coarsening over aspect ratios 1-8: 2D cylinder, spanwise-periodic "
+                         "cylinder, sphere")
     ap.add_argument("--suite", action="store_true",
                     help="time to tolerance of every solver form on the paper-shaped workloads")
     ap.add_argument("--no-large", action="store_true", help="--suite without the 512^3 cube")
@@ -596,6 +647,8 @@ def main():
         return warmstart_bench(args)
     if args.suite:
         return suite(args)
+    if args.fig2:
+        return fig2(args)
     if args.net:
         return net_forward(args)
     args.warmup = max(3, args.warmup)

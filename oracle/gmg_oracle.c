@@ -27,7 +27,9 @@
  *                sum_f b_f = 0 are skipped.
  *   C3 schedule  aniso: axis d halves while n_d is even and n_d/2 >= n_min (on
  *                a periodic axis n_d/2 must stay even); iso: all axes halve
- *                together while every axis qualifies.
+ *                together while every axis qualifies.  An axis of length 1
+ *                (a 2D problem, Fig. 2) takes no part: it never halves, and
+ *                iso halves the other axes together.
  *   C4 coarse b  finite-volume rediscretisation: coarse face = (1/c_d) times
  *                the sum of the fine faces that make it up.
  *   C5 omega     w0 = 1; after each V-cycle rho = |r_k| / |r_prev|; rho < 1
@@ -219,9 +221,9 @@ static int schedule(const int n0[3], const int per[3], int aniso, int n_min, int
         for (int d = 0; d < 3; ++d) {
             h[d] = axis_halves(n[d], per[d], n_min);
             any |= h[d];
-            all &= h[d];
+            if (n[d] > 1) all &= h[d];   /* a length-1 axis is not part of the grid */
         }
-        if (aniso ? !any : !all) break;
+        if (!any || (!aniso && !all)) break;
         for (int d = 0; d < 3; ++d) {
             fac[L - 1][d] = h[d] ? 2 : 1;
             n[d] /= fac[L - 1][d];

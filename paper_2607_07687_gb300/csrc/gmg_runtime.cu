@@ -5,7 +5,8 @@
 // anisotropic coarsening) is planned once per handle:
 //   * the coarsening schedule (each axis halves while its length is even and
 //     length/2 >= n_min; a periodic axis also stays even; isotropic mode
-//     halves all axes together while all qualify);
+//     halves all axes together while all qualify, an axis of length 1 (a 2D
+//     problem) taking no part);
 //   * device buffers of every level and the coefficient hierarchy;
 //   * a fixed list of launches for one V-cycle (sweeps, residual+restriction,
 //     coarsest solve, prolongation folded into the first post-sweep, fine
@@ -115,9 +116,9 @@ int plan_levels(const Geo& g0, int aniso, int n_min, Geo* geo, int (*cf)[3])
         for (int d = 0; d < 3; ++d) {
             h[d] = axis_halves(g.n[d], g.per[d], n_min);
             any |= h[d];
-            all &= h[d];
+            if (g.n[d] > 1) all &= h[d];   // an axis of length 1 (a 2D problem) is not coarsened
         }
-        if (aniso ? !any : !all) break;
+        if (!any || (!aniso && !all)) break;
         for (int d = 0; d < 3; ++d) {
             cf[L - 1][d] = h[d] ? 2 : 1;
             g.n[d] /= cf[L - 1][d];

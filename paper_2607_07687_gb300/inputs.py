@@ -68,7 +68,7 @@ def taylor_green_rhs(n: int, seed: int, noise_var: float = 1e-2) -> np.ndarray:
 
 @dataclass
 class Body:
-    kind: str                      # "sphere" or "box"
+    kind: str                      # "sphere", "box" or "cylinder" (axis along z)
     center: Tuple[float, float, float]   # (x, y, z) in grid units
     r: float                       # radius (sphere) or half-width (box)
 
@@ -80,6 +80,8 @@ def _signed_distance(body: Body, x, y, z):
     if body.kind == "box":
         return np.maximum(np.maximum(np.abs(x - cx), np.abs(y - cy)),
                           np.abs(z - cz)) - body.r
+    if body.kind == "cylinder":
+        return np.sqrt((x - cx) ** 2 + (y - cy) ** 2) + 0.0 * z - body.r
     raise ValueError(f"unknown body kind {body.kind!r}")
 
 
@@ -155,6 +157,21 @@ class FourierPotential:
         waves = np.stack([cand[rng.choice(len(cand), modes, replace=False)]
                           for _ in range(3)])
         coef = rng.standard_normal((3, modes)) / math.sqrt(modes)
+        phase = rng.uniform(0.0, 2.0 * math.pi, (3, modes))
+        return FourierPotential(waves, coef, phase, amp)
+
+    @staticmethod
+    def draw_planar(rng: np.random.Generator, kmax: int = 4, modes: int = 8,
+                    amp: float = 0.1) -> "FourierPotential":
+        """A = (0, 0, A_z(x, y)): a velocity in the x-y plane with no z dependence
+        (the 2D flows of the paper's Fig. 2)."""
+        cand = [(a, b, 0) for a in range(-kmax, kmax + 1) for b in range(-kmax, kmax + 1)
+                if 0 < a * a + b * b <= kmax * kmax]
+        cand = np.array(cand, dtype=np.int64)
+        waves = np.stack([cand[rng.choice(len(cand), modes, replace=False)] for _ in range(3)])
+        coef = rng.standard_normal((3, modes)) / math.sqrt(modes)
+        coef[0] = 0.0
+        coef[1] = 0.0
         phase = rng.uniform(0.0, 2.0 * math.pi, (3, modes))
         return FourierPotential(waves, coef, phase, amp)
 
@@ -273,6 +290,26 @@ def sphere_channel_problem(nx: int = 256, ny: int = 96, nz: int = 96,
     bx, by, bz = apply_walls(*body_beta(shape, bodies))
     return Problem(shape, (False, False, False), b, bx, by, bz, bodies,
                    f"sphere_channel_{nx}x{ny}x{nz}")
+
+
+def cylinder_channel_problem(nx: int = 256, ny: int = 64, nz: int = 1, seed: int = 5,
+                             radius: float = 8.0, center_x: float = 48.0,
+                             periodic_z: bool = False, u_inf: float = 1.0) -> Problem:
+    """A circular cylinder (axis along z) in a channel walled in x and y.
+
+    nz = 1 is the 2D flow past a circle (planar potential, no z coupling);
+    periodic_z gives the spanwise-periodic cylinder, whose velocity varies along
+    the span.  The source is the solenoidal-divergence recipe of the sphere
+    channel with these bodies and potentials."""
+    shape = (nz, ny, nx)
+    periodic = (False, False, bool(periodic_z))
+    bodies = [Body("cylinder", (center_x, ny / 2.0, nz / 2.0), radius)]
+    rng = np.random.default_rng(seed)
+    pot = FourierPotential.draw_planar(rng) if nz == 1 else FourierPotential.draw(rng)
+    b = solenoidal_rhs(shape, bodies, pot, u_inf)
+    bx, by, bz = apply_walls(*body_beta(shape, bodies), periodic=periodic)
+    kind = "2d" if nz == 1 else ("spanwise_periodic" if periodic_z else "walled")
+    return Problem(shape, periodic, b, bx, by, bz, bodies, f"cylinder_{kind}_{nx}x{ny}x{nz}")
 
 
 def random_bodies(rng: np.random.Generator, dims, count: int) -> List[Body]:

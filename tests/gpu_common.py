@@ -71,6 +71,8 @@ def problem(key):
         return I.taylor_green_problem(*args)
     if name == "sphere":
         return I.sphere_channel_problem(*args)
+    if name == "cyl":
+        return I.cylinder_channel_problem(*args)
     raise KeyError(name)
 
 

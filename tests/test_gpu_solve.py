@@ -75,6 +75,37 @@ def test_sphere_channel_fp32_iso(O):
     _parity(got, info, ref, same=_same(O, prob, coarsen="iso"))
 
 
+def _refined_parity(O, key, coarsen, tol=1e-6):
+    """FP64 refinement around FP32 V-cycles to tol; cycles within 2 of the oracle's
+    and the solution against its iterate after the same number of cycles."""
+    prob = problem(key)
+    ref = oracle_cached(key, tol, coarsen=coarsen)
+    got, info, _ = gpu_solve(prob, tol, coarsen=coarsen, precision="ir64_fp32")
+    assert info.status == 0 and info.rel_res <= tol, info.as_dict()
+    assert info.levels == ref.levels
+    assert abs(info.cycles - ref.cycles) <= 2, (info.cycles, ref.cycles)
+    same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles,
+                                                                  coarsen=coarsen)
+    assert rel_l2(got, same.p) <= 1e-5
+    return info
+
+
+@pytest.mark.parametrize("coarsen,levels", [("iso", 5), ("aniso", 7)])
+def test_cylinder_2d(O, coarsen, levels):
+    """2D flow past a circle (256 x 64 x 1, the paper's Fig. 2 setting): the
+    length-1 axis never coarsens.  Its FP32 storage floor lies above 1e-5 (the
+    pressure grows along the channel), so the solve refines in FP64 to 1e-6."""
+    info = _refined_parity(O, ("cyl", 256, 64, 1), coarsen)
+    assert info.levels == levels
+
+
+@pytest.mark.parametrize("coarsen", ["iso", "aniso"])
+def test_cylinder_spanwise_periodic(O, coarsen):
+    """A cylinder spanning a periodic z axis (128 x 64 x 32), refined to 1e-6."""
+    assert problem(("cyl", 128, 64, 32, 5, 8.0, 32.0, True)).periodic == (False, False, True)
+    _refined_parity(O, ("cyl", 128, 64, 32, 5, 8.0, 32.0, True), coarsen)
+
+
 @pytest.mark.parametrize("precision", ["ir64_fp32", "ir64"])
 def test_sphere_channel_refined_to_1e6(O, precision):
     """FP64 refinement around FP32 (and BF16-correction) V-cycles reaches 1e-6."""

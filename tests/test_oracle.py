@@ -198,6 +198,19 @@ def test_schedule_reading():
     assert len(d) == 2
 
 
+def test_schedule_2d():
+    """A length-1 axis (the 2D flows of Fig. 2) never halves and does not stop
+    isotropic coarsening of the other two (reading C3, singleton axes)."""
+    from oracle import oracle as O
+    d, f = O.schedule((256, 64, 1), coarsen="iso")
+    assert d == [(256, 64, 1), (128, 32, 1), (64, 16, 1), (32, 8, 1), (16, 4, 1)]
+    assert all(c[2] == 1 for c in f)
+    d, _ = O.schedule((256, 64, 1), coarsen="aniso")
+    assert d == [(256, 64, 1), (128, 32, 1), (64, 16, 1), (32, 8, 1), (16, 4, 1), (8, 4, 1), (4, 4, 1)]
+    d, _ = O.schedule((1, 1, 1), coarsen="iso")
+    assert d == [(1, 1, 1)]
+
+
 def test_coarse_beta_constant(oracle):
     """beta = 1 coarsens to prod_{e != d} c_e / c_d, the anisotropically spaced
     7-point operator; Neumann wall faces stay zero."""
@@ -327,7 +340,9 @@ def test_fft_solution_is_exact(oracle):
 @pytest.mark.parametrize("dims,periodic", [((8, 8, 8), (False, False, False)),
                                            ((8, 4, 6), (True, False, False)),
                                            ((6, 8, 4), (True, True, True)),
-                                           ((5, 7, 4), (False, False, False))])
+                                           ((5, 7, 4), (False, False, False)),
+                                           ((12, 8, 1), (False, False, False)),
+                                           ((8, 8, 1), (True, True, False))])
 @pytest.mark.parametrize("coarsen", ["iso", "aniso"])
 def test_solve_matches_dense(oracle, dims, periodic, coarsen):
     nx, ny, nz = dims
@@ -359,6 +374,23 @@ def test_solve_matches_fft_32(oracle):
     # relative error <= condition number x relative residual
     assert err < 3 * 32 ** 2 / math.pi ** 2 * 1e-10
     assert err < 1e-9
+
+
+def test_solve_matches_fft_2d(oracle):
+    """A 2D periodic square (64 x 64 x 1, beta = 1) against the FFT solution: the
+    length-1 axis has no neighbours, so its Fourier factor is 0."""
+    shape = (1, 64, 64)
+    rng = np.random.default_rng(8)
+    b = rng.standard_normal(shape)
+    b -= b.mean()
+    ones = np.ones(shape)
+    bx, by, bz = I.apply_walls(ones, ones, ones, (True, True, False))
+    assert not bz.any()
+    res = oracle.solve(b, bx, by, bz, (True, True, False), tol=1e-10, coarsen="iso")
+    assert res.status == oracle.OK and res.levels == 5
+    p_ref = oracle.fft_solve_periodic(b)
+    err = np.linalg.norm(res.p - p_ref) / np.linalg.norm(p_ref)
+    assert err < 2 * 64 ** 2 / math.pi ** 2 * 1e-10
 
 
 def test_smooth_taylor_green_pressure(oracle):

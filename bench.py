@@ -466,6 +466,53 @@ def fig2(args):
     return 0
 
 
+def pcg_compare(args):
+    """The paper's solver comparison (Sec. 3, Table 1): Jacobi-preconditioned CG
+    against the multigrid solve with the adaptive red-black Gauss-Seidel
+    smoother, both FP32 on the GPU from a zero guess to 1e-5 (the tightest
+    tolerance plain FP32 reaches on these flows), on the sphere channel at
+    128x48x48 and 256x96x96 and the 2D cylinder at 512x128x1.  One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2607_07687_gb300 import build as B
+    B.build()
+    from paper_2607_07687_gb300 import binding as G
+    from paper_2607_07687_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tol = 1e-5
+    rows = []
+    for prob in (I.sphere_channel_problem(128, 48, 48, 1, 8.0, 48.0), I.sphere_channel_problem(),
+                 I.cylinder_channel_problem(512, 128, 1, 5, 8.0, 48.0)):
+        f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+        s = G.Solver(prob.dims, prob.periodic, precision="fp32", coarsen="aniso")
+        s.set_coeffs(f32(prob.bx), f32(prob.by), f32(prob.bz))
+        b = f32(prob.b)
+        p = torch.zeros_like(b)
+        row = {"workload": prob.name, "cells": prob.cells}
+        for name, run in (("gmg_rbgs", lambda: s.solve(b, p, tol)), ("pcg_jacobi", lambda: s.pcg_solve(b, p, tol))):
+            p.zero_()
+            run()                                   # warm-up (graphs, work vectors)
+            ts = []
+            for _ in range(3):
+                p.zero_()
+                torch.cuda.synchronize()
+                ev0.record()
+                info = run()
+                ev1.record()
+                torch.cuda.synchronize()
+                ts.append(ev0.elapsed_time(ev1))
+            row[name] = {"ms": float(np.median(ts)), "iterations": int(info.cycles), "status": int(info.status),
+                         "rel_res": float(info.rel_res)}
+        s.close()
+        row["pcg_over_gmg_time"] = row["pcg_jacobi"]["ms"] / row["gmg_rbgs"]["ms"]
+        rows.append(row)
+    print(json.dumps({"experiment": "Jacobi-PCG vs GMG-RBGS, time to 1e-5 from zero (FP32)", "rows": rows,
+                      "paper_table1_ratio_pcg_over_gmg_rbgs": [3.66, 5.78]}), flush=True)
+    return 0
+
+
 def suite(args):
     """Time to tolerance of each solver form on the paper-shaped workloads
     (one JSON line per workload): the Taylor-Green cube 32^3 (FP32, 1e-6), the
@@ -623,6 +670,8 @@ def main():
                     help="autotuner table: loaded when the file exists (no timing of launch shapes), "
                          "else written after the run; a profiler run then launches what a plain run tuned")
     ap.add_argument("--net", action="store_true", help="time --reps forward passes of the warm-start network")
+    ap.add_argument("--pcg", action="store_true",
+                    help="Jacobi-PCG against the multigrid solve (time to 1e-5, FP32)")
     ap.add_argument("--fig2", action="store_true",
                     help="iso vs aniso coarsening over aspect ratios 1-8: 2D cylinder, spanwise-periodic "
                          "cylinder, sphere")
@@ -649,6 +698,8 @@ def main():
         return suite(args)
     if args.fig2:
         return fig2(args)
+    if args.pcg:
+        return pcg_compare(args)
     if args.net:
         return net_forward(args)
     args.warmup = max(3, args.warmup)

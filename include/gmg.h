@@ -134,6 +134,28 @@ int gmg_solve(gmg_handle h, const void* sigma, void* p, double tol, gmg_info* in
 int gmg_solve_host(gmg_handle h, const void* sigma_host, void* p_host, double tol, gmg_info* info);
 
 /*
+ * The comparison solver of the paper (Sec. 3 and Table 1: preconditioned
+ * conjugate gradients, general-purpose but with global inner products in every
+ * iteration and an iteration count that grows with the grid): CG on the same
+ * operator, right-hand-side projection and exit gauge as gmg_solve, with the
+ * Jacobi (diagonal) preconditioner, which the paper does not name.  FP32
+ * vectors, FP64 inner-product partials; alpha, beta and the stop test
+ * (|b - A p| / |b| <= tol, the recursively updated residual) stay on the
+ * device, and iterations run in CUDA graphs of 16.
+ *
+ * h: a single-problem handle with precision GMG_FP32 or GMG_FP32_BF16 and its
+ * coefficients set (only the finest level is used).  sigma, p: device float
+ * arrays of nx*ny*nz, as for gmg_solve (p: initial guess in, solution out).
+ * max_iter >= 1 bounds the iterations.  info->cycles reports CG iterations,
+ * info->levels 1.  Returns GMG_OK, GMG_ERR_NOT_CONVERGED (max_iter reached),
+ * GMG_ERR_DIVERGED (the search direction lost definiteness or the residual is
+ * not finite), GMG_ERR_NONFINITE, GMG_ERR_ARG (IR-precision handle, batch-like
+ * misuse, max_iter < 1, tol <= 0) or GMG_ERR_CUDA.  The first call allocates
+ * six work vectors of nx*ny*nz floats, kept by the handle.
+ */
+int gmg_pcg_solve(gmg_handle h, const void* sigma, void* p, double tol, int max_iter, gmg_info* info);
+
+/*
  * Per-cycle record of the last solve: rel_res[k] (k = 0 .. cycles; entry 0
  * is the initial iterate's relative residual, entry k the accepted iterate's
  * after cycle k), omega[k] and accepted[k] (k = 0 .. cycles-1) for cycle k+1.

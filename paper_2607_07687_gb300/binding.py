@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
     L.gmg_set_coeffs.argtypes = [vp, vp, vp, vp]
     L.gmg_solve.argtypes = [vp, vp, vp, c_double, ctypes.POINTER(Info)]
     L.gmg_solve_host.argtypes = [vp, vp, vp, c_double, ctypes.POINTER(Info)]
+    L.gmg_pcg_solve.argtypes = [vp, vp, vp, c_double, c_int, ctypes.POINTER(Info)]
     L.gmg_history.argtypes = [vp, dp, dp, ip, c_int]
     L.gmg_levels.argtypes = [vp, ip]
     L.gmg_destroy.argtypes = [vp]
@@ -251,6 +252,16 @@ class Solver:
         info = Info()
         rc = lib().gmg_solve(self.h, _ptr(sigma, dt, self.ncells), _ptr(p, dt, self.ncells),
                              float(tol), ctypes.byref(info))
+        _check(rc, self.h, ok=SOLVE_STATUSES)
+        return info
+
+    def pcg_solve(self, sigma, p, tol: float = 1e-6, max_iter: int = 10000) -> Info:
+        """Jacobi-preconditioned CG on the finest level (gmg_pcg_solve): float32 sigma
+        and p (in: initial guess, out: solution); info.cycles = CG iterations."""
+        import torch
+        info = Info()
+        rc = lib().gmg_pcg_solve(self.h, _ptr(sigma, torch.float32, self.ncells), _ptr(p, torch.float32, self.ncells),
+                                 float(tol), int(max_iter), ctypes.byref(info))
         _check(rc, self.h, ok=SOLVE_STATUSES)
         return info
 

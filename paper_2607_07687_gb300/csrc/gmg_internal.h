@@ -234,6 +234,37 @@ struct IrTask {
     double* scale;       // device scalar: inner = outer residual * scale
 };
 
+// Scalars of the conjugate-gradient solve kept on the device.
+struct PcgScal {
+    double rz;           // rho . z of the current residual
+    double alpha, beta;
+};
+
+// One Jacobi-preconditioned CG solve on one level (the comparison solver).
+struct PcgTask {
+    Geo g;
+    const float* bx;
+    const float* by;
+    const float* bz;
+    const float* b;      // projected right-hand side
+    float* x;            // iterate
+    float* r;            // rho = A x - b
+    float* z;            // D^-1 rho
+    float* q;            // A d
+    float* inv_diag;     // D^-1 (0 where no face is open)
+    const float* d_src;  // previous direction
+    float* d_dst;        // new direction
+    double* part;        // 3 per block
+    int nparts;
+    int zc;              // z-chunk of a block
+    Ctl* ctl;            // status, bnorm, r_prev (|rho|), tol, cycles (= iterations), max_cycles
+    PcgScal* scal;
+};
+
+int pcg_blocks(const Geo& g, int zc);
+cudaError_t launch_pcg_start(const PcgTask& t, bool restart, cudaStream_t s);
+cudaError_t launch_pcg_iteration(const PcgTask& t, cudaStream_t s);
+
 // Message returned by gmg_last_error(NULL) for calls without a handle.
 void set_api_error(const char* msg);
 

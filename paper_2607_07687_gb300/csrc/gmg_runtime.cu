@@ -319,6 +319,15 @@ struct Engine {
     int last_cycles = 0;
     long long launches = 0;     // kernels launched since the counter was reset
 
+    // conjugate-gradient comparison solver (problem 0): r, z, q, D^-1, d0, d1
+    float* pcg_buf[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* pcg_part = nullptr;
+    PcgScal* pcg_scal = nullptr;
+    cudaGraphExec_t pcg_exec = nullptr;
+    static constexpr int kPcgZChunk = 8;      // z-planes per block of the CG kernels
+    static constexpr int kPcgGraphIters = 16; // iterations per graph replay (even: d0/d1 alternate)
+    static constexpr int kPcgMaxRestarts = 64; // true-residual checks per solve
+
     ~Engine() { release(); }
 
     void release()
@@ -327,6 +336,9 @@ struct Engine {
         if (graph) cudaGraphDestroy(graph);
         graph_exec = nullptr;
         graph = nullptr;
+        if (pcg_exec) cudaGraphExecDestroy(pcg_exec);
+        pcg_exec = nullptr;
+        for (float*& b : pcg_buf) b = nullptr;
         for (void* a : allocs) cudaFree(a);
         allocs.clear();
         if (ctl_host) cudaFreeHost(ctl_host);
@@ -1392,6 +1404,133 @@ struct Engine {
         return worst;
     }
 
+    // ---------------------------------------------------------------- PCG
+
+    PcgTask pcg_task(int parity)
+    {
+        ProblemMem& M = P[0];
+        PcgTask t{};
+        t.g = M.lev[0].g;
+        t.bx = M.lev[0].beta[0];
+        t.by = M.lev[0].beta[1];
+        t.bz = M.lev[0].beta[2];
+        t.b = M.lev[0].b;
+        t.x = static_cast<float*>(M.lev[0].buf[0]);
+        t.r = pcg_buf[0];
+        t.z = pcg_buf[1];
+        t.q = pcg_buf[2];
+        t.inv_diag = pcg_buf[3];
+        t.d_src = pcg_buf[4 + parity];
+        t.d_dst = pcg_buf[5 - parity];
+        t.part = pcg_part;
+        t.zc = kPcgZChunk;
+        t.nparts = pcg_blocks(t.g, t.zc);
+        t.ctl = M.ctl;
+        t.scal = pcg_scal;
+        return t;
+    }
+
+    cudaError_t pcg_iterations()
+    {
+        if (!opt.use_graph) {
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < kPcgGraphIters && e == cudaSuccess; ++i) e = launch_pcg_iteration(pcg_task(i & 1), stream);
+            launches += 4 * kPcgGraphIters;
+            return e;
+        }
+        if (!pcg_exec) {
+            cudaStream_t cap;
+            cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return e;
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t le = cudaSuccess;
+                for (int i = 0; i < kPcgGraphIters && le == cudaSuccess; ++i) le = launch_pcg_iteration(pcg_task(i & 1), cap);
+                e = cudaStreamEndCapture(cap, &gr);
+                if (le != cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&pcg_exec, gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) return e;
+        }
+        launches += 4 * kPcgGraphIters;
+        return cudaGraphLaunch(pcg_exec, stream);
+    }
+
+    // Jacobi-preconditioned CG on the finest level of problem 0 (the paper's PCG
+    // comparison solver): projection of sigma and copy-in of the guess as for
+    // gmg_solve, CG iterations in graphs of kPcgGraphIters until the device-side
+    // stop test fires, the exit gauge into p.
+    int pcg_solve(const float* sigma, float* p, double tol, int max_iter, gmg_info* info)
+    {
+        if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_pcg_solve");
+        if (P.size() != 1) return fail(GMG_ERR_ARG, "gmg_pcg_solve: single-problem handles only");
+        if (opt.precision == GMG_IR64 || opt.precision == GMG_IR64_FP32)
+            return fail(GMG_ERR_ARG, "gmg_pcg_solve: FP32 handles only (precision GMG_FP32 or GMG_FP32_BF16)");
+        if (max_iter < 1) return fail(GMG_ERR_ARG, "gmg_pcg_solve: max_iter must be >= 1");
+        ProblemMem& M = P[0];
+        if (!pcg_buf[0]) {
+            for (float*& b : pcg_buf)
+                if (!(b = dalloc<float>((size_t)M.n0))) return fail(GMG_ERR_CUDA, "gmg_pcg_solve: out of device memory");
+            pcg_part = dalloc<double>(3 * (size_t)pcg_blocks(M.lev[0].g, kPcgZChunk));
+            pcg_scal = dalloc<PcgScal>(1);
+            if (!pcg_part || !pcg_scal) return fail(GMG_ERR_CUDA, "gmg_pcg_solve: out of device memory");
+        }
+        launches = 0;
+        Ctl c = initial_ctl(M, tol);
+        c.max_cycles = max_iter;
+        c.hist_cap = -1;
+        ctl_host[0] = c;
+        cudaError_t e = cudaMemcpyAsync(ctl_dev, ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, stream);
+        const float* sig[1] = {sigma};
+        float* pin[1] = {p};
+        if (e == cudaSuccess) e = project<float>(sig, (const float* const*)pin, false, nullptr);
+        if (e == cudaSuccess) {
+            launches += 2;
+            e = launch_pcg_start(pcg_task(0), false, stream);
+        }
+        if (e == cudaSuccess) e = read_ctl();
+        // iterate; a pause (done while running) means the updated residual met tol:
+        // restart from the current iterate, where the true residual decides
+        int replays = 0, restarts = 0;
+        while (e == cudaSuccess) {
+            Ctl& h = ctl_host[0];
+            if (h.done && h.status != kRunning) break;
+            if (h.done) {
+                if (++restarts > kPcgMaxRestarts) break;
+                h.done = 0;
+                e = cudaMemcpyAsync(ctl_dev, ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, stream);
+                launches += 2;
+                if (e == cudaSuccess) e = launch_pcg_start(pcg_task(0), true, stream);
+            } else {
+                if ((int64_t)replays++ * kPcgGraphIters > (int64_t)max_iter) break;
+                e = pcg_iterations();
+            }
+            if (e == cudaSuccess) e = read_ctl();
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "gmg_pcg_solve");
+        if (ctl_host[0].status != kNonFinite) {
+            e = gauge<float, float>(pin, false);
+            if (e == cudaSuccess) e = read_ctl();
+            if (e != cudaSuccess) return cuda_fail(e, "gmg_pcg_solve (gauge)");
+        }
+        const Ctl& r = ctl_host[0];
+        const int st = r.status == kRunning ? kNotConverged : r.status;
+        if (info) {
+            info->cycles = r.cycles;
+            info->status = st;
+            info->levels = 1;
+            info->outer = 0;
+            info->launches = (int)launches;
+            info->rel_res = r.bnorm > 0.0 ? r.r_prev / r.bnorm : 0.0;
+            info->omega = 1.0;
+            info->bnorm = r.bnorm;
+        }
+        return st;
+    }
+
     // FP64 iterative refinement (Sec. 3 cycles inside an FP64 outer loop) for every
     // problem of the engine: each outer step computes r64 = b64 - A p64, runs the
     // FP32 (or BF16-coarse) V-cycles of all unfinished problems together on it,
@@ -1687,6 +1826,12 @@ int gmg_solve_host(gmg_handle h, const void* sigma_host, void* p_host, double to
         rc = E.cuda_fail(e, "gmg_solve_host");
     }
     return rc;
+}
+
+int gmg_pcg_solve(gmg_handle h, const void* sigma, void* p, double tol, int max_iter, gmg_info* info)
+{
+    if (!h || !sigma || !p || !(tol > 0.0)) return GMG_ERR_ARG;
+    return h->eng.pcg_solve(static_cast<const float*>(sigma), static_cast<float*>(p), tol, max_iter, info);
 }
 
 int gmg_history(gmg_handle h, double* rel_res, double* omega, int* accepted, int cap)

@@ -1,0 +1,85 @@
+"""GPU Jacobi-PCG (gmg_pcg_solve) against the FP64 conjugate-gradient oracle."""
+import numpy as np
+import pytest
+
+from paper_2607_07687_gb300 import inputs as I
+from tests.gpu_common import host, rel_l2, t32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from oracle import oracle, pcg_oracle
+    oracle.build()
+    return pcg_oracle
+
+
+def gpu_pcg(prob, tol, max_iter=20000, precision="fp32"):
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    s = G.Solver(prob.dims, prob.periodic, precision=precision)
+    try:
+        s.set_coeffs(t32(prob.bx), t32(prob.by), t32(prob.bz))
+        b = t32(prob.b)
+        p = t32(np.zeros(prob.shape))
+        info = s.pcg_solve(b, p, tol, max_iter)
+        torch.cuda.synchronize()
+        return host(p), info
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("dims,periodic", [((40, 24, 16), (False, False, False)), ((32, 16, 12), (True, False, True))])
+@pytest.mark.parametrize("k,bound", [(10, 1e-5), (40, 1e-4)])
+def test_iterates_match_oracle(P, dims, periodic, k, bound):
+    """After k iterations (max_iter = k) the gauged iterate equals the oracle's after
+    k iterations: FP32 against FP64 arithmetic, so the trajectories part slowly."""
+    from paper_2607_07687_gb300 import binding as G
+    prob = I.random_small_problem(dims, periodic, seed=sum(dims) + k)
+    got, info = gpu_pcg(prob, 1e-14, max_iter=k)
+    assert info.status == G.NOT_CONVERGED and info.cycles == k
+    ref = P.pcg_problem(prob, tol=1e-14, max_iter=k)
+    assert ref.iterations == k
+    assert rel_l2(got, ref.x) <= bound, rel_l2(got, ref.x)
+
+
+@pytest.mark.parametrize("key,tol", [(("sphere", 128, 48, 48), 1e-5), (("cyl", 128, 64, 1), 1e-4)])
+def test_converges_like_oracle(P, key, tol):
+    """The true residual of the GPU solution (evaluated in FP64 by the oracle's
+    operator) meets the tolerance (the solver confirms the updated residual's
+    convergence on the true one and restarts while it fails), and the iteration
+    count stays near the oracle's (restarts cost a few iterations).  The 2D
+    cylinder's FP32 floor lies above 1e-5, so it is solved to 1e-4."""
+    from oracle import oracle as O
+    prob = (I.sphere_channel_problem(*key[1:]) if key[0] == "sphere" else I.cylinder_channel_problem(*key[1:]))
+    got, info = gpu_pcg(prob, tol)
+    assert info.status == 0, info.as_dict()
+    ref = P.pcg_problem(prob, tol=tol)
+    assert ref.status == 0
+    assert 0.9 * ref.iterations - 2 <= info.cycles <= 1.5 * ref.iterations + 2, (info.cycles, ref.iterations)
+    b = np.asarray(prob.b, dtype=np.float32).astype(np.float64)
+    act = P.jacobi_diagonal(prob.bx, prob.by, prob.bz, prob.periodic) > 0
+    bp = np.where(act, b - b[act].mean(), 0.0)
+    r = bp - O.apply_A(got, np.float32(prob.bx).astype(np.float64), np.float32(prob.by).astype(np.float64),
+                       np.float32(prob.bz).astype(np.float64), prob.periodic)
+    r = np.where(act, r, 0.0)
+    assert np.linalg.norm(r) / np.linalg.norm(bp) <= 1.2 * tol
+    assert info.rel_res <= tol
+    assert rel_l2(got, ref.x) <= 1e-3
+
+
+def test_zero_rhs_and_bad_handle(P):
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    prob = I.random_small_problem((16, 8, 8), (False, False, False), seed=2)
+    prob.b[...] = 0.0
+    got, info = gpu_pcg(prob, 1e-6)
+    assert info.status == 0 and info.cycles == 0 and not got.any()
+    s = G.Solver(prob.dims, prob.periodic, precision="ir64_fp32")
+    try:
+        s.set_coeffs(t32(prob.bx), t32(prob.by), t32(prob.bz))
+        with pytest.raises(G.GmgError):
+            s.pcg_solve(torch.zeros(prob.cells, device="cuda"), torch.zeros(prob.cells, device="cuda"), 1e-6)
+    finally:
+        s.close()

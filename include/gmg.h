@@ -156,6 +156,24 @@ int gmg_solve_host(gmg_handle h, const void* sigma_host, void* p_host, double to
 int gmg_pcg_solve(gmg_handle h, const void* sigma, void* p, double tol, int max_iter, gmg_info* info);
 
 /*
+ * The paper's GMG-PCG (Table 1): the multigrid V-cycle of gmg_solve (same
+ * hierarchy, coarse coefficients, restriction and prolongation) with PCG as
+ * the smoother instead of the adaptive red-black Gauss-Seidel: nu1 and nu2
+ * Jacobi-PCG iterations before and after the coarse correction and nu_c on
+ * the coarsest level (whose right-hand side is projected to zero mean), each
+ * a fresh run from the level's current iterate that also stops once its
+ * residual has fallen to 1e-5 of its start.  Cycles are always accepted (no
+ * relaxation factor); the solve stops when |b - A p| / |b| <= tol, evaluated
+ * after every cycle.  Each cycle is one CUDA graph replay.
+ *
+ * h: a single-problem GMG_FP32 handle with its coefficients set; sigma, p as
+ * for gmg_solve.  info->cycles reports V-cycles.  Returns GMG_OK,
+ * GMG_ERR_NOT_CONVERGED (max_cycles), GMG_ERR_NONFINITE, GMG_ERR_ARG or
+ * GMG_ERR_CUDA.  The first call allocates six work vectors per level.
+ */
+int gmg_gmgpcg_solve(gmg_handle h, const void* sigma, void* p, double tol, gmg_info* info);
+
+/*
  * Per-cycle record of the last solve: rel_res[k] (k = 0 .. cycles; entry 0
  * is the initial iterate's relative residual, entry k the accepted iterate's
  * after cycle k), omega[k] and accepted[k] (k = 0 .. cycles-1) for cycle k+1.

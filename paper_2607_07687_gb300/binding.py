@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
     L.gmg_solve.argtypes = [vp, vp, vp, c_double, ctypes.POINTER(Info)]
     L.gmg_solve_host.argtypes = [vp, vp, vp, c_double, ctypes.POINTER(Info)]
     L.gmg_pcg_solve.argtypes = [vp, vp, vp, c_double, c_int, ctypes.POINTER(Info)]
+    L.gmg_gmgpcg_solve.argtypes = [vp, vp, vp, c_double, ctypes.POINTER(Info)]
     L.gmg_history.argtypes = [vp, dp, dp, ip, c_int]
     L.gmg_levels.argtypes = [vp, ip]
     L.gmg_destroy.argtypes = [vp]
@@ -262,6 +263,16 @@ class Solver:
         info = Info()
         rc = lib().gmg_pcg_solve(self.h, _ptr(sigma, torch.float32, self.ncells), _ptr(p, torch.float32, self.ncells),
                                  float(tol), int(max_iter), ctypes.byref(info))
+        _check(rc, self.h, ok=SOLVE_STATUSES)
+        return info
+
+    def gmgpcg_solve(self, sigma, p, tol: float = 1e-6) -> Info:
+        """Multigrid with PCG as the smoother (gmg_gmgpcg_solve): float32 sigma and p;
+        info.cycles = V-cycles."""
+        import torch
+        info = Info()
+        rc = lib().gmg_gmgpcg_solve(self.h, _ptr(sigma, torch.float32, self.ncells),
+                                    _ptr(p, torch.float32, self.ncells), float(tol), ctypes.byref(info))
         _check(rc, self.h, ok=SOLVE_STATUSES)
         return info
 

@@ -238,6 +238,8 @@ struct IrTask {
 struct PcgScal {
     double rz;           // rho . z of the current residual
     double alpha, beta;
+    int smoother;        // 1: tolerances relative to the run's first residual, not to |b|
+    int pad;
 };
 
 // One Jacobi-preconditioned CG solve on one level (the comparison solver).
@@ -264,6 +266,8 @@ struct PcgTask {
 int pcg_blocks(const Geo& g, int zc);
 cudaError_t launch_pcg_start(const PcgTask& t, bool restart, cudaStream_t s);
 cudaError_t launch_pcg_iteration(const PcgTask& t, cudaStream_t s);
+// arm a run on the device: done = 0, status running, cycles = 0, max_cycles, tol
+cudaError_t launch_pcg_arm(Ctl* ctl, PcgScal* scal, int max_it, double tol, int smoother, cudaStream_t s);
 
 // Message returned by gmg_last_error(NULL) for calls without a handle.
 void set_api_error(const char* msg);

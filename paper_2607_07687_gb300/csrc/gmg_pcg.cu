@@ -190,7 +190,7 @@ __global__ void k_pcg_control(const __grid_constant__ PcgTask t, int phase)
     if (threadIdx.x != 0) return;
     PcgScal& S = *t.scal;
     if (phase == 0 || phase == 3) {
-        C.bnorm = sqrt(c);
+        C.bnorm = S.smoother ? sqrt(b) : sqrt(c);   // a smoothing run measures against its start
         C.r_prev = sqrt(b);
         if (phase == 0) C.cycles = 0;
         S.rz = a;
@@ -234,6 +234,19 @@ __global__ void k_pcg_control(const __grid_constant__ PcgTask t, int phase)
     }
 }
 
+__global__ void k_pcg_arm(Ctl* ctl, PcgScal* scal, int max_it, double tol, int smoother)
+{
+    Ctl& C = *ctl;
+    C.done = 0;
+    C.status = kRunning;
+    C.cycles = 0;
+    C.max_cycles = max_it;
+    C.tol = tol;
+    C.nonfinite = 0;
+    C.zero_out = 0;
+    scal->smoother = smoother;
+}
+
 dim3 pcg_grid(const PcgTask& t)
 {
     return dim3((unsigned)((t.g.n[0] + kPX - 1) / kPX), (unsigned)((t.g.n[1] + kPY - 1) / kPY),
@@ -261,6 +274,12 @@ cudaError_t launch_pcg_iteration(const PcgTask& t, cudaStream_t s)
     k_pcg_control<<<1, kThreads, 0, s>>>(t, 1);
     k_pcg_update<<<pcg_grid(t), dim3(kPX, kPY), 0, s>>>(t);
     k_pcg_control<<<1, kThreads, 0, s>>>(t, 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_arm(Ctl* ctl, PcgScal* scal, int max_it, double tol, int smoother, cudaStream_t s)
+{
+    k_pcg_arm<<<1, 1, 0, s>>>(ctl, scal, max_it, tol, smoother);
     return cudaGetLastError();
 }
 

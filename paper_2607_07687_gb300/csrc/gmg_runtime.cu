@@ -338,6 +338,11 @@ struct Engine {
         graph = nullptr;
         if (pcg_exec) cudaGraphExecDestroy(pcg_exec);
         pcg_exec = nullptr;
+        if (gp_exec) cudaGraphExecDestroy(gp_exec);
+        gp_exec = nullptr;
+        gp_lev.clear();
+        gp_probe = nullptr;
+        gp_proj = nullptr;
         for (float*& b : pcg_buf) b = nullptr;
         for (void* a : allocs) cudaFree(a);
         allocs.clear();
@@ -1477,6 +1482,7 @@ struct Engine {
             pcg_part = dalloc<double>(3 * (size_t)pcg_blocks(M.lev[0].g, kPcgZChunk));
             pcg_scal = dalloc<PcgScal>(1);
             if (!pcg_part || !pcg_scal) return fail(GMG_ERR_CUDA, "gmg_pcg_solve: out of device memory");
+            if (cudaMemset(pcg_scal, 0, sizeof(PcgScal)) != cudaSuccess) return fail(GMG_ERR_CUDA, "gmg_pcg_solve");
         }
         launches = 0;
         Ctl c = initial_ctl(M, tol);
@@ -1522,6 +1528,180 @@ struct Engine {
             info->cycles = r.cycles;
             info->status = st;
             info->levels = 1;
+            info->outer = 0;
+            info->launches = (int)launches;
+            info->rel_res = r.bnorm > 0.0 ? r.r_prev / r.bnorm : 0.0;
+            info->omega = 1.0;
+            info->bnorm = r.bnorm;
+        }
+        return st;
+    }
+
+    // ---------------------------------------------------------------- GMG-PCG
+
+    // the multigrid with PCG as its smoother (Table 1's GMG-PCG), problem 0: per
+    // level the smoother's work vectors, control block and scalars
+    struct SmoothLevel {
+        float* v[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // r, z, q, D^-1, d0, d1
+        double* part = nullptr;
+        Ctl* ctl = nullptr;
+        PcgScal* scal = nullptr;
+    };
+    std::vector<SmoothLevel> gp_lev;
+    PcgScal* gp_probe = nullptr;                 // scalars of the fine-level residual probe
+    const LevelProjTask* gp_proj = nullptr;      // zero-mean projection of the coarsest level
+    cudaGraphExec_t gp_exec = nullptr;
+    static constexpr double kSmoothEta = 1e-5;  // a smoothing run stops at this fraction of its start
+
+    PcgTask gp_task(int l, int parity)
+    {
+        ProblemMem& M = P[0];
+        const LevelMem& Lm = M.lev[l];
+        SmoothLevel& S = gp_lev[l];
+        PcgTask t{};
+        t.g = Lm.g;
+        t.bx = Lm.beta[0];
+        t.by = Lm.beta[1];
+        t.bz = Lm.beta[2];
+        t.b = Lm.b;
+        t.x = static_cast<float*>(Lm.buf[0]);
+        t.r = S.v[0];
+        t.z = S.v[1];
+        t.q = S.v[2];
+        t.inv_diag = S.v[3];
+        t.d_src = S.v[4 + parity];
+        t.d_dst = S.v[5 - parity];
+        t.part = S.part;
+        t.zc = kPcgZChunk;
+        t.nparts = pcg_blocks(t.g, t.zc);
+        t.ctl = S.ctl;
+        t.scal = S.scal;
+        return t;
+    }
+
+    cudaError_t gp_smooth(int l, int iters, cudaStream_t s)
+    {
+        if (iters <= 0) return cudaSuccess;
+        cudaError_t e = launch_pcg_arm(gp_lev[l].ctl, gp_lev[l].scal, iters, kSmoothEta, 1, s);
+        if (e == cudaSuccess) e = launch_pcg_start(gp_task(l, 0), false, s);
+        for (int i = 0; i < iters && e == cudaSuccess; ++i) e = launch_pcg_iteration(gp_task(l, i & 1), s);
+        return e;
+    }
+
+    // one V-cycle on stream s: PCG smoothing, residual and restriction, coarse
+    // correction by prolongation, the coarsest right-hand side projected to zero mean
+    cudaError_t gp_cycle(cudaStream_t s)
+    {
+        ProblemMem& M = P[0];
+        const int L = M.L;
+        cudaStream_t saved = stream;
+        stream = s;
+        cudaError_t e = cudaSuccess;
+        for (int l = 0; l + 1 < L && e == cudaSuccess; ++l) {
+            e = gp_smooth(l, opt.nu1, s);
+            std::vector<LaunchOp> ops;
+            if (e == cudaSuccess && res_ops(l, {0}, {0}, true, false, ops)) e = cudaErrorMemoryAllocation;
+            for (const LaunchOp& op : ops)
+                if (e == cudaSuccess) e = launch(op);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(M.lev[l + 1].buf[0], 0, sizeof(float) * (size_t)cells(M.lev[l + 1].g), s);
+        }
+        if (e == cudaSuccess) e = launch_project_level(gp_proj, 1, s);
+        if (e == cudaSuccess) e = gp_smooth(L - 1, opt.nu_c, s);
+        for (int l = L - 2; l >= 0 && e == cudaSuccess; --l) {
+            e = launch_prolong_add(M.lev[l].g, M.lev[l].cf, static_cast<const float*>(M.lev[l + 1].buf[0]),
+                                   static_cast<float*>(M.lev[l].buf[0]), s);
+            if (e == cudaSuccess) e = gp_smooth(l, opt.nu2, s);
+        }
+        stream = saved;
+        return e;
+    }
+
+    int gmg_pcg_solve(const float* sigma, float* p, double tol, gmg_info* info)
+    {
+        if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_gmgpcg_solve");
+        if (P.size() != 1) return fail(GMG_ERR_ARG, "gmg_gmgpcg_solve: single-problem handles only");
+        if (opt.precision != GMG_FP32) return fail(GMG_ERR_ARG, "gmg_gmgpcg_solve: GMG_FP32 handles only");
+        ProblemMem& M = P[0];
+        const int L = M.L;
+        if (gp_lev.empty()) {
+            gp_lev.resize(L);
+            for (int l = 0; l < L; ++l) {
+                const size_t n = (size_t)cells(M.lev[l].g);
+                for (float*& v : gp_lev[l].v)
+                    if (!(v = dalloc<float>(n))) return fail(GMG_ERR_CUDA, "gmg_gmgpcg_solve: out of device memory");
+                gp_lev[l].part = dalloc<double>(3 * (size_t)pcg_blocks(M.lev[l].g, kPcgZChunk));
+                gp_lev[l].ctl = dalloc<Ctl>(1);
+                gp_lev[l].scal = dalloc<PcgScal>(1);
+                if (!gp_lev[l].part || !gp_lev[l].ctl || !gp_lev[l].scal)
+                    return fail(GMG_ERR_CUDA, "gmg_gmgpcg_solve: out of device memory");
+                if (cudaMemset(gp_lev[l].ctl, 0, sizeof(Ctl)) != cudaSuccess ||
+                    cudaMemset(gp_lev[l].scal, 0, sizeof(PcgScal)) != cudaSuccess)
+                    return fail(GMG_ERR_CUDA, "gmg_gmgpcg_solve");
+            }
+            gp_probe = dalloc<PcgScal>(1);
+            const LevelMem& C = M.lev[L - 1];
+            gp_proj = upload(std::vector<LevelProjTask>{LevelProjTask{C.g, C.beta[0], C.beta[1], C.beta[2], C.b, nullptr}});
+            if (!gp_probe || !gp_proj || cudaMemset(gp_probe, 0, sizeof(PcgScal)) != cudaSuccess)
+                return fail(GMG_ERR_CUDA, "gmg_gmgpcg_solve: out of device memory");
+        }
+        launches = 0;
+        Ctl c = initial_ctl(M, tol);
+        c.hist_cap = -1;
+        ctl_host[0] = c;
+        cudaError_t e = cudaMemcpyAsync(ctl_dev, ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, stream);
+        const float* sig[1] = {sigma};
+        float* pin[1] = {p};
+        if (e == cudaSuccess) e = project<float>(sig, (const float* const*)pin, false, nullptr);
+        // the fine-level probe: the true residual of the current iterate against |b|
+        auto probe = [&](bool first) {
+            PcgTask t = gp_task(0, 0);
+            t.ctl = M.ctl;
+            t.scal = gp_probe;
+            launches += 2;
+            return launch_pcg_start(t, !first, stream);
+        };
+        if (e == cudaSuccess) e = probe(true);
+        if (e == cudaSuccess) e = read_ctl();
+        int cycles = 0;
+        while (e == cudaSuccess && !ctl_host[0].done && cycles < opt.max_cycles) {
+            if (opt.use_graph) {
+                if (!gp_exec) {
+                    cudaStream_t cap;
+                    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+                    if (e != cudaSuccess) break;
+                    cudaGraph_t gr = nullptr;
+                    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                    if (e == cudaSuccess) {
+                        const cudaError_t le = gp_cycle(cap);
+                        e = cudaStreamEndCapture(cap, &gr);
+                        if (le != cudaSuccess) e = le;
+                    }
+                    if (e == cudaSuccess) e = cudaGraphInstantiate(&gp_exec, gr, 0);
+                    if (gr) cudaGraphDestroy(gr);
+                    cudaStreamDestroy(cap);
+                    if (e != cudaSuccess) break;
+                }
+                e = cudaGraphLaunch(gp_exec, stream);
+            } else {
+                e = gp_cycle(stream);
+            }
+            ++cycles;
+            if (e == cudaSuccess) e = probe(false);
+            if (e == cudaSuccess) e = read_ctl();
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "gmg_gmgpcg_solve");
+        if (ctl_host[0].status != kNonFinite) {
+            e = gauge<float, float>(pin, false);
+            if (e == cudaSuccess) e = read_ctl();
+            if (e != cudaSuccess) return cuda_fail(e, "gmg_gmgpcg_solve (gauge)");
+        }
+        const Ctl& r = ctl_host[0];
+        const int st = r.status == kRunning ? kNotConverged : r.status;
+        if (info) {
+            info->cycles = cycles;
+            info->status = st;
+            info->levels = L;
             info->outer = 0;
             info->launches = (int)launches;
             info->rel_res = r.bnorm > 0.0 ? r.r_prev / r.bnorm : 0.0;
@@ -1832,6 +2012,12 @@ int gmg_pcg_solve(gmg_handle h, const void* sigma, void* p, double tol, int max_
 {
     if (!h || !sigma || !p || !(tol > 0.0)) return GMG_ERR_ARG;
     return h->eng.pcg_solve(static_cast<const float*>(sigma), static_cast<float*>(p), tol, max_iter, info);
+}
+
+int gmg_gmgpcg_solve(gmg_handle h, const void* sigma, void* p, double tol, gmg_info* info)
+{
+    if (!h || !sigma || !p || !(tol > 0.0)) return GMG_ERR_ARG;
+    return h->eng.gmg_pcg_solve(static_cast<const float*>(sigma), static_cast<float*>(p), tol, info);
 }
 
 int gmg_history(gmg_handle h, double* rel_res, double* omega, int* accepted, int cap)

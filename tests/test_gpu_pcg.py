@@ -83,3 +83,37 @@ def test_zero_rhs_and_bad_handle(P):
             s.pcg_solve(torch.zeros(prob.cells, device="cuda"), torch.zeros(prob.cells, device="cuda"), 1e-6)
     finally:
         s.close()
+
+
+def gpu_gmgpcg(prob, tol, **kw):
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    s = G.Solver(prob.dims, prob.periodic, precision="fp32", **kw)
+    try:
+        s.set_coeffs(t32(prob.bx), t32(prob.by), t32(prob.bz))
+        b = t32(prob.b)
+        p = t32(np.zeros(prob.shape))
+        info = s.gmgpcg_solve(b, p, tol)
+        torch.cuda.synchronize()
+        return host(p), info
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("key,coarsen", [(("sphere", 64, 32, 32, 1, 6.0, 20.0), "aniso"),
+                                         (("sphere", 64, 32, 32, 1, 6.0, 20.0), "iso"),
+                                         (("cyl", 128, 64, 1), "aniso")])
+def test_gmg_pcg_like_oracle(P, key, coarsen):
+    """Multigrid with the PCG smoother to 1e-5: V-cycles within 1 of the oracle's,
+    the solution within 1e-4 of the oracle's (FP32 smoother runs stop at 1e-5 of
+    their start, the oracle's at 1e-10), and the true residual at the tolerance."""
+    from oracle import oracle as O
+    prob = (I.sphere_channel_problem(*key[1:]) if key[0] == "sphere" else I.cylinder_channel_problem(*key[1:]))
+    tol = 1e-5 if key[0] == "sphere" else 1e-4
+    got, info = gpu_gmgpcg(prob, tol, coarsen=coarsen)
+    assert info.status == 0, info.as_dict()
+    ref = P.gmg_pcg_solve(prob.b, prob.bx, prob.by, prob.bz, prob.periodic, tol=tol, coarsen=coarsen)
+    assert ref.status == 0
+    assert abs(info.cycles - ref.iterations) <= 1, (info.cycles, ref.iterations)
+    assert info.rel_res <= tol
+    assert rel_l2(got, ref.x) <= 1e-3 if info.cycles != ref.iterations else rel_l2(got, ref.x) <= 1e-4

@@ -104,3 +104,45 @@ def test_history_reaches_tolerance_and_iterations_grow_with_n(O, P):
         assert res.status == 0 and res.history[-1] <= 1e-8
         its.append(res.iterations)
     assert its[0] < its[1] < its[2]
+
+
+# ---------------------------------------------------------------- GMG-PCG (PCG as the smoother)
+
+
+@pytest.mark.parametrize("dims,periodic,coarsen", [((8, 8, 8), (False, False, False), "iso"),
+                                                   ((12, 8, 4), (True, False, False), "aniso")])
+def test_gmg_pcg_matches_dense(O, P, dims, periodic, coarsen):
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    b, (bx, by, bz) = _rand(shape, 13, periodic)
+    res = P.gmg_pcg_solve(b, bx, by, bz, periodic, tol=1e-11, coarsen=coarsen, n_min=2, f32_inputs=False)
+    assert res.status == 0
+    act = P.jacobi_diagonal(bx, by, bz, periodic) > 0
+    bp = np.where(act, b - b[act].mean(), 0.0)
+    ref = O.dense_solve(bp, bx, by, bz, periodic)
+    ref = np.where(act, ref - ref[act].mean(), 0.0)
+    assert np.linalg.norm(res.x - ref) / np.linalg.norm(ref) < 1e-9
+    assert all(h2 < h1 for h1, h2 in zip(res.history, res.history[1:]))
+
+
+def test_gmg_pcg_two_grid_correction(O, P):
+    """Without smoothing, and with the coarse level solved by enough PCG steps,
+    one cycle from zero is the textbook two-grid correction P A_c^+ P^T b
+    (dense matrices; P = piecewise-constant injection), up to a constant."""
+    shape = (4, 4, 8)
+    b, (bx, by, bz) = _rand(shape, 17, (False, False, False), zero_block=False)
+    b -= b.mean()
+    levels = P.hierarchy(bx, by, bz, (False, False, False), "aniso", 2)[:2]
+    fac = levels[0][3]
+    nzc, nyc, nxc = shape[0] // fac[2], shape[1] // fac[1], shape[2] // fac[0]
+    Pm = np.zeros((np.prod(shape), nzc * nyc * nxc))
+    for k in range(shape[0]):
+        for j in range(shape[1]):
+            for i in range(shape[2]):
+                Pm[(k * shape[1] + j) * shape[2] + i, ((k // fac[2]) * nyc + j // fac[1]) * nxc + i // fac[0]] = 1.0
+    Ac = O.dense_operator(*levels[1][:3])
+    ec = np.linalg.lstsq(Ac, Pm.T @ b.ravel(), rcond=None)[0]
+    ref = (Pm @ ec).reshape(shape)
+    got = P.gmg_pcg_vcycle(np.zeros(shape), b, levels, 0, 0, 0, 200, (False, False, False))
+    d = (got - got.mean()) - (ref - ref.mean())
+    assert np.linalg.norm(d) / np.linalg.norm(ref - ref.mean()) < 1e-9

@@ -115,3 +115,15 @@ def test_tune_import_rejects_malformed(L, bad):
     with pytest.raises(G.GmgError):
         G.tune_import("z 1 64 64 64 0 0 0 4\n" + bad)
     assert G.tune_export() == before              # nothing merged from a rejected table
+
+
+def test_comparison_solvers_reject_bad_arguments(L):
+    """The PCG and GMG-PCG entry points check their arguments before any CUDA work."""
+    fake = ctypes.c_void_p(16)
+    info = G.Info()
+    assert L.gmg_pcg_solve(None, fake, fake, 1e-6, 10, ctypes.byref(info)) == G.ERR_ARG
+    assert L.gmg_gmgpcg_solve(None, fake, fake, 1e-6, ctypes.byref(info)) == G.ERR_ARG
+    h = ctypes.c_void_p(8)   # never dereferenced: a non-positive tolerance is refused first
+    assert L.gmg_pcg_solve(h, fake, fake, 0.0, 10, ctypes.byref(info)) == G.ERR_ARG
+    assert L.gmg_gmgpcg_solve(h, fake, fake, -1.0, ctypes.byref(info)) == G.ERR_ARG
+    assert L.gmg_pcg_solve(h, None, fake, 1e-6, 10, ctypes.byref(info)) == G.ERR_ARG

@@ -49,7 +49,26 @@ def flush_l2(buf):
     writing back the flush buffer's dirty lines when it evicts them."""
     buf.fill_(1.0)
     buf.sum()
+
+
 FALLBACK_HBM_GBS = 6800.0
+
+
+def max_over_ranks(ms: float, pg, device="cpu") -> float:
+    """Replicas finish when the slowest rank does: the job's time is the maximum
+    of the ranks' times (pg: torch.distributed, or None on one GPU)."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, cells: int, cycles: int, ms: float) -> float:
+    """Whole-job throughput: every rank solves its own copy of the workload (weak
+    scaling), so the job updates ws x cells x cycles cells in the slowest rank's time."""
+    return ws * cells * cycles / (ms * 1e-3) / 1e9
 
 
 def workload():
@@ -764,14 +783,10 @@ def main():
             infos.append(step())
             ends[i].record(stream)
         barrier()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, pg, dev)
     cycles = infos[-1].cycles
     assert all(i.status == G.OK for i in infos), [i.as_dict() for i in infos]
-    value = ws * cells * cycles / (ms * 1e-3) / 1e9
+    value = job_value(ws, cells, cycles, ms)
 
     # ---- end to end through the C ABI with host buffers (pinned)
     sig_h = torch.from_numpy(np.asarray(prob.b, dtype=np.float32).astype(np.float64)).pin_memory()
@@ -789,12 +804,8 @@ def main():
         ie = solver.solve_host(sig_h, p_h, TOL)
         t_e2e.append(time.perf_counter() - t0)
     barrier()
-    e2e_ms = 1e3 * sum(t_e2e) / len(t_e2e)
-    if pg:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = ws * cells * ie.cycles / (e2e_ms * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(1e3 * sum(t_e2e) / len(t_e2e), pg, dev)
+    e2e_value = job_value(ws, cells, ie.cycles, e2e_ms)
 
     # ---- roofline of the dominant kernel: the fused sweep on the fine level
     b32 = b64.float()

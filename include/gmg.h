@@ -174,7 +174,8 @@ int gmg_pcg_solve(gmg_handle h, const void* sigma, void* p, double tol, int max_
 int gmg_gmgpcg_solve(gmg_handle h, const void* sigma, void* p, double tol, gmg_info* info);
 
 /*
- * Per-cycle record of the last solve: rel_res[k] (k = 0 .. cycles; entry 0
+ * Per-cycle record of the last gmg_solve / gmg_solve_host (the comparison
+ * solvers gmg_pcg_solve and gmg_gmgpcg_solve record none): rel_res[k] (k = 0 .. cycles; entry 0
  * is the initial iterate's relative residual, entry k the accepted iterate's
  * after cycle k), omega[k] and accepted[k] (k = 0 .. cycles-1) for cycle k+1.
  * Host arrays of capacity cap (+1 for rel_res).  Returns the number of cycles

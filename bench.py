@@ -121,12 +121,21 @@ def recorded_traffic():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 20 ms) during the timed region: entering waits
+    for the sampler's first line, and the summary keeps the lines written after
+    that (all lines if the region was shorter than one interval)."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.skip = 0
         self.path = os.path.join(tempfile.gettempdir(), f"gmg_clocks_{os.getpid()}.csv")
+
+    def _lines(self):
+        try:
+            return [ln for ln in open(self.path) if len(ln.split(",")) >= 9]
+        except Exception:
+            return []
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -136,8 +145,12 @@ class Clocks:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            t0 = time.perf_counter()
+            while not self._lines() and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.skip = len(self._lines())
         except Exception:
             self.proc = None
         return self
@@ -154,14 +167,10 @@ class Clocks:
     def summary(self):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        try:
-            for line in open(self.path):
-                f = [x.strip() for x in line.split(",")]
-                if len(f) >= 9:
-                    rows.append(f)
-        except Exception:
-            pass
+        lines = self._lines()
+        if len(lines) > self.skip:
+            lines = lines[self.skip:]
+        rows = [[x.strip() for x in ln.split(",")] for ln in lines]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]

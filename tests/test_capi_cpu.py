@@ -41,6 +41,7 @@ def _create(L, dims, periodic=(0, 0, 0), **kw):
     ((0, 8, 8), (0, 0, 0), {}, "dimension"),
     ((8, -1, 8), (0, 0, 0), {}, "dimension"),
     ((9, 8, 8), (1, 0, 0), {}, "periodic"),
+    ((8, 8, 1), (0, 0, 1), {}, "periodic"),        # a 2D grid's length-1 axis cannot be periodic
     ((8, 8, 8), (0, 0, 0), {"nu2": 0}, "nu2"),
     ((8, 8, 8), (0, 0, 0), {"nu_c": 0}, "nu_c"),
     ((8, 8, 8), (0, 0, 0), {"max_cycles": 0}, "max_cycles"),

@@ -39,7 +39,10 @@
  *   C6 V-cycle   V(nu1, nu2), zero guess on coarse levels, restriction = sum
  *                over children, prolongation = piecewise-constant injection,
  *                nu_c sweeps on the coarsest level after projecting its
- *                right-hand side to zero mean over active cells.
+ *                right-hand side to zero mean over active cells; or, as the
+ *                option for study (coarse_mode 1), the exact minimum-norm
+ *                solve p = A^+ b of the coarsest level, A^+ the Moore-Penrose
+ *                pseudo-inverse of its operator.
  *   C7 stop      |b - A p|_2 / |b|_2 <= tol, checked after each V-cycle.
  *   C8 gauge     at exit p -= mean over active cells; inactive cells p = 0.
  *
@@ -285,7 +288,108 @@ typedef struct {
     int nu1, nu2, nu_c;
     int max_cycles;
     double omega0, omega_min, shrink, grow;
+    int coarse_mode;    /* 0: nu_c sweeps on the coarsest level; 1: minimum-norm dense solve */
 } or_options;
+
+/* ------------------------------------------------------------------------ */
+/* C6 option: the coarsest level solved exactly in the least-squares,        */
+/* minimum-norm sense, p = A^+ b.  A^+ = V diag(1/lambda) V^T over the        */
+/* eigenpairs of the symmetric operator with |lambda| above a relative        */
+/* threshold (the null space -- constants per connected component of the      */
+/* cells -- gets 0).  Eigenpairs by the cyclic Jacobi method (Golub and Van   */
+/* Loan, Matrix Computations, Sec. 8.5): rotations in every (p, q) plane      */
+/* until the off-diagonal part is negligible.                                 */
+/* ------------------------------------------------------------------------ */
+
+/* dense operator of one grid, column j = A e_j (n x n, row-major) */
+static void dense_A(const grid_t* g, const double* const beta[3], double* M)
+{
+    long n = cells(g);
+    double* e = calloc((size_t)n, sizeof(double));
+    double* col = malloc(sizeof(double) * (size_t)n);
+    for (long j = 0; j < n; ++j) {
+        e[j] = 1.0;
+        apply_A(g, beta, e, col);
+        for (long i = 0; i < n; ++i) M[i * n + j] = col[i];
+        e[j] = 0.0;
+    }
+    free(e);
+    free(col);
+}
+
+/* symmetric eigendecomposition of S (n x n, destroyed: its diagonal ends as the
+ * eigenvalues); V receives the eigenvectors as columns */
+static void jacobi_eigen(double* S, double* V, long n)
+{
+    for (long i = 0; i < n; ++i)
+        for (long j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    double fro = 0.0;
+    for (long i = 0; i < n * n; ++i) fro += S[i] * S[i];
+    fro = sqrt(fro);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (long p = 0; p < n; ++p)
+            for (long q = p + 1; q < n; ++q) off += 2.0 * S[p * n + q] * S[p * n + q];
+        if (sqrt(off) <= 1e-15 * fro) break;
+        for (long p = 0; p < n; ++p)
+            for (long q = p + 1; q < n; ++q) {
+                double apq = S[p * n + q];
+                if (apq == 0.0) continue;
+                /* rotation (c, s) that zeroes S[p][q] (Golub-Van Loan Alg. 8.5.1) */
+                double tau = (S[q * n + q] - S[p * n + p]) / (2.0 * apq);
+                double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                /* S <- J^T S J with J the rotation in the (p, q) plane */
+                for (long k = 0; k < n; ++k) {
+                    double skp = S[k * n + p], skq = S[k * n + q];
+                    S[k * n + p] = c * skp - sn * skq;
+                    S[k * n + q] = sn * skp + c * skq;
+                }
+                for (long k = 0; k < n; ++k) {
+                    double spk = S[p * n + k], sqk = S[q * n + k];
+                    S[p * n + k] = c * spk - sn * sqk;
+                    S[q * n + k] = sn * spk + c * sqk;
+                }
+                for (long k = 0; k < n; ++k) {
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - sn * vkq;
+                    V[k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+/* Moore-Penrose pseudo-inverse of the operator of grid g (n x n, row-major) */
+static double* pseudo_inverse(const grid_t* g, const double* const beta[3])
+{
+    long n = cells(g);
+    double* S = malloc(sizeof(double) * (size_t)(n * n));
+    double* V = malloc(sizeof(double) * (size_t)(n * n));
+    double* P = calloc((size_t)(n * n), sizeof(double));
+    dense_A(g, beta, S);
+    jacobi_eigen(S, V, n);
+    double lmax = 0.0;
+    for (long i = 0; i < n; ++i) lmax = fmax(lmax, fabs(S[i * n + i]));
+    for (long m = 0; m < n; ++m) {
+        double lam = S[m * n + m];
+        if (!(fabs(lam) > 1e-10 * lmax)) continue;          /* null space */
+        for (long i = 0; i < n; ++i)
+            for (long j = 0; j < n; ++j) P[i * n + j] += V[i * n + m] * V[j * n + m] / lam;
+    }
+    free(S);
+    free(V);
+    return P;
+}
+
+/* p = A^+ b */
+static void pinv_apply(const double* P, long n, const double* b, double* p)
+{
+    for (long i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (long j = 0; j < n; ++j) s += P[i * n + j] * b[j];
+        p[i] = s;
+    }
+}
 
 typedef struct {
     int levels;
@@ -296,6 +400,7 @@ typedef struct {
     double* b[OR_MAX_LEVELS];
     double* p[OR_MAX_LEVELS];
     double* r[OR_MAX_LEVELS];
+    double* pinv;       /* coarse_mode 1: A^+ of the coarsest level */
 } hierarchy_t;
 
 static void free_hierarchy(hierarchy_t* h)
@@ -304,6 +409,7 @@ static void free_hierarchy(hierarchy_t* h)
         for (int d = 0; d < 3; ++d) free(h->beta[l][d]);
         free(h->b[l]); free(h->p[l]); free(h->r[l]);
     }
+    free(h->pinv);
 }
 
 /* fine coefficients with the wall faces of Neumann axes zeroed, then C4 per level */
@@ -338,6 +444,10 @@ static int build_hierarchy(hierarchy_t* h, const int n[3], const int per[3], con
                 }
     for (int l = 0; l + 1 < h->levels; ++l)
         coarsen_beta(&h->g[l], (const double* const*)h->beta[l], h->fac[l], &h->g[l + 1], h->beta[l + 1]);
+    if (o->coarse_mode == 1) {
+        int c = h->levels - 1;
+        h->pinv = pseudo_inverse(&h->g[c], (const double* const*)h->beta[c]);
+    }
     return OR_OK;
 }
 
@@ -348,7 +458,10 @@ static void vcycle(hierarchy_t* h, int l, const or_options* o, double omega)
     const double* const* beta = (const double* const*)h->beta[l];
     if (l == h->levels - 1) {
         project_active(g, beta, h->b[l]);
-        for (int s = 0; s < o->nu_c; ++s) sweep(g, beta, h->b[l], h->p[l], omega);
+        if (o->coarse_mode == 1)
+            pinv_apply(h->pinv, cells(g), h->b[l], h->p[l]);
+        else
+            for (int s = 0; s < o->nu_c; ++s) sweep(g, beta, h->b[l], h->p[l], omega);
         return;
     }
     for (int s = 0; s < o->nu1; ++s) sweep(g, beta, h->b[l], h->p[l], omega);
@@ -536,5 +649,17 @@ int or_vcycle(int nx, int ny, int nz, const int* periodic, const or_options* o,
     vcycle(&h, 0, o, omega);
     memcpy(p, h.p[0], sizeof(double) * (size_t)N);
     free_hierarchy(&h);
+    return OR_OK;
+}
+
+/* the coarsest-level step of coarse_mode 1 on one grid: p = A^+ b */
+int or_pinv_apply(int nx, int ny, int nz, const int* periodic, const double* bx, const double* by,
+                  const double* bz, const double* b, double* p)
+{
+    grid_t g = {{nx, ny, nz}, {periodic[0] != 0, periodic[1] != 0, periodic[2] != 0}};
+    const double* beta[3] = {bx, by, bz};
+    double* P = pseudo_inverse(&g, beta);
+    pinv_apply(P, cells(&g), b, p);
+    free(P);
     return OR_OK;
 }

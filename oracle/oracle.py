@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
     _fields_ = [("coarsen", ctypes.c_int), ("n_min", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("nu_c", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("omega0", ctypes.c_double), ("omega_min", ctypes.c_double),
-                ("shrink", ctypes.c_double), ("grow", ctypes.c_double)]
+                ("shrink", ctypes.c_double), ("grow", ctypes.c_double), ("coarse_mode", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -54,9 +54,10 @@ class _Info(ctypes.Structure):
 
 def options(coarsen: str = "aniso", n_min: int = 4, nu1: int = 2, nu2: int = 2, nu_c: int = 16,
             max_cycles: int = 100, omega0: float = 1.0, omega_min: float = 0.25,
-            shrink: float = 0.7, grow: float = 1.1) -> Options:
+            shrink: float = 0.7, grow: float = 1.1, coarse_mode: int = 0) -> Options:
+    """coarse_mode 0: nu_c sweeps on the coarsest level; 1: its minimum-norm dense solve."""
     return Options(1 if coarsen == "aniso" else 0, n_min, nu1, nu2, nu_c, max_cycles,
-                   omega0, omega_min, shrink, grow)
+                   omega0, omega_min, shrink, grow, coarse_mode)
 
 
 _lib = None
@@ -80,6 +81,7 @@ def lib():
         _lib.or_prolong_add.argtypes = [c_int, c_int, c_int, I, D, D]
         _lib.or_vcycle.argtypes = [c_int, c_int, c_int, I, ctypes.POINTER(Options), D, D, D, D, D,
                                    c_double]
+        _lib.or_pinv_apply.argtypes = [c_int, c_int, c_int, I, D, D, D, D, D]
     return _lib
 
 
@@ -165,6 +167,14 @@ def vcycle(p, b, bx, by, bz, omega=1.0, periodic=(False, False, False), **opt) -
     o = options(**opt)
     lib().or_vcycle(*_dims(p), _ivec(periodic), ctypes.byref(o), _d(bx), _d(by), _d(bz), _d(b),
                     _d(p), float(omega))
+    return p
+
+
+def pinv_apply(b, bx, by, bz, periodic=(False, False, False)) -> np.ndarray:
+    """The dense coarsest-level step (coarse_mode 1) on one grid: p = A^+ b."""
+    b, bx, by, bz = map(_f64, (b, bx, by, bz))
+    p = np.empty_like(b)
+    lib().or_pinv_apply(*_dims(b), _ivec(periodic), _d(bx), _d(by), _d(bz), _d(b), _d(p))
     return p
 
 

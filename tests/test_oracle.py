@@ -274,21 +274,25 @@ def _sor_colours(A, b, x, omega, shape):
     return x
 
 
-def _matrix_vcycle(lv, l, b, x, omega, nu1, nu2, nu_c):
+def _matrix_vcycle(lv, l, b, x, omega, nu1, nu2, nu_c, dense=False):
     """The V-cycle of Sec. 3 written with dense matrices: smoother, residual,
     R = P^T, recursion, P e, smoother; the coarsest right-hand side is
-    projected to zero mean over active cells before its sweeps."""
+    projected to zero mean over active cells before its sweeps (or, dense,
+    solved by scipy's SVD pseudo-inverse)."""
+    import scipy.linalg
     A, shape = lv[l]["A"], lv[l]["shape"]
     if l == len(lv) - 1:
         act = np.diag(A) < 0
         b = np.where(act, b - b[act].mean(), 0.0)
+        if dense:
+            return scipy.linalg.pinv(A) @ b
         for _ in range(nu_c):
             x = _sor_colours(A, b, x, omega, shape)
         return x
     for _ in range(nu1):
         x = _sor_colours(A, b, x, omega, shape)
     P = lv[l]["P"]
-    e = _matrix_vcycle(lv, l + 1, P.T @ (b - A @ x), np.zeros(P.shape[1]), omega, nu1, nu2, nu_c)
+    e = _matrix_vcycle(lv, l + 1, P.T @ (b - A @ x), np.zeros(P.shape[1]), omega, nu1, nu2, nu_c, dense)
     x = x + P @ e
     for _ in range(nu2):
         x = _sor_colours(A, b, x, omega, shape)
@@ -321,6 +325,81 @@ def test_vcycle_matches_matrix_form(oracle, dims, periodic, coarsen):
     ref = _matrix_vcycle(lv, 0, b.ravel(), p.ravel().copy(), omega, 2, 2, 16)
     got = oracle.vcycle(p, b, bx, by, bz, omega, periodic, coarsen=coarsen, n_min=2)
     np.testing.assert_allclose(got.ravel(), ref, rtol=1e-11, atol=1e-11)
+    # the dense coarsest solve (coarse_mode 1) in place of the coarsest sweeps
+    ref = _matrix_vcycle(lv, 0, b.ravel(), p.ravel().copy(), omega, 2, 2, 16, dense=True)
+    got = oracle.vcycle(p, b, bx, by, bz, omega, periodic, coarsen=coarsen, n_min=2, coarse_mode=1)
+    np.testing.assert_allclose(got.ravel(), ref, rtol=1e-9, atol=1e-9)
+
+
+# ---------------------------------------------------------------- dense coarsest solve (option)
+
+
+@pytest.mark.parametrize("dims,periodic,split", [((4, 6, 6), (False, False, False), False),
+                                                 ((4, 6, 6), (False, False, False), True),
+                                                 ((4, 4, 4), (True, True, True), False),
+                                                 ((6, 4, 4), (True, False, True), True),
+                                                 ((8, 6, 1), (False, False, False), False)])
+def test_pinv_apply_is_the_minimum_norm_solution(oracle, dims, periodic, split):
+    """The coarsest-level step of coarse_mode 1, p = A^+ b from the Jacobi
+    eigendecomposition, equals scipy's SVD pseudo-inverse of the face-by-face
+    dense assembly applied to b and the gelsd least-squares solve, on an
+    incompatible right-hand side: walled, periodic and mixed grids, coefficients
+    with zero blocks (isolated cells), and with a zero wall of faces splitting the
+    cells into two components (one null vector each)."""
+    import scipy.linalg
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    rng = np.random.default_rng(sum(dims) + 3 * split)
+    bx, by, bz = _rand_beta(shape, rng, periodic)
+    if split:                                   # no face across x = nx / 2 (or wrap): two components
+        bx[:, :, nx // 2] = 0.0
+        if periodic[0]:
+            bx[:, :, 0] = 0.0
+    A = oracle.dense_operator(bx, by, bz, periodic)
+    assert (_components(A) >= 2) == split
+    b = rng.standard_normal(shape) + 0.5
+    got = oracle.pinv_apply(b, bx, by, bz, periodic)
+    # singular values below 1e-10 of the largest are the null space (rounding level ~1e-15)
+    ref = (scipy.linalg.pinv(A, rtol=1e-10) @ b.ravel()).reshape(shape)
+    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-10 * np.abs(ref).max())
+    lsq = scipy.linalg.lstsq(A, b.ravel(), cond=1e-10, lapack_driver="gelsd")[0].reshape(shape)
+    np.testing.assert_allclose(got, lsq, atol=1e-9 * np.abs(ref).max())
+    # minimum norm: orthogonal to the constant vector of every component
+    assert abs(got[_active(A).reshape(shape)].sum()) <= 1e-9 * np.abs(got).sum()
+
+
+def test_pinv_apply_periodic_fft(oracle):
+    """beta = 1 on a triple-periodic grid: A^+ b is the FFT closed form of the
+    zero-mean part of b."""
+    shape = (4, 4, 8)
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal(shape)
+    ones = np.ones(shape)
+    got = oracle.pinv_apply(b, ones, ones, ones, (True, True, True))
+    np.testing.assert_allclose(got, oracle.fft_solve_periodic(b), atol=1e-11)
+
+
+@pytest.mark.parametrize("dims,periodic,coarsen", [((8, 8, 8), (False, False, False), "aniso"),
+                                                   ((8, 4, 6), (True, False, False), "iso"),
+                                                   ((12, 8, 1), (False, False, False), "aniso")])
+def test_dense_coarse_solve_matches_dense(oracle, dims, periodic, coarsen):
+    """Whole solves with the dense coarsest level converge to the dense
+    minimum-norm solution, in fewer V-cycles than with the 16 coarsest sweeps."""
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    rng = np.random.default_rng(sum(dims) + 5)
+    bx, by, bz = _rand_beta(shape, rng, periodic)
+    A = oracle.dense_operator(bx, by, bz, periodic)
+    act = _active(A).reshape(shape)
+    b = rng.standard_normal(shape)
+    res = oracle.solve(b, bx, by, bz, periodic, tol=1e-12, coarsen=coarsen, max_cycles=400, coarse_mode=1)
+    assert res.status == oracle.OK
+    bp = np.where(act, b - b[act].mean(), 0.0)
+    p_ref = oracle.dense_solve(bp, bx, by, bz, periodic)
+    p_ref = np.where(act, p_ref - p_ref[act].mean(), 0.0)
+    np.testing.assert_allclose(res.p, p_ref, atol=1e-9 * np.abs(p_ref).max())
+    sweeps = oracle.solve(b, bx, by, bz, periodic, tol=1e-12, coarsen=coarsen, max_cycles=400)
+    assert res.cycles <= sweeps.cycles, (res.cycles, sweeps.cycles)
 
 
 # ---------------------------------------------------------------- closed forms

@@ -40,11 +40,26 @@ typedef enum {
     GMG_ERR_ARG = 1,            /* bad argument (dimensions, null pointer, option range) */
     GMG_ERR_CUDA = 2,           /* a CUDA call failed */
     GMG_ERR_NOT_CONVERGED = 3,  /* max_cycles reached; p holds the best iterate */
-    GMG_ERR_DIVERGED = 4,       /* a cycle grew the residual at omega_min; p holds the best iterate */
+    GMG_ERR_DIVERGED = 4,       /* a cycle grew the residual at omega_min, or omega is not a positive
+                                   finite number; p holds the best iterate */
     GMG_ERR_NONFINITE = 5       /* the right-hand side holds NaN or Inf; p is left untouched */
 } gmg_status;
 
 enum { GMG_COARSEN_ISO = 0, GMG_COARSEN_ANISO = 1 };
+
+/*
+ * Coarsest-level treatment of the V-cycle (Sec. 3: the coarse-grid correction;
+ * Sec. 3.2 ties the iso/aniso effect to how well the coarsest level reduces
+ * the low frequencies).  SWEEPS: its right-hand side is projected to zero mean
+ * over active cells and nu_c red-black sweeps run from zero.  DENSE: after the
+ * same projection it is solved exactly in the minimum-norm least-squares
+ * sense, p = A^+ b, with the Moore-Penrose pseudo-inverse of the coarsest
+ * operator built on the device at gmg_set_coeffs (FP64, about n^3 operations
+ * for n coarsest cells; kept in FP32, n^2 floats per problem).  DENSE needs a
+ * hierarchy of at least two levels and a coarsest level of at most 1024
+ * cells (GMG_ERR_ARG at create otherwise).
+ */
+enum { GMG_COARSE_SWEEPS = 0, GMG_COARSE_DENSE = 1 };
 
 /*
  * Precision modes.  The FP32 V-cycle levels sum squared residuals in FP32 over
@@ -76,6 +91,7 @@ typedef struct {
     int cycles_per_sync;/* V-cycles queued before the host reads the status (default 4) */
     double ir_inner_rtol; /* IR modes: inner V-cycles stop at this residual reduction (default 1e-4) */
     int autotune;       /* time launch shapes at gmg_set_coeffs and keep the fastest (default 1) */
+    int coarse_mode;    /* coarsest level: GMG_COARSE_SWEEPS (default) or GMG_COARSE_DENSE */
 } gmg_options;
 
 typedef struct {
@@ -91,6 +107,15 @@ typedef struct {
 
 typedef struct gmg_solver* gmg_handle;
 typedef struct gmg_batch_solver* gmg_batch;
+
+/*
+ * Departures from the sketch of this interface in the design notes: no
+ * GMG_ERR_SINGULAR_RHS status (the right-hand side is projected onto the
+ * operator's range, so a singular operator never makes it unsolvable; NaN or
+ * Inf in sigma gives GMG_ERR_NONFINITE instead), and no reject_on_growth
+ * switch (a cycle that grows the residual is always rejected: the adaptive
+ * relaxation rule of Sec. 3.1 relies on it).
+ */
 
 /* Fills *opt with the defaults listed above. */
 void gmg_default_options(gmg_options* opt);
@@ -202,7 +227,7 @@ const char* gmg_last_error(gmg_handle h);
  * gmg_tune_export writes the table as text: one line per entry,
  *   "z kind nx ny nz px py pz zchunk"   (kind 0 sweep, 1 sweep with correction,
  *                                        2 residual)
- *   "b nx ny nz px py pz coarsen n_min precision nu_c level"
+ *   "b nx ny nz px py pz coarsen n_min precision nu_c coarse_mode level"
  * into buf (host, capacity cap bytes, NUL-terminated) and its length without
  * the NUL into *len.  buf == NULL only reports the length.  GMG_ERR_ARG when
  * cap is too small (nothing written).
@@ -308,19 +333,20 @@ int gmg_op_residual_norm(int nx, int ny, int nz, const int* periodic, const floa
                          double* rr, void* stream);
 
 /*
- * The paper has no counterpart to this entry point; it serves callers that
- * must not let a library allocate device memory: code recording a CUDA graph
- * (allocation during stream capture is refused or breaks the capture),
- * real-time loops that cannot afford the device-wide synchronisation
- * cudaMalloc / cudaFree may cause, and programs with a device-memory budget
- * fixed up front.
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot let a library allocate device memory: real-time loops that must
+ * never meet the device-wide synchronisation that cudaMalloc / cudaFree may
+ * cause, and programs whose device-memory budget is fixed before they start.
  *
- * Same result as gmg_op_residual_norm (the same kernels, the same summation
- * order), but its scratch (one FP64 partial sum per 32x4x2-cell tile, plus
- * the total) lives in a fixed array inside the library image: at most 65536
- * partial sums, i.e. about 16.7 M cells.  Every GPU that loads the library
- * holds that array (about 512 KB) until the process exits.  The call
- * allocates and frees nothing.
+ * Same quantity as gmg_op_residual_norm, |b - A p|_2^2 with FP64 partial sums,
+ * but its scratch (one FP64 partial sum per 32x4x2-cell tile, plus the total)
+ * lives in a fixed array inside the library image: at most 65536 partial
+ * sums, i.e. about 16.7 M cells.  Every GPU that loads the library holds that
+ * array (about 512 KB) until the process exits.  The call allocates and frees
+ * nothing.  It always runs the per-cell residual kernel; gmg_op_residual_norm
+ * runs the z-marching kernel when rows are a multiple of 4 cells and the
+ * arrays 16-byte aligned, which groups the FP32 squares differently, so the
+ * two results may then differ in the last digits (relative ~1e-7).
  *
  * Errors: GMG_ERR_ARG for bad dimensions, a null pointer, or a grid needing
  * more than 65536 partial sums (message in gmg_last_error(NULL));
@@ -331,12 +357,41 @@ int gmg_op_residual_norm(int nx, int ny, int nz, const int* periodic, const floa
  * call before any stream capture.  All calls on a device share the one array
  * and each overwrites what the previous call left there: calls that overlap
  * on the GPU (concurrent streams, or several host threads) race and must be
- * serialised by the caller.  The call synchronises `stream` before it
- * returns *rr (host memory).
+ * serialised by the caller.  The call synchronises `stream` and copies the
+ * total to *rr (host memory) before it returns.
  */
 int gmg_op_residual_norm_noalloc(int nx, int ny, int nz, const int* periodic, const float* bx,
                                  const float* by, const float* bz, const float* b,
                                  const float* p, double* rr, void* stream);
+
+/* ----------------------------------------------------------------------------
+ * Test hooks (no counterpart in the paper): host-side fault injection for the
+ * failure paths, so that tests need no GPU fault.
+ * -------------------------------------------------------------------------- */
+
+/*
+ * Arms the handle so that its next solve writes NaN into every problem's
+ * device-resident relaxation factor just before V-cycle `cycle` (>= 1) is
+ * launched (a host-to-device copy ordered on the handle's stream between two
+ * cycles; one shot).  The control rule treats a relaxation factor that is not
+ * a positive finite number as corrupt state: that cycle is rejected and the
+ * solve returns GMG_ERR_DIVERGED with the best accepted iterate.
+ * GMG_ERR_ARG if h is NULL or cycle < 1.
+ */
+int gmg_test_poison_omega(gmg_handle h, int cycle);
+
+/*
+ * Poll limit of the ring-slot waits of the pipelined sweep and residual
+ * kernels on the current device (a consumer waiting for a plane, a producer
+ * waiting for a free slot); tries < 0 restores the default (about two seconds
+ * of polling).  With 0 every such wait gives up at once: the block records the
+ * fault, waits (with the full limit) for the copies it already issued, and
+ * returns; the next status read of a solve reports GMG_ERR_CUDA ("the launch
+ * timed out and was terminated") and the handle should be destroyed.  The
+ * setting is process-wide for the device.  GMG_ERR_CUDA if the device
+ * variable cannot be written.
+ */
+int gmg_test_ring_wait_tries(int tries);
 
 #ifdef __cplusplus
 }

@@ -158,8 +158,10 @@ def residual_loss_and_grad(p0, b, apply_A):
     return float(np.sum(r * r)) / den, -2.0 * apply_A(r) / den
 
 
-def backward(params, cache, gout):
-    """Gradients of every parameter for d(loss)/d(out) = gout [D][H][W]."""
+def backward(params, cache, gout, record=None):
+    """Gradients of every parameter for d(loss)/d(out) = gout [D][H][W].  If record
+    is a dict, it receives each layer's output gradient after the ReLU mask (the
+    g its weight gradient sums against the layer's input)."""
     grads = {}
     h = cache["d0b"]
     grads["out.w"] = np.einsum("zyx,izyx->i", gout, h)[None, :]
@@ -168,6 +170,8 @@ def backward(params, cache, gout):
 
     def layer(name, inp, g):
         g = g * (cache[name] > 0)
+        if record is not None:
+            record[name] = g
         gx, gw, gb = conv3_backward(inp, params[name + ".w"], g)
         grads[name + ".w"] = gw
         grads[name + ".b"] = gb

@@ -23,6 +23,7 @@ OK, ERR_ARG, ERR_CUDA, NOT_CONVERGED, DIVERGED, NONFINITE = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {OK: "ok", ERR_ARG: "bad argument", ERR_CUDA: "cuda error",
                 NOT_CONVERGED: "not converged", DIVERGED: "diverged", NONFINITE: "non-finite source"}
 ISO, ANISO = 0, 1
+COARSE_SWEEPS, COARSE_DENSE = 0, 1
 FP32, FP32_BF16, IR64, IR64_FP32 = 0, 1, 2, 3
 PRECISIONS = {"fp32": FP32, "fp32_bf16": FP32_BF16, "ir64": IR64, "ir64_fp32": IR64_FP32}
 
@@ -34,7 +35,7 @@ class Options(ctypes.Structure):
                 ("omega_min", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("grow", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("cycles_per_sync", ctypes.c_int), ("ir_inner_rtol", ctypes.c_double),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("coarse_mode", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -94,6 +95,8 @@ def lib() -> ctypes.CDLL:
     L.gmg_op_coarsen_coeffs.argtypes = [c_int, c_int, c_int, ip, ip, vp, vp, vp, vp, vp, vp, vp]
     L.gmg_op_residual_norm.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
     L.gmg_op_residual_norm_noalloc.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
+    L.gmg_test_poison_omega.argtypes = [vp, c_int]
+    L.gmg_test_ring_wait_tries.argtypes = [c_int]
     L.gmg_tune_export.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.gmg_tune_import.argtypes = [ctypes.c_char_p]
     _net_signatures(L)
@@ -157,6 +160,12 @@ def tune_import(text: str) -> None:
     """Merge an exported tuning table into this process's (gmg_tune_import)."""
     if lib().gmg_tune_import(text.encode()) != OK:
         raise GmgError("gmg_tune_import: malformed tuning table")
+
+
+def test_ring_wait_tries(tries: int) -> None:
+    """Test hook (gmg_test_ring_wait_tries): poll limit of the pipelined kernels' ring
+    waits on the current device; a negative value restores the default."""
+    _check(lib().gmg_test_ring_wait_tries(int(tries)), None)
 
 
 def options(coarsen: str = "aniso", precision: str = "fp32", **kw) -> Options:
@@ -283,8 +292,12 @@ class Solver:
 
         def hp(a):
             if hasattr(a, "data_ptr"):
+                import torch
+                tdt = torch.float64 if self.fp64 else torch.float32
                 if a.is_cuda or not a.is_contiguous() or a.numel() != self.ncells:
                     raise ValueError("expected a contiguous CPU tensor of the grid size")
+                if a.dtype != tdt:
+                    raise ValueError(f"expected a CPU tensor of dtype {tdt}, got {a.dtype}")
                 return a.data_ptr()
             if a.dtype != dt or not a.flags.c_contiguous or a.size != self.ncells:
                 raise ValueError(f"expected a C-contiguous {dt.__name__} array of the grid size")
@@ -294,6 +307,11 @@ class Solver:
                                   float(tol), ctypes.byref(info))
         _check(rc, self.h, ok=SOLVE_STATUSES)
         return info
+
+    def test_poison_omega(self, cycle: int) -> None:
+        """Test hook (gmg_test_poison_omega): NaN into the device omega before V-cycle `cycle`
+        of the next solve."""
+        _check(lib().gmg_test_poison_omega(self.h, int(cycle)), self.h)
 
     def history(self, cap: int = 1000):
         import numpy as np

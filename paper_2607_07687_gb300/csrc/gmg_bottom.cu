@@ -11,7 +11,8 @@
 //   descent  : zero guess, nu1 sweeps, residual summed over the children of
 //              each coarse cell (restriction);
 //   coarsest : right-hand side projected to zero mean over active cells,
-//              nu_c sweeps from zero;
+//              nu_c sweeps from zero, or (coarse_mode 1) p = A^+ b with the
+//              level's pseudo-inverse (a GEMV from global memory);
 //   ascent   : p += e[I / c] (prolongation), nu2 sweeps;
 // and writes level lb's result for the finer level's correction.  Colour
 // phases are separated by block barriers; within a colour the cells are
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
     __shared__ double red[kBottomThreads / 32];
     __shared__ double red2[kBottomThreads / 32];
     __shared__ double s_mean;
+    __shared__ float s_gemv[kBottomThreads];   // dense coarse solve: partial sums of the groups
     // the task (level geometries, offsets, sweep counts) in shared memory: the level
     // views are rebuilt before every phase
     __shared__ __align__(16) BottomTask<TP> T;
@@ -320,8 +322,29 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         for (int i = threadIdx.x; i < C.n; i += blockDim.x)
             C.b[i] = diag_at(C, i) > 0.f ? (float)((double)C.b[i] - mean) : 0.f;
         __syncthreads();
-        if (C.n <= (int)blockDim.x) sweeps_small(C, T.nu_c, w);
-        else sweeps(C, T.nu_c, w);
+        if (T.pinv) {
+            // dense coarse solve p = A^+ b (A^+ symmetric: column j is row j, so the
+            // threads of a group read consecutive entries); the n threads of each of
+            // the G groups sum every G-th column, then the G partials are added in
+            // group order
+            const int n = C.n, G = (int)blockDim.x / n;
+            const int i = threadIdx.x % n, grp = threadIdx.x / n;
+            float acc = 0.f;
+            if (grp < G)
+                for (int j = grp; j < n; j += G) acc = fmaf(__ldg(T.pinv + (int64_t)j * n + i), C.b[j], acc);
+            s_gemv[threadIdx.x] = acc;
+            __syncthreads();
+            if (threadIdx.x < n) {
+                float sum = 0.f;
+                for (int q = 0; q < G; ++q) sum += s_gemv[q * n + threadIdx.x];
+                C.p[threadIdx.x] = sum;
+            }
+            __syncthreads();
+        } else if (C.n <= (int)blockDim.x) {
+            sweeps_small(C, T.nu_c, w);
+        } else {
+            sweeps(C, T.nu_c, w);
+        }
     }
 
     // ascent

@@ -17,6 +17,9 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cstdint>
+#include <string>
+
+#include "gmg_hw.h"
 
 namespace gmg {
 
@@ -155,6 +158,11 @@ struct BottomLevel {
     float inv_nxy;
 };
 
+// coarse_mode 1: the coarsest level (at most kDenseMaxCells cells) is solved by
+// its pseudo-inverse, built at gmg_set_coeffs
+constexpr int kDenseMaxCells = 1024;
+static_assert(kDenseMaxCells <= kBottomThreads, "one thread per coarsest cell in the dense solve");
+
 template <class TP>
 struct BottomTask {
     int nlev;            // levels lb .. L-1; the last one is the coarsest
@@ -163,6 +171,7 @@ struct BottomTask {
     TP* out;             // result of level lb (read by the finer level's correction)
     int nu1, nu2, nu_c;
     const Ctl* ctl;
+    const float* pinv;   // A^+ of the coarsest level (n x n, symmetric), or nullptr: nu_c sweeps
 };
 
 template <class Task>
@@ -272,6 +281,20 @@ cudaError_t launch_pcg_arm(Ctl* ctl, PcgScal* scal, int max_it, double tol, int 
 // Message returned by gmg_last_error(NULL) for calls without a handle.
 void set_api_error(const char* msg);
 
+// Geometry checks shared by every entry point: dimensions >= 1, at most 2^31 - 1
+// cells, even length on periodic axes.  GMG_OK, or GMG_ERR_ARG with msg set.
+int validate_geometry(int nx, int ny, int nz, const int* periodic, std::string& msg);
+
+// Blocks of the persistent grid-stride kernels for `tiles` tiles: at most
+// kResident blocks per SM of the current device.
+int persistent_grid(int64_t tiles);
+
+// Ring-slot waits of the pipelined kernels (a consumer waiting for a plane, a
+// producer waiting for a free slot) give up after this many mbarrier polls;
+// tries < 0 restores the default.  The waits for copies already in flight keep
+// their full limit.  Applies to the current device.
+cudaError_t set_ring_wait_tries(int tries);
+
 // ---------------------------------------------------------------- launchers
 
 template <class TP, class TC>
@@ -298,6 +321,12 @@ cudaError_t launch_bottom(const BottomTask<TP>* tasks, int ntasks, size_t smem, 
 // Reference variant of the sweep: one in-place launch per colour.
 cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const float* bz,
                                   const float* b, float* p, float omega, cudaStream_t s);
+
+// A^+ of one grid's operator (at most kDenseMaxCells cells) in FP32, n x n
+// row-major (symmetric), from its face coefficients (walls already zero);
+// synchronises the stream.
+cudaError_t build_dense_pinv(const Geo& g, const float* bx, const float* by, const float* bz, float* pinv,
+                             cudaStream_t s);
 
 cudaError_t launch_coarsen_coeffs(Geo fine, const int cf[3], const float* bx, const float* by,
                                   const float* bz, float* cbx, float* cby, float* cbz,

@@ -231,6 +231,9 @@ constexpr uint32_t kPlaneBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4)
 constexpr int kWaitTries = 1 << 22;
 
 __device__ int g_wait_fault = 0;
+// poll limit of the ring-slot waits (set_ring_wait_tries); the waits for copies in
+// flight always use kWaitTries
+__device__ int g_ring_tries = kWaitTries;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -591,10 +594,11 @@ __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar)
     asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// bounded wait that also gives up once another warp of the block recorded a fault
-__device__ __forceinline__ bool mbar_wait_live(uint64_t* bar, uint32_t parity, const volatile int* dead)
+// bounded wait on a ring slot that also gives up once another warp of the block
+// recorded a fault
+__device__ __forceinline__ bool mbar_wait_live(uint64_t* bar, uint32_t parity, const volatile int* dead, int tries)
 {
-    for (int i = 0; i < kWaitTries; ++i) {
+    for (int i = 0; i < tries; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 63) == 63 && *dead) return false;
     }
@@ -616,7 +620,7 @@ __device__ __forceinline__ int wrap_plane(int z, int nz, int pz)
 // pt: producer thread 0 .. kProducers - 1.
 template <class TC>
 __device__ __forceinline__ void sweep_produce(const TaskList<SweepTask<float, TC>>& tl, float* smem, uint64_t* full,
-                                              uint64_t* empty, volatile int* dead, int pt)
+                                              uint64_t* empty, volatile int* dead, int pt, int tries)
 {
     constexpr int TX = kSweepTX, TY = kSweepTY;
     constexpr int XO = 4, SW = TX + 8, PL = SW * (TY + 4);
@@ -658,7 +662,7 @@ __device__ __forceinline__ void sweep_produce(const TaskList<SweepTask<float, TC
         }
         const int nh = (z1 - z0) + 4;                      // planes z0-2 .. z1+1
         for (int m = 0; m < nh; ++m, ++g) {
-            if (g >= (uint32_t)R && !mbar_wait_live(&empty[g % R], ((g / R) - 1) & 1u, dead)) {
+            if (g >= (uint32_t)R && !mbar_wait_live(&empty[g % R], ((g / R) - 1) & 1u, dead, tries)) {
                 ok = false;
                 break;
             }
@@ -696,13 +700,13 @@ __device__ __forceinline__ void sweep_produce(const TaskList<SweepTask<float, TC
             }
         }
     }
-    if (!ok) {
-        if (lane == 0) {
-            atomicExch(&g_wait_fault, 1);
-            *dead = 1;
-        }
-        for (uint32_t q = g > (uint32_t)R ? g - R : 0; q < g; ++q) mbar_wait(&full[q % R], (q / R) & 1u);
+    if (!ok && lane == 0) {
+        atomicExch(&g_wait_fault, 1);
+        *dead = 1;
     }
+    // no copy may be in flight when the block exits (the consumers may have given
+    // up): wait, bounded, for the last R groups issued
+    for (uint32_t q = g > (uint32_t)R ? g - R : 0; q < g; ++q) mbar_wait(&full[q % R], (q / R) & 1u);
 }
 
 // ---------------------------------------------------------------- K1: warp-specialised sweep
@@ -752,10 +756,11 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
     }
     __syncthreads();
     volatile int* dead = &s_dead;
+    const int tries = g_ring_tries;
     auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
 
     if (tid >= kSweepConsumers) {
-        sweep_produce<TC>(tl, smem, full, empty, dead, tid - kSweepConsumers);
+        sweep_produce<TC>(tl, smem, full, empty, dead, tid - kSweepConsumers, tries);
         return;
     }
 
@@ -834,7 +839,7 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
         const int nh = nsteps + 2;                             // H(m): plane kr0 - 1 + m
         bool live = true;
         for (int m = 0; m < AHEAD && live; ++m)
-            live = mbar_wait_live(&full[(g + m) % R], ((g + m) / R) & 1u, dead);
+            live = mbar_wait_live(&full[(g + m) % R], ((g + m) / R) & 1u, dead, tries);
         float cur0 = 0.f, cur1 = 0.f;
         if (CORR) {
             if (live) {
@@ -862,7 +867,7 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
             const uint32_t sm = sl == 0 ? R - 1 : sl - 1;                                 // kr-2
             const int kr = kr0 + u;
             bool ok = true;
-            if (u + AHEAD <= nh - 1) ok = mbar_wait_live(&full[sw], pw, dead);
+            if (u + AHEAD <= nh - 1) ok = mbar_wait_live(&full[sw], pw, dead, tries);
             if (CORR && ok && u + 3 <= nh - 1) {
                 float nxt0, nxt1;
                 corr_load(kr + 3, nxt0, nxt1);
@@ -1002,6 +1007,7 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
     }
     __syncthreads();
     volatile int* dead = &s_dead;
+    const int tries = g_ring_tries;
     auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
 
     if (tid >= kResConsumers) {
@@ -1038,7 +1044,7 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
                 }
             }
             for (int m = 0; m < nh; ++m, ++g) {
-                if (g >= (uint32_t)R && !mbar_wait_live(&empty[g % R], ((g / R) - 1) & 1u, dead)) {
+                if (g >= (uint32_t)R && !mbar_wait_live(&empty[g % R], ((g / R) - 1) & 1u, dead, tries)) {
                     ok = false;
                     break;
                 }
@@ -1076,14 +1082,13 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
                 }
             }
         }
-        if (!ok) {
-            // record the fault, then wait (bounded) for the copies still in flight
-            if (lane == 0) {
-                atomicExch(&g_wait_fault, 1);
-                s_dead = 1;
-            }
-            for (uint32_t q = g > (uint32_t)R ? g - R : 0; q < g; ++q) mbar_wait(&full[q % R], (q / R) & 1u);
+        if (!ok && lane == 0) {
+            atomicExch(&g_wait_fault, 1);
+            s_dead = 1;
         }
+        // no copy may be in flight when the block exits (the consumers may have
+        // given up): wait, bounded, for the last R groups issued
+        for (uint32_t q = g > (uint32_t)R ? g - R : 0; q < g; ++q) mbar_wait(&full[q % R], (q / R) & 1u);
         return;
     }
 
@@ -1117,13 +1122,13 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
         float rr32 = 0.f;
         int fold = kNormFold;
         float acc0 = 0.f, acc1 = 0.f;
-        bool live = mbar_wait_live(&full[g % R], (g / R) & 1u, dead) &&
-                    mbar_wait_live(&full[(g + 1) % R], ((g + 1) / R) & 1u, dead);
+        bool live = mbar_wait_live(&full[g % R], (g / R) & 1u, dead, tries) &&
+                    mbar_wait_live(&full[(g + 1) % R], ((g + 1) / R) & 1u, dead, tries);
         auto rs = [&](int arr, uint32_t slot) -> float* { return smem + (arr * R + (int)slot) * PL; };
         uint32_t sl = g % R, sw = (g + 2) % R, pw = ((g + 2) / R) & 1u;   // H(u); H(u+2) and its parity
         for (int u = 0; u < nsteps && live; ++u) {
             const uint32_t s0 = sl + 1 == R ? 0 : sl + 1, su = sw;      // planes k, k+1
-            if (!mbar_wait_live(&full[sw], pw, dead)) {
+            if (!mbar_wait_live(&full[sw], pw, dead, tries)) {
                 live = false;
                 break;
             }
@@ -1613,11 +1618,16 @@ __global__ void k_control_cycle(const CtlTask* __restrict__ tasks)
         Ctl& C = *t.ctl;
         const double rk = sqrt(rr);
         const double w = C.omega;
-        const bool acc = rk < C.r_prev;     // NaN rejects
+        // a relaxation factor that is not a positive finite number means the control
+        // state is corrupt: the solve stops as diverged with the accepted iterate
+        const bool w_ok = isfinite(w) && w > 0.0;
+        const bool acc = w_ok && rk < C.r_prev;     // NaN rejects
         C.r_last = rk;
         C.cycles += 1;
         C.total_cycles += 1;
-        if (acc) {
+        if (!w_ok) {
+            C.status = kDiverged;
+        } else if (acc) {
             C.rot = (C.rot + C.res_role) % 3;
             C.r_prev = rk;
             C.omega = fmin(1.0, C.grow * w);
@@ -1733,7 +1743,8 @@ int grid_for(int64_t n, int per_block = kThreads)
 {
     int64_t b = (n + per_block - 1) / per_block;
     if (b < 1) b = 1;
-    if (b > 152 * 32) b = 152 * 32;
+    const int64_t cap = (int64_t)sm_count() * 32;
+    if (b > cap) b = cap;
     return (int)b;
 }
 
@@ -1922,6 +1933,12 @@ cudaError_t launch_ir_update(const IrTask& t, cudaStream_t s)
     const int64_t N = (int64_t)t.g.n[0] * t.g.n[1] * t.g.n[2];
     k_ir_update<<<grid_for(N), kThreads, 0, s>>>(t.g, t.p64, t.ebuf[0], t.ebuf[1], t.ebuf[2], t.rot);
     return cudaGetLastError();
+}
+
+cudaError_t set_ring_wait_tries(int tries)
+{
+    const int v = tries < 0 ? kWaitTries : tries;
+    return cudaMemcpyToSymbol(g_ring_tries, &v, sizeof(int));
 }
 
 int* wait_fault_flag()

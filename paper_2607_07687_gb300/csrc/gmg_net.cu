@@ -8,6 +8,7 @@
 // transposed weights; the weight gradient is a GEMM per (tap, 16-channel
 // slice) with the cells as K, split over CTAs and summed with FP32 atomics.
 #include "../../include/gmg_net.h"
+#include "gmg_hw.h"
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -479,7 +480,8 @@ int grid_of(int64_t n, int threads = 256)
 {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
-    if (b > 152 * 16) b = 152 * 16;
+    const int64_t cap = (int64_t)gmg::sm_count() * 16;
+    if (b > cap) b = cap;
     return (int)b;
 }
 
@@ -807,7 +809,7 @@ int gmg_net_conv3_wgrad(int D, int H, int W, const gmg_bf16* x, int cx, int ci, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t ncell = (int64_t)D * H * W;
     const int64_t runs = (ncell + kWgRun - 1) / kWgRun;
-    const int splits = (int)std::min<int64_t>(runs, std::max<int64_t>(1, (152 * 8) / (27 * (ci / 16))));
+    const int splits = (int)std::min<int64_t>(runs, std::max<int64_t>(1, ((int64_t)gmg::sm_count() * 8) / (27 * (ci / 16))));
     const dim3 grid(27, ci / 16, splits);
     const bf16* xb = reinterpret_cast<const bf16*>(x);
     const bf16* gb = reinterpret_cast<const bf16*>(g);

@@ -4,13 +4,13 @@
 // Implicit GEMM per CTA: T row tiles, each D_r[128 cells x N out-channels]
 // (FP32, T x N columns of TMEM) = sum over 16-channel input slices s and taps t
 // of A_{s,t,r}[128 x 16] B_{s,t}[16 x N].  The 128 cells of row tile r are
-// consecutive x positions of row y0 + r of plane z0.  For a slice, two TMA
-// boxes (one per 8-channel chunk) bring the input window x0-1 .. x0+128,
-// y0-1 .. y0+T, z0-1 .. z0+1 into shared memory as
-// [chunk][3 z][T+2 y][130 x][8 channels] (zeros outside the grid = zero
-// padding), and the slice's weights as [chunk][27 taps][N][8], shared by the
-// T row tiles; all 128 threads copy them with 16-byte asynchronous copies
-// (one per position and chunk, zero-filled outside the grid).  For tap (dz, dy, dx) and row tile r the A
+// consecutive x positions of row y0 + r of plane z0.  For a slice, all 128
+// threads bring the input window x0-1 .. x0+128, y0-1 .. y0+T, z0-1 .. z0+1
+// into shared memory as [chunk][3 z][T+2 y][130 x][8 channels] (two 8-channel
+// chunks; zeros outside the grid = zero padding) and the slice's weights as
+// [chunk][27 taps][N][8], shared by the T row tiles, with 16-byte asynchronous
+// copies (one per position and chunk, zero-filled outside the grid).  For tap
+// (dz, dy, dx) and row tile r the A
 // operand is the 128 consecutive positions that start at window row
 // (dz, r + dy), column dx: a uniform layout of 8-row x 16-byte core matrices
 // (stride 128 B along M, one chunk region along K), so every (tap, row) is one

@@ -2,10 +2,9 @@
 //
 // gmg_op_residual_norm keeps its per-tile partial sums in a device buffer the
 // library allocates on first use.  Some callers cannot let a library call
-// cudaMalloc: code recording a CUDA graph (allocation inside stream capture
-// is refused or breaks the capture), real-time loops that must never hit the
-// device-wide synchronisation cudaMalloc/cudaFree can cause, and programs
-// that run under a fixed device-memory budget decided up front.  For them,
+// cudaMalloc: real-time loops that must never meet the device-wide
+// synchronisation cudaMalloc / cudaFree can cause, and programs that run under
+// a device-memory budget fixed before they start.  For them,
 // gmg_op_residual_norm_noalloc computes the same quantity with its scratch in
 // a fixed-size array that is part of the library image: every GPU that loads
 // the library holds it (512 KB of partial sums plus one double) until the
@@ -75,16 +74,11 @@ extern "C" int gmg_op_residual_norm_noalloc(int nx, int ny, int nz, const int* p
                                             void* stream)
 {
     using namespace gmg;
-    if (nx < 1 || ny < 1 || nz < 1) {
-        set_api_error("gmg_op_residual_norm_noalloc: every dimension must be >= 1");
+    std::string geo_msg;
+    if (validate_geometry(nx, ny, nz, periodic, geo_msg) != GMG_OK) {
+        set_api_error(("gmg_op_residual_norm_noalloc: " + geo_msg).c_str());
         return GMG_ERR_ARG;
     }
-    const int n[3] = {nx, ny, nz};
-    for (int d = 0; d < 3; ++d)
-        if (periodic && periodic[d] && n[d] % 2) {
-            set_api_error("gmg_op_residual_norm_noalloc: a periodic axis must have even length");
-            return GMG_ERR_ARG;
-        }
     if (!bx || !by || !bz || !b || !p || !rr) {
         set_api_error("gmg_op_residual_norm_noalloc: null pointer");
         return GMG_ERR_ARG;
@@ -130,8 +124,7 @@ extern "C" int gmg_op_residual_norm_noalloc(int nx, int ny, int nz, const int* p
     tl.ntasks = 1;
     tl.total = (int)tiles;
     tl.single = t;
-    const int grid = (int)(tiles < 152 * 8 ? tiles : 152 * 8);
-    e = launch_residual(tl, grid, s);
+    e = launch_residual(tl, persistent_grid(tiles), s);
     if (e == cudaSuccess) e = launch_sum_partials(partials, (int)tiles, total, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(rr, total, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -18,6 +18,7 @@
 #include "../../include/gmg.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -33,7 +34,6 @@ using namespace gmg;
 
 namespace {
 
-constexpr int kSMs = 152;
 constexpr int kResident = 8;    // CTAs per SM targeted by the persistent grids
 
 thread_local std::string g_create_error;
@@ -88,10 +88,34 @@ TmaPlanes* op_tensor_maps(const Geo& g, const float* p, const float* b, const fl
     return d;
 }
 
+}  // namespace
+
+namespace gmg {
+
+int sm_count()
+{
+    constexpr int kDevices = 64;
+    static std::atomic<int> cached[kDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < kDevices) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    if (dev >= 0 && dev < kDevices) cached[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 int persistent_grid(int64_t tiles)
 {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)kSMs * kResident));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * kResident));
 }
+
+}  // namespace gmg
+
+namespace {
 
 // ------------------------------------------------------------ schedule (C3)
 
@@ -185,7 +209,7 @@ int tuned_zchunk(int kind, const Geo& g)
 int default_zchunk(const Geo& g)
 {
     const int64_t cols = (int64_t)ceil_div(g.n[0], kSweepTX) * ceil_div(g.n[1], kSweepTY);
-    const int64_t slots = (int64_t)kSMs * 3;
+    const int64_t slots = (int64_t)sm_count() * 3;
     int best_zc = g.n[2];
     double best = 1e300;
     for (int nc = 1; nc <= std::max(1, g.n[2] / 4); ++nc) {
@@ -274,6 +298,7 @@ struct ProblemMem {
     double* hist_res = nullptr;
     double* hist_omega = nullptr;
     int* hist_acc = nullptr;
+    float* pinv = nullptr;          // coarse_mode 1: A^+ of the coarsest level
 };
 
 enum OpKind { kSweepFF, kSweepFB, kSweepBB, kResF, kResB, kBottomF, kBottomB, kProjLevel, kControl };
@@ -315,6 +340,7 @@ struct Engine {
     CtlTask* init_ctl = nullptr;    // device: init / projection / gauge tasks
     CtlTask* gauge_ctl = nullptr;
     bool coeffs_set = false;
+    int poison_cycle = 0;           // test hook: before this V-cycle of the next solve, omega = NaN
     std::string err;
     int last_cycles = 0;
     long long launches = 0;     // kernels launched since the counter was reset
@@ -411,6 +437,16 @@ struct Engine {
             int cf[kMaxLevels][3];
             M.L = plan_levels(M.g0, o.coarsen == GMG_COARSEN_ANISO, o.n_min, geo, cf);
             M.n0 = cells(M.g0);
+            if (o.coarse_mode == GMG_COARSE_DENSE) {
+                const int64_t nc = cells(geo[M.L - 1]);
+                if (M.L < 2)
+                    return fail(GMG_ERR_ARG, "coarse_mode DENSE needs at least two levels (problem %d does not coarsen)", p);
+                if (nc > kDenseMaxCells)
+                    return fail(GMG_ERR_ARG,
+                                "coarse_mode DENSE needs a coarsest level of at most %d cells (problem %d: %lld)",
+                                kDenseMaxCells, p, (long long)nc);
+                if (!(M.pinv = dalloc<float>((size_t)(nc * nc)))) return fail(GMG_ERR_CUDA, "out of device memory");
+            }
             for (int l = 0; l < M.L; ++l) {
                 LevelMem& Lm = M.lev[l];
                 Lm.g = geo[l];
@@ -795,6 +831,7 @@ struct Engine {
                 t.nu2 = opt.nu2;
                 t.nu_c = opt.nu_c;
                 t.ctl = M.ctl;
+                t.pinv = M.pinv;
                 coarse_result_[p][lb] = 0;
                 if (bf16_coarse) {
                     BottomTask<bf16> tb{};
@@ -806,6 +843,7 @@ struct Engine {
                     tb.nu2 = t.nu2;
                     tb.nu_c = t.nu_c;
                     tb.ctl = t.ctl;
+                    tb.pinv = t.pinv;
                     bb.push_back(tb);
                 } else {
                     t.out = static_cast<float*>(M.lev[lb].buf[0]);
@@ -986,6 +1024,11 @@ struct Engine {
                 step = "active mask";
                 e = launch_active_mask(M.g0, M.lev[0].beta[0], M.lev[0].beta[1], M.lev[0].beta[2], M.mask, stream);
             }
+            if (e == cudaSuccess && M.pinv) {
+                step = "coarsest pseudo-inverse";
+                const LevelMem& C = M.lev[M.L - 1];
+                e = build_dense_pinv(C.g, C.beta[0], C.beta[1], C.beta[2], M.pinv, stream);
+            }
             if (e != cudaSuccess) return fail(GMG_ERR_CUDA, "gmg_set_coeffs (problem %zu, %s): %s", p, step,
                                               cudaGetErrorString(e));
         }
@@ -1152,7 +1195,8 @@ struct Engine {
         int rc = build_cycle();
         if (rc != GMG_OK) return rc;
         const std::vector<int> lb_key = {P[0].g0.n[0], P[0].g0.n[1], P[0].g0.n[2], P[0].g0.per[0], P[0].g0.per[1],
-                                         P[0].g0.per[2], opt.coarsen, opt.n_min, opt.precision, opt.nu_c};
+                                         P[0].g0.per[2], opt.coarsen, opt.n_min, opt.precision, opt.nu_c,
+                                         opt.coarse_mode};
         int cached_lb = 0;
         {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -1352,12 +1396,31 @@ struct Engine {
         return cudaMemcpyAsync(ctl_dev, ctl_host, sizeof(Ctl) * P.size(), cudaMemcpyHostToDevice, stream);
     }
 
+    // test hook (gmg_test_poison_omega): write NaN into every problem's device
+    // relaxation factor, ordered on the stream between two V-cycles
+    cudaError_t poison_omega()
+    {
+        static const double nan_value = std::nan("");
+        for (size_t p = 0; p < P.size(); ++p) {
+            cudaError_t e = cudaMemcpyAsync(&P[p].ctl->omega, &nan_value, sizeof(double), cudaMemcpyHostToDevice,
+                                            stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+
     // cycles until every problem is done; returns the CUDA status
     cudaError_t iterate()
     {
         const int per_sync = std::max(1, opt.cycles_per_sync);
+        int queued = 0;
         for (int guard = 0; guard <= opt.max_cycles; guard += per_sync) {
             for (int k = 0; k < per_sync; ++k) {
+                if (poison_cycle > 0 && ++queued == poison_cycle) {
+                    poison_cycle = 0;
+                    cudaError_t e = poison_omega();
+                    if (e != cudaSuccess) return e;
+                }
                 cudaError_t e = run_cycle();
                 if (e != cudaSuccess) return e;
             }
@@ -1858,7 +1921,9 @@ struct OpScratch {
 };
 std::vector<OpScratch> g_op_scratch;
 
-int validate_geometry(int nx, int ny, int nz, const int* periodic, std::string& msg)
+}  // namespace
+
+int gmg::validate_geometry(int nx, int ny, int nz, const int* periodic, std::string& msg)
 {
     if (nx < 1 || ny < 1 || nz < 1) {
         msg = "every dimension must be >= 1";
@@ -1877,6 +1942,8 @@ int validate_geometry(int nx, int ny, int nz, const int* periodic, std::string& 
     return GMG_OK;
 }
 
+namespace {
+
 int validate_options(const gmg_options& o, std::string& msg)
 {
     if (o.coarsen != GMG_COARSEN_ISO && o.coarsen != GMG_COARSEN_ANISO) msg = "coarsen must be ISO or ANISO";
@@ -1887,6 +1954,8 @@ int validate_options(const gmg_options& o, std::string& msg)
     else if (!(o.omega0 > 0.0) || !(o.omega_min > 0.0) || !(o.shrink > 0.0 && o.shrink < 1.0) || !(o.grow >= 1.0))
         msg = "need omega0 > 0, omega_min > 0, 0 < shrink < 1, grow >= 1";
     else if (!(o.ir_inner_rtol > 0.0 && o.ir_inner_rtol < 1.0)) msg = "need 0 < ir_inner_rtol < 1";
+    else if (o.coarse_mode != GMG_COARSE_SWEEPS && o.coarse_mode != GMG_COARSE_DENSE)
+        msg = "coarse_mode must be SWEEPS or DENSE";
     else return GMG_OK;
     return GMG_ERR_ARG;
 }
@@ -1924,6 +1993,7 @@ void gmg_default_options(gmg_options* o)
     o->cycles_per_sync = 4;
     o->ir_inner_rtol = 1e-4;
     o->autotune = 1;
+    o->coarse_mode = GMG_COARSE_SWEEPS;
 }
 
 int gmg_create(gmg_handle* h, int nx, int ny, int nz, const int* periodic, const gmg_options* opt,
@@ -2059,6 +2129,25 @@ const char* gmg_last_error(gmg_handle h)
     return h->eng.err.c_str();
 }
 
+// ---------------------------------------------------------------- test hooks
+
+int gmg_test_poison_omega(gmg_handle h, int cycle)
+{
+    if (!h || cycle < 1) return GMG_ERR_ARG;
+    h->eng.poison_cycle = cycle;
+    return GMG_OK;
+}
+
+int gmg_test_ring_wait_tries(int tries)
+{
+    const cudaError_t e = gmg::set_ring_wait_tries(tries);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("gmg_test_ring_wait_tries: ") + cudaGetErrorString(e);
+        return GMG_ERR_CUDA;
+    }
+    return GMG_OK;
+}
+
 // ---------------------------------------------------------------- tuning table
 
 int gmg_tune_export(char* buf, size_t cap, size_t* len)
@@ -2104,8 +2193,8 @@ int gmg_tune_import(const char* text)
             if (a < 0 || a > (1L << 30)) return GMG_ERR_ARG;
         if (tag == "z" && v.size() == 8 && v[7] > 0) {
             zs[TuneKey{(int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5], (int)v[6]}] = (int)v[7];
-        } else if (tag == "b" && v.size() == 11 && v[10] > 0) {
-            bs[std::vector<int>(v.begin(), v.begin() + 10)] = (int)v[10];
+        } else if (tag == "b" && v.size() == 12 && v[11] > 0) {
+            bs[std::vector<int>(v.begin(), v.begin() + 11)] = (int)v[11];
         } else {
             return GMG_ERR_ARG;
         }

@@ -32,7 +32,8 @@ def test_default_options(L):
 
 def _create(L, dims, periodic=(0, 0, 0), **kw):
     h = ctypes.c_void_p()
-    o = G.options(**kw)
+    coarsen = kw.pop("coarsen", "aniso")
+    o = G.options(coarsen=coarsen, **kw)
     rc = L.gmg_create(ctypes.byref(h), *dims, G._ivec(periodic), ctypes.byref(o), None)
     return rc, L.gmg_last_error(None).decode()
 
@@ -48,6 +49,9 @@ def _create(L, dims, periodic=(0, 0, 0), **kw):
     ((8, 8, 8), (0, 0, 0), {"shrink": 1.5}, "shrink"),
     ((8, 8, 8), (0, 0, 0), {"n_min": 0}, "n_min"),
     ((8, 8, 8), (0, 0, 0), {"ir_inner_rtol": 0.0}, "ir_inner_rtol"),
+    ((8, 8, 8), (0, 0, 0), {"coarse_mode": 2}, "coarse_mode"),
+    ((6, 6, 6), (0, 0, 0), {"coarse_mode": 1}, "two levels"),           # does not coarsen
+    ((48, 48, 48), (0, 0, 0), {"coarse_mode": 1, "n_min": 16, "coarsen": "iso"}, "1024"),   # coarsest 24^3
 ])
 def test_create_rejects(L, dims, periodic, kw, frag):
     rc, msg = _create(L, dims, periodic, **kw)
@@ -93,7 +97,7 @@ def test_tune_table_round_trip(L):
     """The autotuner's table exports as text and imports back unchanged (no GPU involved)."""
     text = ("z 0 256 96 96 0 0 0 8\n"
             "z 2 128 48 48 0 0 0 12\n"
-            "b 256 96 96 0 0 0 1 4 0 16 3\n")
+            "b 256 96 96 0 0 0 1 4 0 16 0 3\n")
     G.tune_import(text)
     out = G.tune_export()
     for line in text.splitlines():

@@ -76,14 +76,17 @@ def test_sphere_channel_fp32_iso(O):
 
 
 def _refined_parity(O, key, coarsen, tol=1e-6):
-    """FP64 refinement around FP32 V-cycles to tol; cycles within 2 of the oracle's
-    and the solution against its iterate after the same number of cycles."""
+    """FP64 refinement around FP32 V-cycles to tol; cycles within 1 of the oracle's
+    and the solution against its iterate after the same number of cycles.  In exact
+    arithmetic the refinement loop runs the same V-cycle iteration as the oracle
+    (each inner cycle is the cycle applied to the residual equation), so the counts
+    differ only where FP32 rounding moves a residual across the tolerance."""
     prob = problem(key)
     ref = oracle_cached(key, tol, coarsen=coarsen)
     got, info, _ = gpu_solve(prob, tol, coarsen=coarsen, precision="ir64_fp32")
     assert info.status == 0 and info.rel_res <= tol, info.as_dict()
     assert info.levels == ref.levels
-    assert abs(info.cycles - ref.cycles) <= 2, (info.cycles, ref.cycles)
+    assert abs(info.cycles - ref.cycles) <= 1, (info.cycles, ref.cycles)
     same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles,
                                                                   coarsen=coarsen)
     assert rel_l2(got, same.p) <= 1e-5
@@ -114,21 +117,26 @@ def test_sphere_channel_refined_to_1e6(O, precision):
     got, info, _ = gpu_solve(prob, 1e-6, coarsen="aniso", precision=precision)
     assert info.status == 0 and info.rel_res <= 1e-6, info.as_dict()
     assert info.outer >= 1
-    slack = 1 if precision == "ir64_fp32" else 4
-    assert abs(info.cycles - ref.cycles) <= slack, (info.cycles, ref.cycles)
+    assert abs(info.cycles - ref.cycles) <= 1, (info.cycles, ref.cycles)
     same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles)
     assert rel_l2(got, same.p) <= 1e-5
 
 
 def test_bf16_corrections_converge(O):
-    """BF16 storage of the coarse corrections: same tolerance reached, solution
-    within 1e-5 of the oracle (the cycle count may differ)."""
+    """BF16 storage of the coarse corrections: same tolerance reached, V-cycles
+    within 1 of the oracle's.  The BF16 rounding perturbs each coarse correction
+    by up to 2^-9 relative, a perturbation of the cycle's low-frequency part that
+    the next cycle's coarse correction removes, so the contraction per cycle and
+    the count stay those of the FP32 cycle; the solution matches the oracle's
+    iterate after the same number of cycles within 1e-5."""
     prob = problem(("tg", 32, 0))
     ref = oracle_cached(("tg", 32, 0), 1e-6, coarsen="iso")
     got, info, _ = gpu_solve(prob, 1e-6, coarsen="iso", precision="fp32_bf16")
     assert info.status == 0
-    assert info.cycles <= ref.cycles + 3
-    assert rel_l2(got, ref.p) <= 1e-5
+    assert abs(info.cycles - ref.cycles) <= 1, (info.cycles, ref.cycles)
+    same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles,
+                                                                  coarsen="iso")
+    assert rel_l2(got, same.p) <= 1e-5
 
 
 def test_taylor_green_128_refined_vs_fft(O):
@@ -322,3 +330,79 @@ def test_tuning_table_import_is_used():
         assert rel_l2(b, a) <= 1e-5
     finally:
         G.tune_import(table)
+
+
+def _oracle_batch_entry(args):
+    prob, tol = args
+    from oracle import oracle as O
+    O.build()
+    return O.solve_problem(prob, tol=tol)
+
+
+def test_batch_fp64_refinement_matches_oracle():
+    """The batched FP64-refinement solve of config 3's problems at 1e-6: sixteen of
+    the sixty-four uneven problems, every fourth by size from the smallest to the
+    largest, each against the FP64 oracle (V-cycles within 1; the solution within
+    1e-5 of the oracle's iterate after the same number of cycles).  The oracle runs
+    in a spawned process pool (one process per problem)."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+
+    import torch
+    from oracle import oracle as O
+    from paper_2607_07687_gb300 import binding as G
+    every = I.batch_problems(64, seed=3)
+    by_size = sorted(range(64), key=lambda k: every[k].cells)
+    pick = [by_size[k] for k in range(0, 64, 4)]
+    probs = [every[k] for k in pick]
+    assert probs[0].cells <= 32 ** 3 * 2 and probs[-1].cells >= 150_000
+    tol = 1e-6
+    with ProcessPoolExecutor(max_workers=16, mp_context=multiprocessing.get_context("spawn")) as ex:
+        refs = list(ex.map(_oracle_batch_entry, [(p, tol) for p in probs]))
+    bs = G.BatchSolver([p.dims for p in probs], precision="ir64_fp32")
+    bs.set_coeffs([t32(p.bx) for p in probs], [t32(p.by) for p in probs], [t32(p.bz) for p in probs])
+    sig = [t64(f32(p.b)) for p in probs]
+    out = [torch.zeros_like(x) for x in sig]
+    infos = bs.solve(sig, out, tol)
+    torch.cuda.synchronize()
+    bs.close()
+    worst = 0.0
+    for prob, o, inf, ref in zip(probs, out, infos, refs):
+        assert inf.status == 0 and inf.rel_res <= tol, (prob.name, inf.as_dict())
+        assert ref.status == 0, prob.name
+        assert abs(inf.cycles - ref.cycles) <= 1, (prob.name, inf.cycles, ref.cycles)
+        same = ref if inf.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=inf.cycles)
+        err = rel_l2(host(o), same.p)
+        worst = max(worst, err)
+        assert err <= 1e-5, (prob.name, err)
+    print("batch vs oracle: worst rel L2", worst, "cycles", [i.cycles for i in infos])
+
+
+@pytest.mark.parametrize("key,coarsen,tol,precision", [(("tg", 32, 0), "iso", 1e-6, "fp32"),
+                                                       (("sphere",), "aniso", 1e-5, "fp32"),
+                                                       (("sphere",), "aniso", 1e-6, "ir64_fp32"),
+                                                       (("rand", (64, 24, 16), (0, 0, 0)), "aniso", 1e-5, "fp32"),
+                                                       (("rand", (32, 16, 16), (1, 1, 1)), "aniso", 1e-5, "fp32")])
+def test_dense_coarse_solve_matches_oracle(O, key, coarsen, tol, precision):
+    """The dense coarsest-level option (coarse_mode 1: p = A^+ b on the coarsest
+    level, the pseudo-inverse built on the device in FP64): V-cycles within 1 of
+    the oracle's with the same option, the solution within 1e-5 of the oracle's
+    iterate after the same number of cycles, and no more cycles than the default
+    coarsest sweeps need."""
+    from paper_2607_07687_gb300 import binding as G
+    if key[0] == "rand":
+        prob = I.random_small_problem(key[1], key[2], seed=sum(key[1]))
+    else:
+        prob = problem(key)
+    ref = O.solve_problem(prob, tol=tol, coarsen=coarsen, coarse_mode=1)
+    got, info, _ = gpu_solve(prob, tol, coarsen=coarsen, precision=precision, coarse_mode=G.COARSE_DENSE)
+    assert info.status == 0 and info.rel_res <= tol, info.as_dict()
+    assert abs(info.cycles - ref.cycles) <= 1, (info.cycles, ref.cycles)
+    same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles,
+                                                                  coarsen=coarsen, coarse_mode=1)
+    err = rel_l2(got, same.p)
+    assert err <= 1e-5, err
+    sweeps = O.solve_problem(prob, tol=tol, coarsen=coarsen)
+    print(prob.name, "dense coarsest:", info.cycles, "cycles (oracle", ref.cycles, "), sweeps:", sweeps.cycles,
+          "rel L2", err)
+    assert info.cycles <= sweeps.cycles

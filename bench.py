@@ -40,6 +40,7 @@ UNIT = "Gcell-updates/s"
 TOL = 1e-6
 DIMS = (256, 96, 96)
 BYTES_PER_CELL_SWEEP = 24          # read p, b, bx, by, bz; write p (FP32)
+BYTES_PER_CELL_RESIDUAL = 20.5     # read p, b, bx, by, bz; write the 2x2x2-restricted coarse b
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -103,17 +104,17 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the fine sweep from the committed ncu summary,
-    valid only while the kernel source is unchanged."""
+def recorded_traffic(key="k_sweep_ws_256x96x96"):
+    """DRAM bytes per launch of a kernel from the committed ncu summary
+    (profiles/traffic.json), valid only while the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2607_07687_gb300", "csrc", "gmg_kernels.cu")
     try:
         with open(path) as f:
             rec = json.load(f)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        k = rec.get("k_sweep_fine", {})
-        if k.get("source_sha256") == h and k.get("cells") == DIMS[0] * DIMS[1] * DIMS[2]:
+        k = rec.get(key, {})
+        if k.get("source_sha256") == h:
             return float(k["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -179,6 +180,108 @@ class Clocks:
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_ms(launch, flush, stream, reps=10):
+    """Mean CUDA-event time of launch(i) on `stream`, the L2 flushed before each launch."""
+    import torch
+    for i in range(3):
+        launch(i)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for i in range(reps):
+        flush_l2(flush)
+        ev[i][0].record(stream)
+        launch(i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+
+def fft_closed_form(b32):
+    """Exact discrete solution of the beta = 1 triple-periodic problem, in FP64:
+    p_hat(k) = b_hat(k) / lambda(k), lambda(k) = -sum_d 4 sin^2(pi k_d / n_d),
+    p_hat(0) = 0 (the Fourier symbol of the 7-point operator; multithreaded FFT)."""
+    import numpy as np
+    import scipy.fft as sf
+    b = b32.astype(np.float64)
+    b = b - b.mean()
+    nz, ny, nx = b.shape
+    lam = np.zeros((nz, ny, nx // 2 + 1))
+    for axis, n in ((0, nz), (1, ny), (2, nx)):
+        k = np.arange(n if axis < 2 else nx // 2 + 1)
+        sh = [1, 1, 1]
+        sh[axis] = len(k)
+        lam = lam + (-4.0 * np.sin(np.pi * k / n) ** 2).reshape(sh)
+    lam[0, 0, 0] = 1.0
+    ph = sf.rfftn(b, workers=os.cpu_count()) / lam
+    ph[0, 0, 0] = 0.0
+    return sf.irfftn(ph, s=b.shape, axes=(0, 1, 2), workers=os.cpu_count())
+
+
+def record_512(dev, stream, flush, peak, peak_kind):
+    """The 512^3 triple-periodic Taylor-Green cube (FP32 V-cycles inside FP64
+    refinement to 1e-10, isotropic coarsening): its fine-level sweep and residual
+    kernels at the launch shapes the autotuner chose for this grid, each timed with
+    CUDA events on its stream with the L2 flushed before every launch (algorithmic
+    bytes 24 and 20.5 per cell), and the whole solve's time, V-cycles and relative
+    L2 error against the FFT closed form."""
+    import numpy as np
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    from paper_2607_07687_gb300 import inputs as I
+    n = 512
+    shape = (n, n, n)
+    per = (True, True, True)
+    prob = I.taylor_green_problem(n, seed=2)
+    beta = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (prob.bx, prob.by, prob.bz)]
+    b32 = np.asarray(prob.b, dtype=np.float32)
+    b64 = torch.from_numpy(b32.astype(np.float64)).to(dev)
+    solver = G.Solver(prob.dims, prob.periodic, coarsen="iso", precision="ir64_fp32")
+    solver.set_coeffs(*beta)            # times the launch shapes of every level of this grid
+    p = torch.zeros_like(b64)
+    solver.solve(b64, p, 1e-10)
+    ts = []
+    for _ in range(3):
+        p.zero_()
+        flush_l2(flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = solver.solve(b64, p, 1e-10)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    fft = fft_closed_form(b32)
+    got = p.cpu().numpy()
+    fft_err = float(np.linalg.norm(got - fft) / np.linalg.norm(fft))
+    del p, b64
+    # the kernels on random fields of the same grid
+    gen = torch.Generator(device=dev).manual_seed(0)
+    rb = [torch.rand(shape, device=dev, generator=gen) for _ in range(3)]
+    rhs = torch.randn(shape, device=dev, generator=gen)
+    pa = torch.randn(shape, device=dev, generator=gen)
+    pb = torch.zeros_like(pa)
+    coarse = torch.zeros((n // 2, n // 2, n // 2), device=dev)
+    cells = n ** 3
+    out = {"workload": "taylor_green_512^3_periodic_iso", "l2": "flushed before every launch",
+           "solve": {"tol": 1e-10, "precision": "fp32 V-cycles, fp64 refinement", "ms": float(np.median(ts)),
+                     "v_cycles": info.cycles, "refinement_steps": info.outer, "rel_res": info.rel_res,
+                     "fft_rel_l2": fft_err, "gcell_updates_per_s": cells * info.cycles / (np.median(ts) * 1e-3) / 1e9}}
+    kernels = (("sweep", "k_sweep_ws", BYTES_PER_CELL_SWEEP,
+                lambda i: G.op_sweep(*rb, rhs, pa if i % 2 == 0 else pb, pb if i % 2 == 0 else pa, 1.0, per)),
+               ("residual", "k_residual_ws", BYTES_PER_CELL_RESIDUAL,
+                lambda i: G.op_residual_restrict(*rb, rhs, pa, coarse, (2, 2, 2), per)))
+    for key, kname, bpc, launch in kernels:
+        ms = kernel_ms(launch, flush, stream, reps=20)
+        achieved = bpc * cells / (ms * 1e-3) / 1e9
+        out[key] = {"kernel": kname, "bound": "hbm", "ms": ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                    "bytes_per_cell": bpc, "traffic": recorded_traffic(f"{kname}_512"),
+                    "tuning": [ln for ln in G.tune_export().splitlines() if " 512 512 512 " in ln]}
+    solver.close()
+    del rb, rhs, pa, pb, coarse
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_oracle_sample(prob, cycles=None):
@@ -495,6 +598,64 @@ def fig2(args):
     return 0
 
 
+def impulsive(args):
+    """The V-cycles of Fig. 2 (Sec. 3.2): predictor and corrector solves of the first
+    4 time steps of an impulsive start (inputs.impulsive_sources: eight sources on
+    fixed coefficients, the body's uniform-stream source first, the vortical part
+    growing after it), the first solve from zero and each later one from the
+    previous converged pressure, to 1e-6 (FP32 V-cycles inside FP64 refinement).
+    Geometries of --fig2 (2D cylinder 64N x 64 x 1, spanwise-periodic cylinder
+    64N x 64 x 32, sphere 64N x 64 x 64; radius 8 at x = 32), N = 1, 2, 4, 8;
+    isotropic against anisotropic coarsening, each with the coarsest sweeps and
+    with the dense coarsest solve.  One JSON line per geometry."""
+    import numpy as np
+    import torch
+    from paper_2607_07687_gb300 import build as B
+    B.build()
+    from paper_2607_07687_gb300 import binding as G
+    from paper_2607_07687_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    for kind in I.IMPULSIVE_GEOMETRIES:
+        rows = []
+        for n in (1, 2, 4, 8):
+            prob, rhs = I.impulsive_sources(kind, 64 * n)
+            beta = [f32(a) for a in (prob.bx, prob.by, prob.bz)]
+            b64 = [torch.from_numpy(np.asarray(b, dtype=np.float32).astype(np.float64)).to(dev) for b in rhs]
+            row = {"aspect_ratio": n, "dims": list(prob.dims)}
+            for coarsen in ("iso", "aniso"):
+                for mode, label in ((G.COARSE_SWEEPS, "sweeps"), (G.COARSE_DENSE, "dense")):
+                    try:
+                        s = G.Solver(prob.dims, prob.periodic, precision="ir64_fp32", coarsen=coarsen,
+                                     max_cycles=1000, coarse_mode=mode)
+                    except G.GmgError as e:       # the dense option needs a coarsest level of <= 1024 cells
+                        row[f"{coarsen}_{label}"] = {"unavailable": str(e)}
+                        continue
+                    s.set_coeffs(*beta)
+                    p = torch.zeros_like(b64[0])
+                    s.solve(b64[0], p, TOL)            # warm-up (graph capture)
+                    p.zero_()
+                    cyc = []
+                    torch.cuda.synchronize()
+                    ev0.record()
+                    for b in b64:
+                        info = s.solve(b, p, TOL)
+                        cyc.append(int(info.cycles))
+                    ev1.record()
+                    torch.cuda.synchronize()
+                    row[f"{coarsen}_{label}"] = {"v_cycles": cyc, "total": sum(cyc), "ms": ev0.elapsed_time(ev1),
+                                                 "levels": int(info.levels), "status": int(info.status)}
+                    s.close()
+            row["total_ratio_iso_over_aniso"] = row["iso_sweeps"]["total"] / max(1, row["aniso_sweeps"]["total"])
+            rows.append(row)
+        print(json.dumps({"experiment": "impulsive start: predictor + corrector V-cycles of steps 1-4",
+                          "geometry": kind, "tol": TOL, "precision": "FP32 V-cycles in FP64 refinement",
+                          "rows": rows}), flush=True)
+    return 0
+
+
 def pcg_compare(args):
     """The paper's solver comparison (Sec. 3, Table 1): Jacobi-preconditioned CG
     and the multigrid with a PCG smoother (GMG-PCG) against the multigrid with
@@ -694,6 +855,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-512", action="store_true",
+                    help="skip the 512^3 record (sweep and residual rooflines, FP64-refined solve vs FFT)")
     ap.add_argument("--kernel", choices=["sweep", "residual"], default=None,
                     help="only launch one kernel --reps times on a --grid (for profiler captures)")
     ap.add_argument("--grid", default="512,256,128", help="nx,ny,nz of the --kernel grid")
@@ -708,6 +871,9 @@ def main():
     ap.add_argument("--fig2", action="store_true",
                     help="iso vs aniso coarsening over aspect ratios 1-8: 2D cylinder, spanwise-periodic "
                          "cylinder, sphere")
+    ap.add_argument("--impulsive", action="store_true",
+                    help="predictor/corrector V-cycles of the first 4 steps of impulsive starts, iso vs aniso, "
+                         "aspect ratios 1-8 (Fig. 2)")
     ap.add_argument("--suite", action="store_true",
                     help="time to tolerance of every solver form on the paper-shaped workloads")
     ap.add_argument("--no-large", action="store_true", help="--suite without the 512^3 cube")
@@ -731,6 +897,8 @@ def main():
         return suite(args)
     if args.fig2:
         return fig2(args)
+    if args.impulsive:
+        return impulsive(args)
     if args.pcg:
         return pcg_compare(args)
     if args.net:
@@ -859,6 +1027,8 @@ def main():
                     "d2h_bytes_per_step": 8 * cells, "ms_per_step": e2e_ms},
             "gpu_launches": int(infos[-1].launches) * args.steps,
             "clocks": clk.summary()}
+    if not args.no_512:
+        line["roofline_512"] = record_512(dev, stream, flush, peak, peak_kind)
     if rank == 0 and ws == 1 and not args.no_cpu:
         res, dt = cpu_oracle_sample(prob)
         line["cpu_baseline"] = {"value": cells * res.cycles / dt / 1e9, "unit": UNIT, "cores": 1,

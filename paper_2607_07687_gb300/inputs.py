@@ -312,6 +312,57 @@ def cylinder_channel_problem(nx: int = 256, ny: int = 64, nz: int = 1, seed: int
     return Problem(shape, periodic, b, bx, by, bz, bodies, f"cylinder_{kind}_{nx}x{ny}x{nz}")
 
 
+class _NoPotential:
+    """A = 0: the uniform stream alone."""
+
+    @staticmethod
+    def curl(x, y, z, L):
+        return 0.0, 0.0, 0.0
+
+
+IMPULSIVE_GEOMETRIES = ("cylinder_2d", "cylinder_spanwise", "sphere")
+
+
+def impulsive_sources(kind: str, nx: int, ny: int = 64, nz: int = None, steps: int = 4, seed: int = 5,
+                      radius: float = 8.0, center_x: float = 32.0, u_inf: float = 1.0):
+    """Sources of the pressure solves of the first `steps` time steps of an
+    impulsive start (the setting of the paper's Fig. 2): the body moves at u_inf
+    from t = 0, and every step has a predictor and a corrector projection, i.e.
+    2 * steps solves on fixed coefficients.  Solve k (k = 0, 1, ...) has
+
+        b_k = div_h(beta_flow (u_inf e_x + c_k curl A)),   c_k = k / (2 steps),
+
+    with A the geometry's seeded potential (planar for the 2D cylinder): the
+    first solve sees the body's source of the uniform stream alone (the
+    low-wavenumber axial pressure wave of an impulsive start), and the vortical
+    part of the intermediate velocity builds up over the steps.  By linearity
+    b_k = b_body + c_k b_vort, both computed once.
+
+    kind: "cylinder_2d" (nz = 1), "cylinder_spanwise" (z periodic, nz = 32 by
+    default) or "sphere" (walls, nz = 64 by default).  Returns (problem, [b_0,
+    b_1, ...]): the problem carries the coefficients and b_0."""
+    if kind not in IMPULSIVE_GEOMETRIES:
+        raise ValueError(f"kind must be one of {IMPULSIVE_GEOMETRIES}")
+    if nz is None:
+        nz = {"cylinder_2d": 1, "cylinder_spanwise": 32, "sphere": 64}[kind]
+    shape = (nz, ny, nx)
+    if kind == "sphere":
+        periodic = (False, False, False)
+        bodies = [Body("sphere", (center_x, ny / 2.0, nz / 2.0), radius)]
+    else:
+        periodic = (False, False, kind == "cylinder_spanwise")
+        bodies = [Body("cylinder", (center_x, ny / 2.0, nz / 2.0), radius)]
+    rng = np.random.default_rng(seed)
+    pot = FourierPotential.draw_planar(rng) if nz == 1 else FourierPotential.draw(rng)
+    b_body = solenoidal_rhs(shape, bodies, _NoPotential(), u_inf)
+    b_vort = solenoidal_rhs(shape, bodies, pot, 0.0)
+    n = 2 * steps
+    rhs = [b_body + (k / n) * b_vort for k in range(n)]
+    bx, by, bz = apply_walls(*body_beta(shape, bodies), periodic=periodic)
+    prob = Problem(shape, periodic, rhs[0], bx, by, bz, bodies, f"impulsive_{kind}_{nx}x{ny}x{nz}")
+    return prob, rhs
+
+
 def random_bodies(rng: np.random.Generator, dims, count: int) -> List[Body]:
     nx, ny, nz = dims
     out = []

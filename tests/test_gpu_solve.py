@@ -406,3 +406,45 @@ def test_dense_coarse_solve_matches_oracle(O, key, coarsen, tol, precision):
     print(prob.name, "dense coarsest:", info.cycles, "cycles (oracle", ref.cycles, "), sweeps:", sweeps.cycles,
           "rel L2", err)
     assert info.cycles <= sweeps.cycles
+
+
+@pytest.mark.parametrize("kind,nx,ny,nz", [("cylinder_2d", 128, 32, 1), ("cylinder_spanwise", 64, 32, 16),
+                                           ("sphere", 64, 32, 16)])
+@pytest.mark.parametrize("coarsen", ["iso", "aniso"])
+def test_impulsive_sequence_matches_oracle(O, kind, nx, ny, nz, coarsen):
+    """The predictor and corrector solves of the first 4 steps of an impulsive
+    start (Fig. 2's setting, reduced to aspect ratio 4): eight solves on fixed
+    coefficients, the first from zero, each later one from the previous converged
+    pressure, FP32 V-cycles inside FP64 refinement to 1e-6.  Every solve's
+    V-cycle count within 1 of the oracle's on the same sequence (the oracle warm-
+    starting from its own previous solution), and aniso needing fewer in total."""
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    prob, rhs = I.impulsive_sources(kind, nx, ny, nz, radius=4.0, center_x=16.0)
+    coef32 = [f32(a) for a in (prob.bx, prob.by, prob.bz)]
+    s = G.Solver(prob.dims, prob.periodic, coarsen=coarsen, precision="ir64_fp32")
+    try:
+        s.set_coeffs(*[t32(a) for a in coef32])
+        p = t64(np.zeros(prob.shape))
+        pr = np.zeros(prob.shape)
+        got, ref = [], []
+        for b in rhs:
+            info = s.solve(t64(f32(b)), p, 1e-6)
+            assert info.status == 0 and info.rel_res <= 1e-6, info.as_dict()
+            r = O.solve(f32(b), *coef32, prob.periodic, tol=1e-6, p0=pr, coarsen=coarsen)
+            assert r.status == 0
+            pr = r.p
+            got.append(info.cycles)
+            ref.append(r.cycles)
+    finally:
+        s.close()
+    print(prob.name, coarsen, "GPU", got, sum(got), "oracle", ref, sum(ref))
+    assert all(abs(a - b) <= 1 for a, b in zip(got, ref)), (got, ref)
+    if coarsen == "aniso":
+        iso = []
+        pr = np.zeros(prob.shape)
+        for b in rhs:
+            r = O.solve(f32(b), *coef32, prob.periodic, tol=1e-6, p0=pr, coarsen="iso")
+            pr = r.p
+            iso.append(r.cycles)
+        assert sum(got) < sum(iso), (got, iso)

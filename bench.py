@@ -335,6 +335,10 @@ def kernel_only(args):
     B.build()
     from paper_2607_07687_gb300 import binding as G
     nx, ny, nz = (int(v) for v in args.grid.split(","))
+    per = (False, False, False) if args.walls else (True, True, True)
+    if args.zchunk:                 # the launch shape the autotuner would choose, fixed by hand
+        G.tune_import("".join(f"z {k} {nx} {ny} {nz} {int(per[0])} {int(per[1])} {int(per[2])} {args.zchunk}\n"
+                              for k in (0, 1, 2)))
     gen = torch.Generator(device="cuda").manual_seed(0)
     shape = (nz, ny, nx)
     beta = [torch.rand(shape, device="cuda", generator=gen) for _ in range(3)]
@@ -343,7 +347,7 @@ def kernel_only(args):
     pb = torch.zeros_like(pa)
     coarse = torch.zeros((nz // 2, ny // 2, nx // 2), device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    per = (False, False, False) if args.walls else (True, True, True)
+
     def launch(i):
         if args.kernel == "sweep":
             G.op_sweep(*beta, b, pa if i % 2 == 0 else pb, pb if i % 2 == 0 else pa, 1.0, per)
@@ -363,8 +367,11 @@ def kernel_only(args):
         ev[i][1].record()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(c) for a, c in ev) / args.reps
+    bpc = BYTES_PER_CELL_SWEEP if args.kernel == "sweep" else BYTES_PER_CELL_RESIDUAL
+    gbs = bpc * nx * ny * nz / (ms * 1e-3) / 1e9
     print(json.dumps({"kernel": args.kernel, "grid": [nx, ny, nz], "periodic": not args.walls, "reps": args.reps,
-                      "ms_per_launch": ms, "l2": "flushed before each launch"}))
+                      "zchunk": args.zchunk or "tuned/default", "ms_per_launch": ms, "algorithmic_GBs": gbs,
+                      "l2": "flushed before each launch"}))
     return 0
 
 
@@ -862,6 +869,7 @@ def main():
     ap.add_argument("--grid", default="512,256,128", help="nx,ny,nz of the --kernel grid")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--walls", action="store_true", help="--kernel grid with walls instead of periodic axes")
+    ap.add_argument("--zchunk", type=int, default=0, help="--kernel: z-chunk depth of the launch (0: tuned or default)")
     ap.add_argument("--tune-file", default=None,
                     help="autotuner table: loaded when the file exists (no timing of launch shapes), "
                          "else written after the run; a profiler run then launches what a plain run tuned")

@@ -605,6 +605,52 @@ def fig2(args):
     return 0
 
 
+def solve_only(args):
+    """--solve-only WORKLOAD: one warm-up and --reps timed solves of one workload
+    ("sphere": the 256x96x96 sphere channel to 1e-6, "tg512": the 512^3
+    Taylor-Green cube to 1e-10; FP32 V-cycles inside FP64 refinement), with the
+    autotuner's table from --tune-file when it exists (written after the run
+    otherwise), so that a profiler run launches exactly what a plain run timed."""
+    import numpy as np
+    import torch
+    from paper_2607_07687_gb300 import build as B
+    B.build()
+    from paper_2607_07687_gb300 import binding as G
+    from paper_2607_07687_gb300 import inputs as I
+    loaded = bool(args.tune_file and os.path.exists(args.tune_file))
+    if loaded:
+        G.tune_import(open(args.tune_file).read())
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if args.solve_only == "tg512":
+        prob, coarsen, tol = I.taylor_green_problem(512, seed=2), "iso", 1e-10
+    else:
+        prob, coarsen, tol = workload(), "aniso", TOL
+    beta = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev) for a in (prob.bx, prob.by, prob.bz)]
+    b = torch.from_numpy(np.asarray(prob.b, dtype=np.float32).astype(np.float64)).to(dev)
+    s = G.Solver(prob.dims, prob.periodic, coarsen=coarsen, precision="ir64_fp32")
+    s.set_coeffs(*beta)
+    p = torch.zeros_like(b)
+    s.solve(b, p, tol)
+    ts = []
+    for _ in range(args.reps):
+        p.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = s.solve(b, p, tol)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    s.close()
+    if args.tune_file and not loaded:
+        with open(args.tune_file, "w") as f:
+            f.write(G.tune_export())
+    print(json.dumps({"workload": prob.name, "tol": tol, "ms": ts, "v_cycles": info.cycles, "outer": info.outer,
+                      "launches": info.launches, "tuning": "loaded" if loaded else "timed"}), flush=True)
+    return 0
+
+
 def impulsive(args):
     """The V-cycles of Fig. 2 (Sec. 3.2): predictor and corrector solves of the first
     4 time steps of an impulsive start (inputs.impulsive_sources: eight sources on
@@ -879,6 +925,8 @@ def main():
     ap.add_argument("--fig2", action="store_true",
                     help="iso vs aniso coarsening over aspect ratios 1-8: 2D cylinder, spanwise-periodic "
                          "cylinder, sphere")
+    ap.add_argument("--solve-only", choices=["sphere", "tg512"], default=None,
+                    help="only time --reps solves of one workload (for profiler launch lists)")
     ap.add_argument("--impulsive", action="store_true",
                     help="predictor/corrector V-cycles of the first 4 steps of impulsive starts, iso vs aniso, "
                          "aspect ratios 1-8 (Fig. 2)")
@@ -899,6 +947,8 @@ def main():
     args = ap.parse_args()
     if args.kernel:
         return kernel_only(args)
+    if args.solve_only:
+        return solve_only(args)
     if args.warmstart:
         return warmstart_bench(args)
     if args.suite:

@@ -237,7 +237,7 @@ struct IrTask {
     float* b32;          // inner right-hand side
     float* ebuf[3];      // inner iterate roles
     const int* rot;
-    double* partials;    // one per residual tile
+    double* partials;    // one per block of the residual launch (at most one per tile)
     int tiles_x, tiles_y, tiles_z;
     Ctl* ctl;
     double* scale;       // device scalar: inner = outer residual * scale

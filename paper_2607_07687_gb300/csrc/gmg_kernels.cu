@@ -1445,18 +1445,21 @@ __global__ void __launch_bounds__(kThreads) k_project_sum(const __grid_constant_
         const ProjTask<TS>* t = task_of(tl, tile, local);
         const int64_t beg = (int64_t)local * kElemTile;
         const int64_t end = min(t->n, beg + kElemTile);
-        double s = 0.0, c = 0.0, bad = 0.0;
+        // the sum in FP64 (the mean must be exact to the solve's tolerance); the
+        // counts, at most kElemTile / kThreads per thread, in FP32 (exact)
+        double s = 0.0;
+        float c32 = 0.f, bad32 = 0.f;
         for (int64_t i = beg + threadIdx.x; i < end; i += kThreads) {
             const double v = (double)t->sigma[i];
-            if (!isfinite(v)) bad += 1.0;
+            if (!isfinite(v)) bad32 += 1.f;
             if (t->mask[i]) {
                 s += v;
-                c += 1.0;
+                c32 += 1.f;
             }
         }
         s = block_sum(s, red);
-        c = block_sum(c, red);
-        bad = block_sum(bad, red);
+        const double c = block_sum((double)c32, red);
+        const double bad = block_sum((double)bad32, red);
         if (threadIdx.x == 0) {
             t->partials[3 * local + 0] = s;
             t->partials[3 * local + 1] = c;
@@ -1475,23 +1478,27 @@ __global__ void __launch_bounds__(kThreads) k_project_apply(const __grid_constan
         const double mean = t->ctl->mean;
         const int64_t beg = (int64_t)local * kElemTile;
         const int64_t end = min(t->n, beg + kElemTile);
-        double q = 0.0;
+        // |b|^2: for an FP32 right-hand side, FP32 squares over the kElemTile / kThreads
+        // cells of a thread, then FP64 (relative error below 2^-20); FP64 squares for
+        // an FP64 one (no range limit)
+        float q32 = 0.f;
+        double q64 = 0.0;
         for (int64_t i = beg + threadIdx.x; i < end; i += kThreads) {
             const bool act = t->mask[i] != 0;
             const double bv = act ? (double)t->sigma[i] - mean : 0.0;
             if (t->b32) {
                 const float f = (float)bv;
                 t->b32[i] = f;
-                q += (double)f * (double)f;
+                q32 = fmaf(f, f, q32);
             } else {
                 t->b64[i] = bv;
-                q += bv * bv;
+                q64 = fma(bv, bv, q64);
             }
             const double pv = (act && t->p_in) ? (double)t->p_in[i] : 0.0;
             if (t->p32) t->p32[i] = (float)pv;
             if (t->p64) t->p64[i] = pv;
         }
-        q = block_sum(q, red);
+        const double q = block_sum((double)q32 + q64, red);
         if (threadIdx.x == 0) t->bpartials[local] = q;
     }
 }
@@ -1650,43 +1657,77 @@ __global__ void k_control_cycle(const CtlTask* __restrict__ tasks)
 
 // ---------------------------------------------------------------- K9: FP64 refinement
 
+// r64 = b64 - A p64 in FP64 (the refinement's residual), written as the FP32
+// inner right-hand side, with the inner iterate's role-0 buffer cleared.  Cells
+// whose six neighbours lie inside the grid take them at fixed offsets; the
+// others wrap periodic axes and drop wall faces.  Both paths evaluate the same
+// FP64 expression.  Each thread sums the squares of its r in FP64 over all its
+// tiles and each block writes one partial, partials[blockIdx.x] (one block
+// reduction per launch instead of one per tile).
+
 __global__ void __launch_bounds__(kThreads) k_ir_residual(const __grid_constant__ IrTask t)
 {
     __shared__ double red[kThreads / 32];
     const Geo g = t.g;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const int64_t nxy = (int64_t)nx * ny;
     const int tx = threadIdx.x % kResTX;
     const int ty = (threadIdx.x / kResTX) % kResTY;
     const int tz = threadIdx.x / (kResTX * kResTY);
     const int total = t.tiles_x * t.tiles_y * t.tiles_z;
+    double rr = 0.0;
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int cx = tile % t.tiles_x;
         const int rest = tile / t.tiles_x;
         const int cy = rest % t.tiles_y;
         const int cz = rest / t.tiles_y;
         const int x = cx * kResTX + tx, y = cy * kResTY + ty, z = cz * kResTZ + tz;
-        double r = 0.0;
-        if (x < g.n[0] && y < g.n[1] && z < g.n[2]) {
-            auto pv = [&](int xx, int yy, int zz) -> double {
-                if (!wrapc(xx, g.n[0], g.per[0]) || !wrapc(yy, g.n[1], g.per[1]) ||
-                    !wrapc(zz, g.n[2], g.per[2]))
-                    return 0.0;
-                return t.p64[lin(g, xx, yy, zz)];
-            };
-            const double fxl = face_lo(t.bx, g, 0, x, y, z), fxu = face_lo(t.bx, g, 0, x + 1, y, z);
-            const double fyl = face_lo(t.by, g, 1, x, y, z), fyu = face_lo(t.by, g, 1, x, y + 1, z);
-            const double fzl = face_lo(t.bz, g, 2, x, y, z), fzu = face_lo(t.bz, g, 2, x, y, z + 1);
-            const double p0 = pv(x, y, z);
-            const double Ap = ((fxl * (pv(x - 1, y, z) - p0) + fxu * (pv(x + 1, y, z) - p0)) +
-                               (fyl * (pv(x, y - 1, z) - p0) + fyu * (pv(x, y + 1, z) - p0))) +
-                              (fzl * (pv(x, y, z - 1) - p0) + fzu * (pv(x, y, z + 1) - p0));
-            const int64_t I = lin(g, x, y, z);
-            r = t.b64[I] - Ap;
+        if (x < nx && y < ny && z < nz) {
+            const int64_t I = ((int64_t)z * ny + y) * nx + x;
+            const double p0 = t.p64[I];
+            double pxl, pxu, pyl, pyu, pzl, pzu, fxl, fxu, fyl, fyu, fzl, fzu;
+            if (x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && z > 0 && z < nz - 1) {
+                pxl = t.p64[I - 1];
+                pxu = t.p64[I + 1];
+                pyl = t.p64[I - nx];
+                pyu = t.p64[I + nx];
+                pzl = t.p64[I - nxy];
+                pzu = t.p64[I + nxy];
+                fxl = __ldg(t.bx + I);
+                fxu = __ldg(t.bx + I + 1);
+                fyl = __ldg(t.by + I);
+                fyu = __ldg(t.by + I + nx);
+                fzl = __ldg(t.bz + I);
+                fzu = __ldg(t.bz + I + nxy);
+            } else {
+                auto pv = [&](int xx, int yy, int zz) -> double {
+                    if (!wrapc(xx, nx, g.per[0]) || !wrapc(yy, ny, g.per[1]) || !wrapc(zz, nz, g.per[2]))
+                        return 0.0;
+                    return t.p64[lin(g, xx, yy, zz)];
+                };
+                pxl = pv(x - 1, y, z);
+                pxu = pv(x + 1, y, z);
+                pyl = pv(x, y - 1, z);
+                pyu = pv(x, y + 1, z);
+                pzl = pv(x, y, z - 1);
+                pzu = pv(x, y, z + 1);
+                fxl = face_lo(t.bx, g, 0, x, y, z);
+                fxu = face_lo(t.bx, g, 0, x + 1, y, z);
+                fyl = face_lo(t.by, g, 1, x, y, z);
+                fyu = face_lo(t.by, g, 1, x, y + 1, z);
+                fzl = face_lo(t.bz, g, 2, x, y, z);
+                fzu = face_lo(t.bz, g, 2, x, y, z + 1);
+            }
+            const double Ap = ((fxl * (pxl - p0) + fxu * (pxu - p0)) + (fyl * (pyl - p0) + fyu * (pyu - p0))) +
+                              (fzl * (pzl - p0) + fzu * (pzu - p0));
+            const double r = t.b64[I] - Ap;
             t.b32[I] = (float)r;
             t.ebuf[0][I] = 0.f;
+            rr = fma(r, r, rr);
         }
-        const double q = block_sum(r * r, red);
-        if (threadIdx.x == 0) t.partials[tile] = q;
     }
+    const double q = block_sum(rr, red);
+    if (threadIdx.x == 0) t.partials[blockIdx.x] = q;
 }
 
 __global__ void k_ir_begin_inner(Ctl* ctl, const double* __restrict__ part, int n, double tol,

@@ -1835,9 +1835,10 @@ struct Engine {
         e = cudaMemcpyAsync(ctl_dev, ctl_host, sizeof(Ctl) * N, cudaMemcpyHostToDevice, stream);
         auto outer_residual = [&](size_t q) {
             launches += 2;
-            cudaError_t r = launch_ir_residual(t[q], persistent_grid(rt[q].tiles()), stream);
-            if (r == cudaSuccess)
-                r = launch_ir_begin_inner(t[q], (int)rt[q].tiles(), tol, opt.ir_inner_rtol, opt.max_cycles, stream);
+            // one norm partial per block of the residual launch
+            const int grid = persistent_grid(rt[q].tiles());
+            cudaError_t r = launch_ir_residual(t[q], grid, stream);
+            if (r == cudaSuccess) r = launch_ir_begin_inner(t[q], grid, tol, opt.ir_inner_rtol, opt.max_cycles, stream);
             return r;
         };
         for (;;) {

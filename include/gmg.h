@@ -310,6 +310,24 @@ int gmg_op_residual_restrict(int nx, int ny, int nz, const int* periodic, const 
                              const float* bx, const float* by, const float* bz, const float* b,
                              const float* p, float* b_coarse, double* rr, void* stream);
 
+/*
+ * The residual of the FP64 iterative refinement, r = b - A p, on FP64 arrays b
+ * and p (device doubles of nx*ny*nz; faces FP32 as for gmg_op_sweep).
+ * definition 0 is the evaluation the solver runs: the six neighbour differences
+ * p_nb - p_I in FP64, then the products, their sum and b - A p in double-length
+ * FP32 arithmetic (hi + lo pairs of FP32, about 44 significant bits; cells
+ * whose values leave the FP32 exponent range are evaluated in FP64).
+ * definition 1 evaluates everything in FP64 (the reference the first is
+ * checked against).  r_out (device double array) receives r, r32_out (device
+ * float array) r rounded to FP32; either may be NULL.  If rr is not NULL the
+ * host receives the sum of the squares of the FP32 r (FP64 sum; the call then
+ * synchronises the stream).  GMG_ERR_ARG for bad dimensions, null arrays or a
+ * definition other than 0 or 1.
+ */
+int gmg_op_residual64(int nx, int ny, int nz, const int* periodic, const float* bx, const float* by,
+                      const float* bz, const double* b, const double* p, double* r_out, float* r32_out,
+                      double* rr, int definition, void* stream);
+
 /* p[I] += e[I / f] on the fine grid (piecewise-constant prolongation, Sec. 3). */
 int gmg_op_prolong_add(int nx, int ny, int nz, const int* factors, const float* e, float* p,
                        void* stream);

@@ -92,6 +92,7 @@ def lib() -> ctypes.CDLL:
     L.gmg_op_sweep_reference.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, c_double, vp]
     L.gmg_op_residual_restrict.argtypes = [c_int, c_int, c_int, ip, ip, vp, vp, vp, vp, vp, vp, dp, vp]
     L.gmg_op_prolong_add.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp]
+    L.gmg_op_residual64.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, vp, vp, dp, c_int, vp]
     L.gmg_op_coarsen_coeffs.argtypes = [c_int, c_int, c_int, ip, ip, vp, vp, vp, vp, vp, vp, vp]
     L.gmg_op_residual_norm.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
     L.gmg_op_residual_norm_noalloc.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
@@ -443,6 +444,24 @@ def op_residual_norm_noalloc(bx, by, bz, b, p, periodic=(False, False, False), s
     rr = ctypes.c_double(0.0)
     rc = lib().gmg_op_residual_norm_noalloc(*dims, _ivec(periodic), *ptrs, ctypes.byref(rr),
                                             ctypes.c_void_p(_stream(stream)))
+    _check(rc, None)
+    return rr.value
+
+
+def op_residual64(bx, by, bz, b, p, periodic=(False, False, False), definition: int = 0, r_out=None, r32_out=None,
+                  stream=None) -> float:
+    """r = b - A p of the FP64 refinement (gmg_op_residual64): float64 b and p, float32
+    faces; definition 0 (the solver's double-length FP32 evaluation) or 1 (all FP64).
+    Writes r into r_out (float64) and/or r32_out (float32); returns sum r32^2."""
+    import torch
+    dims = _dims_of(b)
+    n = b.numel()
+    fp = [_ptr(t, torch.float32, n) for t in (bx, by, bz)]
+    rr = ctypes.c_double(0.0)
+    rc = lib().gmg_op_residual64(*dims, _ivec(periodic), *fp, _ptr(b, torch.float64, n), _ptr(p, torch.float64, n),
+                                 _ptr(r_out, torch.float64, n) if r_out is not None else None,
+                                 _ptr(r32_out, torch.float32, n) if r32_out is not None else None,
+                                 ctypes.byref(rr), int(definition), ctypes.c_void_p(_stream(stream)))
     _check(rc, None)
     return rr.value
 

@@ -234,8 +234,9 @@ struct IrTask {
     const float* bz;
     const double* b64;
     double* p64;
-    float* b32;          // inner right-hand side
-    float* ebuf[3];      // inner iterate roles
+    float* b32;          // inner right-hand side (FP32 r), or nullptr
+    double* r64;         // r in full, or nullptr (single-step op)
+    float* ebuf[3];      // inner iterate roles (role 0 cleared), ebuf[0] may be nullptr
     const int* rot;
     double* partials;    // one per block of the residual launch (at most one per tile)
     int tiles_x, tiles_y, tiles_z;
@@ -352,7 +353,9 @@ template <class TP, class TD>
 cudaError_t launch_gauge_apply(const TaskList<GaugeTask<TP, TD>>& tl, int grid, cudaStream_t s);
 cudaError_t launch_gauge_finalize(const CtlTask* t, int nprob, cudaStream_t s);
 
-cudaError_t launch_ir_residual(const IrTask& t, int grid, cudaStream_t s);
+// r = b64 - A p64 (double-length FP32 after FP64 differences), or, with
+// fp64_definition, the all-FP64 evaluation it is checked against
+cudaError_t launch_ir_residual(const IrTask& t, int grid, cudaStream_t s, bool fp64_definition = false);
 cudaError_t launch_ir_begin_inner(const IrTask& t, int nparts, double tol, double inner_rtol,
                                   int max_cycles, cudaStream_t s);
 cudaError_t launch_ir_update(const IrTask& t, cudaStream_t s);

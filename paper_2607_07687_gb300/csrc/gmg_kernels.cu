@@ -1657,14 +1657,87 @@ __global__ void k_control_cycle(const CtlTask* __restrict__ tasks)
 
 // ---------------------------------------------------------------- K9: FP64 refinement
 
-// r64 = b64 - A p64 in FP64 (the refinement's residual), written as the FP32
-// inner right-hand side, with the inner iterate's role-0 buffer cleared.  Cells
-// whose six neighbours lie inside the grid take them at fixed offsets; the
-// others wrap periodic axes and drop wall faces.  Both paths evaluate the same
-// FP64 expression.  Each thread sums the squares of its r in FP64 over all its
-// tiles and each block writes one partial, partials[blockIdx.x] (one block
-// reduction per launch instead of one per tile).
+// ---------------------------------------------------------------- double-length FP32 arithmetic
+//
+// A value held as an unevaluated sum hi + lo of two FP32 numbers (Dekker,
+// "A floating-point technique for extending the available precision", 1971):
+// error-free sums (Knuth's two-sum; Dekker's fast two-sum when |a| >= |b|) and
+// the error-free product with a fused multiply-add give about 44 significant
+// bits on the FP32 pipe, which on this part runs 64 times the FP64 rate.
+// Every rounding is spelled out, so no compiled contraction changes them.
+struct DF {
+    float hi, lo;
+};
 
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF s = two_sum(a.hi, b.hi);
+    const DF t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+// a * b for an FP32 b
+__device__ __forceinline__ DF df_mul(DF a, float b)
+{
+    const float p = __fmul_rn(a.hi, b);
+    const float e = __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p));
+    return fast_two_sum(p, e);
+}
+
+// x (FP64) as hi + lo without FP64 arithmetic: hi takes the leading 24 bits of
+// the significand (truncated, exact), lo the 29 bits below them rounded to 24,
+// so |x - hi - lo| <= 2^-47 |x|.  false when x lies outside the range this
+// covers (|x| >= 2^128, non-finite, or |x| < 2^-74, where lo would underflow;
+// zero is covered exactly).
+__device__ __forceinline__ bool split64(double x, DF& out)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    if ((u << 1) == 0) {
+        out = {0.f, 0.f};
+        return true;
+    }
+    const int ef = (int)((u >> 52) & 0x7ff) - 1023 + 127;   // FP32 biased exponent of hi
+    if (ef < 53 || ef > 254) return false;
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    const unsigned long long m = u & 0xFFFFFFFFFFFFFull;
+    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(m >> 29));
+    const float lo = __fmul_rn(__uint2float_rn((unsigned)(m & 0x1FFFFFFFu)), __uint_as_float((unsigned)(ef - 52) << 23));
+    out = {hi, sign ? -lo : lo};
+    return true;
+}
+
+// ---------------------------------------------------------------- K9: FP64 refinement residual
+//
+// r = b64 - A p64, the refinement's residual, written as the FP32 inner
+// right-hand side, with the inner iterate's role-0 buffer cleared.  Cells whose
+// six neighbours lie inside the grid take them at fixed offsets; the others wrap
+// periodic axes and drop wall faces.
+//
+// DF = false is the definition, all in FP64 (about 23 FP64 operations a cell,
+// which bound the kernel: FP64 runs at 1/64 of the FP32 rate on this part).
+// DF = true, the one the solver runs: the six differences p_nb - p_I in FP64
+// (so their rounding is relative to the difference, not to |p|), then every
+// difference and b64 split into hi + lo and the products, sums and b - A p in
+// double-length FP32; eight FP64 operations a cell.  A cell whose values leave
+// the split's range is evaluated by the FP64 expression.  r64, when set,
+// receives r in full (the single-step op; the solver writes only the FP32 r).
+// Each thread sums r^2 in FP64 over all its tiles; each block writes one
+// partial, partials[blockIdx.x].
+template <bool DF_PATH>
 __global__ void __launch_bounds__(kThreads) k_ir_residual(const __grid_constant__ IrTask t)
 {
     __shared__ double red[kThreads / 32];
@@ -1685,7 +1758,8 @@ __global__ void __launch_bounds__(kThreads) k_ir_residual(const __grid_constant_
         if (x < nx && y < ny && z < nz) {
             const int64_t I = ((int64_t)z * ny + y) * nx + x;
             const double p0 = t.p64[I];
-            double pxl, pxu, pyl, pyu, pzl, pzu, fxl, fxu, fyl, fyu, fzl, fzu;
+            double pxl, pxu, pyl, pyu, pzl, pzu;
+            float fxl, fxu, fyl, fyu, fzl, fzu;
             if (x > 0 && x < nx - 1 && y > 0 && y < ny - 1 && z > 0 && z < nz - 1) {
                 pxl = t.p64[I - 1];
                 pxu = t.p64[I + 1];
@@ -1718,12 +1792,38 @@ __global__ void __launch_bounds__(kThreads) k_ir_residual(const __grid_constant_
                 fzl = face_lo(t.bz, g, 2, x, y, z);
                 fzu = face_lo(t.bz, g, 2, x, y, z + 1);
             }
-            const double Ap = ((fxl * (pxl - p0) + fxu * (pxu - p0)) + (fyl * (pyl - p0) + fyu * (pyu - p0))) +
-                              (fzl * (pzl - p0) + fzu * (pzu - p0));
-            const double r = t.b64[I] - Ap;
-            t.b32[I] = (float)r;
-            t.ebuf[0][I] = 0.f;
-            rr = fma(r, r, rr);
+            const double b = t.b64[I];
+            double r = 0.0;
+            float r32 = 0.f;
+            bool done = false;
+            if (DF_PATH) {
+                DF d[6], bb;
+                const bool ok = split64(pxl - p0, d[0]) & split64(pxu - p0, d[1]) & split64(pyl - p0, d[2]) &
+                                split64(pyu - p0, d[3]) & split64(pzl - p0, d[4]) & split64(pzu - p0, d[5]) &
+                                split64(b, bb);
+                if (ok) {
+                    const DF ax = df_add(df_mul(d[0], fxl), df_mul(d[1], fxu));
+                    const DF ay = df_add(df_mul(d[2], fyl), df_mul(d[3], fyu));
+                    const DF az = df_add(df_mul(d[4], fzl), df_mul(d[5], fzu));
+                    const DF ap = df_add(df_add(ax, ay), az);
+                    const DF rd = df_add(bb, {-ap.hi, -ap.lo});
+                    r32 = rd.hi;
+                    if (t.r64) r = (double)rd.hi + (double)rd.lo;
+                    done = true;
+                }
+            }
+            if (!done) {
+                const double Ap = (((double)fxl * (pxl - p0) + (double)fxu * (pxu - p0)) +
+                                   ((double)fyl * (pyl - p0) + (double)fyu * (pyu - p0))) +
+                                  ((double)fzl * (pzl - p0) + (double)fzu * (pzu - p0));
+                r = b - Ap;
+                r32 = (float)r;
+            }
+            if (t.r64) t.r64[I] = r;
+            if (t.b32) t.b32[I] = r32;
+            if (t.ebuf[0]) t.ebuf[0][I] = 0.f;
+            const double rs = (double)r32;
+            rr = fma(rs, rs, rr);
         }
     }
     const double q = block_sum(rr, red);
@@ -1956,9 +2056,10 @@ cudaError_t launch_gauge_finalize(const CtlTask* t, int nprob, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_ir_residual(const IrTask& t, int grid, cudaStream_t s)
+cudaError_t launch_ir_residual(const IrTask& t, int grid, cudaStream_t s, bool fp64_definition)
 {
-    k_ir_residual<<<grid, kThreads, 0, s>>>(t);
+    if (fp64_definition) k_ir_residual<false><<<grid, kThreads, 0, s>>>(t);
+    else k_ir_residual<true><<<grid, kThreads, 0, s>>>(t);
     return cudaGetLastError();
 }
 

@@ -2440,6 +2440,40 @@ static int op_residual(int nx, int ny, int nz, const int* periodic, const int* f
     return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
+int gmg_op_residual64(int nx, int ny, int nz, const int* periodic, const float* bx, const float* by,
+                      const float* bz, const double* b, const double* p, double* r_out, float* r32_out,
+                      double* rr, int definition, void* stream)
+{
+    std::string msg;
+    if (validate_geometry(nx, ny, nz, periodic, msg) != GMG_OK) return GMG_ERR_ARG;
+    if (!bx || !by || !bz || !b || !p || (definition != 0 && definition != 1)) return GMG_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    IrTask t{};
+    t.g = make_geo(nx, ny, nz, periodic);
+    t.bx = bx;
+    t.by = by;
+    t.bz = bz;
+    t.b64 = b;
+    t.p64 = const_cast<double*>(p);
+    t.b32 = r32_out;
+    t.r64 = r_out;
+    const ResTiling rt = res_tiling(t.g);
+    t.tiles_x = rt.tx;
+    t.tiles_y = rt.ty;
+    t.tiles_z = rt.tz;
+    const int grid = persistent_grid(rt.tiles());
+    std::lock_guard<std::mutex> lock(g_op_mutex);
+    double* out = nullptr;
+    if (op_scratch(grid, &t.partials, &out) != GMG_OK) return GMG_ERR_CUDA;
+    cudaError_t e = launch_ir_residual(t, grid, s, definition == 1);
+    if (e == cudaSuccess && rr) {
+        e = launch_sum_partials(t.partials, grid, out, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rr, out, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
+}
+
 int gmg_op_residual_restrict(int nx, int ny, int nz, const int* periodic, const int* factors,
                              const float* bx, const float* by, const float* bz, const float* b,
                              const float* p, float* b_coarse, double* rr, void* stream)

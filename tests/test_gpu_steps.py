@@ -108,3 +108,67 @@ def test_coarsen_coeffs_matches_oracle(O, dims, periodic, fac):
     ref = O.coarsen_beta(*I.apply_walls(bx, by, bz, periodic), fac, periodic)
     for g, r in zip(out, ref):
         _close(host(g), r, rtol=1e-6)
+
+
+def _face_sums(p, bx, by, bz, periodic):
+    """Per cell: sum over its faces of beta_f |p_nb - p_I| and of beta_f (|p_nb| + |p_I|)
+    (walls carry no face), the magnitudes the residual's roundings scale with."""
+    diff = np.zeros_like(p)
+    mag = np.zeros_like(p)
+    for beta, ax, per in ((bx, 2, periodic[0]), (by, 1, periodic[1]), (bz, 0, periodic[2])):
+        lo = beta.copy()
+        hi = np.roll(beta, -1, axis=ax)
+        if not per:
+            idx = [slice(None)] * 3
+            idx[ax] = 0
+            lo[tuple(idx)] = 0.0
+            idx[ax] = -1
+            hi[tuple(idx)] = 0.0
+        for face, nb in ((lo, np.roll(p, 1, axis=ax)), (hi, np.roll(p, -1, axis=ax))):
+            diff += np.abs(face * (nb - p))
+            mag += face * (np.abs(nb) + np.abs(p))
+    return diff, mag
+
+
+@pytest.mark.parametrize("dims,periodic", [((70, 18, 13), (0, 0, 0)), ((64, 16, 14), (1, 1, 1)),
+                                           ((33, 20, 9), (0, 1, 0)), ((130, 40, 6), (1, 0, 0))])
+def test_refinement_residual_definitions(O, dims, periodic):
+    """r = b - A p of the FP64 refinement, on data where r is 1e-9 of b (the
+    cancellation the refinement meets near convergence): the FP64 definition
+    against the oracle's operator, within FP64 rounding of the face terms
+    (2^-50 of sum beta (|p_nb| + |p_I|), since the oracle sums in another order);
+    the solver's evaluation (FP64 differences, double-length FP32 products and
+    sums) against the definition within 2^-40 of sum beta |p_nb - p_I| + |b|
+    (about 2^-44 from the double-length arithmetic, 16x margin); cells with
+    values beyond the FP32 exponent range fall back to the definition exactly."""
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    nx, ny, nz = dims
+    shape = (nz, ny, nx)
+    rng = np.random.default_rng(sum(dims))
+    (bx, by, bz), _, _ = random_fields(dims, periodic, seed=sum(dims) + 1)
+    z, y, x = np.meshgrid(*(np.arange(n) for n in shape), indexing="ij")
+    p = 1e3 * np.sin(2 * np.pi * x / nx) * np.cos(2 * np.pi * y / ny) + 37.0 + rng.standard_normal(shape)
+    p[1, 2, 3] = 3e39                                   # a difference beyond FP32 range: the FP64 path
+    Ap = O.apply_A(p, bx, by, bz, periodic)
+    b = Ap + 1e-9 * np.median(np.abs(Ap)) * rng.standard_normal(shape)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+    tb, tp = T(b), T(p)
+    beta = [t32(a) for a in (bx, by, bz)]
+    r_def, r_df = torch.zeros_like(tb), torch.zeros_like(tb)
+    r32 = torch.zeros(shape, dtype=torch.float32, device="cuda:0")
+    rr_def = G.op_residual64(*beta, tb, tp, periodic, definition=1, r_out=r_def)
+    rr_df = G.op_residual64(*beta, tb, tp, periodic, definition=0, r_out=r_df, r32_out=r32)
+    r_def, r_df, r32 = host(r_def), host(r_df), host(r32)
+    ref = b - Ap
+    diff, mag = _face_sums(p, bx, by, bz, periodic)
+    assert np.all(np.abs(r_def - ref) <= 2.0 ** -50 * (mag + np.abs(b)))
+    assert np.all(np.abs(r_df - r_def) <= 2.0 ** -40 * (diff + np.abs(b)))
+    far = (diff > 1e38)
+    assert far.any() and np.array_equal(r_df[far], r_def[far])
+    assert np.all(np.abs(r32 - r_df) <= 2.0 ** -24 * np.abs(r_df))     # r32: r rounded to FP32
+    near = ~far
+    print("max |r_df - r_def| / scale:", float(np.max(np.abs(r_df - r_def)[near] / (diff + np.abs(b))[near])),
+          "r / b:", float(np.abs(ref[near]).max() / np.abs(b[near]).max()))
+    assert rr_df == pytest.approx(float(np.sum(r32 * r32)), rel=1e-12)
+    assert rr_def > 0

@@ -790,8 +790,8 @@ def suite(args):
             ts.append(ev0.elapsed_time(ev1))
         return float(np.median(ts)), out
 
-    def single(prob, precision, tol, coarsen, reps, warm):
-        s = G.Solver(prob.dims, prob.periodic, precision=precision, coarsen=coarsen)
+    def single(prob, precision, tol, coarsen, reps, warm, coarse_mode=0):
+        s = G.Solver(prob.dims, prob.periodic, precision=precision, coarsen=coarsen, coarse_mode=coarse_mode)
         s.set_coeffs(f32(prob.bx), f32(prob.by), f32(prob.bz))
         fp64 = s.fp64
         b = torch.from_numpy(np.asarray(prob.b, dtype=np.float32).astype(np.float64 if fp64 else np.float32)).to(dev)
@@ -803,34 +803,40 @@ def suite(args):
         ms, info = timed(run, reps, warm)
         s.close()
         cells = prob.cells
-        return {"precision": precision, "ms": ms, "v_cycles": info.cycles, "refinement_steps": info.outer,
+        return {"precision": precision, "coarsest": "dense" if coarse_mode else "sweeps", "ms": ms,
+                "v_cycles": info.cycles, "refinement_steps": info.outer,
                 "rel_res": info.rel_res, "status": info.status,
                 "gcell_updates_per_s": cells * info.cycles / (ms * 1e-3) / 1e9}
 
     lines = []
     prob = I.taylor_green_problem(32, seed=0)
     lines.append({"workload": "taylor_green_32^3_iso", "tol": 1e-6,
-                  "forms": [single(prob, "fp32", 1e-6, "iso", 10, 3)]})
+                  "forms": [single(prob, "fp32", 1e-6, "iso", 10, 3), single(prob, "fp32", 1e-6, "iso", 10, 3, 1)]})
     prob = I.sphere_channel_problem(*DIMS, seed=1)
     lines.append({"workload": "sphere_channel_256x96x96_aniso", "tol": 1e-6,
                   "forms": [single(prob, "ir64_fp32", 1e-6, "aniso", 10, 3),
-                            single(prob, "ir64", 1e-6, "aniso", 10, 3)]})
+                            single(prob, "ir64", 1e-6, "aniso", 10, 3),
+                            single(prob, "ir64_fp32", 1e-6, "aniso", 10, 3, 1)]})
+    lines.append({"workload": "sphere_channel_256x96x96_iso", "tol": 1e-6,
+                  "forms": [single(prob, "ir64_fp32", 1e-6, "iso", 10, 3),
+                            single(prob, "ir64_fp32", 1e-6, "iso", 10, 3, 1)]})
     del prob
     if not args.no_large:
         prob = I.taylor_green_problem(512, seed=2)
         lines.append({"workload": "taylor_green_512^3_iso", "tol": 1e-10,
                       "forms": [single(prob, "ir64_fp32", 1e-10, "iso", 3, 1),
-                                single(prob, "ir64", 1e-10, "iso", 3, 1)]})
+                                single(prob, "ir64", 1e-10, "iso", 3, 1),
+                                single(prob, "ir64_fp32", 1e-10, "iso", 3, 1, 1)]})
         del prob
     probs = I.batch_problems(64, seed=3)
     tol = 1e-6
     cells = sum(pr.cells for pr in probs)
     entry = {"workload": "batch_64_uneven_walls_bodies", "tol": tol, "cells": cells, "forms": []}
-    for precision in ("fp32", "ir64_fp32"):
+    for precision, cmode in (("fp32", 0), ("ir64_fp32", 0), ("ir64_fp32", 1)):
         fp64 = precision == "ir64_fp32"
         rhs = [torch.from_numpy(np.asarray(pr.b, dtype=np.float32).astype(np.float64 if fp64 else np.float32)).to(dev)
                for pr in probs]
-        bs = G.BatchSolver([pr.dims for pr in probs], precision=precision)
+        bs = G.BatchSolver([pr.dims for pr in probs], precision=precision, coarse_mode=cmode)
         bs.set_coeffs([f32(pr.bx) for pr in probs], [f32(pr.by) for pr in probs], [f32(pr.bz) for pr in probs])
         pp = [torch.zeros_like(x) for x in rhs]
 
@@ -842,7 +848,7 @@ def suite(args):
         bs.close()
         sols = []
         for pr, b in zip(probs, rhs):
-            s1 = G.Solver(pr.dims, pr.periodic, precision=precision)
+            s1 = G.Solver(pr.dims, pr.periodic, precision=precision, coarse_mode=cmode)
             s1.set_coeffs(f32(pr.bx), f32(pr.by), f32(pr.bz))
             sols.append((s1, b, torch.zeros_like(b)))
 
@@ -856,7 +862,7 @@ def suite(args):
         for s1, _, _ in sols:
             s1.close()
         entry["forms"].append({
-            "precision": precision,
+            "precision": precision, "coarsest": "dense" if cmode else "sweeps",
             "batched": {"ms": batch_ms, "v_cycles_max": max(i.cycles for i in infos),
                         "converged": sum(int(i.status) == 0 for i in infos),
                         "worst_rel_res": max(i.rel_res for i in infos)},

@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
 {
     constexpr int TX = kSweepTX, TY = kSweepTY;
     constexpr int XO = 4, SW = TX + 8, SH = TY + 4, PL = SW * SH;   // 40 x 12 positions per plane
-    constexpr int R = kSweepRing;               // planes per ring, every array
+    constexpr int R = 6;                        // planes per ring, every array (the step sequence is unrolled by 6)
+    static_assert(R <= kSweepRing, "the shared memory the launcher reserves holds kSweepRing slots");
     constexpr int LA = CORR ? 2 : 3;            // copy lookahead in z-steps
     constexpr int PA = CORR ? 1 : 0;            // p planes arrive PA further ahead (correction)
     static_assert(3 + LA + PA <= R && 3 + LA <= R, "ring depth vs lookahead");
@@ -733,7 +734,6 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
     constexpr int TX = kSweepTX, TY = kSweepTY;
     constexpr int XO = 4, SW = TX + 8, PL = SW * (TY + 4);
     constexpr int R = kSweepRing;
-    constexpr int CPR = SW / 4, NCH = PL / 4;
     constexpr int RPR = (TX + 2) / 2, NRED = RPR * (TY + 2);   // red cells of the tile and its ring
     constexpr int BPR = TX / 2, NBLK = BPR * TY;               // black cells of the tile (x-pairs)
     constexpr int BLK0 = kSweepConsumers - NBLK;               // black duty: the last NBLK consumers

@@ -88,7 +88,8 @@ typedef struct {
     double shrink;      /* factor applied to omega after a rejected cycle (default 0.7) */
     double grow;        /* factor applied after an accepted cycle, capped at 1 (default 1.1) */
     int use_graph;      /* replay the V-cycle from a captured CUDA graph (default 1) */
-    int cycles_per_sync;/* V-cycles queued before the host reads the status (default 4) */
+    int cycles_per_sync;/* at most this many V-cycles queued between two reads of the status; the solver
+                           queues as many as the contraction seen so far predicts (default 8) */
     double ir_inner_rtol; /* IR modes: inner V-cycles stop at this residual reduction (default 1e-4) */
     int autotune;       /* time launch shapes at gmg_set_coeffs and keep the fastest (default 1) */
     int coarse_mode;    /* coarsest level: GMG_COARSE_SWEEPS (default) or GMG_COARSE_DENSE */

@@ -130,6 +130,18 @@ struct ResTask {
     const TmaPlanes* tma;  // plane copies by TMA (marching kernel), or nullptr
 };
 
+// Coarse-grid correction of one level as its own pass (the alternative to folding
+// it into the first post-smoothing sweep): buf[role] += e[I / c], rows of a
+// multiple of 4 cells, 16-byte aligned arrays.
+struct ProlongTask {
+    Geo g;               // fine level
+    int cf[3];           // coarsening factors (cf[0] in {1, 2})
+    const float* e;      // coarse correction
+    float* buf[3];
+    const int* rot;      // nullptr: roles fixed
+    int role;
+};
+
 // Zero-mean projection of one level's right-hand side over its active cells
 // (coarsest levels too large for the bottom kernel; their sweeps then run as k_sweep).
 struct LevelProjTask {
@@ -333,6 +345,7 @@ cudaError_t launch_coarsen_coeffs(Geo fine, const int cf[3], const float* bx, co
                                   const float* bz, float* cbx, float* cby, float* cbz,
                                   cudaStream_t s);
 cudaError_t launch_prolong_add(Geo fine, const int cf[3], const float* e, float* p, cudaStream_t s);
+cudaError_t launch_prolong_rows(const ProlongTask& t, cudaStream_t s);
 cudaError_t launch_active_mask(Geo g, const float* bx, const float* by, const float* bz,
                                uint8_t* mask, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* partials, int n, double* out, cudaStream_t s);

@@ -1396,6 +1396,41 @@ __global__ void k_prolong_add(Geo f, int c0, int c1, int c2, const float* __rest
     }
 }
 
+// buf[role] += e[I / c] by 16-byte chunks of 4 cells of a row (fine rows of a
+// multiple of 4 cells); the same FP32 addition as the correction folded into a
+// sweep's plane loads, so both give the same iterate bit for bit.
+__global__ void __launch_bounds__(kThreads) k_prolong_rows(const __grid_constant__ ProlongTask t)
+{
+    const int nx = t.g.n[0], ny = t.g.n[1], nz = t.g.n[2];
+    const int cpr = nx / 4;                                  // chunks per row
+    const int gcx = nx / t.cf[0], gcy = ny / t.cf[1];
+    const int sy = t.cf[1] - 1, sz = t.cf[2] - 1;             // shifts: factor 2 -> 1, 1 -> 0
+    const int rot = t.rot ? *t.rot : 0;
+    float* p = t.buf[(t.role + rot) % 3];
+    const int64_t total = (int64_t)cpr * ny * nz;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = k / cpr;
+        const int c = (int)(k - row * cpr);
+        const int y = (int)(row % ny), z = (int)(row / ny);
+        const int64_t crow = ((int64_t)(z >> sz) * gcy + (y >> sy)) * gcx;
+        float4 v = *reinterpret_cast<float4*>(p + 4 * k);
+        if (t.cf[0] == 2) {
+            const float2 e2 = __ldg(reinterpret_cast<const float2*>(t.e + crow + 2 * c));
+            v.x += e2.x;
+            v.y += e2.x;
+            v.z += e2.y;
+            v.w += e2.y;
+        } else {
+            const float4 e4 = __ldg(reinterpret_cast<const float4*>(t.e + crow + 4 * c));
+            v.x += e4.x;
+            v.y += e4.y;
+            v.z += e4.z;
+            v.w += e4.w;
+        }
+        *reinterpret_cast<float4*>(p + 4 * k) = v;
+    }
+}
+
 __global__ void k_active_mask(Geo g, const float* __restrict__ bx, const float* __restrict__ by,
                               const float* __restrict__ bz, uint8_t* mask)
 {
@@ -1976,6 +2011,13 @@ cudaError_t launch_prolong_add(Geo fine, const int cf[3], const float* e, float*
 {
     const int64_t N = (int64_t)fine.n[0] * fine.n[1] * fine.n[2];
     k_prolong_add<<<grid_for(N), kThreads, 0, s>>>(fine, cf[0], cf[1], cf[2], e, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_rows(const ProlongTask& t, cudaStream_t s)
+{
+    const int64_t chunks = (int64_t)(t.g.n[0] / 4) * t.g.n[1] * t.g.n[2];
+    k_prolong_rows<<<grid_for(chunks), kThreads, 0, s>>>(t);
     return cudaGetLastError();
 }
 

@@ -177,7 +177,9 @@ struct SweepTiling {
 // ------------------------------------------------------------ autotuned shapes
 // z-chunk depth per (kernel kind, level geometry), filled by Engine::tune from
 // timed trial launches and shared by every handle of the process.
-enum TuneKind { kTuneSweep = 0, kTuneSweepCorr = 1, kTuneResidual = 2 };
+enum TuneKind { kTuneSweep = 0, kTuneSweepCorr = 1, kTuneResidual = 2, kTuneCorrForm = 3 };
+// kTuneCorrForm entries: 1 = correction as its own pass before a plain sweep, 2 = folded into the sweep
+enum { kCorrSeparate = 1, kCorrFused = 2 };
 
 struct TuneKey {
     int kind, n0, n1, n2, p0, p1, p2;
@@ -301,7 +303,7 @@ struct ProblemMem {
     float* pinv = nullptr;          // coarse_mode 1: A^+ of the coarsest level
 };
 
-enum OpKind { kSweepFF, kSweepFB, kSweepBB, kResF, kResB, kBottomF, kBottomB, kProjLevel, kControl };
+enum OpKind { kSweepFF, kSweepFB, kSweepBB, kResF, kResB, kBottomF, kBottomB, kProjLevel, kControl, kProlong };
 
 struct LaunchOp {
     OpKind kind;
@@ -316,6 +318,7 @@ struct LaunchOp {
     size_t smem = 0;
     const LevelProjTask* lp = nullptr;
     const CtlTask* ctl = nullptr;
+    ProlongTask pro{};
     int n = 0;
 };
 
@@ -614,6 +617,33 @@ struct Engine {
         return t;
     }
 
+    // the coarse-grid correction of level l as its own pass into the iterate of `role`
+    ProlongTask prolong_task(int p, int l, int role) const
+    {
+        const ProblemMem& M = P[p];
+        const LevelMem& Lm = M.lev[l];
+        ProlongTask t{};
+        t.g = Lm.g;
+        for (int d = 0; d < 3; ++d) t.cf[d] = Lm.cf[d];
+        t.e = static_cast<const float*>(M.lev[l + 1].buf[coarse_result_[p][l + 1]]);
+        for (int r = 0; r < 3; ++r) t.buf[r] = static_cast<float*>(Lm.buf[r]);
+        t.rot = l == 0 ? &M.ctl->rot : nullptr;
+        t.role = role;
+        return t;
+    }
+
+    // a single FP32 problem whose level l (rows of a multiple of 4 cells, FP32 correction)
+    // may take its correction as a separate pass: the autotuner decides
+    bool corr_separable(int l) const
+    {
+        if (P.size() != 1 || bf16_coarse) return false;
+        const LevelMem& Lm = P[0].lev[l];
+        if (Lm.g.n[0] % 4 || Lm.cf[0] > 2) return false;
+        for (int r = 0; r < 3; ++r)
+            if (Lm.buf[r] && !aligned16(Lm.buf[r])) return false;
+        return aligned16(P[0].lev[l + 1].buf[0]) && aligned16(P[0].lev[l + 1].buf[1]);
+    }
+
     template <class TP>
     ResTask<TP> res_task(int p, int l, int role, bool restrict_to_next, double* partials)
     {
@@ -909,9 +939,18 @@ struct Engine {
                 if (l < stop_[p]) probs.push_back(p);
             if (probs.empty()) continue;
             int cur = pre[l];
+            // the correction: folded into the first post-sweep, or (tuned) its own pass
+            const bool separate = corr_separable(l) && cur >= 0 &&
+                                  tuned_zchunk(kTuneCorrForm, P[0].lev[l].g) == kCorrSeparate;
+            if (separate) {
+                LaunchOp op;
+                op.kind = kProlong;
+                op.pro = prolong_task(0, l, cur);
+                cycle.push_back(op);
+            }
             for (int s = 0; s < opt.nu2; ++s) {
                 const int out = next_out(l, cur < 0 ? (l == 0 ? 0 : 1) : cur);
-                int rc = add_sweeps(l, probs, cur, out, s == 0);
+                int rc = add_sweeps(l, probs, cur, out, s == 0 && !separate);
                 if (rc) return rc;
                 cur = out;
             }
@@ -948,6 +987,7 @@ struct Engine {
         case kBottomB: return launch_bottom(op.bot_b, op.n, op.smem, stream);
         case kProjLevel: return launch_project_level(op.lp, op.n, stream);
         case kControl: return launch_control_cycle(op.ctl, op.n, stream);
+        case kProlong: return launch_prolong_rows(op.pro, stream);
         }
         return cudaErrorInvalidValue;
     }
@@ -1185,6 +1225,31 @@ struct Engine {
                         g_tuned_zchunk[tune_key(kind, g)] = best_zc;
                     }
                 }
+                // the correction folded into the first post-sweep against its own pass plus a plain sweep
+                if (l + 1 < M.L && corr_separable(l) && !tuned_zchunk(kTuneCorrForm, g)) {
+                    SweepTask<float, float> tf = sweep_task<float, float>((int)p, l, in, out, true);
+                    TaskList<SweepTask<float, float>> lf{};
+                    lf.ntasks = 1;
+                    lf.total = (int)sweep_tiling(g, kTuneSweepCorr).tiles();
+                    lf.single = tf;
+                    lf.vec = sweep_vec(tf);
+                    lf.corr = 1;
+                    SweepTask<float, float> tp = sweep_task<float, float>((int)p, l, in, out, false);
+                    TaskList<SweepTask<float, float>> lp{};
+                    lp.ntasks = 1;
+                    lp.total = (int)sweep_tiling(g, kTuneSweep).tiles();
+                    lp.single = tp;
+                    lp.vec = sweep_vec(tp);
+                    const ProlongTask pt = prolong_task((int)p, l, in);
+                    const float fused =
+                        time_ms([&] { return launch_sweep(lf, persistent_grid(lf.total), stream); }, 5);
+                    const float split = time_ms([&] {
+                        cudaError_t e2 = launch_prolong_rows(pt, stream);
+                        return e2 == cudaSuccess ? launch_sweep(lp, persistent_grid(lp.total), stream) : e2;
+                    }, 5);
+                    std::lock_guard<std::mutex> lock(g_tune_mutex);
+                    g_tuned_zchunk[tune_key(kTuneCorrForm, g)] = split < fused ? kCorrSeparate : kCorrFused;
+                }
             }
         }
         cudaError_t e = cudaGetLastError();
@@ -1409,14 +1474,52 @@ struct Engine {
         return cudaSuccess;
     }
 
+    // V-cycles to queue before the next status read: as many as the contraction
+    // seen since the last read (r0, c0: residual and cycle count then) predicts the
+    // slowest unfinished problem still needs, rounded down and at least 1, at most
+    // cycles_per_sync; 2 while no contraction has been seen.  A cycle queued after
+    // every problem finished still costs one launch per kernel of the graph (the
+    // kernels see the done flag and return); an extra status read costs less.
+    int cycles_to_queue(const std::vector<double>& r0, const std::vector<int>& c0) const
+    {
+        const int cap = std::max(1, opt.cycles_per_sync);
+        int q = 0;
+        bool unknown = false;
+        for (size_t p = 0; p < P.size(); ++p) {
+            const Ctl& c = ctl_host[p];
+            if (c.done) continue;
+            const int ran = c.cycles - c0[p];
+            if (ran <= 0 || !(r0[p] > 0.0) || !(c.r_prev > 0.0) || !(c.bnorm > 0.0) || !(c.tol > 0.0)) {
+                unknown = true;
+                continue;
+            }
+            const double rho = std::pow(c.r_prev / r0[p], 1.0 / ran);
+            if (!(rho < 0.95)) {                 // slow, or rejected cycles: a full batch
+                q = cap;
+                continue;
+            }
+            const double need = std::log(c.tol * c.bnorm / c.r_prev) / std::log(rho);
+            q = std::max(q, need >= (double)cap ? cap : (int)std::floor(need));
+        }
+        if (unknown) q = std::max(q, 2);
+        return std::min(cap, std::max(1, q));
+    }
+
     // cycles until every problem is done; returns the CUDA status
     cudaError_t iterate()
     {
-        const int per_sync = std::max(1, opt.cycles_per_sync);
+        const int cap = std::max(1, opt.cycles_per_sync);
+        std::vector<double> r0(P.size());
+        std::vector<int> c0(P.size());
         int queued = 0;
-        for (int guard = 0; guard <= opt.max_cycles; guard += per_sync) {
-            for (int k = 0; k < per_sync; ++k) {
-                if (poison_cycle > 0 && ++queued == poison_cycle) {
+        while (queued <= opt.max_cycles + cap) {
+            const int q = cycles_to_queue(r0, c0);
+            for (size_t p = 0; p < P.size(); ++p) {
+                r0[p] = ctl_host[p].r_prev;
+                c0[p] = ctl_host[p].cycles;
+            }
+            for (int k = 0; k < q; ++k) {
+                if (++queued == poison_cycle) {
                     poison_cycle = 0;
                     cudaError_t e = poison_omega();
                     if (e != cudaSuccess) return e;
@@ -1991,7 +2094,7 @@ void gmg_default_options(gmg_options* o)
     o->shrink = 0.7;
     o->grow = 1.1;
     o->use_graph = 1;
-    o->cycles_per_sync = 4;
+    o->cycles_per_sync = 8;
     o->ir_inner_rtol = 1e-4;
     o->autotune = 1;
     o->coarse_mode = GMG_COARSE_SWEEPS;

@@ -212,6 +212,15 @@ int gmg_history(gmg_handle h, double* rel_res, double* omega, int* accepted, int
 /* Number of levels and their dimensions (host array of 3*levels ints, may be NULL). */
 int gmg_levels(gmg_handle h, int* dims);
 
+/* The bottom of the V-cycle as planned at creation or at the last
+ * gmg_set_coeffs (the autotuner may move it): *level = the first level that the
+ * bottom kernel runs, *ranks = 1 when one CTA runs it, or the number of CTAs of
+ * the thread-block cluster that splits its levels of more than 1024 cells by
+ * rows (then the smaller levels run in the cluster's first CTA); both 0 when no
+ * bottom kernel runs (one level, or a coarsest level too large for one CTA,
+ * which then runs as grid sweeps).  GMG_ERR_ARG on a null argument. */
+int gmg_bottom_form(gmg_handle h, int* level, int* ranks);
+
 /* Releases the handle and its device memory. */
 int gmg_destroy(gmg_handle h);
 
@@ -222,20 +231,26 @@ const char* gmg_last_error(gmg_handle h);
  * The autotuner's results, process-wide (no counterpart in the paper: launch
  * shapes are a property of this implementation).  gmg_set_coeffs with
  * autotune = 1 times the z-chunk depth of each pipelined kernel per level
- * geometry and where the one-CTA bottom of a single problem starts, and keeps
- * them in a table that later handles of the same shapes reuse without timing.
+ * geometry and, for a single problem, where the bottom kernel starts and
+ * whether one CTA or a thread-block cluster runs it, and keeps them in a table that later handles of the same shapes reuse without timing.
  *
  * gmg_tune_export writes the table as text: one line per entry,
  *   "z kind nx ny nz px py pz zchunk"   (kind 0 sweep, 1 sweep with correction,
- *                                        2 residual)
- *   "b nx ny nz px py pz coarsen n_min precision nu_c coarse_mode level"
+ *                                        2 residual; kind 3 keeps the coarse-grid
+ *                                        correction's form, 1 separate, 2 fused)
+ *   "b nx ny nz px py pz coarsen n_min precision nu_c coarse_mode level ranks"
+ *                                       (first level of the bottom kernel; ranks 1:
+ *                                        one CTA, > 1: a cluster of that many CTAs
+ *                                        splits its larger levels; a line without
+ *                                        ranks reads as 1)
  * into buf (host, capacity cap bytes, NUL-terminated) and its length without
  * the NUL into *len.  buf == NULL only reports the length.  GMG_ERR_ARG when
  * cap is too small (nothing written).
  *
  * gmg_tune_import merges such text into the table (entries of the same key
- * are replaced), so that a later process reuses an earlier one's launch
- * shapes: same shapes, same launches, same results bit for bit.  GMG_ERR_ARG,
+ * are replaced; a "b" line of level 0 removes its key's entry), so that a
+ * later process reuses an earlier one's launch shapes: same shapes, same
+ * launches, same results bit for bit.  GMG_ERR_ARG,
  * with the table unchanged, on a malformed line.  Neither call touches the GPU.
  */
 int gmg_tune_export(char* buf, size_t cap, size_t* len);

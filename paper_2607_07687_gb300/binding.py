@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
     L.gmg_gmgpcg_solve.argtypes = [vp, vp, vp, c_double, ctypes.POINTER(Info)]
     L.gmg_history.argtypes = [vp, dp, dp, ip, c_int]
     L.gmg_levels.argtypes = [vp, ip]
+    L.gmg_bottom_form.argtypes = [vp, ip, ip]
     L.gmg_destroy.argtypes = [vp]
     L.gmg_last_error.argtypes = [vp]
     L.gmg_last_error.restype = ctypes.c_char_p
@@ -325,6 +326,13 @@ class Solver:
         if n < 0:
             raise GmgError(lib().gmg_last_error(self.h).decode())
         return res[:n + 1], om[:n], acc[:n].astype(bool)
+
+    def bottom_form(self):
+        """(first level of the bottom kernel, CTAs running it: 1 = one CTA, > 1 =
+        a thread-block cluster; (0, 0) = no bottom kernel)  (gmg_bottom_form)."""
+        lv, rk = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().gmg_bottom_form(self.h, ctypes.byref(lv), ctypes.byref(rk)), self.h)
+        return lv.value, rk.value
 
     def levels(self):
         L = lib().gmg_levels(self.h, None)

@@ -17,8 +17,14 @@
 // and writes level lb's result for the finer level's correction.  Colour
 // phases are separated by block barriers; within a colour the cells are
 // independent, so in-place updates are exact Gauss-Seidel.
+#include <cooperative_groups.h>
+#include <map>
+#include <mutex>
+
 #include "gmg_internal.h"
 #include "gmg_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gmg {
 namespace {
@@ -205,53 +211,45 @@ __device__ void sweeps_small(const LevelView& L, int count, float w)
         }
 }
 
-template <class TP>
-__global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>* __restrict__ tasks)
+// block-reduction and dense-solve scratch of the one-CTA levels
+struct BottomScratch {
+    double red[kBottomThreads / 32];
+    double red2[kBottomThreads / 32];
+    double mean;
+    float gemv[kBottomThreads];   // dense coarse solve: partial sums of the groups
+};
+
+__device__ __forceinline__ LevelView level_view(const BottomLevel& B, float* sm)
 {
-    extern __shared__ __align__(16) float sm[];
-    __shared__ double red[kBottomThreads / 32];
-    __shared__ double red2[kBottomThreads / 32];
-    __shared__ double s_mean;
-    __shared__ float s_gemv[kBottomThreads];   // dense coarse solve: partial sums of the groups
-    // the task (level geometries, offsets, sweep counts) in shared memory: the level
-    // views are rebuilt before every phase
-    __shared__ __align__(16) BottomTask<TP> T;
-    static_assert(sizeof(BottomTask<TP>) % 4 == 0, "task copied in words");
-    {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(tasks + blockIdx.x);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
-        for (int k = threadIdx.x; k < (int)(sizeof(BottomTask<TP>) / 4); k += blockDim.x) dst[k] = __ldg(src + k);
-        __syncthreads();
-    }
-    if (T.ctl && T.ctl->done) return;
-    const int nlev = T.nlev;
-    const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
+    LevelView L;
+    L.g = B.g;
+    L.n = L.g.n[0] * L.g.n[1] * L.g.n[2];
+    L.inv_nx = B.inv_nx;
+    L.inv_nxy = B.inv_nxy;
+    float* base = sm + B.off;
+    L.p = base;
+    L.b = base + L.n;
+    L.x = base + 2 * L.n;
+    L.y = base + 3 * L.n;
+    L.z = base + 4 * L.n;
+    return L;
+}
 
-    auto view = [&](int l) {
-        LevelView L;
-        L.g = T.lev[l].g;
-        L.n = L.g.n[0] * L.g.n[1] * L.g.n[2];
-        L.inv_nx = T.lev[l].inv_nx;
-        L.inv_nxy = T.lev[l].inv_nxy;
-        float* base = sm + T.lev[l].off;
-        L.p = base;
-        L.b = base + L.n;
-        L.x = base + 2 * L.n;
-        L.y = base + 3 * L.n;
-        L.z = base + 4 * L.n;
-        return L;
-    };
-
-    // coefficients of every level (lower faces, walls zeroed) and the top right-hand side
-    for (int l = 0; l < nlev; ++l) {
-        const LevelView L = view(l);
+// Face coefficients of levels first .. nlev-1 (lower faces, walls zeroed) into
+// their blocks, and level first's right-hand side from b when b is given.
+template <class TP>
+__device__ void load_levels(const BottomTask<TP>& T, float* sm, int first, const float* b)
+{
+    for (int l = first; l < T.nlev; ++l) {
+        const LevelView L = level_view(T.lev[l], sm);
         const BottomLevel& B = T.lev[l];
+        const bool rhs = l == first && b;
         if (B.walls_zeroed) {                      // straight copies: independent loads in flight
             for (int i = threadIdx.x; i < L.n; i += blockDim.x) {
                 L.x[i] = __ldg(B.bx + i);
                 L.y[i] = __ldg(B.by + i);
                 L.z[i] = __ldg(B.bz + i);
-                if (l == 0) L.b[i] = T.b[i];
+                if (rhs) L.b[i] = b[i];
             }
             continue;
         }
@@ -260,13 +258,21 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
             L.x[i] = face_lo(B.bx, L.g, 0, x, y, z);
             L.y[i] = face_lo(B.by, L.g, 1, x, y, z);
             L.z[i] = face_lo(B.bz, L.g, 2, x, y, z);
-            if (l == 0) L.b[i] = T.b[i];
+            if (rhs) L.b[i] = b[i];
         }
     }
-    __syncthreads();
+}
+
+// The lower V-cycle over levels first .. nlev-1 in this CTA, from level first's
+// right-hand side in its block to its iterate in its block (block barriers only).
+template <class TP>
+__device__ void local_vcycle(const BottomTask<TP>& T, float* sm, int first, float w, BottomScratch& S)
+{
+    const int nlev = T.nlev;
+    auto view = [&](int l) { return level_view(T.lev[l], sm); };
 
     // descent
-    for (int l = 0; l + 1 < nlev; ++l) {
+    for (int l = first; l + 1 < nlev; ++l) {
         const LevelView L = view(l);
         const LevelView C = view(l + 1);
         for (int i = threadIdx.x; i < L.n; i += blockDim.x) L.p[i] = 0.f;
@@ -305,20 +311,20 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         s = warp_sum(s);
         cnt = warp_sum(cnt);
         if ((threadIdx.x & 31) == 0) {
-            red[threadIdx.x >> 5] = s;
-            red2[threadIdx.x >> 5] = cnt;
+            S.red[threadIdx.x >> 5] = s;
+            S.red2[threadIdx.x >> 5] = cnt;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double ts = 0.0, tc = 0.0;
             for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-                ts += red[k];
-                tc += red2[k];
+                ts += S.red[k];
+                tc += S.red2[k];
             }
-            s_mean = tc > 0.0 ? ts / tc : 0.0;
+            S.mean = tc > 0.0 ? ts / tc : 0.0;
         }
         __syncthreads();
-        const double mean = s_mean;
+        const double mean = S.mean;
         for (int i = threadIdx.x; i < C.n; i += blockDim.x)
             C.b[i] = diag_at(C, i) > 0.f ? (float)((double)C.b[i] - mean) : 0.f;
         __syncthreads();
@@ -332,11 +338,11 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
             float acc = 0.f;
             if (grp < G)
                 for (int j = grp; j < n; j += G) acc = fmaf(__ldg(T.pinv + (int64_t)j * n + i), C.b[j], acc);
-            s_gemv[threadIdx.x] = acc;
+            S.gemv[threadIdx.x] = acc;
             __syncthreads();
             if (threadIdx.x < n) {
                 float sum = 0.f;
-                for (int q = 0; q < G; ++q) sum += s_gemv[q * n + threadIdx.x];
+                for (int q = 0; q < G; ++q) sum += S.gemv[q * n + threadIdx.x];
                 C.p[threadIdx.x] = sum;
             }
             __syncthreads();
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
     }
 
     // ascent
-    for (int l = nlev - 2; l >= 0; --l) {
+    for (int l = nlev - 2; l >= first; --l) {
         const LevelView L = view(l);
         const LevelView C = view(l + 1);
         const int c0 = T.lev[l].cf[0], c1 = T.lev[l].cf[1], c2 = T.lev[l].cf[2];
@@ -358,9 +364,270 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
         if (L.n <= (int)blockDim.x) sweeps_small(L, T.nu2, w);
         else sweeps(L, T.nu2, w);
     }
+}
 
-    const LevelView L = view(0);
+// the task of block `t` into shared memory, word by word
+template <class TP>
+__device__ __forceinline__ void load_task(BottomTask<TP>& T, const BottomTask<TP>* tasks, int t)
+{
+    static_assert(sizeof(BottomTask<TP>) % 4 == 0, "task copied in words");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(tasks + t);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&T);
+    for (int k = threadIdx.x; k < (int)(sizeof(BottomTask<TP>) / 4); k += blockDim.x) dst[k] = __ldg(src + k);
+    __syncthreads();
+}
+
+template <class TP>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>* __restrict__ tasks)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ BottomScratch S;
+    // the task (level geometries, offsets, sweep counts) in shared memory: the level
+    // views are rebuilt before every phase
+    __shared__ __align__(16) BottomTask<TP> T;
+    load_task(T, tasks, blockIdx.x);
+    if (T.ctl && T.ctl->done) return;
+    const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
+    load_levels(T, sm, 0, T.b);
+    __syncthreads();
+    local_vcycle(T, sm, 0, w, S);
+    const LevelView L = level_view(T.lev[0], sm);
     for (int i = threadIdx.x; i < L.n; i += blockDim.x) stv(T.out, (int64_t)i, L.p[i]);
+}
+
+// ------------------------------------------------------------------ cluster form
+//
+// The same lower V-cycle in one thread-block cluster of K CTAs.  A level of more
+// than kBottomThreads cells is distributed: rank r of the cluster owns its cells
+// [r cpr, (r + 1) cpr) in x-fastest order (cpr a whole number of rows), and keeps
+// for them in its shared memory the iterate, right-hand side, residual, the six
+// face coefficients and the diagonal (kDistArrays arrays of cpr floats).  x-
+// neighbours are in the same row, so local; y- and z-neighbours may be owned by
+// another rank and are read through distributed shared memory.  Each colour
+// phase, residual, restriction and prolongation is followed by a cluster
+// barrier (release/acquire at cluster scope).  The levels below, of at most
+// kBottomThreads cells, run in rank 0 exactly as in the one-CTA form while the
+// other ranks wait at the next cluster barrier.  Each distributed phase
+// evaluates the same operands in the same order as the one-CTA form, so both
+// forms give the same bits.
+
+enum { kAP = 0, kAB, kAR, kAXL, kAXU, kAYL, kAYU, kAZL, kAZU, kADG };
+
+struct DistLevel {
+    Geo g;
+    int nx, ny, nxy, n;
+    int cpr, lo, cnt, r0;   // cells per rank; own cells [lo, lo + cnt) = own rows from r0
+    int hx;                 // cells of one colour per row, rounded up
+    float inv_cpr, inv_nx, inv_ny, inv_nxy, inv_hx;
+    float* a;               // own block: array k at a + k * cpr
+};
+
+__device__ __forceinline__ DistLevel dist_view(const BottomLevel& B, float* sm, int rank)
+{
+    DistLevel D;
+    D.g = B.g;
+    D.nx = B.g.n[0];
+    D.ny = B.g.n[1];
+    D.nxy = D.nx * D.ny;
+    D.n = D.nxy * B.g.n[2];
+    D.cpr = B.cpr;
+    D.lo = min(rank * D.cpr, D.n);
+    D.cnt = min(D.cpr, D.n - D.lo);
+    D.r0 = D.lo / D.nx;
+    D.hx = (D.nx + 1) >> 1;
+    D.inv_cpr = B.inv_cpr;
+    D.inv_nx = B.inv_nx;
+    D.inv_ny = 1.0f / (float)D.ny;
+    D.inv_nxy = B.inv_nxy;
+    D.inv_hx = 1.0f / (float)D.hx;
+    D.a = sm + B.off;
+    return D;
+}
+
+// address of array k of cell j (index within the level) in the rank that owns it
+__device__ __forceinline__ const float* dist_at(const DistLevel& D, const cg::cluster_group& cl, int rank, int k, int j)
+{
+    const int o = quot(j, D.cpr, D.inv_cpr);
+    const float* p = D.a + k * D.cpr + (j - o * D.cpr);
+    return o == rank ? p : cl.map_shared_rank(p, (unsigned)o);
+}
+
+// (A p) at own cell c = (x, y, z) of a distributed level, same operands and order as flux_xyz
+__device__ __forceinline__ float dist_flux(const DistLevel& D, const cg::cluster_group& cl, int rank, int c, int x,
+                                           int y, int z, float p0)
+{
+    const float* P = D.a;
+    const int nx = D.nx, i = D.lo + c;
+    const float pxl = x > 0 ? P[c - 1] : (D.g.per[0] ? P[c + nx - 1] : p0);
+    const float pxu = x < nx - 1 ? P[c + 1] : (D.g.per[0] ? P[c - nx + 1] : p0);
+    const int jyl = y > 0 ? i - nx : (D.g.per[1] ? i + (D.ny - 1) * nx : -1);
+    const int jyu = y < D.ny - 1 ? i + nx : (D.g.per[1] ? i - (D.ny - 1) * nx : -1);
+    const int nz = D.g.n[2];
+    const int jzl = z > 0 ? i - D.nxy : (D.g.per[2] ? i + (nz - 1) * D.nxy : -1);
+    const int jzu = z < nz - 1 ? i + D.nxy : (D.g.per[2] ? i - (nz - 1) * D.nxy : -1);
+    const float pyl = jyl < 0 ? p0 : *dist_at(D, cl, rank, kAP, jyl);
+    const float pyu = jyu < 0 ? p0 : *dist_at(D, cl, rank, kAP, jyu);
+    const float pzl = jzl < 0 ? p0 : *dist_at(D, cl, rank, kAP, jzl);
+    const float pzu = jzu < 0 ? p0 : *dist_at(D, cl, rank, kAP, jzu);
+    const float* A = D.a;
+    const int s = D.cpr;
+    return face_flux(A[kAXL * s + c], pxl, A[kAXU * s + c], pxu, A[kAYL * s + c], pyl, A[kAYU * s + c], pyu,
+                     A[kAZL * s + c], pzl, A[kAZU * s + c], pzu, p0);
+}
+
+// own cell c -> (x, y, z)
+__device__ __forceinline__ void dist_decode(const DistLevel& D, int c, int& x, int& y, int& z)
+{
+    const int r = quot(c, D.nx, D.inv_nx);
+    x = c - r * D.nx;
+    const int row = D.r0 + r;
+    z = quot(row, D.ny, D.inv_ny);
+    y = row - z * D.ny;
+}
+
+// nu red-black sweeps of a distributed level; a cluster barrier ends each colour
+__device__ void dist_sweeps(const DistLevel& D, const cg::cluster_group& cl, int rank, int count, float w)
+{
+    const int nt = (D.cnt / D.nx) * D.hx;
+    float* P = D.a;
+    for (int it = 0; it < count; ++it)
+        for (int colour = 0; colour < 2; ++colour) {
+            for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+                const int r = quot(t, D.hx, D.inv_hx);
+                const int j = t - r * D.hx;
+                const int row = D.r0 + r;
+                const int z = quot(row, D.ny, D.inv_ny);
+                const int y = row - z * D.ny;
+                const int x = 2 * j + ((colour + y + z) & 1);
+                if (x < D.nx) {
+                    const int c = r * D.nx + x;
+                    const float p0 = P[c];
+                    const float fl = dist_flux(D, cl, rank, c, x, y, z, p0);
+                    P[c] = gs_update(p0, fl, D.a[kADG * D.cpr + c], D.a[kAB * D.cpr + c], w);
+                }
+            }
+            cl.sync();
+        }
+}
+
+// coarse right-hand side of cell (X, Y, Z): the children's residuals summed in the
+// one-CTA form's order (z, then y, then x innermost)
+__device__ __forceinline__ float dist_child_sum(const DistLevel& F, const cg::cluster_group& cl, int rank,
+                                                const int cf[3], int X, int Y, int Z)
+{
+    float s = 0.f;
+    for (int dz = 0; dz < cf[2]; ++dz)
+        for (int dy = 0; dy < cf[1]; ++dy)
+            for (int dx = 0; dx < cf[0]; ++dx) {
+                const int i = ((Z * cf[2] + dz) * F.ny + Y * cf[1] + dy) * F.nx + X * cf[0] + dx;
+                s += *dist_at(F, cl, rank, kAR, i);
+            }
+    return s;
+}
+
+template <class TP>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom_cluster(const BottomTask<TP>* __restrict__ tasks)
+{
+    extern __shared__ __align__(16) float sm[];
+    __shared__ BottomScratch S;
+    __shared__ __align__(16) BottomTask<TP> T;
+    const cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    load_task(T, tasks, (int)(blockIdx.x / cl.num_blocks()));
+    if (T.ctl && T.ctl->done) return;              // the same flag in every rank of the cluster
+    const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
+    const int nd = T.nd;
+
+    // own cells of the distributed levels: faces (upper ones from the neighbour's
+    // lower face, 0 on walls), diagonal, zero iterate; level 0's right-hand side
+    for (int k = 0; k < nd; ++k) {
+        const DistLevel D = dist_view(T.lev[k], sm, rank);
+        const BottomLevel& B = T.lev[k];
+        for (int c = threadIdx.x; c < D.cnt; c += blockDim.x) {
+            int x, y, z;
+            dist_decode(D, c, x, y, z);
+            const int i = D.lo + c;
+            const float xl = __ldg(B.bx + i), yl = __ldg(B.by + i), zl = __ldg(B.bz + i);
+            const float xu = x < D.nx - 1 ? __ldg(B.bx + i + 1) : (D.g.per[0] ? __ldg(B.bx + i - (D.nx - 1)) : 0.f);
+            const float yu = y < D.ny - 1 ? __ldg(B.by + i + D.nx)
+                                          : (D.g.per[1] ? __ldg(B.by + i - (D.ny - 1) * D.nx) : 0.f);
+            const float zu = z < D.g.n[2] - 1 ? __ldg(B.bz + i + D.nxy)
+                                              : (D.g.per[2] ? __ldg(B.bz + i - (D.g.n[2] - 1) * D.nxy) : 0.f);
+            float* A = D.a;
+            const int s = D.cpr;
+            A[kAP * s + c] = 0.f;
+            A[kAB * s + c] = k == 0 ? T.b[i] : 0.f;
+            A[kAR * s + c] = 0.f;
+            A[kAXL * s + c] = xl;
+            A[kAXU * s + c] = xu;
+            A[kAYL * s + c] = yl;
+            A[kAYU * s + c] = yu;
+            A[kAZL * s + c] = zl;
+            A[kAZU * s + c] = zu;
+            A[kADG * s + c] = diag_sum(xl, xu, yl, yu, zl, zu);
+        }
+    }
+    if (rank == 0) load_levels(T, sm, nd, nullptr);
+    cl.sync();
+
+    // descent over the distributed levels: nu1 sweeps from zero, residual, restriction
+    for (int k = 0; k < nd; ++k) {
+        const DistLevel F = dist_view(T.lev[k], sm, rank);
+        dist_sweeps(F, cl, rank, T.nu1, w);
+        for (int c = threadIdx.x; c < F.cnt; c += blockDim.x) {
+            int x, y, z;
+            dist_decode(F, c, x, y, z);
+            const float p0 = F.a[kAP * F.cpr + c];
+            F.a[kAR * F.cpr + c] = F.a[kAB * F.cpr + c] - dist_flux(F, cl, rank, c, x, y, z, p0);
+        }
+        cl.sync();
+        if (k + 1 < nd) {
+            const DistLevel C = dist_view(T.lev[k + 1], sm, rank);
+            for (int c = threadIdx.x; c < C.cnt; c += blockDim.x) {
+                int X, Y, Z;
+                dist_decode(C, c, X, Y, Z);
+                C.a[kAB * C.cpr + c] = dist_child_sum(F, cl, rank, T.lev[k].cf, X, Y, Z);
+                C.a[kAP * C.cpr + c] = 0.f;
+            }
+        } else if (rank == 0) {
+            const LevelView C = level_view(T.lev[nd], sm);
+            for (CellWalk cw(C, threadIdx.x, blockDim.x); cw.i < C.n; cw.next(C.g, blockDim.x))
+                C.b[cw.i] = dist_child_sum(F, cl, rank, T.lev[k].cf, cw.x, cw.y, cw.z);
+        }
+        cl.sync();
+    }
+
+    // the levels below in rank 0
+    if (rank == 0) local_vcycle(T, sm, nd, w, S);
+    cl.sync();
+
+    // ascent over the distributed levels: prolongation, nu2 sweeps
+    for (int k = nd - 1; k >= 0; --k) {
+        const DistLevel F = dist_view(T.lev[k], sm, rank);
+        const int c0 = T.lev[k].cf[0], c1 = T.lev[k].cf[1], c2 = T.lev[k].cf[2];
+        const Geo& Cg = T.lev[k + 1].g;
+        const bool dist_coarse = k + 1 < nd;
+        const DistLevel C = dist_view(T.lev[dist_coarse ? k + 1 : k], sm, rank);   // used when distributed
+        for (int c = threadIdx.x; c < F.cnt; c += blockDim.x) {
+            int x, y, z;
+            dist_decode(F, c, x, y, z);
+            const int J = ((z >> (c2 - 1)) * Cg.n[1] + (y >> (c1 - 1))) * Cg.n[0] + (x >> (c0 - 1));
+            float e;
+            if (dist_coarse) {
+                e = *dist_at(C, cl, rank, kAP, J);
+            } else {
+                const float* p = sm + T.lev[nd].off + J;   // rank 0's iterate of the first local level
+                e = rank == 0 ? *p : *cl.map_shared_rank(p, 0u);
+            }
+            F.a[kAP * F.cpr + c] += e;
+        }
+        cl.sync();
+        dist_sweeps(F, cl, rank, T.nu2, w);
+    }
+
+    // level 0's result; no rank reads another's shared memory after the last barrier
+    const DistLevel F = dist_view(T.lev[0], sm, rank);
+    for (int c = threadIdx.x; c < F.cnt; c += blockDim.x) stv(T.out, (int64_t)(F.lo + c), F.a[kAP * F.cpr + c]);
 }
 
 }  // namespace
@@ -380,5 +647,74 @@ cudaError_t launch_bottom(const BottomTask<TP>* tasks, int ntasks, size_t smem, 
 }
 template cudaError_t launch_bottom<float>(const BottomTask<float>*, int, size_t, cudaStream_t);
 template cudaError_t launch_bottom<bf16>(const BottomTask<bf16>*, int, size_t, cudaStream_t);
+
+template <class TP>
+cudaError_t launch_bottom_cluster(const BottomTask<TP>* tasks, int ntasks, int ranks, size_t smem, cudaStream_t s)
+{
+    if (ntasks <= 0) return cudaSuccess;
+    if (ranks < 2 || ranks > kClusterMaxRanks || smem > sizeof(float) * (size_t)kClusterMaxFloats)
+        return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ntasks * ranks));
+    cfg.blockDim = dim3(kBottomThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)ranks;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_bottom_cluster<TP>, tasks);
+}
+template cudaError_t launch_bottom_cluster<float>(const BottomTask<float>*, int, int, size_t, cudaStream_t);
+template cudaError_t launch_bottom_cluster<bf16>(const BottomTask<bf16>*, int, int, size_t, cudaStream_t);
+
+// Per device, once: opt both instantiations in to 16-CTA clusters and the full
+// shared-memory budget, then ask the occupancy calculator whether one cluster of
+// 16 (else 8) such CTAs can be resident.
+int bottom_cluster_ranks()
+{
+    static std::mutex m;
+    static std::map<int, int> known;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(m);
+    auto it = known.find(dev);
+    if (it != known.end()) return it->second;
+    const int smem = (int)(sizeof(float) * (size_t)kClusterMaxFloats);
+    int ranks = 0;
+    bool ok = cudaFuncSetAttribute(k_bottom_cluster<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(k_bottom_cluster<bf16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(k_bottom_cluster<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(k_bottom_cluster<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                  cudaSuccess;
+    for (int k : {16, 8}) {
+        if (!ok) break;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)k);
+        cfg.blockDim = dim3(kBottomThreads);
+        cfg.dynamicSmemBytes = (size_t)smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)k;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_bottom_cluster<float>, &cfg) == cudaSuccess && n >= 1) {
+            ranks = k;
+            break;
+        }
+    }
+    cudaGetLastError();   // a refused query leaves no sticky error
+    known[dev] = ranks;
+    return ranks;
+}
 
 }  // namespace gmg

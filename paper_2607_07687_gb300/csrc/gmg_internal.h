@@ -153,10 +153,20 @@ struct LevelProjTask {
     const Ctl* ctl;
 };
 
-// The bottom of the V-cycle (levels lb .. L-1 of one problem) in one CTA.
+// The bottom of the V-cycle (levels lb .. L-1 of one problem) in one CTA, or in
+// one thread-block cluster whose CTAs split the larger of those levels.
 constexpr int kBottomThreads = 1024;
 constexpr int kBottomMaxCells = 10240;   // 5 floats per cell of shared memory: 200 KB
 static_assert(kBottomMaxCells < (1 << 23), "bottom cell indices are decoded with an FP32 estimate");
+// Cluster form: a level of more than kBottomThreads cells is split by rows over
+// the cluster's CTAs (distributed level, 10 floats per cell: iterate,
+// right-hand side, residual, six face coefficients and the diagonal); the
+// smaller levels below it run in CTA 0 as in the one-CTA form.  Each CTA holds
+// at most kClusterMaxFloats floats (200 KB).
+constexpr int kClusterMaxRanks = 16;
+constexpr int kDistArrays = 10;
+constexpr int kClusterMaxFloats = 51200;
+constexpr int kClusterMaxCells = 1 << 22;   // largest distributed level (FP32 index decoding)
 
 struct BottomLevel {
     Geo g;
@@ -168,6 +178,8 @@ struct BottomLevel {
     int walls_zeroed;    // 1: the stored faces already read 0 on walls (coarse levels)
     float inv_nx;        // 1 / nx and 1 / (nx ny): cell index -> (x, y, z) by multiplication
     float inv_nxy;
+    int cpr;             // distributed level: cells per CTA (a whole number of rows)
+    float inv_cpr;       // 1 / cpr
 };
 
 // coarse_mode 1: the coarsest level (at most kDenseMaxCells cells) is solved by
@@ -184,6 +196,8 @@ struct BottomTask {
     int nu1, nu2, nu_c;
     const Ctl* ctl;
     const float* pinv;   // A^+ of the coarsest level (n x n, symmetric), or nullptr: nu_c sweeps
+    int nd;              // cluster form: levels 0 .. nd-1 are distributed (0: one-CTA form)
+    int ranks;           // cluster form: CTAs per cluster (the layout's cpr assumes it)
 };
 
 template <class Task>
@@ -330,6 +344,12 @@ cudaError_t launch_project_level(const LevelProjTask* tasks, int ntasks, cudaStr
 
 template <class TP>
 cudaError_t launch_bottom(const BottomTask<TP>* tasks, int ntasks, size_t smem, cudaStream_t s);
+// cluster form: one cluster of `ranks` CTAs per task
+template <class TP>
+cudaError_t launch_bottom_cluster(const BottomTask<TP>* tasks, int ntasks, int ranks, size_t smem, cudaStream_t s);
+// CTAs per cluster that the current device can co-schedule for the cluster form
+// with its full shared-memory budget (16 or 8), or 0 when it cannot
+int bottom_cluster_ranks();
 
 // Reference variant of the sweep: one in-place launch per colour.
 cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const float* bz,

@@ -192,9 +192,13 @@ struct TuneKey {
 
 std::mutex g_tune_mutex;
 std::map<TuneKey, int> g_tuned_zchunk;
-// tuned start of the one-CTA bottom per (fine geometry, hierarchy options): every
-// handle of the same problem shape then runs the same cycle, bit for bit
-std::map<std::vector<int>, int> g_tuned_lb;
+// tuned start and form of the bottom per (fine geometry, hierarchy options):
+// every handle of the same problem shape then runs the same cycle, bit for bit
+struct BottomChoice {
+    int level;   // first level of the bottom kernel
+    int ranks;   // 1: one CTA; > 1: the cluster form
+};
+std::map<std::vector<int>, BottomChoice> g_tuned_lb;
 
 TuneKey tune_key(int kind, const Geo& g) { return {kind, g.n[0], g.n[1], g.n[2], g.per[0], g.per[1], g.per[2]}; }
 
@@ -316,6 +320,7 @@ struct LaunchOp {
     const BottomTask<float>* bot_f = nullptr;
     const BottomTask<bf16>* bot_b = nullptr;
     size_t smem = 0;
+    int ranks = 1;   // bottom: CTAs per task (> 1: cluster form)
     const LevelProjTask* lp = nullptr;
     const CtlTask* ctl = nullptr;
     ProlongTask pro{};
@@ -715,7 +720,10 @@ struct Engine {
 
     std::vector<std::vector<int>> coarse_result_;   // [p][l] buffer holding the level's result
     std::vector<int> stop_;                         // [p] first level not run by grid kernels
-    int forced_lb_ = 0;                             // tuned start of the one-CTA bottom (0: smallest fit)
+    int forced_lb_ = 0;                             // tuned start of the bottom (0: smallest one-CTA fit)
+    int forced_ranks_ = 1;                          // tuned form of the bottom (> 1: cluster form)
+    std::vector<int> fit_lb_;                       // [p] smallest one-CTA fit, -1 if none
+    int bottom_level_ = 0, bottom_ranks_ = 0;       // problem 0's bottom as planned (0: none)
     bool tuned_ = false;
 
     int add_sweeps(int l, const std::vector<int>& probs, int in, int out, bool with_corr)
@@ -777,6 +785,33 @@ struct Engine {
         return GMG_OK;
     }
 
+    // Cluster form of the bottom of problem M from level lb with `ranks` CTAs: the
+    // number of distributed levels (the leading levels of more than kBottomThreads
+    // cells) and, in *floats, the shared floats of one CTA; 0 when the form does not
+    // apply (no distributed level, a coarsest level too large for one CTA, or more
+    // than kClusterMaxFloats floats)
+    static int cluster_layout(const ProblemMem& M, int lb, int ranks, int* floats)
+    {
+        if (ranks < 2 || ranks > kClusterMaxRanks || lb < 1 || lb >= M.L) return 0;
+        int nd = 0;
+        int64_t off = 0;
+        for (int l = lb; l < M.L; ++l) {
+            const Geo& g = M.lev[l].g;
+            const int64_t n = cells(g);
+            if (n > kBottomThreads) {
+                if (l != lb + nd || n > kClusterMaxCells) return 0;
+                const int64_t rows = (int64_t)g.n[1] * g.n[2];
+                off += (int64_t)kDistArrays * ((rows + ranks - 1) / ranks) * g.n[0];
+                ++nd;
+            } else {
+                off += 5 * n;
+            }
+        }
+        if (nd == 0 || nd == M.L - lb || off > kClusterMaxFloats) return 0;
+        if (floats) *floats = (int)off;
+        return nd;
+    }
+
     int build_cycle()
     {
         const int nprob = (int)P.size();
@@ -787,7 +822,10 @@ struct Engine {
         // they fit in its shared memory; otherwise only the coarsest level is
         // special (grid sweeps); a problem that does not coarsen runs sweeps only
         stop_.assign(nprob, 0);
+        fit_lb_.assign(nprob, -1);
         std::vector<int> bottom(nprob, -1);
+        std::vector<int> bottom_nd(nprob, 0);   // > 0: the cluster form with that many distributed levels
+        const int ranks = nprob == 1 && forced_ranks_ > 1 ? bottom_cluster_ranks() : 0;
         for (int p = 0; p < nprob; ++p) {
             const ProblemMem& M = P[p];
             if (M.L == 1) continue;
@@ -798,9 +836,20 @@ struct Engine {
                 if (acc > kBottomMaxCells) break;
                 lb = l;
             }
-            if (lb >= 1 && forced_lb_ > lb && forced_lb_ < M.L) lb = forced_lb_;
+            fit_lb_[p] = lb;
+            const int nd = ranks > 1 ? cluster_layout(M, forced_lb_, ranks, nullptr) : 0;
+            if (nd > 0) {
+                lb = forced_lb_;
+                bottom_nd[p] = nd;
+            } else if (lb >= 1 && forced_lb_ > lb && forced_lb_ < M.L) {
+                lb = forced_lb_;
+            }
             bottom[p] = lb;
             stop_[p] = lb >= 1 ? lb : M.L - 1;
+            if (p == 0) {
+                bottom_level_ = lb >= 1 ? lb : 0;
+                bottom_ranks_ = lb < 1 ? 0 : (nd > 0 ? ranks : 1);
+            }
         }
         std::vector<int> pre(kMaxLevels, 0);   // role/buffer of the pre-smoothed iterate per level
         // descent
@@ -825,6 +874,7 @@ struct Engine {
             std::vector<BottomTask<float>> bf;
             std::vector<BottomTask<bf16>> bb;
             size_t smem = 0;
+            int cluster_ranks = 1;
             std::vector<int> single;
             std::vector<std::vector<int>> big(kMaxLevels);   // by coarsest level index
             for (int p = 0; p < nprob; ++p) {
@@ -840,6 +890,8 @@ struct Engine {
                 const int lb = bottom[p];
                 BottomTask<float> t{};
                 t.nlev = M.L - lb;
+                t.nd = bottom_nd[p];
+                t.ranks = t.nd > 0 ? ranks : 1;
                 int off = 0;
                 for (int k = 0; k < t.nlev; ++k) {
                     const LevelMem& Lm = M.lev[lb + k];
@@ -853,8 +905,16 @@ struct Engine {
                     B.walls_zeroed = lb + k > 0;   // coarse faces are built with walls read as 0
                     B.inv_nx = 1.0f / (float)Lm.g.n[0];
                     B.inv_nxy = 1.0f / (float)(Lm.g.n[0] * Lm.g.n[1]);
-                    off += 5 * (int)cells(Lm.g);
+                    if (k < t.nd) {                // rows split over the cluster's CTAs
+                        const int rows = Lm.g.n[1] * Lm.g.n[2];
+                        B.cpr = (rows + t.ranks - 1) / t.ranks * Lm.g.n[0];
+                        B.inv_cpr = 1.0f / (float)B.cpr;
+                        off += kDistArrays * B.cpr;
+                    } else {
+                        off += 5 * (int)cells(Lm.g);
+                    }
                 }
+                if (t.nd > 0) cluster_ranks = t.ranks;
                 smem = std::max(smem, sizeof(float) * (size_t)off);
                 t.b = M.lev[lb].b;
                 t.nu1 = opt.nu1;
@@ -866,6 +926,8 @@ struct Engine {
                 if (bf16_coarse) {
                     BottomTask<bf16> tb{};
                     tb.nlev = t.nlev;
+                    tb.nd = t.nd;
+                    tb.ranks = t.ranks;
                     for (int k = 0; k < t.nlev; ++k) tb.lev[k] = t.lev[k];
                     tb.b = t.b;
                     tb.out = static_cast<bf16*>(M.lev[lb].buf[0]);
@@ -886,6 +948,7 @@ struct Engine {
                 op.bot_f = upload(bf);
                 op.n = (int)bf.size();
                 op.smem = smem;
+                op.ranks = cluster_ranks;
                 if (!op.bot_f) return fail(GMG_ERR_CUDA, "upload failed");
                 cycle.push_back(op);
             }
@@ -895,6 +958,7 @@ struct Engine {
                 op.bot_b = upload(bb);
                 op.n = (int)bb.size();
                 op.smem = smem;
+                op.ranks = cluster_ranks;
                 if (!op.bot_b) return fail(GMG_ERR_CUDA, "upload failed");
                 cycle.push_back(op);
             }
@@ -983,8 +1047,12 @@ struct Engine {
         case kSweepBB: return launch_sweep(op.s_bb, op.grid, stream);
         case kResF: return launch_residual(op.r_f, op.grid, stream);
         case kResB: return launch_residual(op.r_b, op.grid, stream);
-        case kBottomF: return launch_bottom(op.bot_f, op.n, op.smem, stream);
-        case kBottomB: return launch_bottom(op.bot_b, op.n, op.smem, stream);
+        case kBottomF:
+            return op.ranks > 1 ? launch_bottom_cluster(op.bot_f, op.n, op.ranks, op.smem, stream)
+                                : launch_bottom(op.bot_f, op.n, op.smem, stream);
+        case kBottomB:
+            return op.ranks > 1 ? launch_bottom_cluster(op.bot_b, op.n, op.ranks, op.smem, stream)
+                                : launch_bottom(op.bot_b, op.n, op.smem, stream);
         case kProjLevel: return launch_project_level(op.lp, op.n, stream);
         case kControl: return launch_control_cycle(op.ctl, op.n, stream);
         case kProlong: return launch_prolong_rows(op.pro, stream);
@@ -1254,7 +1322,10 @@ struct Engine {
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "autotune (z-chunks)");
-        // 2) where the one-CTA bottom starts (one problem): time whole V-cycle graphs
+        // 2) where the bottom starts and in which form (one problem): time whole
+        // V-cycle graphs of each candidate
+        forced_lb_ = 0;
+        forced_ranks_ = 1;
         reset_cycle();
         if (upload_ctl_tasks() != GMG_OK) return fail(GMG_ERR_CUDA, "autotune: control task upload failed");
         int rc = build_cycle();
@@ -1262,35 +1333,45 @@ struct Engine {
         const std::vector<int> lb_key = {P[0].g0.n[0], P[0].g0.n[1], P[0].g0.n[2], P[0].g0.per[0], P[0].g0.per[1],
                                          P[0].g0.per[2], opt.coarsen, opt.n_min, opt.precision, opt.nu_c,
                                          opt.coarse_mode};
-        int cached_lb = 0;
+        BottomChoice cached{0, 1};
         {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
             auto it = g_tuned_lb.find(lb_key);
-            if (it != g_tuned_lb.end()) cached_lb = it->second;
+            if (it != g_tuned_lb.end()) cached = it->second;
         }
-        if (P.size() == 1 && cached_lb > 0) {
-            forced_lb_ = cached_lb;
+        std::vector<BottomChoice> cand;   // one-CTA starts from the smallest fit; cluster starts
+        if (P.size() == 1 && P[0].L > 1 && cached.level == 0) {
+            if (fit_lb_[0] >= 1)
+                for (int lb = fit_lb_[0]; lb < P[0].L; ++lb) cand.push_back({lb, 1});
+            const int ranks = bottom_cluster_ranks();
+            for (int lb = 1; lb < P[0].L; ++lb)
+                if (cluster_layout(P[0], lb, ranks, nullptr) > 0) cand.push_back({lb, ranks});
+        }
+        if (P.size() == 1 && cached.level > 0) {
+            forced_lb_ = cached.level;
+            forced_ranks_ = cached.ranks;
             reset_cycle();
             if ((rc = build_cycle()) != GMG_OK) return rc;
-        } else if (P.size() == 1 && P[0].L > 1 && stop_[0] < P[0].L - 1) {
-            const int first = stop_[0];
+        } else if (cand.size() > 1) {
             float best = 1e30f;
-            int best_lb = first;
-            for (int lb = first; lb < P[0].L; ++lb) {
-                forced_lb_ = lb;
+            BottomChoice best_c = cand[0];
+            for (const BottomChoice& c : cand) {
+                forced_lb_ = c.level;
+                forced_ranks_ = c.ranks;
                 reset_cycle();
                 if ((rc = build_cycle()) != GMG_OK) return rc;
                 if (upload_timing_ctl() != cudaSuccess) return fail(GMG_ERR_CUDA, "autotune: control upload failed");
                 const float ms = time_ms([&] { return run_cycle(); }, 5);
                 if (ms < best) {
                     best = ms;
-                    best_lb = lb;
+                    best_c = c;
                 }
             }
-            forced_lb_ = best_lb;
+            forced_lb_ = best_c.level;
+            forced_ranks_ = best_c.ranks;
             {
                 std::lock_guard<std::mutex> lock(g_tune_mutex);
-                g_tuned_lb[lb_key] = best_lb;
+                g_tuned_lb[lb_key] = best_c;
             }
             reset_cycle();
             if ((rc = build_cycle()) != GMG_OK) return rc;
@@ -2221,6 +2302,14 @@ int gmg_levels(gmg_handle h, int* dims)
     return M.L;
 }
 
+int gmg_bottom_form(gmg_handle h, int* level, int* ranks)
+{
+    if (!h || !level || !ranks) return GMG_ERR_ARG;
+    *level = h->eng.bottom_level_;
+    *ranks = h->eng.bottom_ranks_;
+    return GMG_OK;
+}
+
 int gmg_destroy(gmg_handle h)
 {
     delete h;
@@ -2268,7 +2357,7 @@ int gmg_tune_export(char* buf, size_t cap, size_t* len)
         for (const auto& kv : g_tuned_lb) {
             t += "b";
             for (int v : kv.first) t += " " + std::to_string(v);
-            t += " " + std::to_string(kv.second) + "\n";
+            t += " " + std::to_string(kv.second.level) + " " + std::to_string(kv.second.ranks) + "\n";
         }
     }
     if (len) *len = t.size();
@@ -2282,7 +2371,7 @@ int gmg_tune_import(const char* text)
 {
     if (!text) return GMG_ERR_ARG;
     std::map<TuneKey, int> zs;
-    std::map<std::vector<int>, int> bs;
+    std::map<std::vector<int>, BottomChoice> bs;
     std::istringstream in(text);
     std::string line;
     while (std::getline(in, line)) {
@@ -2297,15 +2386,20 @@ int gmg_tune_import(const char* text)
             if (a < 0 || a > (1L << 30)) return GMG_ERR_ARG;
         if (tag == "z" && v.size() == 8 && v[7] > 0) {
             zs[TuneKey{(int)v[0], (int)v[1], (int)v[2], (int)v[3], (int)v[4], (int)v[5], (int)v[6]}] = (int)v[7];
-        } else if (tag == "b" && v.size() == 12 && v[11] > 0) {
-            bs[std::vector<int>(v.begin(), v.begin() + 11)] = (int)v[11];
+        } else if (tag == "b" && (v.size() == 12 || v.size() == 13) && v[11] < kMaxLevels &&
+                   (v.size() == 12 || (v[12] >= 1 && v[12] <= kClusterMaxRanks))) {
+            // level 0: forget the entry (the next handle of that shape times again)
+            bs[std::vector<int>(v.begin(), v.begin() + 11)] = BottomChoice{(int)v[11], v.size() == 13 ? (int)v[12] : 1};
         } else {
             return GMG_ERR_ARG;
         }
     }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (const auto& kv : zs) g_tuned_zchunk[kv.first] = kv.second;
-    for (const auto& kv : bs) g_tuned_lb[kv.first] = kv.second;
+    for (const auto& kv : bs) {
+        if (kv.second.level == 0) g_tuned_lb.erase(kv.first);
+        else g_tuned_lb[kv.first] = kv.second;
+    }
     return GMG_OK;
 }
 

@@ -97,11 +97,17 @@ def test_tune_table_round_trip(L):
     """The autotuner's table exports as text and imports back unchanged (no GPU involved)."""
     text = ("z 0 256 96 96 0 0 0 8\n"
             "z 2 128 48 48 0 0 0 12\n"
-            "b 256 96 96 0 0 0 1 4 0 16 0 3\n")
+            "b 256 96 96 0 0 0 1 4 0 16 0 3 16\n")
     G.tune_import(text)
     out = G.tune_export()
     for line in text.splitlines():
         assert line in out.splitlines()
+    # a bottom line without the form field reads as the one-CTA form
+    G.tune_import("b 128 96 96 0 0 0 1 4 0 16 0 4\n")
+    assert "b 128 96 96 0 0 0 1 4 0 16 0 4 1" in G.tune_export().splitlines()
+    # level 0 forgets the entry
+    G.tune_import("b 128 96 96 0 0 0 1 4 0 16 0 0\n")
+    assert not any(ln.startswith("b 128 96 96 ") for ln in G.tune_export().splitlines())
     # a replaced entry keeps one line per key
     G.tune_import("z 0 256 96 96 0 0 0 16\n")
     lines = G.tune_export().splitlines()
@@ -114,6 +120,7 @@ def test_tune_table_round_trip(L):
 
 
 @pytest.mark.parametrize("bad", ["z 0 1 2\n", "q 1 2 3\n", "z 0 8 8 8 0 0 0 x\n", "b 1 2 3\n", "z 0 8 8 8 0 0 0 -4\n",
+                                 "b 64 64 64 0 0 0 1 4 0 16 0 3 17\n", "b 64 64 64 0 0 0 1 4 0 16 0 3 0\n",
                                  "z 0 8 8 8 0 0 0 0\n"])
 def test_tune_import_rejects_malformed(L, bad):
     before = G.tune_export()

@@ -1,0 +1,181 @@
+"""The cluster form of the bottom kernel against the one-CTA form and the oracle.
+
+The cluster form splits each bottom level of more than 1024 cells by rows over
+the CTAs of one thread-block cluster (neighbour iterates of other CTAs read
+through distributed shared memory, a cluster barrier after every colour phase,
+residual, restriction and prolongation) and runs the smaller levels in its
+first CTA exactly as the one-CTA form does.  It evaluates every cell with the
+same operands in the same order as the one-CTA form, so from a level where
+both can run the two must give the same bits: any difference is an indexing
+or ordering fault of the distributed levels.  The cases cover walls and
+triple-periodic axes, isotropic and anisotropic coarsening, an odd x-length (a
+row holds one cell fewer of one colour), row counts that the cluster size does
+not divide (a short last CTA, CTAs without rows), the BF16 coarse iterate, the
+dense coarsest solve and FP64 refinement.  From a level that one CTA cannot
+hold, whole solves are compared with the oracle at the tolerances of the other
+whole-solve tests (cycles within 1, solution within 1e-5 of the oracle's
+iterate after the same number of cycles).
+
+Each case pins the bottom through the tuning table and removes its entry
+afterwards, so the other test files keep the autotuner's own choice."""
+import numpy as np
+import pytest
+
+from paper_2607_07687_gb300 import inputs as I
+from tests.gpu_common import f32, host, oracle_cached, problem, rel_l2, t32, t64
+
+pytestmark = pytest.mark.gpu
+
+NOT_CONVERGED = 3   # GMG_NOT_CONVERGED: a fixed number of cycles on the random-coefficient cases
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def _key(prob, o):
+    return list(prob.dims) + [int(bool(v)) for v in prob.periodic] + [o.coarsen, o.n_min, o.precision, o.nu_c,
+                                                                     o.coarse_mode]
+
+
+def _solve(prob, tol, level, ranks, coarsen="aniso", precision="fp32", **kw):
+    """Solve with the bottom pinned to (level, ranks); returns (p, info, history, form)."""
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    o = G.options(coarsen=coarsen, precision=precision, **kw)
+    key = " ".join(str(v) for v in _key(prob, o))
+    G.tune_import(f"b {key} {level} {ranks}\n")
+    try:
+        s = G.Solver(prob.dims, prob.periodic, opts=o)
+        try:
+            s.set_coeffs(t32(prob.bx), t32(prob.by), t32(prob.bz))
+            if s.fp64:
+                b, p = t64(f32(prob.b)), t64(np.zeros(prob.shape))
+            else:
+                b, p = t32(prob.b), t32(np.zeros(prob.shape))
+            info = s.solve(b, p, tol)
+            torch.cuda.synchronize()
+            return host(p), info, s.history()[0], s.bottom_form()
+        finally:
+            s.close()
+    finally:
+        G.tune_import(f"b {key} 0\n")
+
+
+RANKS = 16   # requested; the plan takes what the device can co-schedule (16, else 8)
+
+
+def _same_bits(prob, tol, level, status=0, **kw):
+    """Cluster form and one-CTA form from `level`: identical iterates, histories, counts."""
+    pc, ic, hc, fc = _solve(prob, tol, level, RANKS, **kw)
+    p1, i1, h1, f1 = _solve(prob, tol, level, 1, **kw)
+    assert f1 == (level, 1), f1
+    assert fc[0] == level and fc[1] in (8, 16), fc
+    assert ic.status == i1.status == status, (ic.as_dict(), i1.as_dict())
+    assert ic.cycles == i1.cycles
+    np.testing.assert_array_equal(hc, h1)
+    np.testing.assert_array_equal(pc, p1)
+    return ic
+
+
+def _levels(prob, coarsen):
+    from paper_2607_07687_gb300 import binding as G
+    s = G.Solver(prob.dims, prob.periodic, coarsen=coarsen)
+    try:
+        return s.levels()
+    finally:
+        s.close()
+
+
+def test_sphere_channel_same_bits():
+    """Walls, anisotropic coarsening: 32x12x12 distributed, 16x6x6 .. 4x6x6 in CTA 0."""
+    prob = problem(("sphere",))
+    assert _levels(prob, "aniso")[3] == (32, 12, 12)
+    _same_bits(prob, 1e-5, 3)
+
+
+def test_taylor_green_64_iso_same_bits():
+    """Triple-periodic, isotropic: 16^3 distributed (wrapped y and z neighbours in other CTAs)."""
+    prob = I.taylor_green_problem(64, 0)
+    assert _levels(prob, "iso")[2] == (16, 16, 16)
+    _same_bits(prob, 1e-6, 2, coarsen="iso")
+
+
+def test_ragged_rows_and_idle_ranks_same_bits():
+    """80x6x22 with walls: level 1 (40x6x11, 66 rows) gives 5 rows to each of 13
+    CTAs, 1 row to the 14th and none to the last two; level 2 (20x6x11) too."""
+    prob = I.random_small_problem((80, 6, 22), (False, False, False), seed=11)
+    lv = _levels(prob, "aniso")
+    assert lv[1] == (40, 6, 11) and lv[2] == (20, 6, 11), lv
+    _same_bits(prob, 1e-12, 1, status=NOT_CONVERGED, max_cycles=8)
+
+
+def test_odd_x_same_bits():
+    """9x44x36 with walls: x never coarsens (odd), a 9-cell row holds 5 cells of one
+    colour and 4 of the other; level 1 (9x22x18, 396 rows) leaves a short last CTA."""
+    prob = I.random_small_problem((9, 44, 36), (False, False, False), seed=12)
+    lv = _levels(prob, "aniso")
+    assert lv[1] == (9, 22, 18), lv
+    _same_bits(prob, 1e-12, 1, status=NOT_CONVERGED, max_cycles=8)
+
+
+def test_bf16_coarse_iterate_same_bits():
+    """BF16 storage of the coarse corrections: the bottom's result is written as BF16."""
+    _same_bits(I.taylor_green_problem(64, 0), 1e-5, 2, coarsen="iso", precision="fp32_bf16")
+
+
+def test_dense_coarsest_same_bits():
+    """Dense coarsest solve (pseudo-inverse GEMV) in CTA 0 under distributed levels."""
+    _same_bits(problem(("sphere",)), 1e-5, 3, coarse_mode=1)
+
+
+def test_sphere_channel_cluster_from_level_2_vs_oracle(O):
+    """From 64x24x24 (36,864 cells, beyond one CTA's 10,240): FP64 refinement to 1e-6
+    against the oracle."""
+    prob = problem(("sphere",))
+    ref = oracle_cached(("sphere",), 1e-6, coarsen="aniso")
+    got, info, _, form = _solve(prob, 1e-6, 2, RANKS, precision="ir64_fp32")
+    assert form[0] == 2 and form[1] > 1, form
+    assert info.status == 0 and info.rel_res <= 1e-6, info.as_dict()
+    assert abs(info.cycles - ref.cycles) <= 1, (info.cycles, ref.cycles)
+    same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles)
+    assert rel_l2(got, same.p) <= 1e-5
+
+
+def test_taylor_green_64_cluster_from_level_1_vs_oracle(O):
+    """From 32^3 (32,768 cells, periodic, isotropic): FP32 solve to 1e-6 against the oracle."""
+    prob = I.taylor_green_problem(64, 0)
+    ref = O.solve_problem(prob, tol=1e-6, coarsen="iso")
+    got, info, hist, form = _solve(prob, 1e-6, 1, RANKS, coarsen="iso")
+    assert form[0] == 1 and form[1] > 1, form
+    assert info.status == 0 and info.rel_res <= 1e-6, info.as_dict()
+    assert abs(info.cycles - ref.cycles) <= 1, (info.cycles, ref.cycles)
+    same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles,
+                                                                  coarsen="iso")
+    assert rel_l2(got, same.p) <= 1e-5
+    above = ref.history[:len(hist)] > 1e-5
+    np.testing.assert_allclose(hist[above], ref.history[:len(hist)][above], rtol=1e-4)
+
+
+def test_autotuner_may_choose_the_cluster_form():
+    """Without a pinned entry the tuner times both forms: whatever it picks, the
+    handle reports a valid form and solves the sphere channel to 1e-5."""
+    from paper_2607_07687_gb300 import binding as G
+    prob = problem(("sphere",))
+    o = G.options(coarsen="aniso")
+    G.tune_import("b " + " ".join(str(v) for v in _key(prob, o)) + " 0\n")
+    s = G.Solver(prob.dims, prob.periodic, opts=o)
+    try:
+        s.set_coeffs(t32(prob.bx), t32(prob.by), t32(prob.bz))
+        level, ranks = s.bottom_form()
+        assert 2 <= level <= 6 and ranks in (1, 8, 16), (level, ranks)
+        if level == 2:
+            assert ranks > 1             # 64x24x24 does not fit one CTA
+        b, p = t32(prob.b), t32(np.zeros(prob.shape))
+        info = s.solve(b, p, 1e-5)
+        assert info.status == 0 and info.rel_res <= 1e-5
+    finally:
+        s.close()

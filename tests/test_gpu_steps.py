@@ -55,6 +55,26 @@ def test_sweep_single_launch_equals_two_launches(dims, periodic):
     assert torch.equal(out, ref)
 
 
+@pytest.mark.parametrize("zchunk", [1, 2, 3, 4, 5, 8, 13])
+@pytest.mark.parametrize("dims,periodic", [((68, 18, 13), (0, 0, 0)), ((64, 20, 14), (1, 1, 1))])
+def test_sweep_every_zchunk_equals_two_launches(dims, periodic, zchunk):
+    """Every z-chunk depth of the pipelined sweep (chunks of one plane, odd and even
+    plane counts, a ragged last chunk; each chunk restarts the plane ring with its
+    two halo planes) reproduces the colour-by-colour sweep bit for bit."""
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    nx, ny, nz = dims
+    G.tune_import(f"z 0 {nx} {ny} {nz} {periodic[0]} {periodic[1]} {periodic[2]} {zchunk}\n")
+    (bx, by, bz), b, p = random_fields(dims, periodic, seed=7 * sum(dims) + zchunk)
+    args = [t32(a) for a in (bx, by, bz, b)]
+    out = t32(np.zeros_like(p))
+    G.op_sweep(*args, t32(p), out, 0.8, periodic)
+    ref = t32(p)
+    G.op_sweep_reference(*args, ref, 0.8, periodic)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+
+
 @pytest.mark.parametrize("dims,periodic,fac", [((70, 18, 14), (0, 0, 0), (2, 2, 2)),
                                                ((66, 18, 14), (1, 1, 1), (2, 1, 2)),
                                                ((34, 9, 12), (0, 0, 1), (2, 1, 2)),

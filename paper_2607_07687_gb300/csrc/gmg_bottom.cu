@@ -307,17 +307,23 @@ __device__ void local_vcycle(const BottomTask<TP>& T, float* sm, int first, floa
                 cnt += 1.0;
             }
         }
-        // both sums in one block reduction (the same per-warp and cross-warp order as block_sum)
-        s = warp_sum(s);
-        cnt = warp_sum(cnt);
-        if ((threadIdx.x & 31) == 0) {
-            S.red[threadIdx.x >> 5] = s;
-            S.red2[threadIdx.x >> 5] = cnt;
+        // both sums in one block reduction (the per-warp and cross-warp order of
+        // block_sum) over the warps that hold cells: FP64 issues at a small fraction
+        // of the FP32 rate here, and the other warps' partials are zeros, which
+        // leave the sums unchanged
+        const int nw = min((C.n + 31) >> 5, (int)(blockDim.x >> 5));
+        if ((int)(threadIdx.x >> 5) < nw) {
+            s = warp_sum(s);
+            cnt = warp_sum(cnt);
+            if ((threadIdx.x & 31) == 0) {
+                S.red[threadIdx.x >> 5] = s;
+                S.red2[threadIdx.x >> 5] = cnt;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double ts = 0.0, tc = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            for (int k = 0; k < nw; ++k) {
                 ts += S.red[k];
                 tc += S.red2[k];
             }
@@ -385,7 +391,8 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(const BottomTask<TP>*
     // the task (level geometries, offsets, sweep counts) in shared memory: the level
     // views are rebuilt before every phase
     __shared__ __align__(16) BottomTask<TP> T;
-    load_task(T, tasks, blockIdx.x);
+    load_task(T, tasks, blockIdx.x);          // task lists and face coefficients are written before the cycle
+    pdl_wait();
     if (T.ctl && T.ctl->done) return;
     const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
     load_levels(T, sm, 0, T.b);
@@ -485,26 +492,43 @@ __device__ __forceinline__ void dist_decode(const DistLevel& D, int c, int& x, i
     y = row - z * D.ny;
 }
 
-// nu red-black sweeps of a distributed level; a cluster barrier ends each colour
+// Updated value of the colour's cell t (index among the own cells of that colour)
+// in c, or c = -1 when t names no cell
+__device__ __forceinline__ float dist_red_black(const DistLevel& D, const cg::cluster_group& cl, int rank, int t,
+                                                int nt, int colour, float w, int& c)
+{
+    c = -1;
+    if (t >= nt) return 0.f;
+    const int r = quot(t, D.hx, D.inv_hx);
+    const int j = t - r * D.hx;
+    const int row = D.r0 + r;
+    const int z = quot(row, D.ny, D.inv_ny);
+    const int y = row - z * D.ny;
+    const int x = 2 * j + ((colour + y + z) & 1);
+    if (x >= D.nx) return 0.f;
+    c = r * D.nx + x;
+    const float p0 = D.a[c];
+    const float fl = dist_flux(D, cl, rank, c, x, y, z, p0);
+    return gs_update(p0, fl, D.a[kADG * D.cpr + c], D.a[kAB * D.cpr + c], w);
+}
+
+// nu red-black sweeps of a distributed level; a cluster barrier ends each colour.
+// Each thread takes two cells per round and stores both after computing both
+// (cells of one colour read only cells of the other), so their neighbour loads,
+// several of them from other CTAs, are in flight together.
 __device__ void dist_sweeps(const DistLevel& D, const cg::cluster_group& cl, int rank, int count, float w)
 {
     const int nt = (D.cnt / D.nx) * D.hx;
+    const int bd = blockDim.x;
     float* P = D.a;
     for (int it = 0; it < count; ++it)
         for (int colour = 0; colour < 2; ++colour) {
-            for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-                const int r = quot(t, D.hx, D.inv_hx);
-                const int j = t - r * D.hx;
-                const int row = D.r0 + r;
-                const int z = quot(row, D.ny, D.inv_ny);
-                const int y = row - z * D.ny;
-                const int x = 2 * j + ((colour + y + z) & 1);
-                if (x < D.nx) {
-                    const int c = r * D.nx + x;
-                    const float p0 = P[c];
-                    const float fl = dist_flux(D, cl, rank, c, x, y, z, p0);
-                    P[c] = gs_update(p0, fl, D.a[kADG * D.cpr + c], D.a[kAB * D.cpr + c], w);
-                }
+            for (int t = threadIdx.x; t < nt; t += 2 * bd) {
+                int c0, c1;
+                const float v0 = dist_red_black(D, cl, rank, t, nt, colour, w, c0);
+                const float v1 = dist_red_black(D, cl, rank, t + bd, nt, colour, w, c1);
+                if (c0 >= 0) P[c0] = v0;
+                if (c1 >= 0) P[c1] = v1;
             }
             cl.sync();
         }
@@ -534,8 +558,6 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom_cluster(const BottomT
     const cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     load_task(T, tasks, (int)(blockIdx.x / cl.num_blocks()));
-    if (T.ctl && T.ctl->done) return;              // the same flag in every rank of the cluster
-    const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
     const int nd = T.nd;
 
     // own cells of the distributed levels: faces (upper ones from the neighbour's
@@ -543,42 +565,72 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom_cluster(const BottomT
     for (int k = 0; k < nd; ++k) {
         const DistLevel D = dist_view(T.lev[k], sm, rank);
         const BottomLevel& B = T.lev[k];
-        for (int c = threadIdx.x; c < D.cnt; c += blockDim.x) {
+        struct Faces { float xl, xu, yl, yu, zl, zu; };
+        auto load = [&](int c) {
+            Faces f;
             int x, y, z;
             dist_decode(D, c, x, y, z);
             const int i = D.lo + c;
-            const float xl = __ldg(B.bx + i), yl = __ldg(B.by + i), zl = __ldg(B.bz + i);
-            const float xu = x < D.nx - 1 ? __ldg(B.bx + i + 1) : (D.g.per[0] ? __ldg(B.bx + i - (D.nx - 1)) : 0.f);
-            const float yu = y < D.ny - 1 ? __ldg(B.by + i + D.nx)
-                                          : (D.g.per[1] ? __ldg(B.by + i - (D.ny - 1) * D.nx) : 0.f);
-            const float zu = z < D.g.n[2] - 1 ? __ldg(B.bz + i + D.nxy)
-                                              : (D.g.per[2] ? __ldg(B.bz + i - (D.g.n[2] - 1) * D.nxy) : 0.f);
+            f.xl = __ldg(B.bx + i);
+            f.yl = __ldg(B.by + i);
+            f.zl = __ldg(B.bz + i);
+            f.xu = x < D.nx - 1 ? __ldg(B.bx + i + 1) : (D.g.per[0] ? __ldg(B.bx + i - (D.nx - 1)) : 0.f);
+            f.yu = y < D.ny - 1 ? __ldg(B.by + i + D.nx) : (D.g.per[1] ? __ldg(B.by + i - (D.ny - 1) * D.nx) : 0.f);
+            f.zu = z < D.g.n[2] - 1 ? __ldg(B.bz + i + D.nxy)
+                                    : (D.g.per[2] ? __ldg(B.bz + i - (D.g.n[2] - 1) * D.nxy) : 0.f);
+            return f;
+        };
+        auto store = [&](int c, const Faces& f) {
             float* A = D.a;
             const int s = D.cpr;
             A[kAP * s + c] = 0.f;
-            A[kAB * s + c] = k == 0 ? T.b[i] : 0.f;
+            A[kAB * s + c] = 0.f;
             A[kAR * s + c] = 0.f;
-            A[kAXL * s + c] = xl;
-            A[kAXU * s + c] = xu;
-            A[kAYL * s + c] = yl;
-            A[kAYU * s + c] = yu;
-            A[kAZL * s + c] = zl;
-            A[kAZU * s + c] = zu;
-            A[kADG * s + c] = diag_sum(xl, xu, yl, yu, zl, zu);
+            A[kAXL * s + c] = f.xl;
+            A[kAXU * s + c] = f.xu;
+            A[kAYL * s + c] = f.yl;
+            A[kAYU * s + c] = f.yu;
+            A[kAZL * s + c] = f.zl;
+            A[kAZU * s + c] = f.zu;
+            A[kADG * s + c] = diag_sum(f.xl, f.xu, f.yl, f.yu, f.zl, f.zu);
+        };
+        for (int c = threadIdx.x; c < D.cnt; c += 2 * blockDim.x) {   // two cells' loads in flight
+            const int c1 = c + blockDim.x;
+            const Faces f0 = load(c);
+            Faces f1{};
+            if (c1 < D.cnt) f1 = load(c1);
+            store(c, f0);
+            if (c1 < D.cnt) store(c1, f1);
         }
     }
     if (rank == 0) load_levels(T, sm, nd, nullptr);
+    // the task lists and face coefficients are written before the cycle; the
+    // control state and level 0's right-hand side come from the kernels before
+    pdl_wait();
+    if (T.ctl && T.ctl->done) return;              // the same flag in every rank of the cluster
+    const float w = T.ctl ? (float)T.ctl->omega : 1.0f;
+    {
+        const DistLevel D = dist_view(T.lev[0], sm, rank);
+        for (int c = threadIdx.x; c < D.cnt; c += blockDim.x) D.a[kAB * D.cpr + c] = T.b[D.lo + c];
+    }
     cl.sync();
 
     // descent over the distributed levels: nu1 sweeps from zero, residual, restriction
     for (int k = 0; k < nd; ++k) {
         const DistLevel F = dist_view(T.lev[k], sm, rank);
         dist_sweeps(F, cl, rank, T.nu1, w);
-        for (int c = threadIdx.x; c < F.cnt; c += blockDim.x) {
+        for (int c = threadIdx.x; c < F.cnt; c += 2 * blockDim.x) {   // two cells per round, as in the sweeps
+            const int c1 = c + blockDim.x;
             int x, y, z;
             dist_decode(F, c, x, y, z);
-            const float p0 = F.a[kAP * F.cpr + c];
-            F.a[kAR * F.cpr + c] = F.a[kAB * F.cpr + c] - dist_flux(F, cl, rank, c, x, y, z, p0);
+            const float r0 = F.a[kAB * F.cpr + c] - dist_flux(F, cl, rank, c, x, y, z, F.a[kAP * F.cpr + c]);
+            float r1 = 0.f;
+            if (c1 < F.cnt) {
+                dist_decode(F, c1, x, y, z);
+                r1 = F.a[kAB * F.cpr + c1] - dist_flux(F, cl, rank, c1, x, y, z, F.a[kAP * F.cpr + c1]);
+            }
+            F.a[kAR * F.cpr + c] = r0;
+            if (c1 < F.cnt) F.a[kAR * F.cpr + c1] = r1;
         }
         cl.sync();
         if (k + 1 < nd) {
@@ -608,18 +660,20 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom_cluster(const BottomT
         const Geo& Cg = T.lev[k + 1].g;
         const bool dist_coarse = k + 1 < nd;
         const DistLevel C = dist_view(T.lev[dist_coarse ? k + 1 : k], sm, rank);   // used when distributed
-        for (int c = threadIdx.x; c < F.cnt; c += blockDim.x) {
+        auto parent = [&](int c) {
             int x, y, z;
             dist_decode(F, c, x, y, z);
             const int J = ((z >> (c2 - 1)) * Cg.n[1] + (y >> (c1 - 1))) * Cg.n[0] + (x >> (c0 - 1));
-            float e;
-            if (dist_coarse) {
-                e = *dist_at(C, cl, rank, kAP, J);
-            } else {
-                const float* p = sm + T.lev[nd].off + J;   // rank 0's iterate of the first local level
-                e = rank == 0 ? *p : *cl.map_shared_rank(p, 0u);
-            }
-            F.a[kAP * F.cpr + c] += e;
+            if (dist_coarse) return *dist_at(C, cl, rank, kAP, J);
+            const float* p = sm + T.lev[nd].off + J;   // rank 0's iterate of the first local level
+            return rank == 0 ? *p : *cl.map_shared_rank(p, 0u);
+        };
+        for (int c = threadIdx.x; c < F.cnt; c += 2 * blockDim.x) {   // two cells' loads in flight
+            const int c1 = c + blockDim.x;
+            const float e0 = parent(c);
+            const float e1 = c1 < F.cnt ? parent(c1) : 0.f;
+            F.a[kAP * F.cpr + c] += e0;
+            if (c1 < F.cnt) F.a[kAP * F.cpr + c1] += e1;
         }
         cl.sync();
         dist_sweeps(F, cl, rank, T.nu2, w);
@@ -642,8 +696,7 @@ cudaError_t launch_bottom(const BottomTask<TP>* tasks, int ntasks, size_t smem, 
         if (e != cudaSuccess) return e;
         opted = smem;
     }
-    k_bottom<TP><<<ntasks, kBottomThreads, smem, s>>>(tasks);
-    return cudaGetLastError();
+    return launch_pdl(k_bottom<TP>, ntasks, kBottomThreads, smem, s, 1, tasks);
 }
 template cudaError_t launch_bottom<float>(const BottomTask<float>*, int, size_t, cudaStream_t);
 template cudaError_t launch_bottom<bf16>(const BottomTask<bf16>*, int, size_t, cudaStream_t);
@@ -654,19 +707,8 @@ cudaError_t launch_bottom_cluster(const BottomTask<TP>* tasks, int ntasks, int r
     if (ntasks <= 0) return cudaSuccess;
     if (ranks < 2 || ranks > kClusterMaxRanks || smem > sizeof(float) * (size_t)kClusterMaxFloats)
         return cudaErrorInvalidValue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(ntasks * ranks));
-    cfg.blockDim = dim3(kBottomThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)ranks;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_bottom_cluster<TP>, tasks);
+    return launch_pdl(k_bottom_cluster<TP>, dim3((unsigned)(ntasks * ranks)), dim3(kBottomThreads), smem, s, ranks,
+                      tasks);
 }
 template cudaError_t launch_bottom_cluster<float>(const BottomTask<float>*, int, int, size_t, cudaStream_t);
 template cudaError_t launch_bottom_cluster<bf16>(const BottomTask<bf16>*, int, int, size_t, cudaStream_t);

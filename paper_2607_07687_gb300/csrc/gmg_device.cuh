@@ -98,6 +98,14 @@ __device__ __forceinline__ const Task* task_of(const TaskList<Task>& tl, int til
     return tl.tasks + lo;
 }
 
+// Programmatic dependent launch (kernels started by launch_pdl): wait until every
+// grid this one depends on has completed with its memory visible.  No kernel
+// signals its dependents early (griddepcontrol.launch_dependents): they are
+// scheduled as its blocks exit, which measured faster on the V-cycle than both
+// an early signal (blocks of the next kernel then hold SM resources while they
+// wait) and plain stream order.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 __device__ __forceinline__ double warp_sum(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

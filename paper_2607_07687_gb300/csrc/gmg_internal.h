@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 #include <string>
+#include <utility>
 
 #include "gmg_hw.h"
 
@@ -323,6 +324,37 @@ int persistent_grid(int64_t tiles);
 cudaError_t set_ring_wait_tries(int tries);
 
 // ---------------------------------------------------------------- launchers
+
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// as its predecessor in the stream finishes, before the predecessor's completion
+// is signalled, and must execute griddepcontrol.wait (dev::pdl_wait) before it
+// touches memory that another kernel writes or reads.  A cluster size > 1 adds
+// the thread-block cluster dimension.
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, int cluster,
+                       Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    int n = 0;
+    at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+    if (cluster > 1) {
+        at[n].id = cudaLaunchAttributeClusterDimension;
+        at[n].val.clusterDim.x = (unsigned)cluster;
+        at[n].val.clusterDim.y = 1;
+        at[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 template <class TP, class TC>
 cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaStream_t s);

@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const __grid_constant__ Task
     __shared__ float sBY[2][PL];   // lower y-face coefficients, planes kr-1, kr
     __shared__ float sBZ[3][PL];   // lower z-face coefficients, planes kr-1..kr+1
     const int tid = threadIdx.x;
+    pdl_wait();
 
     for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
         int local;
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
     const int tid = threadIdx.x;
     const int half = tid / (kThreads / 2);      // copy duty: 0 -> p, b, x faces; 1 -> y, z faces
     const int chunk = tid % (kThreads / 2);
+    pdl_wait();
 
     for (int tile = blockIdx.x; tile < tl.total; tile += gridDim.x) {
         int local;
@@ -755,6 +757,7 @@ __global__ void __launch_bounds__(kSweepBlock, 3) k_sweep_ws(const __grid_consta
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_wait();
     volatile int* dead = &s_dead;
     const int tries = g_ring_tries;
     auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
@@ -1006,6 +1009,7 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_wait();
     volatile int* dead = &s_dead;
     const int tries = g_ring_tries;
     auto ring = [&](int a, uint32_t g) -> float* { return smem + (a * R + (int)(g % R)) * PL; };
@@ -1260,6 +1264,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(const __grid_constant__ T
 {
     __shared__ float sr[kResTZ][kResTY][kResTX];
     __shared__ double red[kThreads / 32];
+    pdl_wait();
     const int tx = threadIdx.x % kResTX;
     const int ty = (threadIdx.x / kResTX) % kResTY;
     const int tz = threadIdx.x / (kResTX * kResTY);
@@ -1401,6 +1406,7 @@ __global__ void k_prolong_add(Geo f, int c0, int c1, int c2, const float* __rest
 // sweep's plane loads, so both give the same iterate bit for bit.
 __global__ void __launch_bounds__(kThreads) k_prolong_rows(const __grid_constant__ ProlongTask t)
 {
+    pdl_wait();
     const int nx = t.g.n[0], ny = t.g.n[1], nz = t.g.n[2];
     const int cpr = nx / 4;                                  // chunks per row
     const int gcx = nx / t.cf[0], gcy = ny / t.cf[1];
@@ -1653,6 +1659,7 @@ __global__ void k_control_init(const CtlTask* __restrict__ tasks)
 __global__ void k_control_cycle(const CtlTask* __restrict__ tasks)
 {
     __shared__ double red[kThreads / 32];
+    pdl_wait();
     const CtlTask& t = tasks[blockIdx.x];
     if (t.ctl->done) return;   // uniform in the block
     const double rr = sum_range(t.partials, t.nparts, 1, 0, red);
@@ -1945,16 +1952,13 @@ cudaError_t launch_sweep(const TaskList<SweepTask<TP, TC>>& tl, int grid, cudaSt
             attr = true;
         }
         if (tl.corr) {
-            if (tl.vec >= 4) k_sweep_ws<true, TC><<<grid, kSweepBlock, smem, s>>>(tl);
-            else k_sweep_async<1, true, TC><<<grid, kThreads, smem, s>>>(tl);
-        } else {
-            if (tl.vec >= 4) k_sweep_ws<false, TC><<<grid, kSweepBlock, smem, s>>>(tl);
-            else k_sweep_async<1, false, TC><<<grid, kThreads, smem, s>>>(tl);
+            if (tl.vec >= 4) return launch_pdl(k_sweep_ws<true, TC>, grid, kSweepBlock, smem, s, 1, tl);
+            return launch_pdl(k_sweep_async<1, true, TC>, grid, kThreads, smem, s, 1, tl);
         }
-    } else {
-        k_sweep<TP, TC><<<grid, kThreads, 0, s>>>(tl);
+        if (tl.vec >= 4) return launch_pdl(k_sweep_ws<false, TC>, grid, kSweepBlock, smem, s, 1, tl);
+        return launch_pdl(k_sweep_async<1, false, TC>, grid, kThreads, smem, s, 1, tl);
     }
-    return cudaGetLastError();
+    return launch_pdl(k_sweep<TP, TC>, grid, kThreads, 0, s, 1, tl);
 }
 template cudaError_t launch_sweep<float, float>(const TaskList<SweepTask<float, float>>&, int, cudaStream_t);
 template cudaError_t launch_sweep<float, bf16>(const TaskList<SweepTask<float, bf16>>&, int, cudaStream_t);
@@ -1974,12 +1978,10 @@ cudaError_t launch_residual(const TaskList<ResTask<TP>>& tl, int grid, cudaStrea
                 if (e != cudaSuccess) return e;
                 attr = true;
             }
-            k_residual_ws<<<grid, kResBlock, smem, s>>>(tl);
-            return cudaGetLastError();
+            return launch_pdl(k_residual_ws, grid, kResBlock, smem, s, 1, tl);
         }
     }
-    k_residual<TP><<<grid, kThreads, 0, s>>>(tl);
-    return cudaGetLastError();
+    return launch_pdl(k_residual<TP>, grid, kThreads, 0, s, 1, tl);
 }
 template cudaError_t launch_residual<float>(const TaskList<ResTask<float>>&, int, cudaStream_t);
 template cudaError_t launch_residual<bf16>(const TaskList<ResTask<bf16>>&, int, cudaStream_t);
@@ -2017,8 +2019,7 @@ cudaError_t launch_prolong_add(Geo fine, const int cf[3], const float* e, float*
 cudaError_t launch_prolong_rows(const ProlongTask& t, cudaStream_t s)
 {
     const int64_t chunks = (int64_t)(t.g.n[0] / 4) * t.g.n[1] * t.g.n[2];
-    k_prolong_rows<<<grid_for(chunks), kThreads, 0, s>>>(t);
-    return cudaGetLastError();
+    return launch_pdl(k_prolong_rows, grid_for(chunks), kThreads, 0, s, 1, t);
 }
 
 cudaError_t launch_active_mask(Geo g, const float* bx, const float* by, const float* bz,
@@ -2071,8 +2072,7 @@ cudaError_t launch_control_init(const CtlTask* t, int nprob, cudaStream_t s)
 }
 cudaError_t launch_control_cycle(const CtlTask* t, int nprob, cudaStream_t s)
 {
-    k_control_cycle<<<nprob, kThreads, 0, s>>>(t);
-    return cudaGetLastError();
+    return launch_pdl(k_control_cycle, nprob, kThreads, 0, s, 1, t);
 }
 
 template <class TP, class TD>

@@ -104,9 +104,21 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(key="k_sweep_ws_256x96x96"):
-    """DRAM bytes per launch of a kernel from the committed ncu summary
-    (profiles/traffic.json), valid only while the kernel source is unchanged."""
+def tuned_zchunk(kind, dims, periodic):
+    """z-chunk depth the autotuner chose in this process for a kernel kind (0
+    sweep, 2 residual) on a grid, or None (from gmg_tune_export)."""
+    from paper_2607_07687_gb300 import binding as G
+    key = f"z {kind} {dims[0]} {dims[1]} {dims[2]} {int(bool(periodic[0]))} {int(bool(periodic[1]))} " \
+          f"{int(bool(periodic[2]))} "
+    for ln in G.tune_export().splitlines():
+        if ln.startswith(key):
+            return int(ln.split()[-1])
+    return None
+
+
+def recorded_traffic(key):
+    """DRAM bytes per launch of a kernel at one launch shape from the committed ncu
+    summary (profiles/traffic.json), valid only while the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2607_07687_gb300", "csrc", "gmg_kernels.cu")
     try:
@@ -273,10 +285,12 @@ def record_512(dev, stream, flush, peak, peak_kind):
                 lambda i: G.op_residual_restrict(*rb, rhs, pa, coarse, (2, 2, 2), per)))
     for key, kname, bpc, launch in kernels:
         ms = kernel_ms(launch, flush, stream, reps=20)
+        zc = tuned_zchunk(0 if key == "sweep" else 2, (n, n, n), per)
         achieved = bpc * cells / (ms * 1e-3) / 1e9
         out[key] = {"kernel": kname, "bound": "hbm", "ms": ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
-                    "bytes_per_cell": bpc, "traffic": recorded_traffic(f"{kname}_512"),
+                    "bytes_per_cell": bpc, "zchunk": zc,
+                    "traffic": recorded_traffic(f"{kname}_512x512x512_z{zc}"),
                     "tuning": [ln for ln in G.tune_export().splitlines() if " 512 512 512 " in ln]}
     solver.close()
     del rb, rhs, pa, pb, coarse
@@ -1074,8 +1088,11 @@ def main():
     alg_bytes = BYTES_PER_CELL_SWEEP * cells
     peak, peak_kind = peaks()
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    zc = tuned_zchunk(0, prob.dims, prob.periodic)
+    nx, ny, nz = prob.dims
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(), "kernel": "k_sweep_ws (fine level)",
+                "frac": achieved / peak, "traffic": recorded_traffic(f"k_sweep_ws_{nx}x{ny}x{nz}_z{zc}"),
+                "kernel": "k_sweep_ws (fine level)", "zchunk": zc,
                 "peak_source": f"{peak_kind} hbm_gbs", "l2_flushed": True,
                 "l2_resident_achieved": alg_bytes / (warm_ms * 1e-3) / 1e9,
                 "sweep_gcell_updates_per_s": cells / (sweep_ms * 1e-3) / 1e9}

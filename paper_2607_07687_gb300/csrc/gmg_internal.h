@@ -201,6 +201,8 @@ struct BottomTask {
     int ranks;           // cluster form: CTAs per cluster (the layout's cpr assumes it)
 };
 
+struct CtlTask;
+
 template <class Task>
 struct TaskList {
     const Task* tasks;   // device array, or nullptr: use `single`
@@ -210,6 +212,12 @@ struct TaskList {
     int vec;             // 4: every task's rows split into aligned 16-byte chunks
     int corr;            // sweeps: 1 if any task adds a coarse correction
     int march;           // residuals: 1 = z-marching kernel (tiles of 32 x 8 columns x zchunk)
+    // z-marching norm residual of the fine level: the last block to finish applies
+    // the cycle's control rule for these tasks (nullptr: a separate launch does);
+    // `arrivals` counts finished blocks and is reset to 0 by that last block
+    const CtlTask* ctl_tasks;
+    int nctl;
+    unsigned* arrivals;
     Task single;
 };
 

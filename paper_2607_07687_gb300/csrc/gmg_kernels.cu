@@ -985,6 +985,33 @@ __device__ __forceinline__ bool res_tile(const TaskList<ResTask<float>>& tl, int
     return true;
 }
 
+__device__ void control_rule(Ctl& C, double rr);
+
+// Sum of part[0 .. n) by the kResConsumers consumer threads in exactly the order of
+// sum_range over kThreads threads (each consumer stands for threads tid and tid +
+// kResConsumers of that block), so the folded control rule sees the same bits as
+// k_control_cycle.  Result valid in consumer 0.
+__device__ double consumer_sum(const double* part, int n, double* red)
+{
+    static_assert(kThreads == 2 * kResConsumers, "two virtual threads per consumer");
+    const int tid = threadIdx.x, lane = tid & 31;
+    double a = 0.0, b = 0.0;
+    for (int i = tid; i < n; i += kThreads) a += __ldcg(part + i);
+    for (int i = tid + kResConsumers; i < n; i += kThreads) b += __ldcg(part + i);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+        red[tid >> 5] = a;
+        red[(tid + kResConsumers) >> 5] = b;
+    }
+    asm volatile("bar.sync 1, %0;\n" ::"n"(kResConsumers) : "memory");
+    double s = 0.0;
+    if (tid == 0)
+        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    asm volatile("bar.sync 1, %0;\n" ::"n"(kResConsumers) : "memory");
+    return s;
+}
+
 __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_constant__ TaskList<ResTask<float>> tl)
 {
     constexpr int TX = kSweepTX, TY = kSweepTY;
@@ -1212,7 +1239,7 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
                 atomicExch(&g_wait_fault, 1);
                 s_dead = 1;
             }
-            return;
+            break;   // still counted below, so that a folded control rule is not left waiting
         }
         if (tp->partials) {
             const double q = warp_sum(rr + (double)rr32);
@@ -1224,6 +1251,28 @@ __global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_const
                 tp->partials[t.local] = s;
             }
             asm volatile("bar.sync 1, %0;\n" ::"n"(kResConsumers) : "memory");
+        }
+    }
+
+    // control rule folded into the fine-level norm (Sec. 3.1): the last block to
+    // finish sums every task's partials and updates its control state
+    if (tl.ctl_tasks) {
+        __shared__ int s_last;
+        __shared__ double red_ctl[kThreads / 32];
+        if (tid == 0) {
+            __threadfence();                       // this block's partials before its arrival
+            s_last = atomicAdd(tl.arrivals, 1u) == gridDim.x - 1;
+        }
+        asm volatile("bar.sync 1, %0;\n" ::"n"(kResConsumers) : "memory");
+        if (s_last) {
+            __threadfence();
+            for (int k = 0; k < tl.nctl; ++k) {
+                const CtlTask& ct = tl.ctl_tasks[k];
+                if (*(volatile const int*)&ct.ctl->done) continue;   // the same value in every thread
+                const double rr = consumer_sum(ct.partials, ct.nparts, red_ctl);
+                if (tid == 0) control_rule(*ct.ctl, rr);
+            }
+            if (tid == 0) *tl.arrivals = 0u;     // ready for the next launch
         }
     }
 }
@@ -1655,7 +1704,41 @@ __global__ void k_control_init(const CtlTask* __restrict__ tasks)
     }
 }
 
-// the adaptive relaxation rule after one V-cycle (Sec. 3.1)
+// the adaptive relaxation rule after one V-cycle (Sec. 3.1), from the fine
+// residual's squared norm rr; one thread
+__device__ void control_rule(Ctl& C, double rr)
+{
+    const double rk = sqrt(rr);
+    const double w = C.omega;
+    // a relaxation factor that is not a positive finite number means the control
+    // state is corrupt: the solve stops as diverged with the accepted iterate
+    const bool w_ok = isfinite(w) && w > 0.0;
+    const bool acc = w_ok && rk < C.r_prev;     // NaN rejects
+    C.r_last = rk;
+    C.cycles += 1;
+    C.total_cycles += 1;
+    if (!w_ok) {
+        C.status = kDiverged;
+    } else if (acc) {
+        C.rot = (C.rot + C.res_role) % 3;
+        C.r_prev = rk;
+        C.omega = fmin(1.0, C.grow * w);
+    } else if (w <= C.omega_min) {
+        C.status = kDiverged;
+    } else {
+        C.omega = fmax(C.omega_min, C.shrink * w);
+    }
+    const int k = C.total_cycles;
+    if (k <= C.hist_cap) {
+        C.hist_res[k] = C.r_prev * C.hist_scale;
+        C.hist_omega[k - 1] = w;
+        C.hist_acc[k - 1] = acc ? 1 : 0;
+    }
+    if (C.status != kDiverged && C.r_prev / C.bnorm <= C.tol) C.status = kOk;
+    else if (C.status == kRunning && C.cycles >= C.max_cycles) C.status = kNotConverged;
+    if (C.status != kRunning) C.done = 1;
+}
+
 __global__ void k_control_cycle(const CtlTask* __restrict__ tasks)
 {
     __shared__ double red[kThreads / 32];
@@ -1663,38 +1746,7 @@ __global__ void k_control_cycle(const CtlTask* __restrict__ tasks)
     const CtlTask& t = tasks[blockIdx.x];
     if (t.ctl->done) return;   // uniform in the block
     const double rr = sum_range(t.partials, t.nparts, 1, 0, red);
-    if (threadIdx.x == 0) {
-        Ctl& C = *t.ctl;
-        const double rk = sqrt(rr);
-        const double w = C.omega;
-        // a relaxation factor that is not a positive finite number means the control
-        // state is corrupt: the solve stops as diverged with the accepted iterate
-        const bool w_ok = isfinite(w) && w > 0.0;
-        const bool acc = w_ok && rk < C.r_prev;     // NaN rejects
-        C.r_last = rk;
-        C.cycles += 1;
-        C.total_cycles += 1;
-        if (!w_ok) {
-            C.status = kDiverged;
-        } else if (acc) {
-            C.rot = (C.rot + C.res_role) % 3;
-            C.r_prev = rk;
-            C.omega = fmin(1.0, C.grow * w);
-        } else if (w <= C.omega_min) {
-            C.status = kDiverged;
-        } else {
-            C.omega = fmax(C.omega_min, C.shrink * w);
-        }
-        const int k = C.total_cycles;
-        if (k <= C.hist_cap) {
-            C.hist_res[k] = C.r_prev * C.hist_scale;
-            C.hist_omega[k - 1] = w;
-            C.hist_acc[k - 1] = acc ? 1 : 0;
-        }
-        if (C.status != kDiverged && C.r_prev / C.bnorm <= C.tol) C.status = kOk;
-        else if (C.status == kRunning && C.cycles >= C.max_cycles) C.status = kNotConverged;
-        if (C.status != kRunning) C.done = 1;
-    }
+    if (threadIdx.x == 0) control_rule(*t.ctl, rr);
 }
 
 // ---------------------------------------------------------------- K9: FP64 refinement

@@ -724,6 +724,7 @@ struct Engine {
     int forced_ranks_ = 1;                          // tuned form of the bottom (> 1: cluster form)
     std::vector<int> fit_lb_;                       // [p] smallest one-CTA fit, -1 if none
     int bottom_level_ = 0, bottom_ranks_ = 0;       // problem 0's bottom as planned (0: none)
+    unsigned* arrivals_ = nullptr;                  // block counter of the norm residual with the control rule
     bool tuned_ = false;
 
     int add_sweeps(int l, const std::vector<int>& probs, int in, int out, bool with_corr)
@@ -764,15 +765,6 @@ struct Engine {
             op.grid = persistent_grid(op.s_ff.total);
         }
         cycle.push_back(op);
-        return GMG_OK;
-    }
-
-    int add_residual_roles(const std::vector<int>& probs, const std::vector<int>& roles)
-    {
-        std::vector<LaunchOp> ops;
-        int rc = res_ops(0, probs, roles, false, true, ops);
-        if (rc) return rc;
-        for (auto& op : ops) cycle.push_back(op);
         return GMG_OK;
     }
 
@@ -1023,17 +1015,33 @@ struct Engine {
                 if (l == 0) res_role[p] = cur;
             }
         }
-        // fine residual norm of the candidate, then the control rule
+        // fine residual norm of the candidate, then the control rule: for one
+        // problem on the z-marching residual, inside that launch (its last block)
         {
             std::vector<int> probs(nprob);
             for (int p = 0; p < nprob; ++p) probs[p] = p;
-            int rc = add_residual_roles(probs, res_role);
+            std::vector<LaunchOp> ops;
+            int rc = res_ops(0, probs, res_role, false, true, ops);
             if (rc) return rc;
-            LaunchOp c;
-            c.kind = kControl;
-            c.ctl = cycle_ctl;
-            c.n = nprob;
-            cycle.push_back(c);
+            const bool fold = nprob == 1 && ops.size() == 1 && ops[0].kind == kResF && ops[0].r_f.march;
+            if (fold) {
+                if (!arrivals_) {
+                    arrivals_ = dalloc<unsigned>(1);
+                    if (!arrivals_ || cudaMemset(arrivals_, 0, sizeof(unsigned)) != cudaSuccess)
+                        return fail(GMG_ERR_CUDA, "arrival counter allocation failed");
+                }
+                ops[0].r_f.ctl_tasks = cycle_ctl;
+                ops[0].r_f.nctl = nprob;
+                ops[0].r_f.arrivals = arrivals_;
+            }
+            for (auto& op : ops) cycle.push_back(op);
+            if (!fold) {
+                LaunchOp c;
+                c.kind = kControl;
+                c.ctl = cycle_ctl;
+                c.n = nprob;
+                cycle.push_back(c);
+            }
         }
         return GMG_OK;
     }

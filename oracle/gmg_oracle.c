@@ -31,7 +31,10 @@
  *                (a 2D problem, Fig. 2) takes no part: it never halves, and
  *                iso halves the other axes together.
  *   C4 coarse b  finite-volume rediscretisation: coarse face = (1/c_d) times
- *                the sum of the fine faces that make it up.
+ *                the sum of the fine faces that make it up; or, as the option
+ *                for study (coarse_op 1), the Galerkin operator R A P with
+ *                piecewise-constant P and R = P^T, whose coarse face is that
+ *                sum without the 1/c_d.
  *   C5 omega     w0 = 1; after each V-cycle rho = |r_k| / |r_prev|; rho < 1
  *                accepts and sets w = min(1, grow w); otherwise the cycle is
  *                rejected (iterate restored), w = max(w_min, shrink w), and a
@@ -235,9 +238,10 @@ static int schedule(const int n0[3], const int per[3], int aniso, int n_min, int
     return L;
 }
 
-/* C4: coarse face coefficients by finite-volume rediscretisation */
+/* C4: coarse face coefficients by finite-volume rediscretisation (galerkin 0),
+ * or those of R A P with piecewise-constant P (galerkin 1: no 1/c_d) */
 static void coarsen_beta(const grid_t* fg, const double* const fb[3], const int c[3],
-                         const grid_t* cg, double* const cb[3])
+                         const grid_t* cg, double* const cb[3], int galerkin)
 {
     int J[3];
     for (int d = 0; d < 3; ++d) {
@@ -256,7 +260,7 @@ static void coarsen_beta(const grid_t* fg, const double* const fb[3], const int 
                         for (I[1] = lo[1]; I[1] < hi[1]; ++I[1])
                             for (I[0] = lo[0]; I[0] < hi[0]; ++I[0])
                                 s += fb[d][idx(fg, I[0], I[1], I[2])];
-                    cb[d][idx(cg, J[0], J[1], J[2])] = s / (double)c[d];
+                    cb[d][idx(cg, J[0], J[1], J[2])] = galerkin ? s : s / (double)c[d];
                 }
     }
 }
@@ -289,6 +293,7 @@ typedef struct {
     int max_cycles;
     double omega0, omega_min, shrink, grow;
     int coarse_mode;    /* 0: nu_c sweeps on the coarsest level; 1: minimum-norm dense solve */
+    int coarse_op;      /* 0: finite-volume coarse coefficients; 1: Galerkin R A P (C4) */
 } or_options;
 
 /* ------------------------------------------------------------------------ */
@@ -443,7 +448,8 @@ static int build_hierarchy(hierarchy_t* h, const int n[3], const int per[3], con
                     h->beta[0][d][I] = (c[d] == 0 && !per[d]) ? 0.0 : src[d][I];
                 }
     for (int l = 0; l + 1 < h->levels; ++l)
-        coarsen_beta(&h->g[l], (const double* const*)h->beta[l], h->fac[l], &h->g[l + 1], h->beta[l + 1]);
+        coarsen_beta(&h->g[l], (const double* const*)h->beta[l], h->fac[l], &h->g[l + 1], h->beta[l + 1],
+                     o->coarse_op);
     if (o->coarse_mode == 1) {
         int c = h->levels - 1;
         h->pinv = pseudo_inverse(&h->g[c], (const double* const*)h->beta[c]);
@@ -608,13 +614,13 @@ int or_schedule(int nx, int ny, int nz, const int* periodic, int aniso, int n_mi
 
 int or_coarsen_beta(int nx, int ny, int nz, const int* periodic, const int* fac,
                     const double* bx, const double* by, const double* bz,
-                    double* cbx, double* cby, double* cbz)
+                    double* cbx, double* cby, double* cbz, int galerkin)
 {
     grid_t fg = {{nx, ny, nz}, {periodic[0] != 0, periodic[1] != 0, periodic[2] != 0}};
     grid_t cg = {{nx / fac[0], ny / fac[1], nz / fac[2]}, {fg.per[0], fg.per[1], fg.per[2]}};
     const double* fb[3] = {bx, by, bz};
     double* cb[3] = {cbx, cby, cbz};
-    coarsen_beta(&fg, fb, fac, &cg, cb);
+    coarsen_beta(&fg, fb, fac, &cg, cb, galerkin);
     return OR_OK;
 }
 

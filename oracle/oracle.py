@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
     _fields_ = [("coarsen", ctypes.c_int), ("n_min", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("nu_c", ctypes.c_int), ("max_cycles", ctypes.c_int),
                 ("omega0", ctypes.c_double), ("omega_min", ctypes.c_double),
-                ("shrink", ctypes.c_double), ("grow", ctypes.c_double), ("coarse_mode", ctypes.c_int)]
+                ("shrink", ctypes.c_double), ("grow", ctypes.c_double), ("coarse_mode", ctypes.c_int),
+                ("coarse_op", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -54,10 +55,11 @@ class _Info(ctypes.Structure):
 
 def options(coarsen: str = "aniso", n_min: int = 4, nu1: int = 2, nu2: int = 2, nu_c: int = 16,
             max_cycles: int = 100, omega0: float = 1.0, omega_min: float = 0.25,
-            shrink: float = 0.7, grow: float = 1.1, coarse_mode: int = 0) -> Options:
-    """coarse_mode 0: nu_c sweeps on the coarsest level; 1: its minimum-norm dense solve."""
+            shrink: float = 0.7, grow: float = 1.1, coarse_mode: int = 0, coarse_op: int = 0) -> Options:
+    """coarse_mode 0: nu_c sweeps on the coarsest level; 1: its minimum-norm dense solve.
+    coarse_op 0: finite-volume coarse coefficients; 1: Galerkin R A P (C4's option)."""
     return Options(1 if coarsen == "aniso" else 0, n_min, nu1, nu2, nu_c, max_cycles,
-                   omega0, omega_min, shrink, grow, coarse_mode)
+                   omega0, omega_min, shrink, grow, coarse_mode, coarse_op)
 
 
 _lib = None
@@ -76,7 +78,7 @@ def lib():
         _lib.or_half_sweep.argtypes = [c_int, c_int, c_int, I, D, D, D, D, D, c_double, c_int]
         _lib.or_sweep.argtypes = [c_int, c_int, c_int, I, D, D, D, D, D, c_double]
         _lib.or_schedule.argtypes = [c_int, c_int, c_int, I, c_int, c_int, I, I]
-        _lib.or_coarsen_beta.argtypes = [c_int, c_int, c_int, I, I, D, D, D, D, D, D]
+        _lib.or_coarsen_beta.argtypes = [c_int, c_int, c_int, I, I, D, D, D, D, D, D, c_int]
         _lib.or_restrict.argtypes = [c_int, c_int, c_int, I, D, D]
         _lib.or_prolong_add.argtypes = [c_int, c_int, c_int, I, D, D]
         _lib.or_vcycle.argtypes = [c_int, c_int, c_int, I, ctypes.POINTER(Options), D, D, D, D, D,
@@ -135,13 +137,13 @@ def schedule(dims, periodic=(False, False, False), coarsen: str = "aniso", n_min
             [tuple(f[3 * l:3 * l + 3]) for l in range(L)])
 
 
-def coarsen_beta(bx, by, bz, fac, periodic=(False, False, False)):
+def coarsen_beta(bx, by, bz, fac, periodic=(False, False, False), galerkin: bool = False):
     bx, by, bz = map(_f64, (bx, by, bz))
     nz, ny, nx = bx.shape
     cshape = (nz // fac[2], ny // fac[1], nx // fac[0])
     out = [np.empty(cshape) for _ in range(3)]
     lib().or_coarsen_beta(nx, ny, nz, _ivec(periodic), _ivec(fac), _d(bx), _d(by), _d(bz),
-                          *[_d(o) for o in out])
+                          *[_d(o) for o in out], int(bool(galerkin)))
     return tuple(out)
 
 

@@ -242,8 +242,8 @@ def _prolongation(fine_shape, fac):
 @pytest.mark.parametrize("fac", [(2, 2, 2), (2, 1, 1), (1, 2, 2), (2, 1, 2), (1, 2, 1), (1, 1, 2)])
 def test_transfers_and_galerkin(oracle, fac):
     """Restriction is the transpose of the piecewise-constant prolongation,
-    and the finite-volume coarse faces are 1/c_d times the Galerkin ones
-    (R A P built by matrix products)."""
+    the finite-volume coarse faces are 1/c_d times the Galerkin ones, and the
+    Galerkin option's coarse faces give R A P itself (built by matrix products)."""
     periodic = (False, True, False)
     shape = (4, 4, 8)
     rng = np.random.default_rng(2)
@@ -260,6 +260,8 @@ def test_transfers_and_galerkin(oracle, fac):
     cb = oracle.coarsen_beta(bx, by, bz, fac, periodic)
     scaled = [cb[d] * fac[d] for d in range(3)]
     np.testing.assert_allclose(oracle.dense_operator(*scaled, periodic), RAP, atol=1e-12)
+    gal = oracle.coarsen_beta(bx, by, bz, fac, periodic, galerkin=True)
+    np.testing.assert_allclose(oracle.dense_operator(*gal, periodic), RAP, atol=1e-12)
 
 
 def _sor_colours(A, b, x, omega, shape):
@@ -329,6 +331,16 @@ def test_vcycle_matches_matrix_form(oracle, dims, periodic, coarsen):
     ref = _matrix_vcycle(lv, 0, b.ravel(), p.ravel().copy(), omega, 2, 2, 16, dense=True)
     got = oracle.vcycle(p, b, bx, by, bz, omega, periodic, coarsen=coarsen, n_min=2, coarse_mode=1)
     np.testing.assert_allclose(got.ravel(), ref, rtol=1e-9, atol=1e-9)
+    # the Galerkin option (coarse_op 1): every coarse operator is P^T A P of the
+    # level above, formed here by matrix products alone
+    glv = [dict(lv[0])]
+    for l in range(1, len(lv)):
+        P = lv[l - 1]["P"]
+        glv.append(dict(lv[l], A=P.T @ glv[l - 1]["A"] @ P))
+        glv[l - 1] = dict(glv[l - 1], P=P)
+    ref = _matrix_vcycle(glv, 0, b.ravel(), p.ravel().copy(), omega, 2, 2, 16)
+    got = oracle.vcycle(p, b, bx, by, bz, omega, periodic, coarsen=coarsen, n_min=2, coarse_op=1)
+    np.testing.assert_allclose(got.ravel(), ref, rtol=1e-11, atol=1e-11)
 
 
 # ---------------------------------------------------------------- dense coarsest solve (option)
@@ -499,6 +511,19 @@ def test_history_monotone_heterogeneous(oracle):
     res = oracle.solve_problem(prob, tol=1e-8, max_cycles=80)
     assert res.status == oracle.OK
     assert np.all(np.diff(res.history) <= 0)
+
+
+def test_galerkin_option_solves_with_monotone_history(oracle):
+    """C4's Galerkin option (coarse_op 1) on a heterogeneous channel: the
+    solve reaches the tolerance with the non-increasing history of Sec. 3.1,
+    and its answer agrees with the finite-volume hierarchy's to the tolerance
+    (the coarse operator changes the iteration, not the solution)."""
+    prob = I.sphere_channel_problem(64, 32, 32, seed=5, radius=6.0, center_x=20.0)
+    fv = oracle.solve_problem(prob, tol=1e-9, max_cycles=200)
+    gal = oracle.solve_problem(prob, tol=1e-9, max_cycles=200, coarse_op=1)
+    assert fv.status == oracle.OK and gal.status == oracle.OK
+    assert np.all(np.diff(gal.history) <= 0)
+    assert np.linalg.norm(gal.p - fv.p) <= 1e-6 * np.linalg.norm(fv.p)
 
 
 def test_omega_rejects_growth_then_recovers(oracle):

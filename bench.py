@@ -804,8 +804,9 @@ def suite(args):
             ts.append(ev0.elapsed_time(ev1))
         return float(np.median(ts)), out
 
-    def single(prob, precision, tol, coarsen, reps, warm, coarse_mode=0):
-        s = G.Solver(prob.dims, prob.periodic, precision=precision, coarsen=coarsen, coarse_mode=coarse_mode)
+    def single(prob, precision, tol, coarsen, reps, warm, coarse_mode=0, coarse_op=0):
+        s = G.Solver(prob.dims, prob.periodic, precision=precision, coarsen=coarsen, coarse_mode=coarse_mode,
+                     coarse_op=coarse_op, max_cycles=400)
         s.set_coeffs(f32(prob.bx), f32(prob.by), f32(prob.bz))
         fp64 = s.fp64
         b = torch.from_numpy(np.asarray(prob.b, dtype=np.float32).astype(np.float64 if fp64 else np.float32)).to(dev)
@@ -817,7 +818,8 @@ def suite(args):
         ms, info = timed(run, reps, warm)
         s.close()
         cells = prob.cells
-        return {"precision": precision, "coarsest": "dense" if coarse_mode else "sweeps", "ms": ms,
+        return {"precision": precision, "coarsest": "dense" if coarse_mode else "sweeps",
+                "coarse_operator": "galerkin" if coarse_op else "finite volume", "ms": ms,
                 "v_cycles": info.cycles, "refinement_steps": info.outer,
                 "rel_res": info.rel_res, "status": info.status,
                 "gcell_updates_per_s": cells * info.cycles / (ms * 1e-3) / 1e9}
@@ -825,12 +827,14 @@ def suite(args):
     lines = []
     prob = I.taylor_green_problem(32, seed=0)
     lines.append({"workload": "taylor_green_32^3_iso", "tol": 1e-6,
-                  "forms": [single(prob, "fp32", 1e-6, "iso", 10, 3), single(prob, "fp32", 1e-6, "iso", 10, 3, 1)]})
+                  "forms": [single(prob, "fp32", 1e-6, "iso", 10, 3), single(prob, "fp32", 1e-6, "iso", 10, 3, 1),
+                            single(prob, "fp32", 1e-6, "iso", 10, 3, 0, 1)]})
     prob = I.sphere_channel_problem(*DIMS, seed=1)
     lines.append({"workload": "sphere_channel_256x96x96_aniso", "tol": 1e-6,
                   "forms": [single(prob, "ir64_fp32", 1e-6, "aniso", 10, 3),
                             single(prob, "ir64", 1e-6, "aniso", 10, 3),
-                            single(prob, "ir64_fp32", 1e-6, "aniso", 10, 3, 1)]})
+                            single(prob, "ir64_fp32", 1e-6, "aniso", 10, 3, 1),
+                            single(prob, "ir64_fp32", 1e-6, "aniso", 3, 1, 0, 1)]})
     lines.append({"workload": "sphere_channel_256x96x96_iso", "tol": 1e-6,
                   "forms": [single(prob, "ir64_fp32", 1e-6, "iso", 10, 3),
                             single(prob, "ir64_fp32", 1e-6, "iso", 10, 3, 1)]})

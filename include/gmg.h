@@ -62,6 +62,18 @@ enum { GMG_COARSEN_ISO = 0, GMG_COARSEN_ANISO = 1 };
 enum { GMG_COARSE_SWEEPS = 0, GMG_COARSE_DENSE = 1 };
 
 /*
+ * Coarse operator (the paper does not state one).  GMG_COARSE_OP_FV (default):
+ * finite-volume rediscretisation, each coarse face coefficient 1/c_d times the
+ * sum of the fine faces it covers (c_d = 2 on a coarsened axis, else 1).
+ * GMG_COARSE_OP_GALERKIN, for study: the Galerkin operator R A P with
+ * piecewise-constant prolongation P and R = P^T, the same sums without the
+ * 1/c_d.  On a cell-centred grid that operator over-weights the coarse
+ * correction, so the V-cycles converge several times more slowly (the
+ * solution is the same).
+ */
+enum { GMG_COARSE_OP_FV = 0, GMG_COARSE_OP_GALERKIN = 1 };
+
+/*
  * Precision modes.  The FP32 V-cycle levels sum squared residuals in FP32 over
  * a few cells per thread before the FP64 tile partials, so their norms keep
  * full relative precision while per-cell residuals lie between about 1e-19 and
@@ -93,6 +105,7 @@ typedef struct {
     double ir_inner_rtol; /* IR modes: inner V-cycles stop at this residual reduction (default 1e-4) */
     int autotune;       /* time launch shapes at gmg_set_coeffs and keep the fastest (default 1) */
     int coarse_mode;    /* coarsest level: GMG_COARSE_SWEEPS (default) or GMG_COARSE_DENSE */
+    int coarse_op;      /* coarse operator: GMG_COARSE_OP_FV (default) or GMG_COARSE_OP_GALERKIN */
 } gmg_options;
 
 typedef struct {
@@ -238,7 +251,8 @@ const char* gmg_last_error(gmg_handle h);
  *   "z kind nx ny nz px py pz zchunk"   (kind 0 sweep, 1 sweep with correction,
  *                                        2 residual; kind 3 keeps the coarse-grid
  *                                        correction's form, 1 separate, 2 fused)
- *   "b nx ny nz px py pz coarsen n_min precision nu_c coarse_mode level ranks"
+ *   "b nx ny nz px py pz coarsen n_min precision nu_c coarse level ranks"
+ *                                       (coarse = coarse_mode + 2 coarse_op)
  *                                       (first level of the bottom kernel; ranks 1:
  *                                        one CTA, > 1: a cluster of that many CTAs
  *                                        splits its larger levels; a line without
@@ -350,8 +364,8 @@ int gmg_op_prolong_add(int nx, int ny, int nz, const int* factors, const float* 
 
 /*
  * Coarse face coefficients of the grid coarsened by factors (Sec. 3.2): the
- * coarse d-face is the sum of the fine d-faces it covers divided by f_d; wall
- * faces of Neumann axes are 0.
+ * coarse d-face is the sum of the fine d-faces it covers divided by f_d (the
+ * finite-volume operator, GMG_COARSE_OP_FV); wall faces of Neumann axes are 0.
  */
 int gmg_op_coarsen_coeffs(int nx, int ny, int nz, const int* periodic, const int* factors,
                           const float* bx, const float* by, const float* bz, float* cbx,

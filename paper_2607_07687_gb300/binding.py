@@ -24,6 +24,7 @@ STATUS_NAMES = {OK: "ok", ERR_ARG: "bad argument", ERR_CUDA: "cuda error",
                 NOT_CONVERGED: "not converged", DIVERGED: "diverged", NONFINITE: "non-finite source"}
 ISO, ANISO = 0, 1
 COARSE_SWEEPS, COARSE_DENSE = 0, 1
+COARSE_OP_FV, COARSE_OP_GALERKIN = 0, 1
 FP32, FP32_BF16, IR64, IR64_FP32 = 0, 1, 2, 3
 PRECISIONS = {"fp32": FP32, "fp32_bf16": FP32_BF16, "ir64": IR64, "ir64_fp32": IR64_FP32}
 
@@ -35,7 +36,7 @@ class Options(ctypes.Structure):
                 ("omega_min", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("grow", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("cycles_per_sync", ctypes.c_int), ("ir_inner_rtol", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("coarse_mode", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("coarse_mode", ctypes.c_int), ("coarse_op", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

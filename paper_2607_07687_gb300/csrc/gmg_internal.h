@@ -401,8 +401,10 @@ cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const
 cudaError_t build_dense_pinv(const Geo& g, const float* bx, const float* by, const float* bz, float* pinv,
                              cudaStream_t s);
 
+// coarse face coefficients of the next level: finite volume (galerkin 0) or the
+// Galerkin operator's (galerkin 1)
 cudaError_t launch_coarsen_coeffs(Geo fine, const int cf[3], const float* bx, const float* by,
-                                  const float* bz, float* cbx, float* cby, float* cbz,
+                                  const float* bz, float* cbx, float* cby, float* cbz, int galerkin,
                                   cudaStream_t s);
 cudaError_t launch_prolong_add(Geo fine, const int cf[3], const float* e, float* p, cudaStream_t s);
 cudaError_t launch_prolong_rows(const ProlongTask& t, cudaStream_t s);

@@ -1405,9 +1405,11 @@ __global__ void __launch_bounds__(kThreads) k_project_level(const LevelProjTask*
 
 // ---------------------------------------------------------------- K7 and transfers
 
+// C4: coarse face = (1/c_d) sum of the fine faces it covers (finite volume), or
+// the sum itself (galerkin: the faces of R A P, piecewise-constant P)
 __global__ void k_coarsen(Geo f, int c0, int c1, int c2, const float* __restrict__ bx,
                           const float* __restrict__ by, const float* __restrict__ bz, float* cbx,
-                          float* cby, float* cbz)
+                          float* cby, float* cbz, int galerkin)
 {
     Geo cg = f;
     cg.n[0] = f.n[0] / c0; cg.n[1] = f.n[1] / c1; cg.n[2] = f.n[2] / c2;
@@ -1431,7 +1433,7 @@ __global__ void k_coarsen(Geo f, int c0, int c1, int c2, const float* __restrict
             for (int z = lo[2]; z < hi[2]; ++z)
                 for (int y = lo[1]; y < hi[1]; ++y)
                     for (int x = lo[0]; x < hi[0]; ++x) s += face_lo(fa[d], f, d, x, y, z);
-            ca[d][J] = s / (float)cfac[d];
+            ca[d][J] = galerkin ? s : s / (float)cfac[d];
         }
     }
 }
@@ -2054,10 +2056,11 @@ cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const
 }
 
 cudaError_t launch_coarsen_coeffs(Geo fine, const int cf[3], const float* bx, const float* by,
-                                  const float* bz, float* cbx, float* cby, float* cbz, cudaStream_t s)
+                                  const float* bz, float* cbx, float* cby, float* cbz, int galerkin,
+                                  cudaStream_t s)
 {
     const int64_t N = (int64_t)(fine.n[0] / cf[0]) * (fine.n[1] / cf[1]) * (fine.n[2] / cf[2]);
-    k_coarsen<<<grid_for(N), kThreads, 0, s>>>(fine, cf[0], cf[1], cf[2], bx, by, bz, cbx, cby, cbz);
+    k_coarsen<<<grid_for(N), kThreads, 0, s>>>(fine, cf[0], cf[1], cf[2], bx, by, bz, cbx, cby, cbz, galerkin);
     return cudaGetLastError();
 }
 

@@ -1135,7 +1135,7 @@ struct Engine {
             for (int l = 0; l + 1 < M.L && e == cudaSuccess; ++l)
                 e = launch_coarsen_coeffs(M.lev[l].g, M.lev[l].cf, M.lev[l].beta[0], M.lev[l].beta[1],
                                           M.lev[l].beta[2], M.lev[l + 1].beta[0], M.lev[l + 1].beta[1],
-                                          M.lev[l + 1].beta[2], stream);
+                                          M.lev[l + 1].beta[2], opt.coarse_op == GMG_COARSE_OP_GALERKIN, stream);
             if (e == cudaSuccess) {
                 step = "active mask";
                 e = launch_active_mask(M.g0, M.lev[0].beta[0], M.lev[0].beta[1], M.lev[0].beta[2], M.mask, stream);
@@ -1340,7 +1340,7 @@ struct Engine {
         if (rc != GMG_OK) return rc;
         const std::vector<int> lb_key = {P[0].g0.n[0], P[0].g0.n[1], P[0].g0.n[2], P[0].g0.per[0], P[0].g0.per[1],
                                          P[0].g0.per[2], opt.coarsen, opt.n_min, opt.precision, opt.nu_c,
-                                         opt.coarse_mode};
+                                         opt.coarse_mode + 2 * opt.coarse_op};
         BottomChoice cached{0, 1};
         {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -2149,6 +2149,8 @@ int validate_options(const gmg_options& o, std::string& msg)
     else if (!(o.ir_inner_rtol > 0.0 && o.ir_inner_rtol < 1.0)) msg = "need 0 < ir_inner_rtol < 1";
     else if (o.coarse_mode != GMG_COARSE_SWEEPS && o.coarse_mode != GMG_COARSE_DENSE)
         msg = "coarse_mode must be SWEEPS or DENSE";
+    else if (o.coarse_op != GMG_COARSE_OP_FV && o.coarse_op != GMG_COARSE_OP_GALERKIN)
+        msg = "coarse_op must be FV or GALERKIN";
     else return GMG_OK;
     return GMG_ERR_ARG;
 }
@@ -2187,6 +2189,7 @@ void gmg_default_options(gmg_options* o)
     o->ir_inner_rtol = 1e-4;
     o->autotune = 1;
     o->coarse_mode = GMG_COARSE_SWEEPS;
+    o->coarse_op = GMG_COARSE_OP_FV;
 }
 
 int gmg_create(gmg_handle* h, int nx, int ny, int nz, const int* periodic, const gmg_options* opt,
@@ -2714,7 +2717,7 @@ int gmg_op_coarsen_coeffs(int nx, int ny, int nz, const int* periodic, const int
     if (!bx || !by || !bz || !cbx || !cby || !cbz || check_factors(nx, ny, nz, factors) != GMG_OK)
         return GMG_ERR_ARG;
     Geo g = make_geo(nx, ny, nz, periodic);
-    return launch_coarsen_coeffs(g, factors, bx, by, bz, cbx, cby, cbz, static_cast<cudaStream_t>(stream)) ==
+    return launch_coarsen_coeffs(g, factors, bx, by, bz, cbx, cby, cbz, 0, static_cast<cudaStream_t>(stream)) ==
                    cudaSuccess
                ? GMG_OK
                : GMG_ERR_CUDA;

@@ -50,6 +50,7 @@ def _create(L, dims, periodic=(0, 0, 0), **kw):
     ((8, 8, 8), (0, 0, 0), {"n_min": 0}, "n_min"),
     ((8, 8, 8), (0, 0, 0), {"ir_inner_rtol": 0.0}, "ir_inner_rtol"),
     ((8, 8, 8), (0, 0, 0), {"coarse_mode": 2}, "coarse_mode"),
+    ((8, 8, 8), (0, 0, 0), {"coarse_op": 2}, "coarse_op"),
     ((6, 6, 6), (0, 0, 0), {"coarse_mode": 1}, "two levels"),           # does not coarsen
     ((48, 48, 48), (0, 0, 0), {"coarse_mode": 1, "n_min": 16, "coarsen": "iso"}, "1024"),   # coarsest 24^3
 ])

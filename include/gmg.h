@@ -441,6 +441,14 @@ int gmg_test_poison_omega(gmg_handle h, int cycle);
  */
 int gmg_test_ring_wait_tries(int tries);
 
+/*
+ * Largest thread-block cluster the cluster form of the bottom may use in
+ * handles planned after this call: 16 or 8 (the form's fallback where a device
+ * cannot co-schedule 16 CTAs), 0 restores the default (the largest the device
+ * co-schedules).  Process-wide.  GMG_ERR_ARG for any other value.
+ */
+int gmg_test_cluster_ranks(int ranks);
+
 #ifdef __cplusplus
 }
 #endif

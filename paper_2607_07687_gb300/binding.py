@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
     L.gmg_op_residual_norm_noalloc.argtypes = [c_int, c_int, c_int, ip, vp, vp, vp, vp, vp, dp, vp]
     L.gmg_test_poison_omega.argtypes = [vp, c_int]
     L.gmg_test_ring_wait_tries.argtypes = [c_int]
+    L.gmg_test_cluster_ranks.argtypes = [c_int]
     L.gmg_tune_export.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.gmg_tune_import.argtypes = [ctypes.c_char_p]
     _net_signatures(L)
@@ -169,6 +170,12 @@ def test_ring_wait_tries(tries: int) -> None:
     """Test hook (gmg_test_ring_wait_tries): poll limit of the pipelined kernels' ring
     waits on the current device; a negative value restores the default."""
     _check(lib().gmg_test_ring_wait_tries(int(tries)), None)
+
+
+def test_cluster_ranks(ranks: int) -> None:
+    """Test hook (gmg_test_cluster_ranks): largest cluster size of the cluster-form
+    bottom in handles planned afterwards (16 or 8; 0 restores the default)."""
+    _check(lib().gmg_test_cluster_ranks(int(ranks)), None)
 
 
 def options(coarsen: str = "aniso", precision: str = "fp32", **kw) -> Options:

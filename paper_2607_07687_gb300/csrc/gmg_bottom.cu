@@ -18,6 +18,7 @@
 // phases are separated by block barriers; within a colour the cells are
 // independent, so in-place updates are exact Gauss-Seidel.
 #include <cooperative_groups.h>
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -716,7 +717,21 @@ template cudaError_t launch_bottom_cluster<bf16>(const BottomTask<bf16>*, int, i
 // Per device, once: opt both instantiations in to 16-CTA clusters and the full
 // shared-memory budget, then ask the occupancy calculator whether one cluster of
 // 16 (else 8) such CTAs can be resident.
+static std::atomic<int> g_cluster_cap{kClusterMaxRanks};   // test hook: largest cluster size used
+
+void set_cluster_cap(int ranks) { g_cluster_cap.store(ranks); }
+
+static int device_cluster_ranks();
+
 int bottom_cluster_ranks()
+{
+    const int dev = device_cluster_ranks();
+    const int cap = g_cluster_cap.load();
+    if (dev >= 16 && cap >= 16) return 16;
+    return dev >= 8 && cap >= 8 ? 8 : 0;   // a device that co-schedules 16 CTAs co-schedules 8
+}
+
+static int device_cluster_ranks()
 {
     static std::mutex m;
     static std::map<int, int> known;

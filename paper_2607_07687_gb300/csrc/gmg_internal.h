@@ -390,6 +390,8 @@ cudaError_t launch_bottom_cluster(const BottomTask<TP>* tasks, int ntasks, int r
 // CTAs per cluster that the current device can co-schedule for the cluster form
 // with its full shared-memory budget (16 or 8), or 0 when it cannot
 int bottom_cluster_ranks();
+// test hook: the largest cluster size bottom_cluster_ranks may return (16 or 8)
+void set_cluster_cap(int ranks);
 
 // Reference variant of the sweep: one in-place launch per colour.
 cudaError_t launch_sweep_two_pass(Geo g, const float* bx, const float* by, const float* bz,

@@ -2352,6 +2352,13 @@ int gmg_test_ring_wait_tries(int tries)
     return GMG_OK;
 }
 
+int gmg_test_cluster_ranks(int ranks)
+{
+    if (ranks != 0 && ranks != 8 && ranks != 16) return GMG_ERR_ARG;
+    gmg::set_cluster_cap(ranks == 0 ? gmg::kClusterMaxRanks : ranks);
+    return GMG_OK;
+}
+
 // ---------------------------------------------------------------- tuning table
 
 int gmg_tune_export(char* buf, size_t cap, size_t* len)

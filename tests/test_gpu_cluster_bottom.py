@@ -132,6 +132,50 @@ def test_dense_coarsest_same_bits():
     _same_bits(problem(("sphere",)), 1e-5, 3, coarse_mode=1)
 
 
+@pytest.fixture
+def eight_ranks():
+    """Clusters of 8 CTAs (the form's fallback where 16 cannot be co-scheduled)."""
+    from paper_2607_07687_gb300 import binding as G
+    G.test_cluster_ranks(8)
+    yield
+    G.test_cluster_ranks(0)
+
+
+def test_eight_rank_clusters_same_bits(eight_ranks):
+    """The 8-CTA layout gives the one-CTA form's bits: the sphere channel from
+    32x12x12 (144 rows, 18 a CTA) and the ragged 80x6x22 case from level 1
+    (66 rows: 9 a CTA, a short last CTA)."""
+    pc, ic, hc, fc = _solve(problem(("sphere",)), 1e-5, 3, RANKS)
+    p1, i1, h1, f1 = _solve(problem(("sphere",)), 1e-5, 3, 1)
+    assert fc == (3, 8) and f1 == (3, 1), (fc, f1)
+    assert ic.cycles == i1.cycles and ic.status == i1.status == 0
+    np.testing.assert_array_equal(pc, p1)
+    prob = I.random_small_problem((80, 6, 22), (False, False, False), seed=11)
+    pc, ic, hc, fc = _solve(prob, 1e-12, 1, RANKS, max_cycles=8)
+    p1, i1, h1, f1 = _solve(prob, 1e-12, 1, 1, max_cycles=8)
+    assert fc == (1, 8) and f1 == (1, 1), (fc, f1)
+    np.testing.assert_array_equal(hc, h1)
+    np.testing.assert_array_equal(pc, p1)
+
+
+def test_eight_rank_cluster_vs_oracle(O, eight_ranks):
+    """8-CTA clusters holding 32^3 and 16^3 distributed (the Taylor-Green cube
+    from level 1, beyond one CTA): FP32 solve to 1e-6 against the oracle.  (The
+    sphere channel from 64x24x24 needs more shared memory than 8 CTAs hold, so
+    with 8 CTAs its bottom stays at the one-CTA start.)"""
+    prob = I.taylor_green_problem(64, 0)
+    ref = O.solve_problem(prob, tol=1e-6, coarsen="iso")
+    got, info, _, form = _solve(prob, 1e-6, 1, RANKS, coarsen="iso")
+    assert form == (1, 8), form
+    assert info.status == 0 and info.rel_res <= 1e-6, info.as_dict()
+    assert abs(info.cycles - ref.cycles) <= 1, (info.cycles, ref.cycles)
+    same = ref if info.cycles == ref.cycles else O.solve_problem(prob, tol=1e-300, max_cycles=info.cycles,
+                                                                  coarsen="iso")
+    assert rel_l2(got, same.p) <= 1e-5
+    _, _, _, form16 = _solve(problem(("sphere",)), 1e-5, 2, RANKS)
+    assert form16 == (3, 1), form16           # no 8-CTA layout of 64x24x24 fits: the one-CTA start
+
+
 def test_sphere_channel_cluster_from_level_2_vs_oracle(O):
     """From 64x24x24 (36,864 cells, beyond one CTA's 10,240): FP64 refinement to 1e-6
     against the oracle."""

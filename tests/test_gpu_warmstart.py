@@ -107,6 +107,31 @@ def test_conv3_forward(ci, co):
         assert np.all(err <= U_BF16 * np.abs(ref) + 1e-5 * np.abs(ref).max()), (relu, err.max())
 
 
+@pytest.mark.parametrize("co", [16, 32, 64])
+@pytest.mark.parametrize("shape", [(9, 6, 40), (13, 5, 150)])
+def test_conv3_forward_z_marching(co, shape):
+    """Layers with 16 input channels march a column of planes per block (a ring of
+    input planes, double-buffered accumulators): grids of 9 and 13 planes split
+    into several z-chunks with a ragged last one, rows of 40 and of 150 cells (a
+    full tile and a tail), every output against the FP64 oracle."""
+    torch = _torch()
+    ci = 16
+    rng = np.random.default_rng(co * 10 + shape[0])
+    x = bf(rng.standard_normal((ci,) + shape))
+    w = rand_w(rng, co, ci)
+    b = rng.standard_normal(co).astype(np.float32).astype(np.float64)
+    _, wb, _ = pack_weights(w)
+    bias = torch.from_numpy(b.astype(np.float32)).to("cuda:0")
+    xt = to_cl(x)
+    y = torch.zeros((xt.shape[0], co), dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_conv3", shape[0], shape[1], shape[2], ptr(xt), ci, ci, ptr(wb), ptr(bias), co, 1, ptr(y),
+         co, 0, stream())
+    ref = O.relu(O.conv3(x, w, b))
+    got = from_cl(y, shape)
+    err = np.abs(got - ref)
+    assert np.all(err <= U_BF16 * np.abs(ref) + 1e-5 * np.abs(ref).max()), err.max()
+
+
 @pytest.mark.parametrize("shape", [(2, 5, 192), (2, 5, 300)])
 @pytest.mark.parametrize("ci,co", [(16, 16), (32, 64), (96, 32), (48, 96)])
 def test_conv3_forward_long_rows(ci, co, shape):

@@ -96,13 +96,6 @@ __device__ __forceinline__ float flux_xyz(const LevelView& L, int i, int x, int 
                      zl < 0 ? p0 : L.p[zl], fzu, zu < 0 ? p0 : L.p[zu], p0);
 }
 
-__device__ __forceinline__ float flux_at(const LevelView& L, int i, float& dg)
-{
-    int x, y, z;
-    decode(L, i, x, y, z);
-    return flux_xyz(L, i, x, y, z, dg);
-}
-
 // diagonal (sum of the six face coefficients) of cell i
 __device__ __forceinline__ float diag_at(const LevelView& L, int i)
 {

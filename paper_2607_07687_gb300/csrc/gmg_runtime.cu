@@ -422,8 +422,6 @@ struct Engine {
         return d;
     }
 
-    void* level_buf(int p, int l, int role) const { return P[p].lev[l].buf[role]; }
-
     // ---------------------------------------------------------------- planning
 
     int plan(int nprob, const int* dims, const int* periodic, const gmg_options& o, cudaStream_t s)

@@ -1120,6 +1120,10 @@ def main():
                                 "kind": "oracle",
                                 "sample": f"one full FP64 oracle solve of the workload to {TOL} "
                                           f"({res.cycles} V-cycles, {dt:.1f} s)"}
+    lb, ranks_b = solver.bottom_form()
+    line["config"]["bottom"] = {"level": lb, "ctas": ranks_b,
+                                "form": "thread-block cluster" if ranks_b > 1 else "one CTA"}
+    line["config"]["launches_per_solve"] = int(infos[-1].launches)
     solver.close()
     if args.tune_file and not tune_loaded and rank == 0:
         with open(args.tune_file, "w") as f:

@@ -1359,19 +1359,27 @@ struct Engine {
             reset_cycle();
             if ((rc = build_cycle()) != GMG_OK) return rc;
         } else if (cand.size() > 1) {
+            std::vector<float> ms(cand.size());
             float best = 1e30f;
-            BottomChoice best_c = cand[0];
-            for (const BottomChoice& c : cand) {
-                forced_lb_ = c.level;
-                forced_ranks_ = c.ranks;
+            for (size_t i = 0; i < cand.size(); ++i) {
+                forced_lb_ = cand[i].level;
+                forced_ranks_ = cand[i].ranks;
                 reset_cycle();
                 if ((rc = build_cycle()) != GMG_OK) return rc;
                 if (upload_timing_ctl() != cudaSuccess) return fail(GMG_ERR_CUDA, "autotune: control upload failed");
-                const float ms = time_ms([&] { return run_cycle(); }, 5);
-                if (ms < best) {
-                    best = ms;
+                ms[i] = time_ms([&] { return run_cycle(); }, 5);
+                best = std::min(best, ms[i]);
+            }
+            // within 2 % of the fastest (the spread of these short timings) take the
+            // bottom that starts highest, cluster before one CTA: the fewest launches
+            // per cycle, so the choice does not flip with timing noise
+            BottomChoice best_c{0, 1};
+            for (size_t i = 0; i < cand.size(); ++i) {
+                if (ms[i] > 1.02f * best) continue;
+                const BottomChoice& c = cand[i];
+                if (best_c.level == 0 || c.level < best_c.level ||
+                    (c.level == best_c.level && c.ranks > best_c.ranks))
                     best_c = c;
-                }
             }
             forced_lb_ = best_c.level;
             forced_ranks_ = best_c.ranks;

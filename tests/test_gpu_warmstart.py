@@ -132,6 +132,33 @@ def test_conv3_forward_z_marching(co, shape):
     assert np.all(err <= U_BF16 * np.abs(ref) + 1e-5 * np.abs(ref).max()), err.max()
 
 
+@pytest.mark.parametrize("ci,co", [(16, 16), (48, 16)])
+def test_conv3_full_size_sampled(ci, co):
+    """The network's level-0 layers at their full size (192 x 64 x 64: the 16 -> 16
+    layer in the z-marching form with its ragged last z-chunk, the decoder's
+    48 -> 16 in the one-plane form): 4096 sampled outputs against the
+    convolution's definition evaluated in FP64 at those cells (zero padding)."""
+    torch = _torch()
+    rng = np.random.default_rng(ci * 7 + co)
+    shape = (64, 64, 192)
+    x = bf(rng.standard_normal((ci,) + shape))
+    w = rand_w(rng, co, ci)
+    b = rng.standard_normal(co).astype(np.float32).astype(np.float64)
+    _, wb, _ = pack_weights(w)
+    bias = torch.from_numpy(b.astype(np.float32)).to("cuda:0")
+    xt = to_cl(x)
+    y = torch.zeros((xt.shape[0], co), dtype=torch.bfloat16, device="cuda:0")
+    call("gmg_net_conv3", shape[0], shape[1], shape[2], ptr(xt), ci, ci, ptr(wb), ptr(bias), co, 0, ptr(y),
+         co, 0, stream())
+    got = y.float().cpu().numpy().astype(np.float64).reshape(shape + (co,))
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (1, 1)))
+    zs, ys, xs = (rng.integers(0, n, 4096) for n in shape)
+    ref = np.stack([np.einsum("ocijk,cijk->o", w, xp[:, z:z + 3, yy:yy + 3, xx:xx + 3]) + b
+                    for z, yy, xx in zip(zs, ys, xs)])
+    err = np.abs(got[zs, ys, xs] - ref)
+    assert np.all(err <= U_BF16 * np.abs(ref) + 1e-5 * np.abs(ref).max()), err.max()
+
+
 @pytest.mark.parametrize("shape", [(2, 5, 192), (2, 5, 300)])
 @pytest.mark.parametrize("ci,co", [(16, 16), (32, 64), (96, 32), (48, 96)])
 def test_conv3_forward_long_rows(ci, co, shape):

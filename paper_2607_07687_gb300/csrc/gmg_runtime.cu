@@ -17,6 +17,8 @@
 #include "gmg_internal.h"
 #include "../../include/gmg.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -152,6 +154,15 @@ int plan_levels(const Geo& g0, int aniso, int n_min, Geo* geo, int (*cf)[3])
 }
 
 int64_t cells(const Geo& g) { return (int64_t)g.n[0] * g.n[1] * g.n[2]; }
+
+// NVTX range over a host-side phase (set-up, autotuning, a solve, a refinement
+// step), for profilers that filter or group launches by range
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
@@ -1112,6 +1123,7 @@ struct Engine {
 
     int set_coeffs(const float* const* bx, const float* const* by, const float* const* bz)
     {
+        NvtxRange range("gmg_set_coeffs");
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "gmg_set_coeffs: pending error from an earlier call");
         int* bad = dalloc<int>(1);
@@ -1218,6 +1230,7 @@ struct Engine {
 
     int tune()
     {
+        NvtxRange range("gmg autotune");
         // timed launches run on zeros: right-hand sides and iterates of every level
         for (auto& M : P)
             for (int l = 0; l < M.L; ++l) {
@@ -1631,6 +1644,7 @@ struct Engine {
 
     int solve32(const float* const* sigma, float* const* p, double tol, gmg_info* infos)
     {
+        NvtxRange range("gmg_solve (FP32 V-cycles)");
         if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_solve");
         launches = 0;
         cudaError_t e = upload_ctl(tol);
@@ -1731,6 +1745,7 @@ struct Engine {
     // stop test fires, the exit gauge into p.
     int pcg_solve(const float* sigma, float* p, double tol, int max_iter, gmg_info* info)
     {
+        NvtxRange range("gmg_pcg_solve");
         if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_pcg_solve");
         if (P.size() != 1) return fail(GMG_ERR_ARG, "gmg_pcg_solve: single-problem handles only");
         if (opt.precision == GMG_IR64 || opt.precision == GMG_IR64_FP32)
@@ -1880,6 +1895,7 @@ struct Engine {
 
     int gmg_pcg_solve(const float* sigma, float* p, double tol, gmg_info* info)
     {
+        NvtxRange range("gmg_gmgpcg_solve");
         if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_gmgpcg_solve");
         if (P.size() != 1) return fail(GMG_ERR_ARG, "gmg_gmgpcg_solve: single-problem handles only");
         if (opt.precision != GMG_FP32) return fail(GMG_ERR_ARG, "gmg_gmgpcg_solve: GMG_FP32 handles only");
@@ -1979,6 +1995,7 @@ struct Engine {
     // meets tol (or its inner solve diverged).
     int solve64(const double* const* sigma, double* const* p, double tol, gmg_info* infos)
     {
+        NvtxRange range("gmg_solve (FP64 refinement)");
         if (!coeffs_set) return fail(GMG_ERR_ARG, "gmg_set_coeffs must precede gmg_solve");
         const size_t N = P.size();
         launches = 0;
@@ -2057,6 +2074,7 @@ struct Engine {
                 }
             }
             if (!any) break;
+            NvtxRange step("gmg refinement step (inner V-cycles)");
             e = iterate();
             for (size_t q = 0; q < N && e == cudaSuccess; ++q)
                 if (!finished[q]) {

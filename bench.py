@@ -116,9 +116,17 @@ def tuned_zchunk(kind, dims, periodic):
     return None
 
 
-def recorded_traffic(key):
-    """DRAM bytes per launch of a kernel at one launch shape from the committed ncu
-    summary (profiles/traffic.json), valid only while the kernel source is unchanged."""
+def march_ctas(dims, zc):
+    """CTAs of a z-marching sweep or residual launch: one per 32 x 8 column tile and z-chunk."""
+    nx, ny, nz = dims
+    zc = min(zc, nz) if zc else nz
+    return -(-nx // 32) * -(-ny // 8) * -(-nz // zc)
+
+
+def recorded_traffic(key, ctas):
+    """DRAM bytes per launch of a kernel at one launch shape (z-chunk and grid of
+    `ctas` blocks) from the committed ncu summary (profiles/traffic.json), valid
+    only while the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_2607_07687_gb300", "csrc", "gmg_kernels.cu")
     try:
@@ -126,7 +134,7 @@ def recorded_traffic(key):
             rec = json.load(f)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         k = rec.get(key, {})
-        if k.get("source_sha256") == h:
+        if k.get("source_sha256") == h and k.get("grid_ctas") == f"({ctas}, 1, 1)":
             return float(k["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -290,7 +298,7 @@ def record_512(dev, stream, flush, peak, peak_kind):
         out[key] = {"kernel": kname, "bound": "hbm", "ms": ms, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                     "bytes_per_cell": bpc, "zchunk": zc,
-                    "traffic": recorded_traffic(f"{kname}_512x512x512_z{zc}"),
+                    "traffic": recorded_traffic(f"{kname}_512x512x512_z{zc}", march_ctas((n, n, n), zc)),
                     "tuning": [ln for ln in G.tune_export().splitlines() if " 512 512 512 " in ln]}
     solver.close()
     del rb, rhs, pa, pb, coarse
@@ -1095,7 +1103,8 @@ def main():
     zc = tuned_zchunk(0, prob.dims, prob.periodic)
     nx, ny, nz = prob.dims
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(f"k_sweep_ws_{nx}x{ny}x{nz}_z{zc}"),
+                "frac": achieved / peak, "traffic": recorded_traffic(f"k_sweep_ws_{nx}x{ny}x{nz}_z{zc}",
+                                                                       march_ctas(prob.dims, zc)),
                 "kernel": "k_sweep_ws (fine level)", "zchunk": zc,
                 "peak_source": f"{peak_kind} hbm_gbs", "l2_flushed": True,
                 "l2_resident_achieved": alg_bytes / (warm_ms * 1e-3) / 1e9,

@@ -401,11 +401,10 @@ int gmg_op_residual_norm(int nx, int ny, int nz, const int* periodic, const floa
  * GMG_ERR_CUDA if a CUDA call fails.
  *
  * The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  All calls on a device share the one array
- * and each overwrites what the previous call left there: calls that overlap
- * on the GPU (concurrent streams, or several host threads) race and must be
- * serialised by the caller.  The call synchronises `stream` and copies the
+ * device (cudaGetSymbolAddress, with that device current).  All calls on a
+ * device share the one array and each overwrites what the previous call left
+ * there: calls that overlap on the GPU (concurrent streams, or several host
+ * threads) race and must be serialised by the caller.  The call synchronises `stream` and copies the
  * total to *rr (host memory) before it returns.
  */
 int gmg_op_residual_norm_noalloc(int nx, int ny, int nz, const int* periodic, const float* bx,

@@ -115,6 +115,27 @@ int persistent_grid(int64_t tiles)
     return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * kResident));
 }
 
+// Grids of the z-marching kernels (k_sweep_ws, k_residual_ws) of one problem:
+// one block per tile.  The hardware starts the blocks in tile order as earlier
+// ones finish, so tiles that share halo rows (neighbours in x and y sit close in
+// that order) stream the same planes at about the same time and their halos come
+// from L2; blocks of a persistent grid, each walking a fixed stride of tiles,
+// drift apart over many tiles and read the halos from DRAM again (512^3
+// triple-periodic sweep: DRAM reads 1.08 instead of 1.63 times the inputs).
+// Levels of at most one tile per resident block launch the same grid either way.
+// Batched launches keep the persistent grid: their problems' short columns would
+// each pay a pipeline start in a block of its own (64-problem batch 12 % slower).
+template <class TC>
+int sweep_grid(const TaskList<SweepTask<float, TC>>& tl)
+{
+    return tl.vec >= 4 && tl.ntasks <= 1 ? std::max(1, tl.total) : persistent_grid(tl.total);
+}
+
+int residual_grid(const TaskList<ResTask<float>>& tl)
+{
+    return tl.march && tl.ntasks <= 1 ? std::max(1, tl.total) : persistent_grid(tl.total);
+}
+
 }  // namespace gmg
 
 namespace {
@@ -720,7 +741,7 @@ struct Engine {
                 op.kind = kResF;
                 if ((rc = make_list(v, tiles, op.r_f))) return rc;
                 op.r_f.march = m;
-                op.grid = persistent_grid(op.r_f.total);
+                op.grid = residual_grid(op.r_f);
             }
             ops.push_back(op);
         }
@@ -762,7 +783,7 @@ struct Engine {
             op.s_fb.vec = 4;
             for (const auto& t : v) op.s_fb.vec = std::min(op.s_fb.vec, sweep_vec(t));
             op.s_fb.corr = with_corr ? 1 : 0;
-            op.grid = persistent_grid(op.s_fb.total);
+            op.grid = sweep_grid(op.s_fb);
         } else {
             std::vector<SweepTask<float, float>> v;
             for (int p : probs) v.push_back(sweep_task<float, float>(p, l, in, out, with_corr));
@@ -771,7 +792,7 @@ struct Engine {
             op.s_ff.vec = 4;
             for (const auto& t : v) op.s_ff.vec = std::min(op.s_ff.vec, sweep_vec(t));
             op.s_ff.corr = with_corr ? 1 : 0;
-            op.grid = persistent_grid(op.s_ff.total);
+            op.grid = sweep_grid(op.s_ff);
         }
         cycle.push_back(op);
         return GMG_OK;
@@ -1277,7 +1298,7 @@ struct Engine {
                             tl.total = (int)rt.tiles();
                             tl.single = t;
                             tl.march = 1;
-                            ms = time_ms([&] { return launch_residual(tl, persistent_grid(tl.total), stream); }, 5);
+                            ms = time_ms([&] { return launch_residual(tl, residual_grid(tl), stream); }, 5);
                         } else if (kind == kTuneSweepCorr && bf16_coarse) {
                             SweepTask<float, bf16> t = sweep_task<float, bf16>((int)p, l, in, out, true);
                             t.zchunk = st.zchunk;
@@ -1288,7 +1309,7 @@ struct Engine {
                             tl.single = t;
                             tl.vec = sweep_vec(t);
                             tl.corr = 1;
-                            ms = time_ms([&] { return launch_sweep(tl, persistent_grid(tl.total), stream); }, 5);
+                            ms = time_ms([&] { return launch_sweep(tl, sweep_grid(tl), stream); }, 5);
                         } else {
                             SweepTask<float, float> t =
                                 sweep_task<float, float>((int)p, l, in, out, kind == kTuneSweepCorr);
@@ -1300,7 +1321,7 @@ struct Engine {
                             tl.single = t;
                             tl.vec = sweep_vec(t);
                             tl.corr = kind == kTuneSweepCorr ? 1 : 0;
-                            ms = time_ms([&] { return launch_sweep(tl, persistent_grid(tl.total), stream); }, 5);
+                            ms = time_ms([&] { return launch_sweep(tl, sweep_grid(tl), stream); }, 5);
                         }
                         if (ms < best) {
                             best = ms;
@@ -1329,10 +1350,10 @@ struct Engine {
                     lp.vec = sweep_vec(tp);
                     const ProlongTask pt = prolong_task((int)p, l, in);
                     const float fused =
-                        time_ms([&] { return launch_sweep(lf, persistent_grid(lf.total), stream); }, 5);
+                        time_ms([&] { return launch_sweep(lf, sweep_grid(lf), stream); }, 5);
                     const float split = time_ms([&] {
                         cudaError_t e2 = launch_prolong_rows(pt, stream);
-                        return e2 == cudaSuccess ? launch_sweep(lp, persistent_grid(lp.total), stream) : e2;
+                        return e2 == cudaSuccess ? launch_sweep(lp, sweep_grid(lp), stream) : e2;
                     }, 5);
                     std::lock_guard<std::mutex> lock(g_tune_mutex);
                     g_tuned_zchunk[tune_key(kTuneCorrForm, g)] = split < fused ? kCorrSeparate : kCorrFused;
@@ -2582,7 +2603,7 @@ int gmg_op_sweep(int nx, int ny, int nz, const int* periodic, const float* bx, c
     TmaPlanes* dmap = op_tensor_maps(t.g, p_in, b, bx, by, bz, tl.vec == 4, s);
     t.tma = dmap;
     tl.single = t;
-    cudaError_t e = launch_sweep(tl, persistent_grid(tl.total), s);
+    cudaError_t e = launch_sweep(tl, sweep_grid(tl), s);
     return e == cudaSuccess ? GMG_OK : GMG_ERR_CUDA;
 }
 
@@ -2670,7 +2691,7 @@ static int op_residual(int nx, int ny, int nz, const int* periodic, const int* f
     TmaPlanes* dmap = op_tensor_maps(t.g, p, b, bx, by, bz, march, s);
     t.tma = dmap;
     tl.single = t;
-    cudaError_t e = launch_residual(tl, persistent_grid(tl.total), s);
+    cudaError_t e = launch_residual(tl, residual_grid(tl), s);
     if (e == cudaSuccess && rr) {
         e = launch_sum_partials(t.partials, (int)rt.tiles(), out, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(rr, out, sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -630,7 +630,8 @@ def fig2(args):
 def solve_only(args):
     """--solve-only WORKLOAD: one warm-up and --reps timed solves of one workload
     ("sphere": the 256x96x96 sphere channel to 1e-6, "tg512": the 512^3
-    Taylor-Green cube to 1e-10; FP32 V-cycles inside FP64 refinement), with the
+    Taylor-Green cube to 1e-10, "batch": the 64 uneven problems to 1e-6 in one
+    batched solve; FP32 V-cycles inside FP64 refinement), with the
     autotuner's table from --tune-file when it exists (written after the run
     otherwise), so that a profiler run launches exactly what a plain run timed."""
     import numpy as np
@@ -644,6 +645,8 @@ def solve_only(args):
         G.tune_import(open(args.tune_file).read())
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    if args.solve_only == "batch":
+        return solve_only_batch(args, G, I, dev, loaded)
     if args.solve_only == "tg512":
         prob, coarsen, tol = I.taylor_green_problem(512, seed=2), "iso", 1e-10
     else:
@@ -670,6 +673,41 @@ def solve_only(args):
             f.write(G.tune_export())
     print(json.dumps({"workload": prob.name, "tol": tol, "ms": ts, "v_cycles": info.cycles, "outer": info.outer,
                       "launches": info.launches, "tuning": "loaded" if loaded else "timed"}), flush=True)
+    return 0
+
+
+def solve_only_batch(args, G, I, dev, loaded):
+    """--solve-only batch: the 64 uneven walled problems (14.4 M cells) in one
+    batched solve, FP32 V-cycles inside FP64 refinement, to 1e-6."""
+    import numpy as np
+    import torch
+    probs = I.batch_problems(64, seed=3)
+    tol = 1e-6
+    f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    rhs = [torch.from_numpy(np.asarray(pr.b, dtype=np.float32).astype(np.float64)).to(dev) for pr in probs]
+    bs = G.BatchSolver([pr.dims for pr in probs], precision="ir64_fp32")
+    bs.set_coeffs([f32(pr.bx) for pr in probs], [f32(pr.by) for pr in probs], [f32(pr.bz) for pr in probs])
+    pp = [torch.zeros_like(x) for x in rhs]
+    ts = []
+    for i in range(args.reps + 1):
+        for x in pp:
+            x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = bs.solve(rhs, pp, tol)
+        e1.record()
+        torch.cuda.synchronize()
+        if i:
+            ts.append(e0.elapsed_time(e1))
+    bs.close()
+    if args.tune_file and not loaded:
+        with open(args.tune_file, "w") as f:
+            f.write(G.tune_export())
+    print(json.dumps({"workload": "batch_64_uneven_walls_bodies", "cells": sum(pr.cells for pr in probs),
+                      "tol": tol, "ms": ts, "v_cycles_max": max(i.cycles for i in infos),
+                      "converged": sum(int(i.status) == 0 for i in infos),
+                      "tuning": "loaded" if loaded else "timed"}), flush=True)
     return 0
 
 
@@ -957,7 +995,7 @@ def main():
     ap.add_argument("--fig2", action="store_true",
                     help="iso vs aniso coarsening over aspect ratios 1-8: 2D cylinder, spanwise-periodic "
                          "cylinder, sphere")
-    ap.add_argument("--solve-only", choices=["sphere", "tg512"], default=None,
+    ap.add_argument("--solve-only", choices=["sphere", "tg512", "batch"], default=None,
                     help="only time --reps solves of one workload (for profiler launch lists)")
     ap.add_argument("--impulsive", action="store_true",
                     help="predictor/corrector V-cycles of the first 4 steps of impulsive starts, iso vs aniso, "

@@ -244,8 +244,10 @@ const char* gmg_last_error(gmg_handle h);
  * The autotuner's results, process-wide (no counterpart in the paper: launch
  * shapes are a property of this implementation).  gmg_set_coeffs with
  * autotune = 1 times the z-chunk depth of each pipelined kernel per level
- * geometry and, for a single problem, where the bottom kernel starts and
- * whether one CTA or a thread-block cluster runs it, and keeps them in a table that later handles of the same shapes reuse without timing.
+ * geometry; for a single problem, where the bottom kernel starts and whether
+ * one CTA or a thread-block cluster runs it; for a batch, how its batched
+ * levels are cut into z-chunks (whole V-cycles timed).  It keeps them in a
+ * table that later handles of the same shapes reuse without timing.
  *
  * gmg_tune_export writes the table as text: one line per entry,
  *   "z kind nx ny nz px py pz zchunk"   (kind 0 sweep, 1 sweep with correction,
@@ -257,6 +259,13 @@ const char* gmg_last_error(gmg_handle h);
  *                                        one CTA, > 1: a cluster of that many CTAs
  *                                        splits its larger levels; a line without
  *                                        ranks reads as 1)
+ *   "c nprob hash choice"               (a batch of nprob >= 2 problems, hash: a
+ *                                        30-bit hash of their geometries and the
+ *                                        hierarchy options; choice 0: each batched
+ *                                        level keeps its geometry's z-chunks,
+ *                                        t + 1: every column of a batched level is
+ *                                        cut into the fewest chunks that give the
+ *                                        launch t tiles)
  * into buf (host, capacity cap bytes, NUL-terminated) and its length without
  * the NUL into *len.  buf == NULL only reports the length.  GMG_ERR_ARG when
  * cap is too small (nothing written).

@@ -231,6 +231,10 @@ struct BottomChoice {
     int ranks;   // 1: one CTA; > 1: the cluster form
 };
 std::map<std::vector<int>, BottomChoice> g_tuned_lb;
+// tuned z-chunk policy of a batch per (problem count, 30-bit hash of the problems'
+// geometries and the hierarchy options): the target tiles per batched launch + 1
+// (0: the depths of each level's geometry)
+std::map<std::pair<int, int>, int> g_tuned_batch;
 
 TuneKey tune_key(int kind, const Geo& g) { return {kind, g.n[0], g.n[1], g.n[2], g.per[0], g.per[1], g.per[2]}; }
 
@@ -569,7 +573,7 @@ struct Engine {
         std::vector<CtlTask> cyc(nprob), ini(nprob), gau(nprob);
         for (int p = 0; p < nprob; ++p) {
             ProblemMem& M = P[p];
-            M.res_zchunk0 = res_marches(M.g0, true) ? march_tiling(M.g0).zchunk : 0;
+            M.res_zchunk0 = res_marches(M.g0, true) ? march_tiling(M.g0, batch_zchunk(p, 0)).zchunk : 0;
             M.norm_tiles = (int)res0_tiling(M).tiles();
             if (M.norm_tiles > M.norm_cap) return GMG_ERR_CUDA;
             cyc[p] = CtlTask{M.ctl, M.norm_part, M.norm_tiles, nullptr, 0, nullptr, 0};
@@ -641,7 +645,7 @@ struct Engine {
             t.corr = static_cast<const TC*>(M.lev[l + 1].buf[coarse_result_[p][l + 1]]);
             for (int d = 0; d < 3; ++d) t.cf[d] = Lm.cf[d];
         }
-        const SweepTiling st = sweep_tiling(Lm.g, with_corr ? kTuneSweepCorr : kTuneSweep);
+        const SweepTiling st = sweep_tiling(Lm.g, with_corr ? kTuneSweepCorr : kTuneSweep, batch_zchunk(p, l));
         t.tiles_x = st.tx;
         t.tiles_y = st.ty;
         t.zchunk = st.zchunk;
@@ -695,8 +699,11 @@ struct Engine {
         t.role = role;
         t.bc = restrict_to_next ? M.lev[l + 1].b : nullptr;
         for (int d = 0; d < 3; ++d) t.cf[d] = restrict_to_next ? Lm.cf[d] : 1;
-        const ResTiling rt = (l == 0 && M.res_zchunk0 > 0) ? res0_tiling(M)
-                                                            : level_res_tiling(Lm.g, std::is_same<TP, float>::value);
+        constexpr bool fp32 = std::is_same<TP, float>::value;
+        const int bzc = batch_zchunk(p, l);
+        const ResTiling rt = (l == 0 && M.res_zchunk0 > 0)        ? res0_tiling(M)
+                             : (bzc > 0 && res_marches(Lm.g, fp32)) ? march_tiling(Lm.g, bzc)
+                                                                   : level_res_tiling(Lm.g, fp32);
         t.tiles_x = rt.tx;
         t.tiles_y = rt.ty;
         t.tiles_z = rt.tz;
@@ -756,6 +763,49 @@ struct Engine {
     int bottom_level_ = 0, bottom_ranks_ = 0;       // problem 0's bottom as planned (0: none)
     unsigned* arrivals_ = nullptr;                  // block counter of the norm residual with the control rule
     bool tuned_ = false;
+    int batch_target_ = -1;                         // batches: tiles each level's launch aims for (-1: per-geometry depths)
+
+    // z-chunk depth of problem p's level l in a batched launch: every column of the
+    // level's launch gets the same number of chunks, the fewest that give the launch
+    // batch_target_ tiles (0: the depth tuned or chosen for the level's geometry
+    // alone, as a single problem uses)
+    // 30-bit FNV-1a hash of the batch's geometries and hierarchy options: the key of
+    // its z-chunk policy in the tuning table
+    int batch_hash() const
+    {
+        uint32_t h = 2166136261u;
+        auto mix = [&](int v) {
+            for (int i = 0; i < 4; ++i) {
+                h ^= (uint32_t)(v >> (8 * i)) & 0xffu;
+                h *= 16777619u;
+            }
+        };
+        for (const ProblemMem& Q : P)
+            for (int d = 0; d < 3; ++d) {
+                mix(Q.g0.n[d]);
+                mix(Q.g0.per[d]);
+            }
+        for (int v : {opt.coarsen, opt.n_min, opt.precision, opt.nu1, opt.nu2, opt.nu_c, opt.coarse_mode,
+                      opt.coarse_op})
+            mix(v);
+        return (int)(h & ((1u << 30) - 1));
+    }
+
+    int batch_zchunk(int p, int l) const
+    {
+        if (P.size() < 2 || batch_target_ < 0) return 0;
+        int64_t cols = 0;
+        int nz_max = 1;
+        for (const ProblemMem& Q : P) {
+            if (l >= Q.L) continue;
+            const Geo& g = Q.lev[l].g;
+            cols += (int64_t)ceil_div(g.n[0], kSweepTX) * ceil_div(g.n[1], kSweepTY);
+            nz_max = std::max(nz_max, g.n[2]);
+        }
+        int nc = 1;
+        while (cols * nc < batch_target_ && nc < nz_max) ++nc;
+        return ceil_div(P[p].lev[l].g.n[2], nc);
+    }
 
     int add_sweeps(int l, const std::vector<int>& probs, int in, int out, bool with_corr)
     {
@@ -764,7 +814,8 @@ struct Engine {
         LaunchOp op;
         std::vector<int64_t> tiles;
         for (int p : probs)
-            tiles.push_back(sweep_tiling(P[p].lev[l].g, with_corr ? kTuneSweepCorr : kTuneSweep).tiles());
+            tiles.push_back(sweep_tiling(P[p].lev[l].g, with_corr ? kTuneSweepCorr : kTuneSweep, batch_zchunk(p, l))
+                                .tiles());
         int rc;
         if (coarse_bf) {
             std::vector<SweepTask<bf16, bf16>> v;
@@ -1422,6 +1473,50 @@ struct Engine {
                 g_tuned_lb[lb_key] = best_c;
             }
             reset_cycle();
+            if ((rc = build_cycle()) != GMG_OK) return rc;
+        }
+        // 3) a batch: z-chunks of its batched levels.  The depths tuned per geometry
+        // above fit a problem that runs alone, which splits its few columns into many
+        // short chunks; one launch over many problems has columns enough, and fewer,
+        // deeper chunks pay less for halo planes and pipeline starts.  Whole V-cycles
+        // are timed with the per-geometry depths and with each level's columns cut
+        // into the fewest chunks that give its launch 1, 1, 2 or 4 waves of blocks.
+        if (P.size() > 1) {
+            const std::pair<int, int> key{(int)P.size(), batch_hash()};
+            int cached_choice = -1;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                auto it = g_tuned_batch.find(key);
+                if (it != g_tuned_batch.end()) cached_choice = it->second;
+            }
+            const int slots = sm_count() * 3;
+            std::vector<int> targets = {-1, 1, slots, 2 * slots, 4 * slots};
+            if (cached_choice >= 0) targets = {cached_choice - 1};
+            float best = 1e30f;
+            int best_target = -1;
+            for (int target : targets) {
+                if (targets.size() == 1) {
+                    best_target = target;
+                    break;
+                }
+                batch_target_ = target;
+                reset_cycle();
+                if (upload_ctl_tasks() != GMG_OK) return fail(GMG_ERR_CUDA, "autotune: control task upload failed");
+                if ((rc = build_cycle()) != GMG_OK) return rc;
+                if (upload_timing_ctl() != cudaSuccess) return fail(GMG_ERR_CUDA, "autotune: control upload failed");
+                const float ms = time_ms([&] { return run_cycle(); }, 5);
+                if (ms < best) {
+                    best = ms;
+                    best_target = target;
+                }
+            }
+            batch_target_ = best_target;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                g_tuned_batch[key] = best_target + 1;
+            }
+            reset_cycle();
+            if (upload_ctl_tasks() != GMG_OK) return fail(GMG_ERR_CUDA, "autotune: control task upload failed");
             if ((rc = build_cycle()) != GMG_OK) return rc;
         }
         e = cudaStreamSynchronize(stream);
@@ -2422,6 +2517,9 @@ int gmg_tune_export(char* buf, size_t cap, size_t* len)
             for (int v : kv.first) t += " " + std::to_string(v);
             t += " " + std::to_string(kv.second.level) + " " + std::to_string(kv.second.ranks) + "\n";
         }
+        for (const auto& kv : g_tuned_batch)
+            t += "c " + std::to_string(kv.first.first) + " " + std::to_string(kv.first.second) + " " +
+                 std::to_string(kv.second) + "\n";
     }
     if (len) *len = t.size();
     if (!buf) return GMG_OK;
@@ -2435,6 +2533,7 @@ int gmg_tune_import(const char* text)
     if (!text) return GMG_ERR_ARG;
     std::map<TuneKey, int> zs;
     std::map<std::vector<int>, BottomChoice> bs;
+    std::map<std::pair<int, int>, int> cs;
     std::istringstream in(text);
     std::string line;
     while (std::getline(in, line)) {
@@ -2453,12 +2552,15 @@ int gmg_tune_import(const char* text)
                    (v.size() == 12 || (v[12] >= 1 && v[12] <= kClusterMaxRanks))) {
             // level 0: forget the entry (the next handle of that shape times again)
             bs[std::vector<int>(v.begin(), v.begin() + 11)] = BottomChoice{(int)v[11], v.size() == 13 ? (int)v[12] : 1};
+        } else if (tag == "c" && v.size() == 3 && v[0] >= 2) {
+            cs[{(int)v[0], (int)v[1]}] = (int)v[2];
         } else {
             return GMG_ERR_ARG;
         }
     }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (const auto& kv : zs) g_tuned_zchunk[kv.first] = kv.second;
+    for (const auto& kv : cs) g_tuned_batch[kv.first] = kv.second;
     for (const auto& kv : bs) {
         if (kv.second.level == 0) g_tuned_lb.erase(kv.first);
         else g_tuned_lb[kv.first] = kv.second;

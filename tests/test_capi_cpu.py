@@ -98,7 +98,8 @@ def test_tune_table_round_trip(L):
     """The autotuner's table exports as text and imports back unchanged (no GPU involved)."""
     text = ("z 0 256 96 96 0 0 0 8\n"
             "z 2 128 48 48 0 0 0 12\n"
-            "b 256 96 96 0 0 0 1 4 0 16 0 3 16\n")
+            "b 256 96 96 0 0 0 1 4 0 16 0 3 16\n"
+            "c 64 123456789 457\n")
     G.tune_import(text)
     out = G.tune_export()
     for line in text.splitlines():
@@ -113,6 +114,10 @@ def test_tune_table_round_trip(L):
     G.tune_import("z 0 256 96 96 0 0 0 16\n")
     lines = G.tune_export().splitlines()
     assert "z 0 256 96 96 0 0 0 16" in lines and "z 0 256 96 96 0 0 0 8" not in lines
+    # a batch's chunk policy: one line per (problem count, hash), replaced in place
+    G.tune_import("c 64 123456789 0\n")
+    lines = G.tune_export().splitlines()
+    assert "c 64 123456789 0" in lines and "c 64 123456789 457" not in lines
     # too small a buffer is refused and reports the length
     n = ctypes.c_size_t(0)
     buf = ctypes.create_string_buffer(4)
@@ -122,7 +127,7 @@ def test_tune_table_round_trip(L):
 
 @pytest.mark.parametrize("bad", ["z 0 1 2\n", "q 1 2 3\n", "z 0 8 8 8 0 0 0 x\n", "b 1 2 3\n", "z 0 8 8 8 0 0 0 -4\n",
                                  "b 64 64 64 0 0 0 1 4 0 16 0 3 17\n", "b 64 64 64 0 0 0 1 4 0 16 0 3 0\n",
-                                 "z 0 8 8 8 0 0 0 0\n"])
+                                 "z 0 8 8 8 0 0 0 0\n", "c 1 5 2\n", "c 64 5\n", "c 64 5 -1\n"])
 def test_tune_import_rejects_malformed(L, bad):
     before = G.tune_export()
     with pytest.raises(G.GmgError):

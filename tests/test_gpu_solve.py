@@ -334,6 +334,34 @@ def test_batch_fp64_refinement_equals_single():
         assert np.array_equal(host(o), single)
 
 
+def test_one_block_per_tile_equals_persistent_grid():
+    """A single problem's z-marching sweeps and residuals launch one block per
+    tile, a batch a persistent grid whose blocks walk the tiles.  On a level with
+    more tiles than the persistent grid has blocks (z-chunks of 6 planes imported
+    for a walled 256x104x96 channel: 8 x 13 x 16 = 1664 tiles against 1216
+    blocks) the two launches give the same bits: the same cycles and the same
+    iterate as the single solve."""
+    import torch
+    from paper_2607_07687_gb300 import binding as G
+    prob = I.sphere_channel_problem(256, 104, 96, seed=5)
+    nx, ny, nz = prob.dims
+    G.tune_import("".join(f"z {k} {nx} {ny} {nz} 0 0 0 6\n" for k in (0, 1, 2)))
+    probs = [prob, I.batch_problems(1, seed=3)[0]]
+    bs = G.BatchSolver([p.dims for p in probs])
+    try:
+        bs.set_coeffs([t32(p.bx) for p in probs], [t32(p.by) for p in probs], [t32(p.bz) for p in probs])
+        sig = [t32(p.b) for p in probs]
+        out = [torch.zeros_like(s) for s in sig]
+        infos = bs.solve(sig, out, 1e-5)
+        torch.cuda.synchronize()
+    finally:
+        bs.close()
+    single, si, _ = gpu_solve(prob, 1e-5, autotune=0)
+    assert infos[0].status == si.status == 0, (infos[0].as_dict(), si.as_dict())
+    assert infos[0].cycles == si.cycles
+    assert np.array_equal(host(out[0]), single)
+
+
 def test_tuning_table_import_is_used():
     """The autotuner's table, edited and imported, decides the launch shapes of the next
     handle of the same shape (no re-timing), and the solve still converges to the same answer."""

@@ -261,11 +261,13 @@ const char* gmg_last_error(gmg_handle h);
  *                                        ranks reads as 1)
  *   "c nprob hash choice"               (a batch of nprob >= 2 problems, hash: a
  *                                        30-bit hash of their geometries and the
- *                                        hierarchy options; choice 0: each batched
- *                                        level keeps its geometry's z-chunks,
- *                                        t + 1: every column of a batched level is
- *                                        cut into the fewest chunks that give the
- *                                        launch t tiles)
+ *                                        hierarchy options; choice = 2 (t + 1) + g:
+ *                                        t = -1, each batched level keeps its
+ *                                        geometry's z-chunks, t >= 1, every column
+ *                                        of a batched level is cut into the fewest
+ *                                        chunks that give the launch t tiles; g = 1,
+ *                                        one block per tile in the z-marching
+ *                                        launches, g = 0, a persistent grid)
  * into buf (host, capacity cap bytes, NUL-terminated) and its length without
  * the NUL into *len.  buf == NULL only reports the length.  GMG_ERR_ARG when
  * cap is too small (nothing written).

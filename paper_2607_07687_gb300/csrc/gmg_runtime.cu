@@ -123,17 +123,18 @@ int persistent_grid(int64_t tiles)
 // drift apart over many tiles and read the halos from DRAM again (512^3
 // triple-periodic sweep: DRAM reads 1.08 instead of 1.63 times the inputs).
 // Levels of at most one tile per resident block launch the same grid either way.
-// Batched launches keep the persistent grid: their problems' short columns would
-// each pay a pipeline start in a block of its own (64-problem batch 12 % slower).
+// A batched launch takes one block per tile only where its autotuner chose it
+// (`batch_one_block`): with the short z-chunks a problem tuned alone gets, each
+// block would pay a pipeline start for a few planes (64-problem batch 12 % slower).
 template <class TC>
-int sweep_grid(const TaskList<SweepTask<float, TC>>& tl)
+int sweep_grid(const TaskList<SweepTask<float, TC>>& tl, bool batch_one_block = false)
 {
-    return tl.vec >= 4 && tl.ntasks <= 1 ? std::max(1, tl.total) : persistent_grid(tl.total);
+    return tl.vec >= 4 && (tl.ntasks <= 1 || batch_one_block) ? std::max(1, tl.total) : persistent_grid(tl.total);
 }
 
-int residual_grid(const TaskList<ResTask<float>>& tl)
+int residual_grid(const TaskList<ResTask<float>>& tl, bool batch_one_block = false)
 {
-    return tl.march && tl.ntasks <= 1 ? std::max(1, tl.total) : persistent_grid(tl.total);
+    return tl.march && (tl.ntasks <= 1 || batch_one_block) ? std::max(1, tl.total) : persistent_grid(tl.total);
 }
 
 }  // namespace gmg
@@ -231,9 +232,10 @@ struct BottomChoice {
     int ranks;   // 1: one CTA; > 1: the cluster form
 };
 std::map<std::vector<int>, BottomChoice> g_tuned_lb;
-// tuned z-chunk policy of a batch per (problem count, 30-bit hash of the problems'
-// geometries and the hierarchy options): the target tiles per batched launch + 1
-// (0: the depths of each level's geometry)
+// tuned z-chunk policy and grid of a batch per (problem count, 30-bit hash of the
+// problems' geometries and the hierarchy options): 2 (target tiles per batched
+// launch + 1) + 1 if one block per tile (target -1: the depths of each level's
+// geometry)
 std::map<std::pair<int, int>, int> g_tuned_batch;
 
 TuneKey tune_key(int kind, const Geo& g) { return {kind, g.n[0], g.n[1], g.n[2], g.per[0], g.per[1], g.per[2]}; }
@@ -748,7 +750,7 @@ struct Engine {
                 op.kind = kResF;
                 if ((rc = make_list(v, tiles, op.r_f))) return rc;
                 op.r_f.march = m;
-                op.grid = residual_grid(op.r_f);
+                op.grid = residual_grid(op.r_f, batch_one_block_);
             }
             ops.push_back(op);
         }
@@ -764,6 +766,7 @@ struct Engine {
     unsigned* arrivals_ = nullptr;                  // block counter of the norm residual with the control rule
     bool tuned_ = false;
     int batch_target_ = -1;                         // batches: tiles each level's launch aims for (-1: per-geometry depths)
+    bool batch_one_block_ = false;                  // batches: one block per tile in the z-marching launches
 
     // z-chunk depth of problem p's level l in a batched launch: every column of the
     // level's launch gets the same number of chunks, the fewest that give the launch
@@ -834,7 +837,7 @@ struct Engine {
             op.s_fb.vec = 4;
             for (const auto& t : v) op.s_fb.vec = std::min(op.s_fb.vec, sweep_vec(t));
             op.s_fb.corr = with_corr ? 1 : 0;
-            op.grid = sweep_grid(op.s_fb);
+            op.grid = sweep_grid(op.s_fb, batch_one_block_);
         } else {
             std::vector<SweepTask<float, float>> v;
             for (int p : probs) v.push_back(sweep_task<float, float>(p, l, in, out, with_corr));
@@ -843,7 +846,7 @@ struct Engine {
             op.s_ff.vec = 4;
             for (const auto& t : v) op.s_ff.vec = std::min(op.s_ff.vec, sweep_vec(t));
             op.s_ff.corr = with_corr ? 1 : 0;
-            op.grid = sweep_grid(op.s_ff);
+            op.grid = sweep_grid(op.s_ff, batch_one_block_);
         }
         cycle.push_back(op);
         return GMG_OK;
@@ -1480,7 +1483,8 @@ struct Engine {
         // short chunks; one launch over many problems has columns enough, and fewer,
         // deeper chunks pay less for halo planes and pipeline starts.  Whole V-cycles
         // are timed with the per-geometry depths and with each level's columns cut
-        // into the fewest chunks that give its launch 1, 1, 2 or 4 waves of blocks.
+        // into the fewest chunks that give its launch 1, 1, 2 or 4 waves of blocks,
+        // each on the persistent grid and with one block per tile.
         if (P.size() > 1) {
             const std::pair<int, int> key{(int)P.size(), batch_hash()};
             int cached_choice = -1;
@@ -1490,16 +1494,23 @@ struct Engine {
                 if (it != g_tuned_batch.end()) cached_choice = it->second;
             }
             const int slots = sm_count() * 3;
-            std::vector<int> targets = {-1, 1, slots, 2 * slots, 4 * slots};
-            if (cached_choice >= 0) targets = {cached_choice - 1};
+            // choice = 2 (target + 1) + (1 if one block per tile)
+            std::vector<int> choices;
+            if (cached_choice >= 0) {
+                choices = {cached_choice};
+            } else {
+                for (int target : {-1, 1, slots, 2 * slots, 4 * slots})
+                    for (int one : {0, 1}) choices.push_back(2 * (target + 1) + one);
+            }
             float best = 1e30f;
-            int best_target = -1;
-            for (int target : targets) {
-                if (targets.size() == 1) {
-                    best_target = target;
+            int best_choice = 0;
+            for (int choice : choices) {
+                if (choices.size() == 1) {
+                    best_choice = choice;
                     break;
                 }
-                batch_target_ = target;
+                batch_target_ = choice / 2 - 1;
+                batch_one_block_ = choice % 2 == 1;
                 reset_cycle();
                 if (upload_ctl_tasks() != GMG_OK) return fail(GMG_ERR_CUDA, "autotune: control task upload failed");
                 if ((rc = build_cycle()) != GMG_OK) return rc;
@@ -1507,13 +1518,14 @@ struct Engine {
                 const float ms = time_ms([&] { return run_cycle(); }, 5);
                 if (ms < best) {
                     best = ms;
-                    best_target = target;
+                    best_choice = choice;
                 }
             }
-            batch_target_ = best_target;
+            batch_target_ = best_choice / 2 - 1;
+            batch_one_block_ = best_choice % 2 == 1;
             {
                 std::lock_guard<std::mutex> lock(g_tune_mutex);
-                g_tuned_batch[key] = best_target + 1;
+                g_tuned_batch[key] = best_choice;
             }
             reset_cycle();
             if (upload_ctl_tasks() != GMG_OK) return fail(GMG_ERR_CUDA, "autotune: control task upload failed");

@@ -34,8 +34,12 @@ constexpr int kSweepTY = 8;
 // R plane slots each
 constexpr int kSweepRing = 6;
 constexpr size_t kSweepSmemBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4) * 6 * kSweepRing;
-// the pipelined residual stages the same rings without the merged plane
-constexpr size_t kResidualSmemBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4) * 5 * kSweepRing;
+// the pipelined residual stages the same rings without the merged plane, in
+// kResRing slots: 48 KB a block, so that 4 blocks (24 warps) share an SM, where
+// 6 slots left room for 3 (18 warps; the 512^3 residual took 0.72 instead of
+// 0.62 ms)
+constexpr int kResRing = 5;
+constexpr size_t kResidualSmemBytes = sizeof(float) * (kSweepTX + 8) * (kSweepTY + 4) * 5 * kResRing;
 // residual tile (fine cells)
 constexpr int kResTX = 32;
 constexpr int kResTY = 4;

@@ -574,11 +574,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_async(const __grid_consta
 // next level and summed in squares (FP64, one partial per tile).  Warp-
 // specialised: warps 0-3 (consumers) each own two tile rows, one x-pair of
 // cells per thread; warps 4-5 (producers) stream whole planes of p, b and the
-// three face arrays into a ring of R plane slots.  Group H(g) (the g-th plane
-// this block streams, over all its tiles) lands in slot g mod R and completes
-// on full[g mod R]: by TMA (one box per array, zeros outside the grid) when the
-// box needs no periodic wrap in x or y, else by 16-byte asynchronous copies of
-// the producers' lanes.  The consumers release a slot on empty[] once no later
+// three face arrays into a ring of R = kResRing plane slots (4 blocks per SM).
+// Group H(g) (the g-th plane this block streams, over all its tiles) lands in
+// slot g mod R and completes on full[g mod R]: by TMA (one box per array, zeros
+// outside the grid) when the box needs no periodic wrap in x or y, else by
+// 16-byte asynchronous copies of the producers' lanes.  The consumers release a slot on empty[] once no later
 // step reads it; the producer waits for that release before refilling the
 // slot.  Restriction: x-pairs in the thread, y-pairs with the lane 16 apart,
 // z-pairs across two steps, so coarse cells are written without atomics.
@@ -1012,11 +1012,11 @@ __device__ double consumer_sum(const double* part, int n, double* red)
     return s;
 }
 
-__global__ void __launch_bounds__(kResBlock, 3) k_residual_ws(const __grid_constant__ TaskList<ResTask<float>> tl)
+__global__ void __launch_bounds__(kResBlock, 4) k_residual_ws(const __grid_constant__ TaskList<ResTask<float>> tl)
 {
     constexpr int TX = kSweepTX, TY = kSweepTY;
     constexpr int XO = 4, SW = TX + 8, PL = SW * (TY + 4);
-    constexpr int R = kSweepRing;
+    constexpr int R = kResRing;
     constexpr int CPR = SW / 4, NCH = PL / 4;
     constexpr int BPR = TX / 2;
     static_assert(BPR * TY == kResConsumers && BPR == 16, "one x-pair per consumer thread, two rows per warp");

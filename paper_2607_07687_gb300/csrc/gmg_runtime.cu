@@ -1483,8 +1483,8 @@ struct Engine {
         // short chunks; one launch over many problems has columns enough, and fewer,
         // deeper chunks pay less for halo planes and pipeline starts.  Whole V-cycles
         // are timed with the per-geometry depths and with each level's columns cut
-        // into the fewest chunks that give its launch 1, 1, 2 or 4 waves of blocks,
-        // each on the persistent grid and with one block per tile.
+        // into the fewest chunks that give its launch one chunk a column or 1, 2 or
+        // 4 waves of blocks, each on the persistent grid and with one block per tile.
         if (P.size() > 1) {
             const std::pair<int, int> key{(int)P.size(), batch_hash()};
             int cached_choice = -1;
